@@ -1,0 +1,274 @@
+#!/usr/bin/env python3
+"""Throughput of one multiple-shooting objective + gradient evaluation on GB300.
+
+Workload: 4 transmons x 3 levels (N=81 rows, E=16 essential columns), all-pair cross-Kerr,
+2 carriers per transmon with 40 B-spline coefficients each (d=640), QFT_16 target,
+T=600 ns, 100000 implicit-midpoint steps, M windows (default 64), seeded synthetic controls
+and non-unitary window states.  A step of this benchmark is one full evaluation
+(controls, forward sweep of every window, terminal conditions, adjoint sweep with the fused
+gradient, reductions).  The midpoint-state history (2 GB) is far larger than L2, so no L2
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--windows M]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank evaluates its own independent
+problem (weak scaling, no collective on the data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2407_13950_gb300 import synthetic as S  # noqa: E402
+
+METRIC = "4-qubit QFT objective+gradient evals/s"
+UNIT = "evals/s"
+
+
+def flops_model(spec):
+    """Algorithmic FP64 flops of one evaluation: one H-apply per implicit solve, the 2Ubar-U
+    update, and the gradient inner products (8 flops per complex multiply-add)."""
+    N, q, L, E, nt = spec.N, spec.q, spec.L, spec.E, spec.nsteps
+    nnz = q * 2 * N * (L - 1) // L                 # ladder-term nonzeros per column
+    f_step = 8 * nnz + 2 * N + 4 * N
+    fwd = E * nt * f_step
+    adj = E * nt * (f_step + 8 * nnz)
+    return {"forward": fwd, "adjoint": adj, "total": fwd + adj}
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for i, nm in enumerate(names):
+                    if r[5 + i].lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(spec, alpha, W, budget_s: float = 20.0):
+    """The oracle, as it stands, on this host's cores, on a bounded sample of the workload:
+    the first `ncores` windows (forward + adjoint), scaled to a full evaluation by the number of
+    window rounds the full problem needs on the same cores."""
+    import oracle
+    cores = os.cpu_count() or 1
+    nwin = min(spec.M, cores)
+    t0 = time.perf_counter()
+    oracle.evaluate(spec, alpha, W, windows=(1, nwin), nthreads=cores)
+    dt = time.perf_counter() - t0
+    rounds = math.ceil(spec.M / cores)
+    per_eval = dt * rounds * (nwin / min(nwin, cores))
+    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"windows 1-{nwin} of {spec.M} (forward+adjoint, {spec.nsteps // spec.M} steps each) "
+                      f"on {cores} threads in {dt:.2f} s, scaled x{rounds} window rounds"}
+
+
+def run_reference(args, spec):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    alpha, W = S.random_alpha(spec, 1), S.random_W(spec, 1)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    nwin = min(spec.M, cores)
+    rounds = math.ceil(spec.M / cores)
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.evaluate(spec, alpha, W, windows=(1, nwin), nthreads=cores)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt * rounds)
+    per_eval = float(np.mean(times))
+    value = 1.0 / per_eval
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec.name, "N": spec.N, "E": spec.E, "nsteps": spec.nsteps, "windows": spec.M,
+                       "T_ns": spec.T, "d": spec.d},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: windows 1-{nwin} of {spec.M} (forward+adjoint) on {cores} threads, "
+                                       f"scaled x{rounds} window rounds"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, spec):
+    import torch
+    from paper_2407_13950_gb300 import msqoc
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    alpha, W = S.random_alpha(spec, 1, problem=rank), S.random_W(spec, 1, problem=rank)
+    dev = torch.device("cuda", local)
+    a_d = torch.tensor(alpha, device=dev, dtype=torch.float64)
+    W_d = torch.tensor(W, device=dev, dtype=torch.float64)
+    P_d = torch.zeros(1, device=dev, dtype=torch.float64)
+    ga_d = torch.zeros(spec.d, device=dev, dtype=torch.float64)
+    gW_d = torch.zeros(spec.nW, device=dev, dtype=torch.float64)
+    stream = torch.cuda.current_stream(dev)
+    solver = msqoc.SOLVER_FP64 if args.solver == "fp64" else msqoc.SOLVER_MIXED
+    prob = msqoc.Problem(spec, solver=solver, col_block=args.col_block, profile=True)
+    peak_tflops = msqoc.measure_fp64_peak()
+
+    for _ in range(args.warmup):
+        prob.eval_gradient_into(a_d, W_d, P_d, ga_d, gW_d, stream=stream)
+    barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    kt = {k: 0.0 for k in msqoc.KERNEL_NAMES}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        prob.eval_gradient_into(a_d, W_d, P_d, ga_d, gW_d, stream=stream)
+        t = prob.kernel_times()
+        for k in kt:
+            kt[k] += t[k]
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers (H2D of alpha and W, D2H of P and gradients)
+    e2e_times = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prob.eval_gradient(alpha, W)
+        if it >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_ms = float(np.mean(e2e_times)) * 1e3
+    if dist is not None:
+        tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    fl = flops_model(spec)
+    dom = max(("forward", "adjoint"), key=lambda k: kt[k])
+    dom_ms = kt[dom] / args.steps
+    achieved = fl[dom] / (dom_ms * 1e-3) / 1e12
+    launches_per_eval = 6 if spec.M > 1 else 5
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": spec.name, "N": spec.N, "E": spec.E, "nsteps": spec.nsteps, "windows": spec.M,
+                   "T_ns": spec.T, "d": spec.d, "solver": args.solver, "col_block": args.col_block or "auto",
+                   "l2": "inputs larger than L2 (2 GB midpoint history per evaluation)",
+                   "parallelism": f"independent problem per GPU x{world}"},
+        "roofline": {"bound": "alu", "kernel": f"k_sweep ({dom})", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "peak_source": "measured FP64 FMA microbenchmark (msqoc_measure_fp64_peak), same run",
+                     "algorithmic_flops_per_launch": fl[dom], "avg_launch_ms": dom_ms},
+        "kernel_ms": {k: v / args.steps for k, v in kt.items()},
+        "whole_eval": {"algorithmic_tflops": fl["total"] / (ms * 1e-3) / 1e12,
+                       "frac_of_fp64_peak": fl["total"] / (ms * 1e-3) / 1e12 / peak_tflops},
+        "e2e": {"value": world / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * (spec.d + spec.nW), "d2h_bytes_per_step": 8 * (1 + spec.d + spec.nW)},
+        "gpu_launches": launches_per_eval * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec, alpha, W)
+    prob.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--windows", type=int, default=64)
+    ap.add_argument("--solver", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--col-block", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    spec = S.config_4q(M=args.windows)
+    if args.impl == "reference":
+        run_reference(args, spec)
+    else:
+        run_ours(args, spec)
+
+
+if __name__ == "__main__":
+    main()

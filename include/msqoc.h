@@ -1,0 +1,170 @@
+/*
+ * msqoc.h — C ABI of the GB300 multiple-shooting quantum-optimal-control evaluator.
+ *
+ * One call evaluates the multiple-shooting penalty objective of Petersson, Guenther, Chung,
+ * "A time-parallel multiple-shooting method for large-scale quantum optimal control"
+ * (arXiv 2407.13950), Sec. 3, Eq. penalty-fcn:
+ *
+ *     P(alpha, W^1..W^{M-1}) = J_V(U^M(t_M)) + mu/2 sum_{m<M} ||U^m(t_m) - W^m||_F^2,
+ *
+ * where window m propagates U^m from U^m(t_{m-1}) = W^{m-1} (W^0 = identity embedding of the
+ * essential subspace; Eqs. sch-op, sch-ic) with the implicit midpoint rule (Sec. 5) under
+ * H(t) = H_s + sum_k d_k(t) a_k + conj(d_k(t)) a_k^+ (Eqs. ctrl-ham, dj-ctrl), and
+ * J_V(U) = ||U||^2/E - |<V,U>_F|^2/E^2 is the generalized infidelity (Eq. mod-infid, n := E).
+ * The gradient is the exact discrete adjoint of the midpoint rule (Sec. 5): Eq. grad-int
+ * for alpha and Eq. dP-dW (with the factor 2 of Appendix B, Eq. dT-dW-j) for W.
+ *
+ * Model conventions
+ *   - q subsystems, L levels each (the first `ness` essential); N = L^q rows, E = ness^q
+ *     columns.  Full index i = sum_k l_k L^(q-1-k) (subsystem 0 most significant); essential
+ *     column e = sum_k b_k ness^(q-1-k).
+ *   - Drift (diagonal): H_s = sum_k -xi_k/2 a_k^+a_k^+a_k a_k - sum_{k<l} xi_kl a_k^+a_k a_l^+a_l
+ *     (transmons with self- and cross-Kerr in per-qubit rotating frames), optionally
+ *     + sum_k detune_k a_k^+ a_k.  The paper's dipole exchange (Eq. sys-ham, J_kl) is not
+ *     supported by this library: jx must be NULL or all zero (MSQOC_ERR_UNSUPPORTED).
+ *   - Controls: d_k(t) = sum_f exp(i Omega_kf t) sum_s (alpha1_kfs + i alpha2_kfs) B_s(t),
+ *     quadratic cardinal B-splines on knots j*dtau, dtau = T/(d1-2), spline s centred at
+ *     (s - 1/2) dtau (Sec. 2 and Sec. 5: d1 = T/dtau + 2).  alpha layout [k][f][s][2],
+ *     d = 2 d1 sum_k N_f(k) doubles.
+ *   - Time grid: h = T/nsteps, controls evaluated at t_{n+1/2} = (n + 1/2) h, window m
+ *     (1-based) owns steps [floor((m-1) nsteps/M), floor(m nsteps/M)).
+ *   - Target V: N x E, column-major complex; NULL selects QFT_E on the essential rows
+ *     (Sec. 5: V_jk = kappa^{jk}/sqrt(E), kappa = exp(2 pi i/E)), guard rows zero.
+ *
+ * Memory layouts (complex = interleaved re, im doubles)
+ *   alpha     : d doubles.
+ *   W         : (M-1) x E x N complex = 2 N E (M-1) doubles; W^m column c row i at
+ *               2*(((m-1) E + c) N + i).  W^0 is never passed.
+ *   grad_W    : same layout as W; entry (re, im) = (dP/dRe W, dP/dIm W) (real-valued
+ *               formalism, Sec. 5).
+ *   pen       : M-1 doubles, pen[m-1] = mu/2 ||U^m(t_m) - W^m||^2.
+ *
+ * Pointers: every array argument may be host or device memory (detected with
+ * cudaPointerGetAttributes).  With device outputs the call is asynchronous on `stream`;
+ * with any host output it synchronizes `stream` before returning.  Inputs are read during
+ * the call (host) or until the stream work completes (device).  The caller owns every
+ * array it passes; the library owns the device buffers it allocates for a problem.
+ *
+ * Errors: every function returns MSQOC_OK (0) or a negative msqoc_status; no C++ exception
+ * crosses this boundary.  msqoc_last_error() copies the calling thread's last message.
+ * Calls on the same problem must not overlap (they share its scratch buffers); different
+ * problems may be used from different threads and streams.
+ */
+#ifndef MSQOC_H
+#define MSQOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t msqoc_status;
+
+#define MSQOC_OK 0
+#define MSQOC_ERR_INVALID_ARG (-1)   /* malformed description, size or pointer */
+#define MSQOC_ERR_OUT_OF_MEMORY (-2) /* a device allocation failed */
+#define MSQOC_ERR_NOT_ADMITTED (-3)  /* refused by a memory budget (batch/serving layer) */
+#define MSQOC_ERR_CUDA (-4)          /* a CUDA runtime call failed */
+#define MSQOC_ERR_TIMEOUT (-5)       /* a bounded device wait gave up (status word set) */
+#define MSQOC_ERR_UNSUPPORTED (-6)   /* valid input outside what the kernels implement */
+#define MSQOC_ERR_INTERNAL (-7)
+
+/* Linear solver inside each implicit-midpoint step.
+ *  MIXED: FP64 residual of the step equation with FP32 inner corrections (iterative
+ *         refinement); the step is solved to FP64 round-off.  Default.
+ *  FP64 : diagonal-preconditioned fixed-point iteration carried out entirely in FP64. */
+#define MSQOC_SOLVER_DEFAULT 0
+#define MSQOC_SOLVER_FP64 1
+#define MSQOC_SOLVER_MIXED 2
+
+typedef struct msqoc_hamiltonian {
+    int32_t nqubits;        /* q >= 1 */
+    int32_t nlevels;        /* L >= 2, same for every subsystem */
+    int32_t ness;           /* essential levels per subsystem, 1 <= ness <= L */
+    const double* xi;       /* [q] self-Kerr xi_k (rad/ns); host memory */
+    const double* xi_cross; /* [q*q] row-major, entry (k,l) with k<l used; NULL = 0; host */
+    const double* detune;   /* [q] or NULL; host */
+    const double* jx;       /* must be NULL or zero (see above); host */
+} msqoc_hamiltonian;
+
+typedef struct msqoc_controls {
+    const int32_t* ncarriers; /* [q] carriers per subsystem, >= 1; host */
+    const double* carriers;   /* [sum ncarriers] Omega_kf (rad/ns), subsystem-major; host */
+    int32_t nsplines;         /* d1 >= 3 spline coefficients per carrier */
+} msqoc_controls;
+
+typedef struct msqoc_options {
+    int32_t solver;        /* MSQOC_SOLVER_* */
+    int32_t col_block;     /* columns per tile; 0 = automatic; must divide E */
+    int32_t ckpt_interval; /* forward states kept for the adjoint sweep: 1 = every step
+                              (only value implemented; 0 = automatic = 1) */
+    int32_t profile;       /* 1 = record CUDA events around every kernel (msqoc_kernel_times) */
+    int32_t reserved[4];
+} msqoc_options;
+
+/* Kernels of one evaluation, in launch order, as indexed by msqoc_kernel_times. */
+#define MSQOC_KERNEL_CONTROLS 0  /* control evaluation at the step midpoints */
+#define MSQOC_KERNEL_FORWARD 1   /* forward sweep of every window */
+#define MSQOC_KERNEL_TERMINAL 2  /* window terminal conditions and objective terms */
+#define MSQOC_KERNEL_ADJOINT 3   /* adjoint sweep with the fused gradient quadrature */
+#define MSQOC_KERNEL_FINALIZE 4  /* deterministic reductions and the W-gradient */
+#define MSQOC_NKERNELS 5
+
+typedef struct msqoc_problem msqoc_problem;
+
+/* Create a problem: validates the description, packs the model tables (drift diagonal,
+ * preconditioner, strides, spline and carrier tables, target) into device memory of the
+ * current device and sizes the scratch buffers.  mu <= 0 selects mu = 2/E (Sec. 5).
+ * nwindows M >= 1 (M = 1 is single shooting) and M <= nsteps.  opt may be NULL.
+ * target: N x E complex column-major host array or NULL (QFT_E).  *out receives the
+ * handle (NULL on failure). */
+msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
+                                  const double* target, double T, int64_t nsteps,
+                                  int32_t nwindows, double mu, const msqoc_options* opt,
+                                  msqoc_problem** out);
+
+/* Sizes: d (control parameters), nW (doubles of the W vector, 2 N E (M-1)) and the bytes of
+ * device memory the problem holds once a gradient has been evaluated.  Any pointer may be
+ * NULL. */
+msqoc_status msqoc_query(const msqoc_problem* p, int64_t* d, int64_t* nW, size_t* device_bytes);
+
+/* Objective only (forward sweep of every window, Eq. penalty-fcn).  P_out: 1 double;
+ * J_out (1 double) and pen_out (M-1 doubles) may be NULL. */
+msqoc_status msqoc_eval_objective(msqoc_problem* p, const double* alpha, const double* W,
+                                  double* P_out, double* J_out, double* pen_out, void* stream);
+
+/* Objective and gradient (forward sweep, terminal conditions Eq. terminal, discrete adjoint
+ * sweep with the fused Eq. grad-int quadrature, Eq. dP-dW).  grad_alpha: d doubles;
+ * grad_W: 2 N E (M-1) doubles (may be NULL when M = 1).  P_out may be NULL. */
+msqoc_status msqoc_eval_gradient(msqoc_problem* p, const double* alpha, const double* W,
+                                 double* P_out, double* grad_alpha, double* grad_W, void* stream);
+
+/* Release every resource of the problem (synchronizes the device first). NULL is a no-op. */
+msqoc_status msqoc_destroy_problem(msqoc_problem* p);
+
+/* Copy the calling thread's last error message (NUL-terminated, truncated to len).
+ * Returns the full message length. */
+int32_t msqoc_last_error(char* buf, size_t len);
+
+/* Device time (ms) of each kernel of the last evaluation on a problem created with
+ * options.profile = 1, measured with CUDA events recorded on the evaluation's stream around
+ * each launch (synchronizes on the last event).  ms[MSQOC_NKERNELS]; kernels that did not run
+ * in the last evaluation report 0.  Not part of the paper's method: measurement support. */
+msqoc_status msqoc_kernel_times(msqoc_problem* p, float* ms);
+
+/* FP64 throughput of the current device, measured with a fused-multiply-add microbenchmark
+ * (8 independent FMA chains per thread on every SM, best of several runs).  *tflops receives
+ * FP64 TFLOP/s (an FMA counts 2 flops).  Used as the roofline denominator of the sweeps; not
+ * part of the paper's method. */
+msqoc_status msqoc_measure_fp64_peak(double* tflops);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t msqoc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSQOC_H */

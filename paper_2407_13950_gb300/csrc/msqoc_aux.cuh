@@ -1,0 +1,138 @@
+// Small kernels around the sweeps: control evaluation, window terminal conditions and the
+// deterministic final reductions.
+#pragma once
+
+#include "msqoc_internal.h"
+
+namespace msqoc {
+
+// Controls at every step midpoint t_{n+1/2} = (n + 1/2) h (Eq. dj-ctrl with the quadratic
+// B-spline envelope of Sec. 2): d_k(t) = sum_f e^{i Omega_kf t} sum_s (a1 + i a2)_kfs B_s(t).
+// On [j dtau, (j+1) dtau) the three non-zero splines are s = j, j+1, j+2 with weights
+// (1-x)^2/2, 3/4 - (x-1/2)^2, x^2/2 (x = t/dtau - j).  Also stores the spline weights and the
+// carrier phases for the gradient quadrature of the adjoint sweep.
+__global__ void k_controls(const ProbDev pd) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; n < pd.nsteps; n += stride) {
+        const double t = (double(n) + 0.5) * pd.h;
+        const double tau = t / pd.dtau;
+        int s0 = static_cast<int>(floor(tau));
+        s0 = s0 < 0 ? 0 : (s0 > pd.d1 - 3 ? pd.d1 - 3 : s0);
+        const double x = tau - s0;
+        const double w0 = 0.5 * (1.0 - x) * (1.0 - x);
+        const double w1 = 0.75 - (x - 0.5) * (x - 0.5);
+        const double w2 = 0.5 * x * x;
+        pd.spl[n] = Spline4{double(s0), w0, w1, w2};
+        for (int k = 0; k < pd.q; ++k) {
+            double2 dk = make_double2(0.0, 0.0);
+            for (int fi = pd.cof[k]; fi < pd.cof[k + 1]; ++fi) {
+                double sn, cs;
+                sincos(pd.omega[fi] * t, &sn, &cs);
+                pd.phase[size_t(n) * pd.nfsum + fi] = make_double2(cs, sn);
+                const double* a = pd.alpha + (size_t(fi) * pd.d1 + s0) * 2;
+                const double er = a[0] * w0 + a[2] * w1 + a[4] * w2;
+                const double ei = a[1] * w0 + a[3] * w1 + a[5] * w2;
+                dk.x += cs * er - sn * ei;
+                dk.y += cs * ei + sn * er;
+            }
+            pd.ctrl[size_t(n) * pd.q + k] = dk;
+        }
+    }
+}
+
+// block-wide sum with a fixed reduction order (deterministic)
+template <int NT>
+__device__ double block_sum(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+#pragma unroll
+    for (int o = NT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+constexpr int TERM_THREADS = 256;
+
+// Terminal conditions per window (Eq. terminal) and the window's objective term:
+//   m < M: pen_m = mu/2 ||U^m - W^m||^2,  Lambda^m(t_m) = mu/2 (W^m - U^m)
+//   m = M: gamma = <V, U^M>, J = ||U^M||^2/E - |gamma|^2/E^2, Lambda^M(t_M) = (gamma V - E U^M)/E^2
+__global__ void __launch_bounds__(TERM_THREADS) k_terminal(const ProbDev pd, const int want_lambda) {
+    __shared__ double sh[TERM_THREADS];
+    const int m = blockIdx.x + 1;
+    const size_t ne = size_t(pd.N) * pd.E;
+    const double2* U = pd.Uend + size_t(m - 1) * ne;
+    double2* Lt = pd.Lterm + size_t(m - 1) * ne;
+    if (m < pd.M) {
+        const double2* Wm = pd.W + size_t(m - 1) * ne;
+        double s = 0.0;
+        for (size_t e = threadIdx.x; e < ne; e += TERM_THREADS) {
+            const double2 u = U[e], w = Wm[e];
+            const double cx = u.x - w.x, cy = u.y - w.y;
+            s = fma(cx, cx, fma(cy, cy, s));
+            if (want_lambda) Lt[e] = make_double2(-0.5 * pd.mu * cx, -0.5 * pd.mu * cy);
+        }
+        s = block_sum<TERM_THREADS>(s, sh);
+        if (threadIdx.x == 0) pd.term[m - 1] = 0.5 * pd.mu * s;
+    } else {
+        double gr = 0.0, gi = 0.0, nr = 0.0;
+        for (size_t e = threadIdx.x; e < ne; e += TERM_THREADS) {
+            const double2 u = U[e], v = pd.V[e];
+            gr = fma(v.x, u.x, fma(v.y, u.y, gr));
+            gi = fma(v.x, u.y, fma(-v.y, u.x, gi));
+            nr = fma(u.x, u.x, fma(u.y, u.y, nr));
+        }
+        gr = block_sum<TERM_THREADS>(gr, sh);
+        gi = block_sum<TERM_THREADS>(gi, sh);
+        nr = block_sum<TERM_THREADS>(nr, sh);
+        const double E = pd.E;
+        if (threadIdx.x == 0) pd.term[m - 1] = nr / E - (gr * gr + gi * gi) / (E * E);
+        if (want_lambda) {
+            const double inv = 1.0 / (E * E);
+            for (size_t e = threadIdx.x; e < ne; e += TERM_THREADS) {
+                const double2 u = U[e], v = pd.V[e];
+                const double lx = (gr * v.x - gi * v.y) - E * u.x;
+                const double ly = (gr * v.y + gi * v.x) - E * u.y;
+                Lt[e] = make_double2(lx * inv, ly * inv);
+            }
+        }
+    }
+}
+
+// P = J + sum_m pen_m (window order), J and pen outputs, and the alpha-gradient as the sum of
+// the per-tile partials in tile order.
+__global__ void k_finalize_scalars(const ProbDev pd, double* P_out, double* J_out, double* pen_out,
+                                   double* galpha_out) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double P = 0.0;
+        for (int m = 1; m <= pd.M; ++m) P += pd.term[m - 1];
+        if (P_out) *P_out = P;
+        if (J_out) *J_out = pd.term[pd.M - 1];
+        if (pen_out)
+            for (int m = 1; m < pd.M; ++m) pen_out[m - 1] = pd.term[m - 1];
+    }
+    if (galpha_out) {
+        for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < pd.d; l += gridDim.x * blockDim.x) {
+            double s = 0.0;
+            for (int t = 0; t < pd.ntiles; ++t) s += pd.gpart[size_t(t) * pd.d + l];
+            galpha_out[l] = s;
+        }
+    }
+}
+
+// dP/dW^m = mu (W^m - U^m(t_m)) - 2 Lambda^{m+1}(t_m) = 2 (Lambda^m(t_m) - Lambda^{m+1}(t_m))
+// (Eq. dP-dW with the factor of Appendix B, Eq. dT-dW-j), m = 1..M-1.
+__global__ void k_grad_W(const ProbDev pd, double2* gW) {
+    const size_t ne = size_t(pd.N) * pd.E;
+    const size_t total = ne * (pd.M - 1);
+    for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += size_t(gridDim.x) * blockDim.x) {
+        const double2 lt = pd.Lterm[e];
+        const double2 l0 = pd.Lam0[e + ne];
+        gW[e] = make_double2(2.0 * (lt.x - l0.x), 2.0 * (lt.y - l0.y));
+    }
+}
+
+}  // namespace msqoc

@@ -1,0 +1,233 @@
+"""ctypes binding of libmsqoc (include/msqoc.h): argument marshalling only.
+
+Every step of an evaluation runs in the CUDA library; this module converts Python arguments
+(numpy arrays in host memory, or torch tensors on the GPU or host) into the pointers and sizes
+of the C ABI and raises ``MsqocError`` on any non-zero status.  The names follow the C ABI:
+``create_problem``, ``eval_objective``, ``eval_gradient``, ``query``, ``destroy_problem``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+MSQOC_OK = 0
+STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OUT_OF_MEMORY", -3: "NOT_ADMITTED", -4: "CUDA_ERROR",
+                -5: "TIMEOUT", -6: "UNSUPPORTED", -7: "INTERNAL"}
+SOLVER_DEFAULT, SOLVER_FP64, SOLVER_MIXED = 0, 1, 2
+
+EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_eval_objective", "msqoc_eval_gradient",
+            "msqoc_destroy_problem", "msqoc_last_error", "msqoc_version", "msqoc_kernel_times",
+            "msqoc_measure_fp64_peak"]
+KERNEL_NAMES = ["controls", "forward", "terminal", "adjoint", "finalize"]
+
+
+class MsqocError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"msqoc {STATUS_NAMES.get(status, status)} ({status}): {message}")
+        self.status = status
+
+
+class Hamiltonian(ctypes.Structure):
+    _fields_ = [("nqubits", ctypes.c_int32), ("nlevels", ctypes.c_int32), ("ness", ctypes.c_int32),
+                ("xi", ctypes.c_void_p), ("xi_cross", ctypes.c_void_p), ("detune", ctypes.c_void_p),
+                ("jx", ctypes.c_void_p)]
+
+
+class Controls(ctypes.Structure):
+    _fields_ = [("ncarriers", ctypes.c_void_p), ("carriers", ctypes.c_void_p), ("nsplines", ctypes.c_int32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int32), ("col_block", ctypes.c_int32), ("ckpt_interval", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmsqoc.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise MsqocError(-7, f"{path} is missing: build it with paper_2407_13950_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        sigs = {
+            "msqoc_create_problem": (i32, [vp, vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, vp, vp]),
+            "msqoc_query": (i32, [vp, vp, vp, vp]),
+            "msqoc_eval_objective": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+            "msqoc_eval_gradient": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+            "msqoc_destroy_problem": (i32, [vp]),
+            "msqoc_last_error": (i32, [vp, sz]),
+            "msqoc_version": (i32, []),
+            "msqoc_kernel_times": (i32, [vp, vp]),
+            "msqoc_measure_fp64_peak": (i32, [vp]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    lib = load()
+    buf = ctypes.create_string_buffer(1024)
+    lib.msqoc_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(status: int):
+    if status != MSQOC_OK:
+        raise MsqocError(status, last_error())
+
+
+def _ptr(x) -> Optional[int]:
+    """Data pointer of a numpy array or torch tensor (must be contiguous float64)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("arrays must be contiguous float64")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):  # torch.Tensor
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+class Problem:
+    """One multiple-shooting problem living on the current CUDA device."""
+
+    def __init__(self, spec, target: Optional[np.ndarray] = None, solver: int = SOLVER_DEFAULT,
+                 col_block: int = 0, ckpt_interval: int = 0, profile: bool = False):
+        lib = load()
+        self.spec = spec
+        q = spec.q
+        self._xi = np.ascontiguousarray(spec.xi, dtype=np.float64)
+        self._xc = np.ascontiguousarray(np.asarray(spec.xi_cross, dtype=np.float64).reshape(q, q))
+        self._det = None if spec.detune is None else np.ascontiguousarray(spec.detune, dtype=np.float64)
+        self._jx = None if spec.jx is None else np.ascontiguousarray(np.asarray(spec.jx, dtype=np.float64).reshape(q, q))
+        self._nf = np.ascontiguousarray([len(w) for w in spec.omega], dtype=np.int32)
+        self._om = np.ascontiguousarray([x for w in spec.omega for x in w], dtype=np.float64)
+        self._tgt = None if target is None else np.ascontiguousarray(target, dtype=np.float64)
+        H = Hamiltonian(q, spec.L, spec.ness, self._xi.ctypes.data, self._xc.ctypes.data,
+                        None if self._det is None else self._det.ctypes.data,
+                        None if self._jx is None else self._jx.ctypes.data)
+        C = Controls(self._nf.ctypes.data, self._om.ctypes.data, spec.d1)
+        O = Options(solver, col_block, ckpt_interval, 1 if profile else 0)
+        h = ctypes.c_void_p()
+        _check(lib.msqoc_create_problem(ctypes.byref(H), ctypes.byref(C),
+                                        None if self._tgt is None else self._tgt.ctypes.data,
+                                        float(spec.T), int(spec.nsteps), int(spec.M), float(spec.mu),
+                                        ctypes.byref(O), ctypes.byref(h)))
+        self.handle = h
+        d, nW, nbytes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        _check(lib.msqoc_query(h, ctypes.byref(d), ctypes.byref(nW), ctypes.byref(nbytes)))
+        self.d, self.nW, self.device_bytes = d.value, nW.value, nbytes.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().msqoc_destroy_problem(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def kernel_times(self) -> dict:
+        """Device ms of each kernel of the last evaluation (problem created with profile=True)."""
+        ms = (ctypes.c_float * 5)()
+        _check(load().msqoc_kernel_times(self.handle, ms))
+        return dict(zip(KERNEL_NAMES, [float(x) for x in ms]))
+
+    # ---- host-array convenience API (numpy in, numpy out; synchronous)
+    def eval_objective(self, alpha, W=None, stream=None) -> dict:
+        M = self.spec.M
+        P, J = np.zeros(1), np.zeros(1)
+        pen = np.zeros(max(M - 1, 1))
+        w = W if M > 1 else None
+        _check(load().msqoc_eval_objective(self.handle, _ptr(alpha), _ptr(w), _ptr(P), _ptr(J),
+                                           _ptr(pen) if M > 1 else None, _stream_handle(stream)))
+        return {"P": float(P[0]), "J": float(J[0]), "pen": pen[:M - 1].copy()}
+
+    def eval_gradient(self, alpha, W=None, stream=None) -> dict:
+        M = self.spec.M
+        P = np.zeros(1)
+        ga = np.zeros(self.d)
+        gW = np.zeros(max(self.nW, 1))
+        w = W if M > 1 else None
+        _check(load().msqoc_eval_gradient(self.handle, _ptr(alpha), _ptr(w), _ptr(P), _ptr(ga),
+                                          _ptr(gW) if M > 1 else None, _stream_handle(stream)))
+        return {"P": float(P[0]), "grad_alpha": ga, "grad_W": gW[:self.nW].copy()}
+
+    # ---- pointer-level API (device tensors; asynchronous on the stream)
+    def eval_gradient_into(self, alpha, W, P_out, grad_alpha, grad_W, stream=None):
+        _check(load().msqoc_eval_gradient(self.handle, _ptr(alpha), _ptr(W), _ptr(P_out), _ptr(grad_alpha),
+                                          _ptr(grad_W), _stream_handle(stream)))
+
+    def eval_objective_into(self, alpha, W, P_out, J_out=None, pen_out=None, stream=None):
+        _check(load().msqoc_eval_objective(self.handle, _ptr(alpha), _ptr(W), _ptr(P_out), _ptr(J_out),
+                                           _ptr(pen_out), _stream_handle(stream)))
+
+
+# C-ABI-named functions
+def create_problem(spec, target=None, **kw) -> Problem:
+    return Problem(spec, target, **kw)
+
+
+def eval_objective(problem: Problem, alpha, W=None, stream=None) -> dict:
+    return problem.eval_objective(alpha, W, stream)
+
+
+def eval_gradient(problem: Problem, alpha, W=None, stream=None) -> dict:
+    return problem.eval_gradient(alpha, W, stream)
+
+
+def query(problem: Problem):
+    return problem.d, problem.nW, problem.device_bytes
+
+
+def destroy_problem(problem: Problem):
+    problem.close()
+
+
+def measure_fp64_peak() -> float:
+    """FP64 TFLOP/s of the current device (FMA microbenchmark in the library)."""
+    t = ctypes.c_double()
+    _check(load().msqoc_measure_fp64_peak(ctypes.byref(t)))
+    return t.value

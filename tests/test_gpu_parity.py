@@ -1,0 +1,149 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on seeded inputs.
+
+Bar: objective within 1e-12 relative; every gradient component within 1e-10 relative (plus a
+round-off floor of 1e-13 of the largest component).  Sizes are small enough for the oracle to
+finish in seconds while still spanning several tiles, several warps per tile, ragged windows
+and both solvers; the full 4-transmon workload is checked on sampled windows in
+test_gpu_fullsize.py.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_13950_gb300 import msqoc
+from paper_2407_13950_gb300 import synthetic as S
+
+from gpu_helpers import assert_grad_close, assert_objective_close
+
+pytestmark = pytest.mark.gpu
+
+SOLVERS = {"mixed": msqoc.SOLVER_MIXED, "fp64": msqoc.SOLVER_FP64}
+
+
+def run_both(spec, alpha, W, solver, col_block=0, grad=True):
+    want = oracle.evaluate(spec, alpha, W, grad=grad)
+    with msqoc.Problem(spec, solver=solver, col_block=col_block) as p:
+        got = p.eval_gradient(alpha, W) if grad else p.eval_objective(alpha, W)
+        obj = p.eval_objective(alpha, W)
+    return got, obj, want
+
+
+def check(spec, alpha, W, solver, col_block=0):
+    got, obj, want = run_both(spec, alpha, W, solver, col_block)
+    assert_objective_close(got["P"], want["P"])
+    assert_objective_close(obj["P"], want["P"])
+    if spec.M > 1:
+        # a penalty whose residual is at round-off ((1e-14)^2) has no relative accuracy
+        np.testing.assert_allclose(obj["pen"], want["pen"], rtol=1e-12, atol=1e-24)
+    assert_objective_close(obj["J"], want["J"])
+    assert_grad_close(got["grad_alpha"], want["grad_alpha"], what="grad_alpha")
+    if spec.M > 1:
+        assert_grad_close(got["grad_W"], want["grad_W"], what="grad_W")
+    return got, want
+
+
+CASES = {
+    "1q": S.transmon_spec(1, 10.0, 200, 4, 5),
+    "2q-config": S.config_2q(),
+    "3q-ragged": S.transmon_spec(3, 30.0, 2000, 7, 8),
+    "4q-short": S.transmon_spec(4, 1.8, 300, 3, 5),
+}
+
+
+@pytest.mark.parametrize("solver", list(SOLVERS))
+@pytest.mark.parametrize("case", list(CASES))
+def test_parity_small(case, solver):
+    spec = CASES[case]
+    alpha, W = S.random_alpha(spec, 101), S.random_W(spec, 101)
+    check(spec, alpha, W, SOLVERS[solver])
+
+
+@pytest.mark.parametrize("cb", [1, 2, 4, 8, 16])
+def test_parity_column_blocks_4q(cb):
+    spec = S.transmon_spec(4, 0.6, 100, 2, 4)
+    alpha, W = S.random_alpha(spec, 7), S.random_W(spec, 7)
+    check(spec, alpha, W, msqoc.SOLVER_MIXED, col_block=cb)
+
+
+def test_parity_5q_tiny():
+    spec = S.transmon_spec(5, 0.12, 20, 2, 4)
+    alpha, W = S.random_alpha(spec, 5), S.random_W(spec, 5)
+    check(spec, alpha, W, msqoc.SOLVER_MIXED)
+
+
+def test_single_shooting():
+    spec = S.config_2q(M=1).replace(nsteps=500, T=12.5)
+    alpha = S.random_alpha(spec, 3)
+    check(spec, alpha, np.zeros(0), msqoc.SOLVER_MIXED)
+
+
+def test_one_step_per_window():
+    spec = S.transmon_spec(2, 0.4, 16, 16, 4)
+    alpha, W = S.random_alpha(spec, 4), S.random_W(spec, 4)
+    check(spec, alpha, W, msqoc.SOLVER_MIXED)
+    check(spec, alpha, W, msqoc.SOLVER_FP64)
+
+
+def test_zero_controls():
+    spec = S.transmon_spec(3, 3.0, 200, 4, 5)
+    alpha, W = np.zeros(spec.d), S.random_W(spec, 9)
+    check(spec, alpha, W, msqoc.SOLVER_MIXED)
+
+
+@pytest.mark.parametrize("solver", list(SOLVERS))
+def test_strong_controls_need_more_iterations(solver):
+    """Control amplitudes 25x the workload's: the contraction factor grows to ~1e-2 and the
+    step solver must take more sweeps / refinement passes to stay at round-off."""
+    spec = S.transmon_spec(2, 20.0, 800, 4, 6)
+    alpha, W = S.random_alpha(spec, 12, amp=25 * S.ALPHA_AMP), S.random_W(spec, 12)
+    check(spec, alpha, W, SOLVERS[solver])
+
+
+def test_consistent_windows_have_zero_penalty():
+    spec = S.transmon_spec(2, 20.0, 800, 5, 6)
+    alpha = S.random_alpha(spec, 13)
+    W = oracle.rollout(spec, alpha)
+    got, want = check(spec, alpha, W, msqoc.SOLVER_MIXED)
+    with msqoc.Problem(spec) as p:
+        pen = p.eval_objective(alpha, W)["pen"]
+    assert np.all(np.abs(pen) < 1e-24)
+
+
+def test_solvers_agree_with_each_other():
+    spec = S.transmon_spec(3, 30.0, 2000, 6, 8)
+    alpha, W = S.random_alpha(spec, 14), S.random_W(spec, 14)
+    with msqoc.Problem(spec, solver=msqoc.SOLVER_MIXED) as a, msqoc.Problem(spec, solver=msqoc.SOLVER_FP64) as b:
+        ra, rb = a.eval_gradient(alpha, W), b.eval_gradient(alpha, W)
+    assert_objective_close(ra["P"], rb["P"], rtol=1e-13)
+    assert_grad_close(ra["grad_alpha"], rb["grad_alpha"], rtol=1e-11)
+    assert_grad_close(ra["grad_W"], rb["grad_W"], rtol=1e-11)
+
+
+def test_device_pointers_match_host_pointers():
+    torch = pytest.importorskip("torch")
+    spec = S.config_2q()
+    alpha, W = S.random_alpha(spec, 15), S.random_W(spec, 15)
+    with msqoc.Problem(spec) as p:
+        host = p.eval_gradient(alpha, W)
+        a_d = torch.tensor(alpha, device="cuda", dtype=torch.float64)
+        W_d = torch.tensor(W, device="cuda", dtype=torch.float64)
+        P_d = torch.zeros(1, device="cuda", dtype=torch.float64)
+        ga_d = torch.zeros(p.d, device="cuda", dtype=torch.float64)
+        gW_d = torch.zeros(p.nW, device="cuda", dtype=torch.float64)
+        s = torch.cuda.current_stream()
+        p.eval_gradient_into(a_d, W_d, P_d, ga_d, gW_d, stream=s)
+        torch.cuda.synchronize()
+    assert P_d.item() == host["P"]
+    np.testing.assert_array_equal(ga_d.cpu().numpy(), host["grad_alpha"])
+    np.testing.assert_array_equal(gW_d.cpu().numpy(), host["grad_W"])
+
+
+def test_repeated_calls_are_bitwise_reproducible():
+    spec = S.transmon_spec(3, 30.0, 1000, 4, 8)
+    alpha, W = S.random_alpha(spec, 16), S.random_W(spec, 16)
+    with msqoc.Problem(spec) as p:
+        r1 = p.eval_gradient(alpha, W)
+        r2 = p.eval_gradient(alpha, W)
+    assert r1["P"] == r2["P"]
+    np.testing.assert_array_equal(r1["grad_alpha"], r2["grad_alpha"])
+    np.testing.assert_array_equal(r1["grad_W"], r2["grad_W"])
