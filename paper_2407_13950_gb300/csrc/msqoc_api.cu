@@ -169,7 +169,11 @@ std::vector<int> fiber_order_for(int L, int q) {
 }
 
 int choose_col_block(int E, int F, int M, int q, int L, int N, int d, int solver, int sms) {
+    // Makespan model: a tile occupies one SM for the whole window; an SM's time grows with the
+    // warps (lanes, idle ones included) of the tiles it runs.  Tiles are spread evenly, so the
+    // busiest SM runs ceil(tiles / sms) of them.  Ties go to the larger block (fewer tiles).
     int best = -1;
+    double best_cost = 0.0;
     for (int cb = E; cb >= 1; --cb) {
         if (E % cb) continue;
         if (cb * F > 512) continue;
@@ -177,9 +181,12 @@ int choose_col_block(int E, int F, int M, int q, int L, int N, int d, int solver
         const size_t s1 = sweep_layout(q, L, N, cb, nthreads, d, solver, true).total;
         const size_t s0 = sweep_layout(q, L, N, cb, nthreads, d, solver, false).total;
         if (std::max(s0, s1) > 200 * 1024) continue;
-        if (best < 0) best = cb;  // largest feasible
-        if (M * (E / cb) >= sms) best = cb;  // prefer enough tiles to cover every SM
-        else break;
+        const long tiles = long(M) * (E / cb);
+        const double cost = double((tiles + sms - 1) / sms) * nthreads;
+        if (best < 0 || cost < best_cost * 0.999) {
+            best = cb;
+            best_cost = cost;
+        }
     }
     return best;
 }

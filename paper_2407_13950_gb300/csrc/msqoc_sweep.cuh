@@ -95,20 +95,53 @@ __device__ __forceinline__ void cjmac(double2& w, double2 a, double2 b) {
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
-// acc + s * (c * w) for s = +-1, complex c (FP64): 4 FMA
+// acc + s * (c * w) for s = +-1, complex c: 4 FMA (the signs are FMA operand negations)
 template <int S>
 __device__ __forceinline__ double2 cadd_scaled(double2 acc, double2 c, double2 w) {
     double2 r;
-    r.x = fma(S * c.x, w.x, fma(-S * c.y, w.y, acc.x));
-    r.y = fma(S * c.x, w.y, fma(S * c.y, w.x, acc.y));
+    if constexpr (S > 0) {
+        r.x = fma(c.x, w.x, fma(-c.y, w.y, acc.x));
+        r.y = fma(c.x, w.y, fma(c.y, w.x, acc.y));
+    } else {
+        r.x = fma(-c.x, w.x, fma(c.y, w.y, acc.x));
+        r.y = fma(-c.x, w.y, fma(-c.y, w.x, acc.y));
+    }
     return r;
 }
 template <int S>
 __device__ __forceinline__ float2 cadd_scaled(float2 acc, float2 c, float2 w) {
     float2 r;
-    r.x = fmaf(S * c.x, w.x, fmaf(-S * c.y, w.y, acc.x));
-    r.y = fmaf(S * c.x, w.y, fmaf(S * c.y, w.x, acc.y));
+    if constexpr (S > 0) {
+        r.x = fmaf(c.x, w.x, fmaf(-c.y, w.y, acc.x));
+        r.y = fmaf(c.x, w.y, fmaf(c.y, w.x, acc.y));
+    } else {
+        r.x = fmaf(-c.x, w.x, fmaf(c.y, w.y, acc.x));
+        r.y = fmaf(-c.x, w.y, fmaf(-c.y, w.x, acc.y));
+    }
     return r;
+}
+
+// -d + s * (c * w): the FP64 residual of the refinement when the current iterate is b + d
+// (the negations are FMA operand modifiers; nothing is materialized)
+template <int S>
+__device__ __forceinline__ double2 resid_from(double2 d, double2 c, double2 w) {
+    double2 r;
+    if constexpr (S > 0) {
+        r.x = fma(c.x, w.x, fma(-c.y, w.y, -d.x));
+        r.y = fma(c.x, w.y, fma(c.y, w.x, -d.y));
+    } else {
+        r.x = fma(-c.x, w.x, fma(c.y, w.y, -d.x));
+        r.y = fma(-c.x, w.y, fma(-c.y, w.x, -d.y));
+    }
+    return r;
+}
+// 2 z - u as one FMA per component
+__device__ __forceinline__ double2 reflect(double2 z, double2 u) {
+    return make_double2(fma(2.0, z.x, -u.x), fma(2.0, z.y, -u.y));
+}
+// sqrt(l) for small l, as compile-time constants
+__host__ __device__ constexpr double sqrt_small(int l) {
+    return l == 0 ? 0.0 : l == 1 ? 1.0 : l == 2 ? 1.4142135623730951 : l == 3 ? 1.7320508075688772 : 2.0;
 }
 
 // ------------------------------------------------------------------ async bulk copies (TMA, 1D)
@@ -308,21 +341,33 @@ __device__ __forceinline__ void step_coefficients(const ProbDev& pd, int lane, c
                 a = int(ceilf(-38.8162f / lr)) - 1;   // log(2^-56) = -38.816
                 a = a < 1 ? 1 : (a > 60 ? 60 : a);
             } else {
-                const float u32 = 6.0e-8f;
-                // FP32 stage: truncation rho^(j1+1) below the FP32 floor u32*rho
-                a = int(ceilf(logf(u32) / lr));
-                a = a < 1 ? 1 : (a > 30 ? 30 : a);
-                // correction sweeps: rho^(j2+1) <= u32
-                b = int(ceilf(logf(u32) / lr)) - 1;
-                b = b < 1 ? 1 : (b > 30 ? 30 : b);
-                // refinement passes: e1 * phi^R <= 2^-56
-                const float e1 = 4.f * (u32 * rho + __powf(rho, float(a + 1)));
-                const float phi = 4.f * (u32 + __powf(rho, float(b + 1)));
-                r = 1;
-                float e = e1 * phi;
-                while (e > 1.4e-17f && r < 6) {
-                    e *= phi;
-                    ++r;
+                // Error model (relative to |P rhs|): the FP32 stage leaves e1 = c u32 rho + rho^(j1+1)
+                // (FP32 rounding of the right-hand side and of the sweeps, times the contraction,
+                // plus truncation); each FP64 residual + FP32 correction multiplies it by
+                // phi = c u32 + rho^(j2+1).  c = 4 rounding units per FP32 sweep output; target: the
+                // FP64 unit roundoff 2^-53.  Extra FP32 sweeps are cheaper than an FP64 pass, so
+                // j1, j2 grow (by up to 2) before a second refinement pass is added.
+                const float u32 = 5.9604645e-8f, c = 4.f, target = 1.1102230e-16f;
+                const int j0 = max(1, min(30, int(ceilf(logf(u32) / lr))));
+                r = 0;
+                for (int pass = 1; pass <= 6 && r == 0; ++pass) {
+                    for (int extra = 0; extra <= 2 && r == 0; ++extra) {
+                        const int ja = min(30, j0 + extra), jb = max(1, min(30, j0 - 1 + extra));
+                        const float e1 = c * u32 * rho + __powf(rho, float(ja + 1));
+                        const float phi = c * u32 + __powf(rho, float(jb + 1));
+                        float e = e1;
+                        for (int t = 0; t < pass; ++t) e *= phi;
+                        if (e <= target) {
+                            a = ja;
+                            b = jb;
+                            r = pass;
+                        }
+                    }
+                }
+                if (r == 0) {
+                    a = min(30, j0 + 2);
+                    b = min(30, j0 + 1);
+                    r = 6;
                 }
             }
             if (rho >= 0.5f) bad = 1;
@@ -547,13 +592,13 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
 #pragma unroll
                 for (int l = 0; l < L; ++l) df[l] = cadd_scaled<S>(make_float2(0.f, 0.f), Pf[l], w[l]);
             }
-            // ---- FP64 refinement: z = b + d, residual r = (b - z) + s P w(z), correction in FP32
-            double2 bmz[L];
+            // ---- FP64 refinement: z = b + d, residual r = (b - z) + s P w(z), correction in FP32.
+            // dacc accumulates z - b (= d, then d + e, ...); b - z = -dacc up to the rounding of z.
+            double2 dacc[L];
 #pragma unroll
             for (int l = 0; l < L; ++l) {
-                const double2 dd = f64_of(df[l]);
-                z[l] = make_double2(b[l].x + dd.x, b[l].y + dd.y);
-                bmz[l] = make_double2(-dd.x, -dd.y);
+                dacc[l] = f64_of(df[l]);
+                z[l] = make_double2(b[l].x + dacc[l].x, b[l].y + dacc[l].y);
             }
             for (int pass = 0; pass < R; ++pass) {
                 if (act) {
@@ -566,7 +611,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
                 float2 rf[L], e[L];
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
-                    const double2 r = cadd_scaled<S>(bmz[l], Pd[l], w[l]);
+                    const double2 r = resid_from<S>(dacc[l], Pd[l], w[l]);
                     rf[l] = f32_of(r);
                     e[l] = rf[l];
                 }
@@ -587,7 +632,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
                 for (int l = 0; l < L; ++l) {
                     const double2 ed = f64_of(e[l]);
                     z[l] = make_double2(z[l].x + ed.x, z[l].y + ed.y);
-                    if (pass + 1 < R) bmz[l] = make_double2(bmz[l].x - ed.x, bmz[l].y - ed.y);
+                    if (pass + 1 < R) dacc[l] = make_double2(dacc[l].x + ed.x, dacc[l].y + ed.y);
                 }
                 // a later pass rewrites D0: every thread must be done reading it
                 if (pass + 1 < R) __syncthreads();
@@ -608,7 +653,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
                 fence_proxy_async_smem();
             }
 #pragma unroll
-            for (int l = 0; l < L; ++l) u[l] = make_double2(2.0 * z[l].x - u[l].x, 2.0 * z[l].y - u[l].y);
+            for (int l = 0; l < L; ++l) u[l] = reflect(z[l], u[l]);
         } else {
             // ---- gradient quadrature on the midpoints (fused): needs Ubar_n of the tile
             const int slot = jj & 1;
@@ -627,19 +672,28 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
                 double2 zq = make_double2(0.0, 0.0), yq = make_double2(0.0, 0.0);
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
+                    // z: conj(Lbar_l) sqrt(l+1) Ubar_{l+1};  y: conj(Lbar_l) sqrt(l) Ubar_{l-1}
                     if (l < L - 1) {
-                        double2 p = make_double2(0.0, 0.0);
-                        cjmac(p, z[l], UB[fb.xo + l + 1]);
-                        const double wgt = pd.wsq[2 * l + 0];
-                        zq.x = fma(wgt, p.x, zq.x);
-                        zq.y = fma(wgt, p.y, zq.y);
+                        const double wz = sqrt_small(l + 1);   // folded after unrolling
+                        if (wz == 1.0) {
+                            cjmac(zq, z[l], UB[fb.xo + l + 1]);
+                        } else {
+                            double2 p = make_double2(0.0, 0.0);
+                            cjmac(p, z[l], UB[fb.xo + l + 1]);
+                            zq.x = fma(wz, p.x, zq.x);
+                            zq.y = fma(wz, p.y, zq.y);
+                        }
                     }
                     if (l > 0) {
-                        double2 p = make_double2(0.0, 0.0);
-                        cjmac(p, z[l], UB[fb.xo + l - 1]);
-                        const double wgt = pd.wsq[2 * l + 1];
-                        yq.x = fma(wgt, p.x, yq.x);
-                        yq.y = fma(wgt, p.y, yq.y);
+                        const double wy = sqrt_small(l);
+                        if (wy == 1.0) {
+                            cjmac(yq, z[l], UB[fb.xo + l - 1]);
+                        } else {
+                            double2 p = make_double2(0.0, 0.0);
+                            cjmac(p, z[l], UB[fb.xo + l - 1]);
+                            yq.x = fma(wy, p.x, yq.x);
+                            yq.y = fma(wy, p.y, yq.y);
+                        }
                     }
                 }
                 acc[4 * kl + 0] = zq.x;
@@ -697,7 +751,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
             }
             // Lambda_n = 2 Lbar - Lambda_{n+1}
 #pragma unroll
-            for (int l = 0; l < L; ++l) u[l] = make_double2(2.0 * z[l].x - u[l].x, 2.0 * z[l].y - u[l].y);
+            for (int l = 0; l < L; ++l) u[l] = reflect(z[l], u[l]);
         }
 
         // warp 0 folds the previous step's reduced products into the alpha-gradient
