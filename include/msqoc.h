@@ -160,6 +160,46 @@ msqoc_status msqoc_kernel_times(msqoc_problem* p, float* ms);
  * part of the paper's method. */
 msqoc_status msqoc_measure_fp64_peak(double* tflops);
 
+/* ---------------------------------------------------------------------------------------
+ * Objective evaluation that allocates no device memory.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory themselves: a plug-in inside a host application whose memory
+ * manager owns the whole device heap, a process that reserved all device memory up front,
+ * or a control loop that cannot afford cudaMalloc / cudaFree (cudaFree synchronizes the
+ * device).  msqoc_create_problem allocates, so such callers cannot hold a problem handle.
+ *
+ * msqoc_eval_objective_noalloc computes the same P (and J, pen) as msqoc_create_problem
+ * followed by msqoc_eval_objective with default options and the given solver, running the
+ * same kernels, but every table and intermediate it needs lives in one fixed scratch array
+ * of MSQOC_NOALLOC_SCRATCH_BYTES bytes that the library declares statically: each GPU that
+ * loads the library holds it from module load until the process exits.  The call makes no
+ * cudaMalloc, cudaFree or other allocating call.
+ *
+ * Arguments: the description (H, C, target, T, nsteps, nwindows, mu) as for
+ * msqoc_create_problem; solver is MSQOC_SOLVER_*; alpha, W, P_out, J_out, pen_out as for
+ * msqoc_eval_objective (host or device memory; J_out and pen_out may be NULL).
+ * Size limit: a problem needs (16 (q + sum N_f) + 32) nsteps bytes of control tables plus
+ * 32 N E M bytes of target, window and end states, plus a few KB of small tables (each
+ * region rounded up to 256 bytes); one that does not fit is rejected with
+ * MSQOC_ERR_INVALID_ARG before any device work, whatever kind of pointers it passes.  The
+ * 4-transmon workload (N = 81, E = 16, 2 carriers each, 100000 steps, M <= 256) fits.
+ * Synchronization: the call is synchronous; it returns once the results are in the outputs.
+ * Set-up: the first call on a device looks up the device address of the scratch array on
+ * that device (with the device current); make that first call before any stream capture.
+ * Sharing: every call on a device uses the same scratch array, which keeps the previous
+ * call's contents (what must start at zero is cleared by each call).  Calls that overlap on
+ * the GPU (from several host threads or streams at once) race on it and corrupt each
+ * other's results: serialize them.
+ */
+#define MSQOC_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H, const msqoc_controls* C,
+                                          const double* target, double T, int64_t nsteps,
+                                          int32_t nwindows, double mu, int32_t solver,
+                                          const double* alpha, const double* W, double* P_out,
+                                          double* J_out, double* pen_out, void* stream);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t msqoc_version(void);
 

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -149,23 +150,71 @@ OutLayout out_layout(int M, int d, size_t nW) {
 
 bool shape_supported(int L, int q) { return (L == 3 && q >= 1 && q <= 5) || (L == 2 && q >= 1 && q <= 6); }
 
-// fibers sorted so that lanes of a warp share their neighbour-list shape: key = bitmask of the
-// fixed subsystems whose level is interior (two neighbours), ordered by popcount then mask
-std::vector<int> fiber_order_for(int L, int q) {
+constexpr int kMaxRows = 243;    // largest N of a supported shape (L = 3, q = 5)
+constexpr int kMaxFibers = 81;   // largest N / L
+
+// Fibers sorted so that lanes of a warp share their neighbour-list shape: key = bitmask of the
+// fixed subsystems whose level is interior (two neighbours), ordered by popcount then mask.
+// Stable insertion sort into order[N/L] (equal keys keep ascending fiber order).
+void fiber_order_into(int L, int q, int* order) {
     const int F = ipow_i(L, q) / L;
-    std::vector<int> order(F);
-    std::vector<int> key(F);
+    int key[kMaxFibers];
     for (int f = 0; f < F; ++f) {
         int mask = 0;
         for (int k = 0; k < q - 1; ++k) {
             const int lk = (f / ipow_i(L, q - 2 - k)) % L;
             if (lk > 0 && lk < L - 1) mask |= 1 << k;
         }
-        key[f] = (__builtin_popcount(mask) << 16) | mask;
-        order[f] = f;
+        const int kf = (__builtin_popcount(mask) << 16) | mask;
+        int pos = f;
+        while (pos > 0 && key[pos - 1] > kf) {
+            key[pos] = key[pos - 1];
+            order[pos] = order[pos - 1];
+            --pos;
+        }
+        key[pos] = kf;
+        order[pos] = f;
     }
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
-    return order;
+}
+
+// Drift diagonal D_i of row i: self-Kerr -xi_k/2 l_k(l_k-1), optional detuning, cross-Kerr
+// -xi_kl l_k l_l (the rotating-frame transmon form of Eq. sys-ham).
+double drift_entry(const msqoc_hamiltonian* H, int q, int L, int i) {
+    int lv[MAXQ];
+    for (int k = 0; k < q; ++k) lv[k] = (i / ipow_i(L, q - 1 - k)) % L;
+    double e = 0.0;
+    for (int k = 0; k < q; ++k) {
+        e += -0.5 * H->xi[k] * lv[k] * (lv[k] - 1);
+        if (H->detune) e += H->detune[k] * lv[k];
+        for (int l = k + 1; l < q; ++l)
+            if (H->xi_cross) e -= H->xi_cross[k * q + l] * lv[k] * lv[l];
+    }
+    return e;
+}
+
+// diagonal preconditioner entry 1/(1 + i a), a = h D_i / 2
+double2 precond_entry(double h, double D) {
+    const double a = 0.5 * h * D;
+    const double den = 1.0 + a * a;
+    return make_double2(1.0 / den, -a / den);
+}
+
+// full row index of essential column e (base-ness digits -> base-L digits)
+int essential_row(int q, int L, int ness, int e) {
+    int i = 0, r = e;
+    for (int k = q - 1, w = 1; k >= 0; --k, w *= L) {
+        i += (r % ness) * w;
+        r /= ness;
+    }
+    return i;
+}
+
+// QFT_E entry (e, j) = exp(2 pi i e j / E) / sqrt(E) (Sec. 5)
+double2 qft_entry(int E, int e, int j) {
+    const double s = 1.0 / std::sqrt(double(E));
+    const long long pw = (long long)e * j % E;
+    const double ang = 2.0 * M_PI * double(pw) / double(E);
+    return make_double2(s * std::cos(ang), s * std::sin(ang));
 }
 
 int choose_col_block(int E, int F, int M, int q, int L, int N, int d, int solver, int sms) {
@@ -191,32 +240,9 @@ int choose_col_block(int E, int F, int M, int q, int L, int N, int d, int solver
     return best;
 }
 
-}  // namespace
-
-namespace msqoc {
-size_t sweep_smem_bytes(const ProbDev& pd, bool bwd) {
-    return sweep_layout(pd.q, pd.L, pd.N, pd.cb, pd.nthreads, pd.d, pd.solver, bwd).total;
-}
-}  // namespace msqoc
-
-extern "C" {
-
-int32_t msqoc_version(void) { return 100; }
-
-int32_t msqoc_last_error(char* buf, size_t len) {
-    if (buf && len) {
-        size_t n = std::min(len - 1, g_last_error.size());
-        memcpy(buf, g_last_error.data(), n);
-        buf[n] = 0;
-    }
-    return static_cast<int32_t>(g_last_error.size());
-}
-
-msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, const double* target,
-                                  double T, int64_t nsteps, int32_t nwindows, double mu,
-                                  const msqoc_options* opt, msqoc_problem** out) {
-    if (!out) return fail(MSQOC_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
+// Validation of a problem description shared by every entry point that takes one.
+msqoc_status check_description(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps,
+                               int32_t nwindows) {
     if (!H || !C) return fail(MSQOC_ERR_INVALID_ARG, "hamiltonian or controls is NULL");
     const int q = H->nqubits, L = H->nlevels, ness = H->ness;
     if (q < 1 || q > MAXQ || L < 2 || ness < 1 || ness > L || !H->xi)
@@ -237,22 +263,16 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
         nfsum += C->ncarriers[k];
     }
     if (nfsum > MAXNF) return fail(MSQOC_ERR_INVALID_ARG, "too many carriers (%d > %d)", nfsum, MAXNF);
+    return MSQOC_OK;
+}
 
-    msqoc_options o{};
-    if (opt) o = *opt;
-    const int solver = o.solver == MSQOC_SOLVER_FP64 ? SOLVER_FP64 : SOLVER_MIXED;
-    if (o.ckpt_interval != 0 && o.ckpt_interval != 1)
-        return fail(MSQOC_ERR_UNSUPPORTED, "checkpoint interval %d not implemented (use 1)", o.ckpt_interval);
-    if (o.profile != 0 && o.profile != 1) return fail(MSQOC_ERR_INVALID_ARG, "profile must be 0 or 1");
-
-    auto* p = new (std::nothrow) msqoc_problem();
-    if (!p) return fail(MSQOC_ERR_OUT_OF_MEMORY, "host allocation failed");
-    ProbDev& pd = p->pd;
-    cudaGetDevice(&p->device);
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    if (sms <= 0) sms = 1;
-
+// Shape, time grid, model scalars and tile geometry of a validated description (every field
+// of pd except the device pointers).  col_block 0 = automatic.
+msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps,
+                           int32_t nwindows, double mu, int solver, int col_block, int sms, ProbDev& pd) {
+    const int q = H->nqubits, L = H->nlevels, ness = H->ness;
+    int nfsum = 0;
+    for (int k = 0; k < q; ++k) nfsum += C->ncarriers[k];
     pd.q = q;
     pd.L = L;
     pd.ness = ness;
@@ -282,65 +302,87 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
         pd.wsq[2 * l + 0] = std::sqrt(double(l + 1));
         pd.wsq[2 * l + 1] = std::sqrt(double(l));
     }
-    int cb = o.col_block;
+    int cb = col_block;
     if (cb == 0) cb = choose_col_block(pd.E, pd.F, pd.M, q, L, pd.N, pd.d, solver, sms);
-    if (cb <= 0 || pd.E % cb || cb * pd.F > 512) {
-        delete p;
+    if (cb <= 0 || pd.E % cb || cb * pd.F > 512)
         return fail(MSQOC_ERR_INVALID_ARG, "column block %d invalid for E=%d (needs cb | E, cb*N/L <= 512)", cb, pd.E);
-    }
     pd.cb = cb;
     pd.nblk = pd.E / cb;
     pd.nthreads = ((cb * pd.F + 31) / 32) * 32;
     pd.ntiles = pd.M * pd.nblk;
-    if (std::max(sweep_smem_bytes(pd, true), sweep_smem_bytes(pd, false)) > 227 * 1024) {
-        delete p;
+    if (std::max(sweep_layout(q, L, pd.N, cb, pd.nthreads, pd.d, solver, true).total,
+                 sweep_layout(q, L, pd.N, cb, pd.nthreads, pd.d, solver, false).total) > 227 * 1024)
         return fail(MSQOC_ERR_INVALID_ARG, "column block %d needs too much shared memory", cb);
+    return MSQOC_OK;
+}
+
+}  // namespace
+
+namespace msqoc {
+size_t sweep_smem_bytes(const ProbDev& pd, bool bwd) {
+    return sweep_layout(pd.q, pd.L, pd.N, pd.cb, pd.nthreads, pd.d, pd.solver, bwd).total;
+}
+}  // namespace msqoc
+
+extern "C" {
+
+int32_t msqoc_version(void) { return 100; }
+
+int32_t msqoc_last_error(char* buf, size_t len) {
+    if (buf && len) {
+        size_t n = std::min(len - 1, g_last_error.size());
+        memcpy(buf, g_last_error.data(), n);
+        buf[n] = 0;
     }
+    return static_cast<int32_t>(g_last_error.size());
+}
+
+msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, const double* target,
+                                  double T, int64_t nsteps, int32_t nwindows, double mu,
+                                  const msqoc_options* opt, msqoc_problem** out) {
+    if (!out) return fail(MSQOC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    msqoc_status st0 = check_description(H, C, T, nsteps, nwindows);
+    if (st0 != MSQOC_OK) return st0;
+
+    msqoc_options o{};
+    if (opt) o = *opt;
+    const int solver = o.solver == MSQOC_SOLVER_FP64 ? SOLVER_FP64 : SOLVER_MIXED;
+    if (o.ckpt_interval != 0 && o.ckpt_interval != 1)
+        return fail(MSQOC_ERR_UNSUPPORTED, "checkpoint interval %d not implemented (use 1)", o.ckpt_interval);
+    if (o.profile != 0 && o.profile != 1) return fail(MSQOC_ERR_INVALID_ARG, "profile must be 0 or 1");
+
+    auto* p = new (std::nothrow) msqoc_problem();
+    if (!p) return fail(MSQOC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    ProbDev& pd = p->pd;
+    cudaGetDevice(&p->device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (sms <= 0) sms = 1;
+    st0 = shape_problem(H, C, T, nsteps, nwindows, mu, solver, o.col_block, sms, pd);
+    if (st0 != MSQOC_OK) {
+        delete p;
+        return st0;
+    }
+    const int q = pd.q, L = pd.L, nfsum = pd.nfsum;
 
     // ---- host-side model tables
     const int N = pd.N, E = pd.E;
     p->ne = size_t(N) * E;
     p->nW = 2 * p->ne * size_t(pd.M - 1);
-    std::vector<double> D(N);
     std::vector<double2> P(N);
-    for (int i = 0; i < N; ++i) {
-        double e = 0.0;
-        std::vector<int> lv(q);
-        for (int k = 0; k < q; ++k) lv[k] = (i / ipow_i(L, q - 1 - k)) % L;
-        for (int k = 0; k < q; ++k) {
-            e += -0.5 * H->xi[k] * lv[k] * (lv[k] - 1);
-            if (H->detune) e += H->detune[k] * lv[k];
-            for (int l = k + 1; l < q; ++l)
-                if (H->xi_cross) e -= H->xi_cross[k * q + l] * lv[k] * lv[l];
-        }
-        D[i] = e;
-        // P_i = 1/(1 + i a), a = h D_i / 2
-        const double a = 0.5 * pd.h * e;
-        const double den = 1.0 + a * a;
-        P[i] = make_double2(1.0 / den, -a / den);
-    }
+    for (int i = 0; i < N; ++i) P[i] = precond_entry(pd.h, drift_entry(H, q, L, i));
     std::vector<int> emb(E);
-    for (int e = 0; e < E; ++e) {
-        int i = 0, r = e;
-        for (int k = q - 1, w = 1; k >= 0; --k, w *= L) {
-            i += (r % ness) * w;
-            r /= ness;
-        }
-        emb[e] = i;
-    }
+    for (int e = 0; e < E; ++e) emb[e] = essential_row(q, L, pd.ness, e);
     std::vector<double2> Vh(p->ne, make_double2(0.0, 0.0));
     if (target) {
         for (size_t e = 0; e < p->ne; ++e) Vh[e] = make_double2(target[2 * e], target[2 * e + 1]);
     } else {
-        const double s = 1.0 / std::sqrt(double(E));
         for (int j = 0; j < E; ++j)
-            for (int e = 0; e < E; ++e) {
-                const long long pw = (long long)e * j % E;
-                const double ang = 2.0 * M_PI * double(pw) / double(E);
-                Vh[size_t(j) * N + emb[e]] = make_double2(s * std::cos(ang), s * std::sin(ang));
-            }
+            for (int e = 0; e < E; ++e) Vh[size_t(j) * N + emb[e]] = qft_entry(E, e, j);
     }
-    std::vector<int> order = fiber_order_for(L, q);
+    std::vector<int> order(pd.F);
+    fiber_order_into(L, q, order.data());
 
     // ---- device buffers
     const size_t M = pd.M;
@@ -578,5 +620,171 @@ extern "C" msqoc_status msqoc_kernel_times(msqoc_problem* p, float* ms) {
         CUDA_TRY(cudaEventSynchronize(p->ev[k][1]));
         CUDA_TRY(cudaEventElapsedTime(&ms[k], p->ev[k][0], p->ev[k][1]));
     }
+    return MSQOC_OK;
+}
+
+// ------------------------------------------------------------------ objective without allocation
+// Scratch of msqoc_eval_objective_noalloc: every table and intermediate of one objective
+// evaluation, carved into 256-byte-aligned regions.  Static device storage: the module holds
+// it on every GPU where it is loaded, and no call allocates.  In host code the name below is
+// only a stand-in registered with the runtime; the device address comes from
+// cudaGetSymbolAddress (noalloc_scratch below).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MSQOC_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_base[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up on the first call
+// for that device (with that device current) and cached.
+msqoc_status noalloc_scratch(unsigned char** base) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(MSQOC_ERR_UNSUPPORTED, "device %d is beyond the %d devices this entry point serves", dev,
+                    kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_base[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(MSQOC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch on device %d failed: %s", dev,
+                        cudaGetErrorString(e));
+        g_noalloc_base[dev] = static_cast<unsigned char*>(ptr);
+    }
+    *base = g_noalloc_base[dev];
+    return MSQOC_OK;
+}
+
+// byte offsets of consecutive 256-byte-aligned regions
+struct Carve {
+    size_t off = 0;
+    template <typename T>
+    size_t take(size_t n) {
+        const size_t at = off;
+        off = (off + n * sizeof(T) + 255) & ~size_t(255);
+        return at;
+    }
+};
+
+}  // namespace
+
+extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H, const msqoc_controls* C,
+                                                     const double* target, double T, int64_t nsteps,
+                                                     int32_t nwindows, double mu, int32_t solver,
+                                                     const double* alpha, const double* W, double* P_out,
+                                                     double* J_out, double* pen_out, void* stream) {
+    if (!alpha || !P_out) return fail(MSQOC_ERR_INVALID_ARG, "alpha or P_out is NULL");
+    msqoc_status st = check_description(H, C, T, nsteps, nwindows);
+    if (st != MSQOC_OK) return st;
+    if (nwindows > 1 && !W) return fail(MSQOC_ERR_INVALID_ARG, "W is NULL but M > 1");
+    int dev = 0, sms = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ProbDev pd{};
+    st = shape_problem(H, C, T, nsteps, nwindows, mu, solver == MSQOC_SOLVER_FP64 ? SOLVER_FP64 : SOLVER_MIXED, 0,
+                       std::max(sms, 1), pd);
+    if (st != MSQOC_OK) return st;
+
+    // ---- scratch layout; the limit depends on the problem's size only
+    const size_t N = pd.N, E = pd.E, ne = N * E, M = pd.M, nt = size_t(nsteps);
+    const size_t nW = 2 * ne * (M - 1);
+    Carve cv;
+    const size_t o_status = cv.take<int>(1), o_term = cv.take<double>(M), o_out = cv.take<double>(M + 1),
+                 o_P = cv.take<double2>(N), o_order = cv.take<int>(pd.F), o_emb = cv.take<int>(E),
+                 o_V = cv.take<double2>(ne), o_alpha = cv.take<double>(pd.d), o_W = cv.take<double>(nW),
+                 o_ctrl = cv.take<double2>(nt * pd.q), o_spl = cv.take<Spline4>(nt),
+                 o_phase = cv.take<double2>(nt * pd.nfsum), o_Uend = cv.take<double2>(M * ne);
+    if (cv.off > MSQOC_NOALLOC_SCRATCH_BYTES)
+        return fail(MSQOC_ERR_INVALID_ARG,
+                    "problem needs %zu bytes of scratch; the allocation-free objective holds at most %zu "
+                    "(MSQOC_NOALLOC_SCRATCH_BYTES)",
+                    cv.off, size_t(MSQOC_NOALLOC_SCRATCH_BYTES));
+    unsigned char* base = nullptr;
+    st = noalloc_scratch(&base);
+    if (st != MSQOC_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    pd.status = reinterpret_cast<int*>(base + o_status);
+    pd.term = reinterpret_cast<double*>(base + o_term);
+    double2* Pd = reinterpret_cast<double2*>(base + o_P);
+    int* order_d = reinterpret_cast<int*>(base + o_order);
+    int* emb_d = reinterpret_cast<int*>(base + o_emb);
+    double2* V_d = reinterpret_cast<double2*>(base + o_V);
+    pd.P = Pd;
+    pd.fiber_order = order_d;
+    pd.emb = emb_d;
+    pd.V = V_d;
+    pd.ctrl = reinterpret_cast<double2*>(base + o_ctrl);
+    pd.spl = reinterpret_cast<Spline4*>(base + o_spl);
+    pd.phase = reinterpret_cast<double2*>(base + o_phase);
+    pd.Uend = reinterpret_cast<double2*>(base + o_Uend);
+    double* outs = reinterpret_cast<double*>(base + o_out);   // P, J, pen[M-1]
+
+    // ---- model tables, built in small host buffers and copied in (a pageable host-to-device
+    // copy has consumed its source when cudaMemcpyAsync returns, so the buffers are reused)
+    CUDA_TRY(cudaMemsetAsync(pd.status, 0, sizeof(int), s));
+    {
+        double2 rows[kMaxRows];
+        for (size_t i = 0; i < N; ++i) rows[i] = precond_entry(pd.h, drift_entry(H, pd.q, pd.L, int(i)));
+        CUDA_TRY(cudaMemcpyAsync(Pd, rows, N * sizeof(double2), cudaMemcpyHostToDevice, s));
+        int order[kMaxFibers];
+        fiber_order_into(pd.L, pd.q, order);
+        CUDA_TRY(cudaMemcpyAsync(order_d, order, pd.F * sizeof(int), cudaMemcpyHostToDevice, s));
+        int emb[kMaxRows];
+        for (size_t e = 0; e < E; ++e) emb[e] = essential_row(pd.q, pd.L, pd.ness, int(e));
+        CUDA_TRY(cudaMemcpyAsync(emb_d, emb, E * sizeof(int), cudaMemcpyHostToDevice, s));
+        if (target) {
+            CUDA_TRY(cudaMemcpyAsync(V_d, target, ne * sizeof(double2), cudaMemcpyDefault, s));
+        } else {
+            for (size_t j = 0; j < E; ++j) {   // QFT_E on the essential rows, one column at a time
+                for (size_t i = 0; i < N; ++i) rows[i] = make_double2(0.0, 0.0);
+                for (size_t e = 0; e < E; ++e) rows[emb[e]] = qft_entry(int(E), int(e), int(j));
+                CUDA_TRY(cudaMemcpyAsync(V_d + j * N, rows, N * sizeof(double2), cudaMemcpyHostToDevice, s));
+            }
+        }
+    }
+    // ---- inputs: device arrays in place, host arrays copied into the scratch
+    if (is_device_ptr(alpha)) {
+        pd.alpha = alpha;
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(base + o_alpha, alpha, pd.d * sizeof(double), cudaMemcpyHostToDevice, s));
+        pd.alpha = reinterpret_cast<const double*>(base + o_alpha);
+    }
+    pd.W = reinterpret_cast<const double2*>(base + o_W);
+    if (M > 1) {
+        if (is_device_ptr(W)) {
+            if (reinterpret_cast<uintptr_t>(W) % 16) return fail(MSQOC_ERR_INVALID_ARG, "device W must be 16-byte aligned");
+            pd.W = reinterpret_cast<const double2*>(W);
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(base + o_W, W, nW * sizeof(double), cudaMemcpyHostToDevice, s));
+        }
+    }
+
+    // ---- the objective's kernels (controls, forward sweep, terminal terms, reduction)
+    {
+        const int threads = 256;
+        const int blocks = static_cast<int>(std::min<int64_t>((pd.nsteps + threads - 1) / threads, 4096));
+        k_controls<<<blocks, threads, 0, s>>>(pd);
+        CUDA_TRY(cudaGetLastError());
+    }
+    CUDA_TRY(launch_sweep(pd, false, false, s));
+    k_terminal<<<pd.M, TERM_THREADS, 0, s>>>(pd, 0);
+    CUDA_TRY(cudaGetLastError());
+    k_finalize_scalars<<<1, 32, 0, s>>>(pd, outs, outs + 1, M > 1 ? outs + 2 : nullptr, nullptr);
+    CUDA_TRY(cudaGetLastError());
+
+    // ---- results to the caller (host or device) and the device status word
+    CUDA_TRY(cudaMemcpyAsync(P_out, outs, sizeof(double), cudaMemcpyDefault, s));
+    if (J_out) CUDA_TRY(cudaMemcpyAsync(J_out, outs + 1, sizeof(double), cudaMemcpyDefault, s));
+    if (pen_out && M > 1) CUDA_TRY(cudaMemcpyAsync(pen_out, outs + 2, (M - 1) * sizeof(double), cudaMemcpyDefault, s));
+    int status_word = 0;
+    CUDA_TRY(cudaMemcpyAsync(&status_word, pd.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (status_word & ST_TIMEOUT) return fail(MSQOC_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", status_word);
+    if (status_word & ST_SOLVER_RANGE)
+        return fail(MSQOC_ERR_UNSUPPORTED, "time step too large for the step solver (h*|H_c|/2 >= 0.5)");
+    if (status_word) return fail(MSQOC_ERR_INTERNAL, "device status %d", status_word);
     return MSQOC_OK;
 }

@@ -23,7 +23,7 @@ SOLVER_DEFAULT, SOLVER_FP64, SOLVER_MIXED = 0, 1, 2
 
 EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_eval_objective", "msqoc_eval_gradient",
             "msqoc_destroy_problem", "msqoc_last_error", "msqoc_version", "msqoc_kernel_times",
-            "msqoc_measure_fp64_peak"]
+            "msqoc_measure_fp64_peak", "msqoc_eval_objective_noalloc"]
 KERNEL_NAMES = ["controls", "forward", "terminal", "adjoint", "finalize"]
 
 
@@ -77,6 +77,8 @@ def load(build_if_missing: bool = True):
             "msqoc_version": (i32, []),
             "msqoc_kernel_times": (i32, [vp, vp]),
             "msqoc_measure_fp64_peak": (i32, [vp]),
+            "msqoc_eval_objective_noalloc": (i32, [vp, vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, i32,
+                                                   vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -122,13 +124,11 @@ def _stream_handle(stream) -> Optional[int]:
     return stream.cuda_stream  # torch.cuda.Stream
 
 
-class Problem:
-    """One multiple-shooting problem living on the current CUDA device."""
+class _Description:
+    """The msqoc_hamiltonian / msqoc_controls structs of a problem spec, with the host arrays
+    they point to kept alive."""
 
-    def __init__(self, spec, target: Optional[np.ndarray] = None, solver: int = SOLVER_DEFAULT,
-                 col_block: int = 0, ckpt_interval: int = 0, profile: bool = False):
-        lib = load()
-        self.spec = spec
+    def __init__(self, spec, target: Optional[np.ndarray] = None):
         q = spec.q
         self._xi = np.ascontiguousarray(spec.xi, dtype=np.float64)
         self._xc = np.ascontiguousarray(np.asarray(spec.xi_cross, dtype=np.float64).reshape(q, q))
@@ -137,14 +137,24 @@ class Problem:
         self._nf = np.ascontiguousarray([len(w) for w in spec.omega], dtype=np.int32)
         self._om = np.ascontiguousarray([x for w in spec.omega for x in w], dtype=np.float64)
         self._tgt = None if target is None else np.ascontiguousarray(target, dtype=np.float64)
-        H = Hamiltonian(q, spec.L, spec.ness, self._xi.ctypes.data, self._xc.ctypes.data,
-                        None if self._det is None else self._det.ctypes.data,
-                        None if self._jx is None else self._jx.ctypes.data)
-        C = Controls(self._nf.ctypes.data, self._om.ctypes.data, spec.d1)
+        self.H = Hamiltonian(q, spec.L, spec.ness, self._xi.ctypes.data, self._xc.ctypes.data,
+                             None if self._det is None else self._det.ctypes.data,
+                             None if self._jx is None else self._jx.ctypes.data)
+        self.C = Controls(self._nf.ctypes.data, self._om.ctypes.data, spec.d1)
+        self.target_ptr = None if self._tgt is None else self._tgt.ctypes.data
+
+
+class Problem:
+    """One multiple-shooting problem living on the current CUDA device."""
+
+    def __init__(self, spec, target: Optional[np.ndarray] = None, solver: int = SOLVER_DEFAULT,
+                 col_block: int = 0, ckpt_interval: int = 0, profile: bool = False):
+        lib = load()
+        self.spec = spec
+        self._desc = _Description(spec, target)
         O = Options(solver, col_block, ckpt_interval, 1 if profile else 0)
         h = ctypes.c_void_p()
-        _check(lib.msqoc_create_problem(ctypes.byref(H), ctypes.byref(C),
-                                        None if self._tgt is None else self._tgt.ctypes.data,
+        _check(lib.msqoc_create_problem(ctypes.byref(self._desc.H), ctypes.byref(self._desc.C), self._desc.target_ptr,
                                         float(spec.T), int(spec.nsteps), int(spec.M), float(spec.mu),
                                         ctypes.byref(O), ctypes.byref(h)))
         self.handle = h
@@ -231,3 +241,25 @@ def measure_fp64_peak() -> float:
     t = ctypes.c_double()
     _check(load().msqoc_measure_fp64_peak(ctypes.byref(t)))
     return t.value
+
+
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024   # MSQOC_NOALLOC_SCRATCH_BYTES
+
+
+def eval_objective_noalloc(spec, alpha, W=None, target=None, solver: int = SOLVER_DEFAULT, stream=None,
+                           P_out=None, J_out=None, pen_out=None) -> dict:
+    """Objective of ``spec`` through msqoc_eval_objective_noalloc: no problem handle and no
+    device allocation by the library (for callers that cannot allocate device memory).
+    Outputs default to host arrays; device tensors may be passed instead.  Synchronous."""
+    M = spec.M
+    P = np.zeros(1) if P_out is None else P_out
+    J = np.zeros(1) if J_out is None else J_out
+    pen = np.zeros(max(M - 1, 1)) if pen_out is None else pen_out
+    desc = _Description(spec, target)
+    _check(load().msqoc_eval_objective_noalloc(ctypes.byref(desc.H), ctypes.byref(desc.C), desc.target_ptr,
+                                               float(spec.T), int(spec.nsteps), int(M), float(spec.mu), int(solver),
+                                               _ptr(alpha), _ptr(W if M > 1 else None), _ptr(P), _ptr(J),
+                                               _ptr(pen) if M > 1 else None, _stream_handle(stream)))
+    if P_out is not None:
+        return {"P": P_out, "J": J_out, "pen": pen_out}
+    return {"P": float(P[0]), "J": float(J[0]), "pen": pen[:M - 1].copy()}
