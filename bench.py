@@ -10,6 +10,7 @@ gradient, reductions).  The midpoint-state history (2 GB) is far larger than L2,
 flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--windows M]
+                  [--solver mixed|fp64] [--col-block CB] [--nsteps NT] [--no-cpu-baseline]
 
 Prints one JSON line.  Under torchrun (N > 1) every rank evaluates its own independent
 problem (weak scaling, no collective on the data path); rank 0 prints.
@@ -262,8 +263,13 @@ def main():
     ap.add_argument("--solver", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--col-block", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nsteps", type=int, default=0,
+                    help="shorter time grid with the same step size (small profiling case); 0 = 100000 steps")
     args = ap.parse_args()
     spec = S.config_4q(M=args.windows)
+    if args.nsteps:
+        spec = spec.replace(nsteps=args.nsteps, T=spec.T * args.nsteps / spec.nsteps,
+                            name=f"{spec.name}-{args.nsteps}steps")
     if args.impl == "reference":
         run_reference(args, spec)
     else:
