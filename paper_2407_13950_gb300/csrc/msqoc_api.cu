@@ -225,7 +225,7 @@ int choose_col_block(int E, int F, int M, int q, int L, int N, int d, int solver
     double best_cost = 0.0;
     for (int cb = E; cb >= 1; --cb) {
         if (E % cb) continue;
-        if (cb * F > 512) continue;
+        if (cb * F > MAX_TILE_THREADS) continue;
         const int nthreads = ((cb * F + 31) / 32) * 32;
         const size_t s1 = sweep_layout(q, L, N, cb, nthreads, d, solver, true).total;
         const size_t s0 = sweep_layout(q, L, N, cb, nthreads, d, solver, false).total;
@@ -304,8 +304,9 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
     }
     int cb = col_block;
     if (cb == 0) cb = choose_col_block(pd.E, pd.F, pd.M, q, L, pd.N, pd.d, solver, sms);
-    if (cb <= 0 || pd.E % cb || cb * pd.F > 512)
-        return fail(MSQOC_ERR_INVALID_ARG, "column block %d invalid for E=%d (needs cb | E, cb*N/L <= 512)", cb, pd.E);
+    if (cb <= 0 || pd.E % cb || cb * pd.F > MAX_TILE_THREADS)
+        return fail(MSQOC_ERR_INVALID_ARG, "column block %d invalid for E=%d (needs cb | E, cb*N/L <= %d)", cb, pd.E,
+                    MAX_TILE_THREADS);
     pd.cb = cb;
     pd.nblk = pd.E / cb;
     pd.nthreads = ((cb * pd.F + 31) / 32) * 32;

@@ -6,8 +6,56 @@
 
 namespace msqoc {
 
+// Iteration counts of the implicit-midpoint solve of one step from the contraction bound
+// rho = ||P iX_C|| <= (h/2) lam sum_k |d_k(t_{n+1/2})| of the diagonally preconditioned
+// fixed point (P = (I + i h/2 D)^-1).  Packed as j1 | j2 << 8 | passes << 16 | bad << 24.
+//   FP64 solver : j1 = K sweeps with rho^(K+1) <= 2^-56.
+//   mixed solver: the FP32 stage leaves the error e1 = c u32 rho + rho^(j1+1) relative to
+//     |P rhs| (FP32 rounding of the right-hand side and of the sweeps, times the contraction,
+//     plus truncation); each FP64 residual + FP32 correction multiplies it by
+//     phi = c u32 + rho^(j2+1).  c = 4 rounding units per FP32 sweep output; target: the FP64
+//     unit roundoff 2^-53.  Extra FP32 sweeps are cheaper than an FP64 pass, so j1 and j2 grow
+//     (by up to 2) before a second refinement pass is added.
+//   bad: rho >= 1/2, outside the range the counts are derived for.
+__device__ inline int step_counts(int solver, float rho) {
+    int a = 1, b = 1, r = 1, bad = 0;
+    if (rho > 1e-30f) {
+        const float lr = logf(rho);
+        if (solver == SOLVER_FP64) {
+            a = int(ceilf(-38.8162f / lr)) - 1;   // log(2^-56) = -38.816
+            a = a < 1 ? 1 : (a > 60 ? 60 : a);
+        } else {
+            const float u32 = 5.9604645e-8f, c = 4.f, target = 1.1102230e-16f;
+            const int j0 = max(1, min(30, int(ceilf(logf(u32) / lr))));
+            r = 0;
+            for (int pass = 1; pass <= 6 && r == 0; ++pass) {
+                for (int extra = 0; extra <= 2 && r == 0; ++extra) {
+                    const int ja = min(30, j0 + extra), jb = max(1, min(30, j0 - 1 + extra));
+                    const float e1 = c * u32 * rho + __powf(rho, float(ja + 1));
+                    const float phi = c * u32 + __powf(rho, float(jb + 1));
+                    float e = e1;
+                    for (int t = 0; t < pass; ++t) e *= phi;
+                    if (e <= target) {
+                        a = ja;
+                        b = jb;
+                        r = pass;
+                    }
+                }
+            }
+            if (r == 0) {
+                a = min(30, j0 + 2);
+                b = min(30, j0 + 1);
+                r = 6;
+            }
+        }
+        if (rho >= 0.5f) bad = 1;
+    }
+    return a | (b << 8) | (r << 16) | (bad << 24);
+}
+
 // Controls at every step midpoint t_{n+1/2} = (n + 1/2) h (Eq. dj-ctrl with the quadratic
-// B-spline envelope of Sec. 2): d_k(t) = sum_f e^{i Omega_kf t} sum_s (a1 + i a2)_kfs B_s(t).
+// B-spline envelope of Sec. 2): d_k(t) = sum_f e^{i Omega_kf t} sum_s (a1 + i a2)_kfs B_s(t),
+// and the step solver's iteration counts (step_counts).
 // On [j dtau, (j+1) dtau) the three non-zero splines are s = j, j+1, j+2 with weights
 // (1-x)^2/2, 3/4 - (x-1/2)^2, x^2/2 (x = t/dtau - j).  Also stores the spline weights and the
 // carrier phases for the gradient quadrature of the adjoint sweep.
@@ -22,7 +70,7 @@ __global__ void k_controls(const ProbDev pd) {
         const double w0 = 0.5 * (1.0 - x) * (1.0 - x);
         const double w1 = 0.75 - (x - 0.5) * (x - 0.5);
         const double w2 = 0.5 * x * x;
-        pd.spl[n] = Spline4{double(s0), w0, w1, w2};
+        double mag = 0.0;   // sum_k |d_k| for the contraction bound
         for (int k = 0; k < pd.q; ++k) {
             double2 dk = make_double2(0.0, 0.0);
             for (int fi = pd.cof[k]; fi < pd.cof[k + 1]; ++fi) {
@@ -36,7 +84,10 @@ __global__ void k_controls(const ProbDev pd) {
                 dk.y += cs * ei + sn * er;
             }
             pd.ctrl[size_t(n) * pd.q + k] = dk;
+            mag += sqrt(dk.x * dk.x + dk.y * dk.y);
         }
+        const float rho = float(0.5 * pd.h * pd.lam * mag) * 1.0001f;
+        pd.spl[n] = Spline4{s0, step_counts(pd.solver, rho), w0, w1, w2};
     }
 }
 

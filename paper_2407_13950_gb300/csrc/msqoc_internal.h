@@ -9,15 +9,19 @@ namespace msqoc {
 constexpr int MAXQ = 6;       // subsystems
 constexpr int MAXNF = 64;     // carriers over all subsystems
 constexpr int MAXL = 4;       // levels per subsystem handled by the sweep kernels
+constexpr int MAX_TILE_THREADS = 256;  // threads of one sweep tile (leaves 255 registers a thread)
 
 enum Solver { SOLVER_FP64 = 1, SOLVER_MIXED = 2 };
 
 // device status word bits
 enum Status { ST_OK = 0, ST_TIMEOUT = 1, ST_BAD_LAUNCH = 2, ST_SOLVER_RANGE = 4 };
 
-// spline window of one step: first active spline index and the three weights
+// Per-step table: first active spline index, the step solver's iteration counts packed as
+// j1 | j2 << 8 | passes << 16 | out-of-range << 24, and the three spline weights.
 struct __align__(16) Spline4 {
-    double s, w0, w1, w2;
+    int s;
+    int cnt;
+    double w0, w1, w2;
 };
 
 // Everything a kernel needs about one problem and one evaluation.  Passed by value.
@@ -47,7 +51,7 @@ struct ProbDev {
     const double2* W;            // [M-1][E][N]
     // scratch
     double2* ctrl;               // [nsteps][q] d_k(t_{n+1/2})
-    Spline4* spl;                // [nsteps] (first spline index, w0, w1, w2)
+    Spline4* spl;                // [nsteps] (first spline index, solver counts, w0, w1, w2)
     double2* phase;              // [nsteps][nfsum] exp(i Omega t_{n+1/2})
     double2* hist;               // [nsteps][nblk][cb][N] midpoint states Ubar_n
     double2* Uend;               // [M][E][N] U^m(t_m)

@@ -306,82 +306,46 @@ __host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cb, i
 
 // ------------------------------------------------------------------ per-step coefficients
 // Warp 0: slot (k, l, dir) -> i (h/2) sqrt(l+1) d_k (dir 0, a_k) or i (h/2) sqrt(l) conj(d_k)
-// (dir 1, a_k^+); contraction bound and iteration counts for this step.
-template <int L, int Q, int SOLVER>
-__device__ __forceinline__ void step_coefficients(const ProbDev& pd, int lane, const double2 (&dk)[1],
-                                                  double2* cfd, float2* cff, int* prm) {
+// (dir 1, a_k^+); lane k' < NSLOT holds d_k of its slot's subsystem.  The iteration counts of
+// the step (packed by step_counts in the controls kernel) are unpacked into prm.
+template <int L, int Q>
+__device__ __forceinline__ void step_coefficients(const ProbDev& pd, int lane, double2 dk, int cnt, double2* cfd,
+                                                  float2* cff, int* prm) {
     constexpr int NSLOT = Q * L * 2;
-    // each lane < NSLOT handles one slot; dk[0] holds d_k of the lane's subsystem
-    double2 v = make_double2(0.0, 0.0);
     if (lane < NSLOT) {
         const int dir = lane & 1;
         const int l = (lane >> 1) % L;
         const bool valid = dir == 0 ? (l < L - 1) : (l > 0);
         const double s = pd.sc[2 * l + dir];
-        const double2 d = dk[0];
-        if (valid) v = dir == 0 ? make_double2(-s * d.y, s * d.x) : make_double2(s * d.y, s * d.x);
+        double2 v = make_double2(0.0, 0.0);
+        if (valid) v = dir == 0 ? make_double2(-s * dk.y, s * dk.x) : make_double2(s * dk.y, s * dk.x);
         cfd[lane] = v;
         cff[lane] = f32_of(v);
     }
-    // |d_k| in FP32 for the contraction bound: lanes with l == 0 and dir == 0 (one per subsystem)
-    float mag = 0.f;
-    if (lane < NSLOT && ((lane >> 1) % L) == 0 && (lane & 1) == 0) {
-        const float2 df = f32_of(dk[0]);
-        mag = sqrtf(df.x * df.x + df.y * df.y);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mag += __shfl_xor_sync(0xffffffffu, mag, o);
     if (lane == 0) {
-        const float rho = float(0.5 * pd.h * pd.lam) * mag * 1.0001f;
-        int a = 1, b = 1, r = 1, bad = 0;
-        if (rho > 1e-30f) {
-            const float lr = logf(rho);
-            if (SOLVER == SOLVER_FP64) {
-                // error after K sweeps <= rho^(K+1)
-                a = int(ceilf(-38.8162f / lr)) - 1;   // log(2^-56) = -38.816
-                a = a < 1 ? 1 : (a > 60 ? 60 : a);
-            } else {
-                // Error model (relative to |P rhs|): the FP32 stage leaves e1 = c u32 rho + rho^(j1+1)
-                // (FP32 rounding of the right-hand side and of the sweeps, times the contraction,
-                // plus truncation); each FP64 residual + FP32 correction multiplies it by
-                // phi = c u32 + rho^(j2+1).  c = 4 rounding units per FP32 sweep output; target: the
-                // FP64 unit roundoff 2^-53.  Extra FP32 sweeps are cheaper than an FP64 pass, so
-                // j1, j2 grow (by up to 2) before a second refinement pass is added.
-                const float u32 = 5.9604645e-8f, c = 4.f, target = 1.1102230e-16f;
-                const int j0 = max(1, min(30, int(ceilf(logf(u32) / lr))));
-                r = 0;
-                for (int pass = 1; pass <= 6 && r == 0; ++pass) {
-                    for (int extra = 0; extra <= 2 && r == 0; ++extra) {
-                        const int ja = min(30, j0 + extra), jb = max(1, min(30, j0 - 1 + extra));
-                        const float e1 = c * u32 * rho + __powf(rho, float(ja + 1));
-                        const float phi = c * u32 + __powf(rho, float(jb + 1));
-                        float e = e1;
-                        for (int t = 0; t < pass; ++t) e *= phi;
-                        if (e <= target) {
-                            a = ja;
-                            b = jb;
-                            r = pass;
-                        }
-                    }
-                }
-                if (r == 0) {
-                    a = min(30, j0 + 2);
-                    b = min(30, j0 + 1);
-                    r = 6;
-                }
-            }
-            if (rho >= 0.5f) bad = 1;
-        }
-        prm[0] = a;
-        prm[1] = b;
-        prm[2] = r;
-        prm[3] = bad;
+        prm[0] = cnt & 0xff;
+        prm[1] = (cnt >> 8) & 0xff;
+        prm[2] = (cnt >> 16) & 0xff;
+        prm[3] = (cnt >> 24) & 0xff;
     }
+}
+
+// Barrier of the tile's threads; a warp barrier when the tile is a single warp (blockDim is
+// uniform, so the branch is too).
+__device__ __forceinline__ void tile_sync() {
+    if (blockDim.x == 32)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+__device__ __forceinline__ int tile_sync_or(int p) {
+    if (blockDim.x == 32) return __any_sync(0xffffffffu, p);
+    return __syncthreads_or(p);
 }
 
 // ------------------------------------------------------------------ the sweep kernel
 template <int L, int Q, int SOLVER, bool BWD>
-__global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int want_hist) {
+__global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const ProbDev pd, const int want_hist) {
     constexpr int N = ipow_c(L, Q);
     constexpr int F = N / L;
     constexpr int NSLOT = Q * L * 2;
@@ -462,7 +426,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
             mbar_init(&mbar[1], 1);
             fence_mbar_init();
         }
-        __syncthreads();
+        tile_sync();
         if (tid == 0 && ns > 0) {
             const int64_t n = n0 + ns - 1;
             mbar_expect_tx(&mbar[0], blk_bytes);
@@ -472,9 +436,13 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
 
     // warp 0 keeps d_k of the next step in registers (lane -> subsystem of its slot)
     const int my_k = (lane < NSLOT) ? (lane / (2 * L)) : 0;
-    double2 dk_next[1];
+    double2 dk_next = make_double2(0.0, 0.0);
+    int cnt_next = 0;
     auto load_ctrl = [&](int64_t n) {
-        dk_next[0] = (warp == 0 && lane < NSLOT) ? pd.ctrl[size_t(n) * pd.q + my_k] : make_double2(0.0, 0.0);
+        if (warp == 0) {
+            dk_next = lane < NSLOT ? pd.ctrl[size_t(n) * pd.q + my_k] : make_double2(0.0, 0.0);
+            cnt_next = pd.spl[n].cnt;
+        }
     };
     // warp 0 lanes that scatter gradient entries: (k, f, j) with 3 active splines per carrier
     const int nscat = pd.nfsum * 3;
@@ -494,9 +462,18 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
         int* prm = params + par * 4;
 
         if (warp == 0) {
-            double2 dk[1] = {dk_next[0]};
+            const double2 dk = dk_next;
+            const int cnt = cnt_next;
             if (jj + 1 < ns) load_ctrl(BWD ? n - 1 : n + 1);
-            step_coefficients<L, Q, SOLVER>(pd, lane, dk, cfd, cff, prm);
+            step_coefficients<L, Q>(pd, lane, dk, cnt, cfd, cff, prm);
+        }
+        // adjoint: warp 0 fetches what the gradient fold of the previous step (n + 1) needs
+        // now, so the loads are in flight during the solve
+        Spline4 sp_prev{};
+        double2 ph_prev = make_double2(0.0, 0.0);
+        if (BWD && jj > 0 && warp == 0) {
+            sp_prev = pd.spl[n + 1];
+            if (lane < nscat) ph_prev = pd.phase[size_t(n + 1) * pd.nfsum + lane / 3];
         }
 
         // right-hand side of the preconditioned step equation: b = P u (conj(P) for the adjoint)
@@ -515,7 +492,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
 #pragma unroll
                 for (int l = 0; l < L; ++l) Dc[fb.xo + l] = z[l];
             }
-            __syncthreads();
+            tile_sync();
             // first sync of the step: publish the previous step's history block / issue prefetch
             if (!BWD && want_hist && tid == 0 && jj > 0) {
                 fence_proxy_async_smem();
@@ -534,7 +511,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
 #pragma unroll
                         for (int l = 0; l < L; ++l) Dc[fb.xo + l] = z[l];
                     }
-                    __syncthreads();
+                    tile_sync();
                 }
                 double2 w[L];
                 apply_off<L, Q, double2>(Dc, cfd, fb, z, w);
@@ -560,7 +537,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
 #pragma unroll
                     for (int l = 0; l < L; ++l) Fb[fb.xo + l] = y[l];
                 }
-                __syncthreads();
+                tile_sync();
                 if (!BWD && want_hist && tid == 0 && jj > 0) {
                     fence_proxy_async_smem();
                     bulk_s2g(pd.hist + (size_t(n - 1) * pd.nblk + blk) * blk_elems, H, blk_bytes);
@@ -586,7 +563,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
 #pragma unroll
                     for (int l = 0; l < L; ++l) Fb[fb.xo + l] = y[l];
                 }
-                __syncthreads();
+                tile_sync();
                 float2 w[L];
                 apply_off<L, Q, float2>(Fb, cff, fb, y, w);
 #pragma unroll
@@ -600,12 +577,12 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
                 dacc[l] = f64_of(df[l]);
                 z[l] = make_double2(b[l].x + dacc[l].x, b[l].y + dacc[l].y);
             }
-            for (int pass = 0; pass < R; ++pass) {
+            for (int pass = 0;; ++pass) {
                 if (act) {
 #pragma unroll
                     for (int l = 0; l < L; ++l) D0[fb.xo + l] = z[l];
                 }
-                __syncthreads();
+                tile_sync();
                 double2 w[L];
                 apply_off<L, Q, double2>(D0, cfd, fb, z, w);
                 float2 rf[L], e[L];
@@ -622,20 +599,24 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
 #pragma unroll
                         for (int l = 0; l < L; ++l) Fb[fb.xo + l] = e[l];
                     }
-                    __syncthreads();
+                    tile_sync();
                     float2 wf[L];
                     apply_off<L, Q, float2>(Fb, cff, fb, e, wf);
 #pragma unroll
                     for (int l = 0; l < L; ++l) e[l] = cadd_scaled<S>(rf[l], Pf[l], wf[l]);
                 }
+                double2 ed[L];
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
-                    const double2 ed = f64_of(e[l]);
-                    z[l] = make_double2(z[l].x + ed.x, z[l].y + ed.y);
-                    if (pass + 1 < R) dacc[l] = make_double2(dacc[l].x + ed.x, dacc[l].y + ed.y);
+                    ed[l] = f64_of(e[l]);
+                    z[l] = make_double2(z[l].x + ed[l].x, z[l].y + ed[l].y);
                 }
-                // a later pass rewrites D0: every thread must be done reading it
-                if (pass + 1 < R) __syncthreads();
+                if (pass + 1 >= R) break;
+                // another pass: dacc accumulates the correction; it rewrites D0, so every thread
+                // must be done reading it
+#pragma unroll
+                for (int l = 0; l < L; ++l) dacc[l] = make_double2(dacc[l].x + ed[l].x, dacc[l].y + ed[l].y);
+                tile_sync();
             }
         }
 
@@ -645,7 +626,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
             // ---- history of midpoint states for the adjoint sweep (async bulk store)
             if (want_hist) {
                 if (tid == 0) bulk_wait_read_all();
-                __syncthreads();
+                tile_sync();
                 if (act) {
 #pragma unroll
                     for (int l = 0; l < L; ++l) H[fb.xo + l] = z[l];
@@ -659,7 +640,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
             const int slot = jj & 1;
             double2* UB = slot ? UB1 : UB0;
             const bool ok = mbar_wait(&mbar[slot], (jj >> 1) & 1);
-            if (__syncthreads_or(!ok)) {
+            if (tile_sync_or(!ok)) {
                 timed_out = true;
                 break;
             }
@@ -765,15 +746,15 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
                 zy[pp * 4 * Q + lane] = s;
             }
             __syncwarp();
-            const Spline4 sp = pd.spl[np];
-            const int s0 = static_cast<int>(sp.s);
+            const Spline4 sp = sp_prev;
+            const int s0 = sp.s;
             for (int i = lane; i < nscat; i += 32) {
                 const int kf = i / 3, jw = i % 3;
                 int k = 0;
                 while (k + 1 < Q && pd.cof[k + 1] <= kf) ++k;
                 const double2 zk = make_double2(zy[pp * 4 * Q + 4 * k + 0], zy[pp * 4 * Q + 4 * k + 1]);
                 const double2 yk = make_double2(zy[pp * 4 * Q + 4 * k + 2], zy[pp * 4 * Q + 4 * k + 3]);
-                const double2 ph = pd.phase[size_t(np) * pd.nfsum + kf];
+                const double2 ph = i == lane ? ph_prev : pd.phase[size_t(np) * pd.nfsum + kf];
                 const double wgt = -2.0 * pd.h * (jw == 0 ? sp.w0 : (jw == 1 ? sp.w1 : sp.w2));
                 const double A = zk.y + yk.y, B = zk.x - yk.x;
                 const int idx = (kf * pd.d1 + s0 + jw) * 2;
@@ -784,7 +765,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
     }
 
     if (!timed_out) {
-        __syncthreads();
+        tile_sync();
         if (!BWD) {
             if (want_hist && tid == 0 && ns > 0) {
                 fence_proxy_async_smem();
@@ -806,7 +787,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
                 }
                 __syncwarp();
                 const Spline4 sp = pd.spl[np];
-                const int s0 = static_cast<int>(sp.s);
+                const int s0 = sp.s;
                 for (int i = lane; i < nscat; i += 32) {
                     const int kf = i / 3, jw = i % 3;
                     int k = 0;
@@ -821,7 +802,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const ProbDev pd, const int wa
                     galpha[idx + 1] += wgt * fma(ph.x, B, -ph.y * A);
                 }
             }
-            __syncthreads();
+            tile_sync();
             for (int jx = tid; jx < pd.d; jx += blockDim.x) pd.gpart[size_t(tile) * pd.d + jx] = galpha[jx];
             if (act) {
 #pragma unroll

@@ -58,11 +58,18 @@ def test_parity_small(case, solver):
     check(spec, alpha, W, SOLVERS[solver])
 
 
-@pytest.mark.parametrize("cb", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("cb", [1, 2, 4, 8])
 def test_parity_column_blocks_4q(cb):
     spec = S.transmon_spec(4, 0.6, 100, 2, 4)
     alpha, W = S.random_alpha(spec, 7), S.random_W(spec, 7)
     check(spec, alpha, W, msqoc.SOLVER_MIXED, col_block=cb)
+
+
+def test_column_block_beyond_the_tile_limit_is_rejected():
+    spec = S.transmon_spec(4, 0.6, 100, 2, 4)
+    with pytest.raises(msqoc.MsqocError) as err:
+        msqoc.Problem(spec, col_block=16)     # 16 columns x 27 fibers > 256 threads
+    assert err.value.status == -1
 
 
 def test_parity_5q_tiny():
