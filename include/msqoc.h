@@ -97,9 +97,15 @@ typedef struct msqoc_controls {
 
 typedef struct msqoc_options {
     int32_t solver;        /* MSQOC_SOLVER_* */
-    int32_t col_block;     /* columns per tile; 0 = automatic; must divide E */
-    int32_t ckpt_interval; /* forward states kept for the adjoint sweep: 1 = every step
-                              (only value implemented; 0 = automatic = 1) */
+    int32_t col_block;     /* columns per sweep tile (1 <= col_block <= E, col_block * N/L <= 256;
+                              tiles run along the window-major column list and may cover two
+                              windows; a one-warp tile must divide E); 0 = automatic */
+    int32_t ckpt_interval; /* K: forward states kept for the adjoint sweep.  1 = every midpoint
+                              state (history of nsteps * E * N complex); K > 1 = the state every
+                              K steps of each window, each K-step segment recomputed before its
+                              adjoint sweep (one more forward sweep of work); 0 = automatic (1
+                              unless that history exceeds a quarter of the device memory, then
+                              64) */
     int32_t profile;       /* 1 = record CUDA events around every kernel (msqoc_kernel_times) */
     int32_t reserved[4];
 } msqoc_options;

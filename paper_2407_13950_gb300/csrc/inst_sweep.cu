@@ -15,26 +15,41 @@
 namespace msqoc {
 
 template <int SOLVER, bool BWD>
-static cudaError_t launch_one(const ProbDev& pd, bool want_hist, cudaStream_t s) {
+static cudaError_t launch_one(const SweepArgs& a, int ntiles, cudaStream_t s) {
     auto kern = k_sweep<MSQOC_L, MSQOC_Q, SOLVER, BWD>;
-    static bool configured = false;
-    if (!configured) {
-        int dev = 0, maxsmem = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem);
+    const size_t smem = sweep_smem_bytes(a);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        configured = true;
     }
-    const size_t smem = sweep_smem_bytes(pd, BWD);
-    kern<<<pd.ntiles, pd.nthreads, smem, s>>>(pd, want_hist ? 1 : 0);
+    if (ntiles <= 0) return cudaSuccess;
+    kern<<<ntiles, a.nthreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t MSQOC_CAT(launch_sweep, MSQOC_L, MSQOC_Q)(const ProbDev& pd, bool bwd, bool want_hist, cudaStream_t s) {
-    if (pd.solver == SOLVER_FP64)
-        return bwd ? launch_one<SOLVER_FP64, true>(pd, want_hist, s) : launch_one<SOLVER_FP64, false>(pd, want_hist, s);
-    return bwd ? launch_one<SOLVER_MIXED, true>(pd, want_hist, s) : launch_one<SOLVER_MIXED, false>(pd, want_hist, s);
+template <int SOLVER, bool BWD>
+static int occupancy_one(const SweepArgs& a) {
+    auto kern = k_sweep<MSQOC_L, MSQOC_Q, SOLVER, BWD>;
+    const size_t smem = sweep_smem_bytes(a);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, a.nthreads, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t MSQOC_CAT(launch_sweep, MSQOC_L, MSQOC_Q)(const SweepArgs& a, int ntiles, cudaStream_t s) {
+    const bool bwd = a.mode == SWEEP_ADJOINT;
+    if (a.solver == SOLVER_FP64)
+        return bwd ? launch_one<SOLVER_FP64, true>(a, ntiles, s) : launch_one<SOLVER_FP64, false>(a, ntiles, s);
+    return bwd ? launch_one<SOLVER_MIXED, true>(a, ntiles, s) : launch_one<SOLVER_MIXED, false>(a, ntiles, s);
+}
+
+int MSQOC_CAT(sweep_occupancy, MSQOC_L, MSQOC_Q)(const SweepArgs& a) {
+    const bool bwd = a.mode == SWEEP_ADJOINT;
+    if (a.solver == SOLVER_FP64) return bwd ? occupancy_one<SOLVER_FP64, true>(a) : occupancy_one<SOLVER_FP64, false>(a);
+    return bwd ? occupancy_one<SOLVER_MIXED, true>(a) : occupancy_one<SOLVER_MIXED, false>(a);
 }
 
 }  // namespace msqoc

@@ -1,4 +1,4 @@
-// Host side of libmsqoc: problem packing, device memory, launches and the C ABI.
+// Host side of libmsqoc: problem packing, tile layout, device memory, launches and the C ABI.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -62,67 +62,9 @@ cudaError_t dalloc(T** p, size_t n) {
     return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
 }
 
-}  // namespace
+constexpr int kMaxRows = 243;    // largest N of a supported shape (L = 3, q = 5)
 
-struct msqoc_problem {
-    ProbDev pd{};
-    int device = 0;
-    size_t nW = 0;         // doubles in W
-    size_t ne = 0;         // N*E
-    // owned device buffers
-    double2* P = nullptr;
-    int* fiber_order = nullptr;
-    int* emb = nullptr;
-    double2* V = nullptr;
-    double* alpha_dev = nullptr;   // staging of host inputs
-    double* W_dev = nullptr;
-    double2* ctrl = nullptr;
-    Spline4* spl = nullptr;
-    double2* phase = nullptr;
-    double2* hist = nullptr;
-    double2* Uend = nullptr;
-    double2* Lterm = nullptr;
-    double2* Lam0 = nullptr;
-    double* term = nullptr;
-    double* gpart = nullptr;
-    int* status = nullptr;
-    double* out_dev = nullptr;     // staging of outputs: P, J, pen[M-1], galpha[d], gW[nW]
-    int* status_host = nullptr;    // pinned
-    size_t bytes = 0;
-    // profiling: CUDA events around each kernel of an evaluation
-    bool profile = false;
-    cudaEvent_t ev[MSQOC_NKERNELS][2] = {};
-    bool ran[MSQOC_NKERNELS] = {};
-};
-
-namespace {
-
-void free_problem(msqoc_problem* p) {
-    void* bufs[] = {p->P, p->fiber_order, p->emb, p->V, p->alpha_dev, p->W_dev, p->ctrl, p->spl, p->phase,
-                    p->hist, p->Uend, p->Lterm, p->Lam0, p->term, p->gpart, p->status, p->out_dev};
-    for (void* b : bufs)
-        if (b) cudaFree(b);
-    if (p->status_host) cudaFreeHost(p->status_host);
-    for (auto& e : p->ev)
-        for (auto& x : e)
-            if (x) cudaEventDestroy(x);
-}
-
-// brackets a kernel launch with profiling events when enabled
-struct Mark {
-    msqoc_problem* p;
-    int k;
-    cudaStream_t s;
-    Mark(msqoc_problem* p_, int k_, cudaStream_t s_) : p(p_), k(k_), s(s_) {
-        if (p->profile) {
-            cudaEventRecord(p->ev[k][0], s);
-            p->ran[k] = true;
-        }
-    }
-    ~Mark() {
-        if (p->profile) cudaEventRecord(p->ev[k][1], s);
-    }
-};
+bool shape_supported(int L, int q) { return (L == 3 && q >= 1 && q <= 5) || (L == 2 && q >= 1 && q <= 6); }
 
 double ladder_norm(int L) {
     // largest eigenvalue of a + a^+ on L levels (zeros of the Hermite polynomial H_L / sqrt 2)
@@ -131,49 +73,6 @@ double ladder_norm(int L) {
         case 3: return std::sqrt(3.0);
         case 4: return std::sqrt(3.0 + std::sqrt(6.0));
         default: return std::sqrt(2.0 * L);  // safe upper bound (Gershgorin)
-    }
-}
-
-// Output staging layout in out_dev (doubles): P, J, pen[M-1], grad_alpha[d], grad_W[nW].
-// grad_alpha and grad_W start at even offsets: grad_W is written as double2 (16-byte aligned).
-struct OutLayout {
-    size_t pen, ga, gw, total;
-};
-OutLayout out_layout(int M, int d, size_t nW) {
-    OutLayout o;
-    o.pen = 2;
-    o.ga = (o.pen + size_t(M - 1) + 1) & ~size_t(1);
-    o.gw = (o.ga + size_t(d) + 1) & ~size_t(1);
-    o.total = o.gw + nW + 2;
-    return o;
-}
-
-bool shape_supported(int L, int q) { return (L == 3 && q >= 1 && q <= 5) || (L == 2 && q >= 1 && q <= 6); }
-
-constexpr int kMaxRows = 243;    // largest N of a supported shape (L = 3, q = 5)
-constexpr int kMaxFibers = 81;   // largest N / L
-
-// Fibers sorted so that lanes of a warp share their neighbour-list shape: key = bitmask of the
-// fixed subsystems whose level is interior (two neighbours), ordered by popcount then mask.
-// Stable insertion sort into order[N/L] (equal keys keep ascending fiber order).
-void fiber_order_into(int L, int q, int* order) {
-    const int F = ipow_i(L, q) / L;
-    int key[kMaxFibers];
-    for (int f = 0; f < F; ++f) {
-        int mask = 0;
-        for (int k = 0; k < q - 1; ++k) {
-            const int lk = (f / ipow_i(L, q - 2 - k)) % L;
-            if (lk > 0 && lk < L - 1) mask |= 1 << k;
-        }
-        const int kf = (__builtin_popcount(mask) << 16) | mask;
-        int pos = f;
-        while (pos > 0 && key[pos - 1] > kf) {
-            key[pos] = key[pos - 1];
-            order[pos] = order[pos - 1];
-            --pos;
-        }
-        key[pos] = kf;
-        order[pos] = f;
     }
 }
 
@@ -217,24 +116,120 @@ double2 qft_entry(int E, int e, int j) {
     return make_double2(s * std::cos(ang), s * std::sin(ang));
 }
 
-int choose_col_block(int E, int F, int M, int q, int L, int N, int d, int solver, int sms) {
-    // Makespan model: a tile occupies one SM for the whole window; an SM's time grows with the
-    // warps (lanes, idle ones included) of the tiles it runs.  Tiles are spread evenly, so the
-    // busiest SM runs ceil(tiles / sms) of them.  Ties go to the larger block (fewer tiles).
+// ------------------------------------------------------------------ tile layout
+// Class of a fiber: bitmask of the fixed subsystems (all but the last) at an interior level,
+// i.e. with a neighbour on both sides.  Lanes of one class take the same branches in the apply.
+int fiber_class(int L, int q, int f) {
+    int mask = 0;
+    for (int k = 0; k < q - 1; ++k) {
+        const int lk = (f / ipow_i(L, q - 2 - k)) % L;
+        if (lk > 0 && lk < L - 1) mask |= 1 << k;
+    }
+    return mask;
+}
+// position of a mask in the reflected Gray-code sequence (neighbours differ in one bit)
+int gray_rank(int g) {
+    int r = 0;
+    for (; g; g >>= 1) r ^= g;
+    return r;
+}
+
+// Threads of a tile with ncol columns, the first ncol0 of window m0: each window's
+// (column, fiber) pairs are ordered by the Gray rank of the fiber class, so that a warp spans
+// few classes (its branch cost is the union of its lanes' branches); window m0's pairs come
+// first so at most one warp has lanes of both windows.  Idle lanes mirror the last active pair.
+// Writes out[nthreads]; no allocation.
+void build_lanemap(int L, int q, int ncol, int ncol0, int nthreads, int* out) {
+    const int F = ipow_i(L, q) / L;
+    int key[MAX_TILE_THREADS], val[MAX_TILE_THREADS];
+    int n = 0;
+    for (int part = 0; part < 2; ++part) {
+        const int first = n;
+        const int ca = part == 0 ? 0 : ncol0, cb = part == 0 ? ncol0 : ncol;
+        for (int f = 0; f < F; ++f)
+            for (int c = ca; c < cb; ++c) {
+                // stable insertion by key within this window's pairs
+                const int k = gray_rank(fiber_class(L, q, f));
+                int pos = n++;
+                while (pos > first && key[pos - 1] > k) {
+                    key[pos] = key[pos - 1];
+                    val[pos] = val[pos - 1];
+                    --pos;
+                }
+                key[pos] = k;
+                val[pos] = (c << 16) | f;
+            }
+    }
+    for (int t = 0; t < nthreads; ++t) out[t] = t < n ? val[t] : ~val[n - 1];
+}
+
+// Tile t of one problem for `cpt` columns per tile: a consecutive run of the window-major column
+// list (windows m = 1..M, columns 0..E-1 each).  cpt <= E, so a tile covers at most two windows.
+// Lane map index: ncol0 - 1 for full tiles, cpt for the (single, last) partial tile.
+Tile tile_at(long t, int M, int E, int cpt, int prob) {
+    const long total = long(M) * E, g0 = t * cpt;
+    Tile x{};
+    x.prob = prob;
+    x.ncol = static_cast<int>(std::min<long>(cpt, total - g0));
+    x.m0 = static_cast<int>(g0 / E) + 1;
+    x.c0 = static_cast<int>(g0 % E);
+    x.ncol0 = std::min(x.ncol, E - x.c0);
+    x.map = x.ncol == cpt ? x.ncol0 - 1 : cpt;
+    x.tloc = static_cast<int>(t);
+    return x;
+}
+long tile_count(int M, int E, int cpt) { return (long(M) * E + cpt - 1) / cpt; }
+
+// The cpt + 1 lane maps of a problem's tiles (out[(cpt + 1) * nthreads]); map cpt serves the
+// last tile when it is partial.
+void build_lanemaps(int L, int q, int M, int E, int cpt, int nthreads, int* out) {
+    for (int k = 0; k < cpt; ++k) build_lanemap(L, q, cpt, k + 1, nthreads, out + size_t(k) * nthreads);
+    const Tile last = tile_at(tile_count(M, E, cpt) - 1, M, E, cpt, 0);
+    build_lanemap(L, q, last.ncol, last.ncol0, nthreads, out + size_t(cpt) * nthreads);
+}
+
+int tile_threads(int cpt, int F) { return ((cpt * F + 31) / 32) * 32; }
+
+// Is `cpt` columns per tile usable?  Tiles must fit MAX_TILE_THREADS threads and the shared
+// memory; a tile that covers two windows needs two warps (one per window's coefficients), so a
+// one-warp tile must divide the window's columns.
+bool tile_width_ok(int cpt, int E, int F, int q, int L, int N, int d, int solver) {
+    if (cpt < 1 || cpt > E || cpt * F > MAX_TILE_THREADS) return false;
+    const int nthreads = tile_threads(cpt, F);
+    if (nthreads == 32 && E % cpt) return false;
+    const size_t s1 = sweep_layout(q, L, N, cpt, nthreads, d, solver, true).total;
+    const size_t s0 = sweep_layout(q, L, N, cpt, nthreads, d, solver, false).total;
+    return std::max(s0, s1) <= 200 * 1024;
+}
+
+// Columns per tile.  Makespan model, from FP64 throughput probes and sweep timings on this GPU:
+// the FP64 units belong to the SM's four sub-partitions and idle lanes cost as much as busy
+// ones; the sweeps' time follows the sub-partition with the most warps.  Candidates are ranked by
+//   1. tiles that stay inside one window (a tile over two windows pays a second gradient
+//      reduction and wider class mixing in its warps: measured slower on the 4-transmon
+//      adjoint at 64, 128 and 256 windows, although it uses more SMs);
+//   2. warps on the busiest sub-partition: ceil(ceil(tiles / SMs) * warps per tile / 4);
+//   3. the idle-lane fraction of a tile.
+int choose_tile_width(int M, int E, int F, int q, int L, int N, int d, int solver, int sms) {
     int best = -1;
-    double best_cost = 0.0;
-    for (int cb = E; cb >= 1; --cb) {
-        if (E % cb) continue;
-        if (cb * F > MAX_TILE_THREADS) continue;
-        const int nthreads = ((cb * F + 31) / 32) * 32;
-        const size_t s1 = sweep_layout(q, L, N, cb, nthreads, d, solver, true).total;
-        const size_t s0 = sweep_layout(q, L, N, cb, nthreads, d, solver, false).total;
-        if (std::max(s0, s1) > 200 * 1024) continue;
-        const long tiles = long(M) * (E / cb);
-        const double cost = double((tiles + sms - 1) / sms) * nthreads;
-        if (best < 0 || cost < best_cost * 0.999) {
-            best = cb;
-            best_cost = cost;
+    long best_a = 0;
+    int best_b = 0;
+    double best_c = 0.0;
+    for (int cpt = std::min(E, MAX_TILE_THREADS / F); cpt >= 1; --cpt) {
+        if (!tile_width_ok(cpt, E, F, q, L, N, d, solver)) continue;
+        const long tiles = (long(M) * E + cpt - 1) / cpt;
+        const int warps = tile_threads(cpt, F) / 32;
+        const long per_sm = (tiles + sms - 1) / sms;
+        const long ca = (per_sm * warps + 3) / 4;
+        const int cb = (E % cpt) ? 1 : 0;
+        const double cc = 1.0 - double(cpt * F) / (32.0 * warps);
+        const bool better =
+            best < 0 || cb < best_b || (cb == best_b && (ca < best_a || (ca == best_a && cc < best_c - 1e-9)));
+        if (better) {
+            best = cpt;
+            best_a = ca;
+            best_b = cb;
+            best_c = cc;
         }
     }
     return best;
@@ -267,7 +262,7 @@ msqoc_status check_description(const msqoc_hamiltonian* H, const msqoc_controls*
 }
 
 // Shape, time grid, model scalars and tile geometry of a validated description (every field
-// of pd except the device pointers).  col_block 0 = automatic.
+// of pd except the device pointers and the history segmentation).  col_block 0 = automatic.
 msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps,
                            int32_t nwindows, double mu, int solver, int col_block, int sms, ProbDev& pd) {
     const int q = H->nqubits, L = H->nlevels, ness = H->ness;
@@ -302,32 +297,144 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
         pd.wsq[2 * l + 0] = std::sqrt(double(l + 1));
         pd.wsq[2 * l + 1] = std::sqrt(double(l));
     }
-    int cb = col_block;
-    if (cb == 0) cb = choose_col_block(pd.E, pd.F, pd.M, q, L, pd.N, pd.d, solver, sms);
-    if (cb <= 0 || pd.E % cb || cb * pd.F > MAX_TILE_THREADS)
-        return fail(MSQOC_ERR_INVALID_ARG, "column block %d invalid for E=%d (needs cb | E, cb*N/L <= %d)", cb, pd.E,
-                    MAX_TILE_THREADS);
-    pd.cb = cb;
-    pd.nblk = pd.E / cb;
-    pd.nthreads = ((cb * pd.F + 31) / 32) * 32;
-    pd.ntiles = pd.M * pd.nblk;
-    if (std::max(sweep_layout(q, L, pd.N, cb, pd.nthreads, pd.d, solver, true).total,
-                 sweep_layout(q, L, pd.N, cb, pd.nthreads, pd.d, solver, false).total) > 227 * 1024)
-        return fail(MSQOC_ERR_INVALID_ARG, "column block %d needs too much shared memory", cb);
+    int cpt = col_block;
+    if (cpt == 0) cpt = choose_tile_width(pd.M, pd.E, pd.F, q, L, pd.N, pd.d, solver, sms);
+    if (!tile_width_ok(cpt, pd.E, pd.F, q, L, pd.N, pd.d, solver))
+        return fail(MSQOC_ERR_INVALID_ARG,
+                    "column block %d invalid for E=%d (needs 1 <= cb <= E, cb*N/L <= %d, cb | E for one-warp "
+                    "tiles, and the shared memory)",
+                    cpt, pd.E, MAX_TILE_THREADS);
+    pd.cb = cpt;
+    pd.nthreads = tile_threads(cpt, pd.F);
+    pd.ntiles = static_cast<int>((long(pd.M) * pd.E + cpt - 1) / cpt);
+    // whole windows in one history segment unless a checkpoint interval is set later
+    const int64_t max_ns = (nsteps + nwindows - 1) / nwindows;
+    pd.kseg = static_cast<int>(max_ns);
+    pd.nseg = 1;
     return MSQOC_OK;
+}
+
+// history segmentation for a checkpoint interval K (1 = keep every midpoint state)
+void set_segments(ProbDev& pd, int K) {
+    const int64_t max_ns = (pd.nsteps + pd.M - 1) / pd.M;
+    pd.kseg = (K <= 1 || K >= max_ns) ? static_cast<int>(max_ns) : K;
+    pd.nseg = static_cast<int>((max_ns + pd.kseg - 1) / pd.kseg);
+}
+
+// sweep launch arguments of a single problem
+SweepArgs sweep_args(const ProbDev& pd, const ProbDev* pds_dev, const Tile* tiles, const int* lanemap, int mode,
+                     int seg) {
+    SweepArgs a{};
+    a.pds = pds_dev;
+    a.tiles = tiles;
+    a.lanemap = lanemap;
+    a.cpt = pd.cb;
+    a.dmax = pd.d;
+    a.mode = mode;
+    a.seg = seg;
+    a.L = pd.L;
+    a.q = pd.q;
+    a.solver = pd.solver;
+    a.nthreads = pd.nthreads;
+    return a;
+}
+
+// Output staging layout in out_dev (doubles): P, J, pen[M-1], grad_alpha[d], grad_W[nW].
+// grad_alpha and grad_W start at even offsets: grad_W is written as double2 (16-byte aligned).
+struct OutLayout {
+    size_t pen, ga, gw, total;
+};
+OutLayout out_layout(int M, int d, size_t nW) {
+    OutLayout o;
+    o.pen = 2;
+    o.ga = (o.pen + size_t(M - 1) + 1) & ~size_t(1);
+    o.gw = (o.ga + size_t(d) + 1) & ~size_t(1);
+    o.total = o.gw + nW + 2;
+    return o;
 }
 
 }  // namespace
 
-namespace msqoc {
-size_t sweep_smem_bytes(const ProbDev& pd, bool bwd) {
-    return sweep_layout(pd.q, pd.L, pd.N, pd.cb, pd.nthreads, pd.d, pd.solver, bwd).total;
+struct msqoc_problem {
+    ProbDev pd{};
+    int device = 0;
+    int ckpt_interval = 1;   // K (1 = every midpoint state kept)
+    size_t nW = 0;           // doubles in W
+    size_t ne = 0;           // N*E
+    // owned device buffers
+    ProbDev* pds = nullptr;        // device copy of pd (read by the sweeps)
+    Tile* tiles = nullptr;
+    int* lanemap = nullptr;
+    double2* P = nullptr;
+    int* emb = nullptr;
+    double2* V = nullptr;
+    double* alpha_dev = nullptr;   // the evaluation's inputs (copied from the caller's arrays)
+    double* W_dev = nullptr;
+    double2* ctrl = nullptr;
+    Spline4* spl = nullptr;
+    double2* phase = nullptr;
+    double2* hist = nullptr;       // allocated by the first gradient evaluation
+    double2* ckpt = nullptr;       // (with hist, when K > 1)
+    double2* Lstate = nullptr;     // (with hist, when K > 1)
+    double2* Uend = nullptr;
+    double2* Lterm = nullptr;
+    double2* Lam0 = nullptr;
+    double* term = nullptr;
+    double* gpart = nullptr;
+    int* status = nullptr;
+    double* out_dev = nullptr;     // staging of outputs: P, J, pen[M-1], galpha[d], gW[nW]
+    int* status_host = nullptr;    // pinned
+    size_t bytes = 0;              // device bytes held now
+    size_t grad_bytes = 0;         // bytes the first gradient evaluation adds
+    // profiling: CUDA events around each kernel of an evaluation
+    bool profile = false;
+    cudaEvent_t ev[MSQOC_NKERNELS][2] = {};
+    bool ran[MSQOC_NKERNELS] = {};
+};
+
+namespace {
+
+void free_problem(msqoc_problem* p) {
+    void* bufs[] = {p->pds,   p->tiles, p->lanemap, p->P,     p->emb,   p->V,     p->alpha_dev, p->W_dev,
+                    p->ctrl,  p->spl,   p->phase,   p->hist,  p->ckpt,  p->Lstate, p->Uend,     p->Lterm,
+                    p->Lam0,  p->term,  p->gpart,   p->status, p->out_dev};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (p->status_host) cudaFreeHost(p->status_host);
+    for (auto& e : p->ev)
+        for (auto& x : e)
+            if (x) cudaEventDestroy(x);
 }
-}  // namespace msqoc
+
+// brackets a stretch of launches with profiling events when enabled
+struct Mark {
+    msqoc_problem* p;
+    int k;
+    cudaStream_t s;
+    Mark(msqoc_problem* p_, int k_, cudaStream_t s_) : p(p_), k(k_), s(s_) {
+        if (p->profile) {
+            cudaEventRecord(p->ev[k][0], s);
+            p->ran[k] = true;
+        }
+    }
+    ~Mark() {
+        if (p->profile) cudaEventRecord(p->ev[k][1], s);
+    }
+};
+
+// device bytes of the history, checkpoints and segment state of one problem
+size_t gradient_bytes(const ProbDev& pd) {
+    const size_t ne = size_t(pd.N) * pd.E;
+    size_t b = size_t(pd.M) * pd.kseg * ne * sizeof(double2);
+    if (pd.nseg > 1) b += (size_t(pd.M) * pd.nseg * ne + size_t(pd.M) * ne) * sizeof(double2);
+    return b;
+}
+
+}  // namespace
 
 extern "C" {
 
-int32_t msqoc_version(void) { return 100; }
+int32_t msqoc_version(void) { return 200; }
 
 int32_t msqoc_last_error(char* buf, size_t len) {
     if (buf && len) {
@@ -349,8 +456,7 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
     msqoc_options o{};
     if (opt) o = *opt;
     const int solver = o.solver == MSQOC_SOLVER_FP64 ? SOLVER_FP64 : SOLVER_MIXED;
-    if (o.ckpt_interval != 0 && o.ckpt_interval != 1)
-        return fail(MSQOC_ERR_UNSUPPORTED, "checkpoint interval %d not implemented (use 1)", o.ckpt_interval);
+    if (o.ckpt_interval < 0) return fail(MSQOC_ERR_INVALID_ARG, "checkpoint interval %d < 0", o.ckpt_interval);
     if (o.profile != 0 && o.profile != 1) return fail(MSQOC_ERR_INVALID_ARG, "profile must be 0 or 1");
 
     auto* p = new (std::nothrow) msqoc_problem();
@@ -366,8 +472,19 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
         return st0;
     }
     const int q = pd.q, L = pd.L, nfsum = pd.nfsum;
+    // checkpoint interval: 0 = automatic (every midpoint state unless that history would take
+    // more than a quarter of the device memory, else every 64 steps)
+    int K = o.ckpt_interval;
+    if (K == 0) {
+        size_t freeb = 0, totalb = 0;
+        cudaMemGetInfo(&freeb, &totalb);
+        set_segments(pd, 1);
+        K = (totalb && gradient_bytes(pd) > totalb / 4) ? 64 : 1;
+    }
+    p->ckpt_interval = K;
+    set_segments(pd, K);
 
-    // ---- host-side model tables
+    // ---- host-side model tables and tile layout
     const int N = pd.N, E = pd.E;
     p->ne = size_t(N) * E;
     p->nW = 2 * p->ne * size_t(pd.M - 1);
@@ -382,8 +499,10 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
         for (int j = 0; j < E; ++j)
             for (int e = 0; e < E; ++e) Vh[size_t(j) * N + emb[e]] = qft_entry(E, e, j);
     }
-    std::vector<int> order(pd.F);
-    fiber_order_into(L, q, order.data());
+    std::vector<Tile> tiles(pd.ntiles);
+    for (int t = 0; t < pd.ntiles; ++t) tiles[t] = tile_at(t, pd.M, E, pd.cb, 0);
+    std::vector<int> maps(size_t(pd.cb + 1) * pd.nthreads);
+    build_lanemaps(L, q, pd.M, E, pd.cb, pd.nthreads, maps.data());
 
     // ---- device buffers
     const size_t M = pd.M;
@@ -393,8 +512,10 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
             st = fail(e == cudaErrorMemoryAllocation ? MSQOC_ERR_OUT_OF_MEMORY : MSQOC_ERR_CUDA,
                       "allocating %s: %s", what, cudaGetErrorString(e));
     };
+    A(dalloc(&p->pds, 1), "problem record");
+    A(dalloc(&p->tiles, tiles.size()), "tiles");
+    A(dalloc(&p->lanemap, maps.size()), "lane maps");
     A(dalloc(&p->P, N), "P");
-    A(dalloc(&p->fiber_order, pd.F), "fiber order");
     A(dalloc(&p->emb, E), "embedding");
     A(dalloc(&p->V, p->ne), "target");
     A(dalloc(&p->alpha_dev, pd.d), "alpha");
@@ -415,33 +536,38 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
         for (auto& e : p->ev)
             for (auto& x : e) A(cudaEventCreate(&x), "profiling event");
     if (st == MSQOC_OK) {
+        pd.P = p->P;
+        pd.emb = p->emb;
+        pd.V = p->V;
+        pd.alpha = p->alpha_dev;
+        pd.W = reinterpret_cast<const double2*>(p->W_dev);
+        pd.ctrl = p->ctrl;
+        pd.spl = p->spl;
+        pd.phase = p->phase;
+        pd.Uend = p->Uend;
+        pd.Lterm = p->Lterm;
+        pd.Lam0 = p->Lam0;
+        pd.term = p->term;
+        pd.gpart = p->gpart;
+        pd.status = p->status;
+        A(cudaMemcpy(p->tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice), "tiles copy");
+        A(cudaMemcpy(p->lanemap, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice), "lane map copy");
         A(cudaMemcpy(p->P, P.data(), N * sizeof(double2), cudaMemcpyHostToDevice), "P copy");
-        A(cudaMemcpy(p->fiber_order, order.data(), pd.F * sizeof(int), cudaMemcpyHostToDevice), "order copy");
         A(cudaMemcpy(p->emb, emb.data(), E * sizeof(int), cudaMemcpyHostToDevice), "emb copy");
         A(cudaMemcpy(p->V, Vh.data(), p->ne * sizeof(double2), cudaMemcpyHostToDevice), "target copy");
+        A(cudaMemset(p->W_dev, 0, std::max<size_t>(p->nW, 2) * sizeof(double)), "W init");
         A(cudaMemset(p->status, 0, sizeof(int)), "status init");
+        A(cudaMemcpy(p->pds, &pd, sizeof(ProbDev), cudaMemcpyHostToDevice), "problem record copy");
     }
     if (st != MSQOC_OK) {
         free_problem(p);
         delete p;
         return st;
     }
-    pd.P = p->P;
-    pd.fiber_order = p->fiber_order;
-    pd.emb = p->emb;
-    pd.V = p->V;
-    pd.ctrl = p->ctrl;
-    pd.spl = p->spl;
-    pd.phase = p->phase;
-    pd.Uend = p->Uend;
-    pd.Lterm = p->Lterm;
-    pd.Lam0 = p->Lam0;
-    pd.term = p->term;
-    pd.gpart = p->gpart;
-    pd.status = p->status;
     p->bytes = sizeof(double2) * (N + p->ne * (1 + 3 * M) + size_t(nsteps) * (q + nfsum)) +
                sizeof(Spline4) * size_t(nsteps) + sizeof(double) * (pd.d + p->nW + M + size_t(pd.ntiles) * pd.d) +
-               sizeof(int) * (pd.F + E + 1);
+               sizeof(int) * (E + 1 + maps.size()) + sizeof(Tile) * tiles.size() + sizeof(ProbDev);
+    p->grad_bytes = gradient_bytes(pd);
     *out = p;
     return MSQOC_OK;
 }
@@ -450,8 +576,7 @@ msqoc_status msqoc_query(const msqoc_problem* p, int64_t* d, int64_t* nW, size_t
     if (!p) return fail(MSQOC_ERR_INVALID_ARG, "problem is NULL");
     if (d) *d = p->pd.d;
     if (nW) *nW = static_cast<int64_t>(p->nW);
-    if (device_bytes)
-        *device_bytes = p->bytes + size_t(p->pd.nsteps) * p->ne * sizeof(double2);  // + history
+    if (device_bytes) *device_bytes = p->bytes + (p->hist ? 0 : p->grad_bytes);
     return MSQOC_OK;
 }
 
@@ -467,31 +592,48 @@ msqoc_status msqoc_destroy_problem(msqoc_problem* p) {
 
 namespace {
 
-// stage the inputs on the device (copies host arrays; device arrays are used in place)
+// copy the evaluation's inputs into the problem's input buffers (stream-ordered)
 msqoc_status stage_inputs(msqoc_problem* p, const double* alpha, const double* W, cudaStream_t s) {
     if (!alpha) return fail(MSQOC_ERR_INVALID_ARG, "alpha is NULL");
     if (p->pd.M > 1 && !W) return fail(MSQOC_ERR_INVALID_ARG, "W is NULL but M > 1");
-    if (is_device_ptr(alpha)) {
-        p->pd.alpha = alpha;
-    } else {
-        CUDA_TRY(cudaMemcpyAsync(p->alpha_dev, alpha, p->pd.d * sizeof(double), cudaMemcpyHostToDevice, s));
-        p->pd.alpha = p->alpha_dev;
-    }
-    if (p->pd.M > 1) {
-        if (is_device_ptr(W)) {
-            if (reinterpret_cast<uintptr_t>(W) % 16) return fail(MSQOC_ERR_INVALID_ARG, "device W must be 16-byte aligned");
-            p->pd.W = reinterpret_cast<const double2*>(W);
-        } else {
-            CUDA_TRY(cudaMemcpyAsync(p->W_dev, W, p->nW * sizeof(double), cudaMemcpyHostToDevice, s));
-            p->pd.W = reinterpret_cast<const double2*>(p->W_dev);
-        }
-    } else {
-        p->pd.W = reinterpret_cast<const double2*>(p->W_dev);
-    }
+    CUDA_TRY(cudaMemcpyAsync(p->alpha_dev, alpha, p->pd.d * sizeof(double), cudaMemcpyDefault, s));
+    if (p->pd.M > 1) CUDA_TRY(cudaMemcpyAsync(p->W_dev, W, p->nW * sizeof(double), cudaMemcpyDefault, s));
     return MSQOC_OK;
 }
 
-msqoc_status launch_forward_part(msqoc_problem* p, bool want_hist, cudaStream_t s) {
+// the history, checkpoints and segment state, on the first gradient evaluation
+msqoc_status ensure_gradient_buffers(msqoc_problem* p, cudaStream_t s) {
+    if (p->hist) return MSQOC_OK;
+    ProbDev& pd = p->pd;
+    const size_t M = pd.M;
+    cudaError_t e = dalloc(&p->hist, M * pd.kseg * p->ne);
+    if (e == cudaSuccess && pd.nseg > 1) e = dalloc(&p->ckpt, M * pd.nseg * p->ne);
+    if (e == cudaSuccess && pd.nseg > 1) e = dalloc(&p->Lstate, M * p->ne);
+    if (e != cudaSuccess) {
+        for (void* b : {static_cast<void*>(p->hist), static_cast<void*>(p->ckpt), static_cast<void*>(p->Lstate)})
+            if (b) cudaFree(b);
+        p->hist = p->ckpt = p->Lstate = nullptr;
+        cudaGetLastError();
+        return fail(MSQOC_ERR_OUT_OF_MEMORY, "history buffers (%zu bytes, checkpoint interval %d): %s", p->grad_bytes,
+                    p->ckpt_interval, cudaGetErrorString(e));
+    }
+    pd.hist = p->hist;
+    pd.ckpt = p->ckpt;
+    pd.Lstate = p->Lstate;
+    p->bytes += p->grad_bytes;
+    // a pageable host-to-device copy has consumed its source when the call returns
+    CUDA_TRY(cudaMemcpyAsync(p->pds, &pd, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
+    return MSQOC_OK;
+}
+
+msqoc_status sweep(msqoc_problem* p, int mode, int seg, cudaStream_t s) {
+    const SweepArgs a = sweep_args(p->pd, p->pds, p->tiles, p->lanemap, mode, seg);
+    CUDA_TRY(launch_sweep(a, p->pd.ntiles, s));
+    return MSQOC_OK;
+}
+
+// controls, forward sweep over whole windows, terminal conditions
+msqoc_status launch_forward_part(msqoc_problem* p, int mode, cudaStream_t s) {
     ProbDev& pd = p->pd;
     for (bool& r : p->ran) r = false;
     {
@@ -503,14 +645,22 @@ msqoc_status launch_forward_part(msqoc_problem* p, bool want_hist, cudaStream_t 
     }
     {
         Mark mk(p, MSQOC_KERNEL_FORWARD, s);
-        CUDA_TRY(launch_sweep(pd, false, want_hist, s));
+        const msqoc_status st = sweep(p, mode, 0, s);
+        if (st) return st;
     }
     {
         Mark mk(p, MSQOC_KERNEL_TERMINAL, s);
-        k_terminal<<<pd.M, TERM_THREADS, 0, s>>>(pd, want_hist ? 1 : 0);
+        k_terminal<<<pd.M, TERM_THREADS, 0, s>>>(pd, mode == SWEEP_OBJECTIVE ? 0 : 1);
         CUDA_TRY(cudaGetLastError());
     }
     return MSQOC_OK;
+}
+
+msqoc_status status_error(int st) {
+    if (st & ST_TIMEOUT) return fail(MSQOC_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", st);
+    if (st & ST_SOLVER_RANGE)
+        return fail(MSQOC_ERR_UNSUPPORTED, "time step too large for the step solver (h*|H_c|/2 >= 0.5)");
+    return fail(MSQOC_ERR_INTERNAL, "device status %d", st);
 }
 
 msqoc_status check_status_sync(msqoc_problem* p, cudaStream_t s) {
@@ -519,10 +669,7 @@ msqoc_status check_status_sync(msqoc_problem* p, cudaStream_t s) {
     const int st = *p->status_host;
     if (st) {
         cudaMemsetAsync(p->status, 0, sizeof(int), s);
-        if (st & ST_TIMEOUT) return fail(MSQOC_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", st);
-        if (st & ST_SOLVER_RANGE)
-            return fail(MSQOC_ERR_UNSUPPORTED, "time step too large for the step solver (h*|H_c|/2 >= 0.5)");
-        return fail(MSQOC_ERR_INTERNAL, "device status %d", st);
+        return status_error(st);
     }
     return MSQOC_OK;
 }
@@ -538,14 +685,14 @@ msqoc_status msqoc_eval_objective(msqoc_problem* p, const double* alpha, const d
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     msqoc_status st = stage_inputs(p, alpha, W, s);
     if (st) return st;
-    st = launch_forward_part(p, false, s);
+    st = launch_forward_part(p, SWEEP_OBJECTIVE, s);
     if (st) return st;
     const ProbDev& pd = p->pd;
     const bool dP = is_device_ptr(P_out), dJ = !J_out || is_device_ptr(J_out), dpen = !pen_out || is_device_ptr(pen_out);
     double* o = p->out_dev;
     {
         Mark mk(p, MSQOC_KERNEL_FINALIZE, s);
-            k_finalize_scalars<<<1, 32, 0, s>>>(pd, dP ? P_out : o, J_out ? (dJ ? J_out : o + 1) : nullptr,
+        k_finalize_scalars<<<1, 32, 0, s>>>(pd, dP ? P_out : o, J_out ? (dJ ? J_out : o + 1) : nullptr,
                                            pen_out && pd.M > 1 ? (dpen ? pen_out : o + 2) : nullptr, nullptr);
         CUDA_TRY(cudaGetLastError());
     }
@@ -564,24 +711,25 @@ msqoc_status msqoc_eval_gradient(msqoc_problem* p, const double* alpha, const do
     if (!grad_alpha) return fail(MSQOC_ERR_INVALID_ARG, "grad_alpha is NULL");
     if (p->pd.M > 1 && !grad_W) return fail(MSQOC_ERR_INVALID_ARG, "grad_W is NULL but M > 1");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (!p->hist) {
-        const size_t n = size_t(p->pd.nsteps) * p->ne;
-        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->hist), n * sizeof(double2));
-        if (e != cudaSuccess) {
-            p->hist = nullptr;
-            return fail(MSQOC_ERR_OUT_OF_MEMORY, "history buffer (%zu bytes): %s", n * sizeof(double2),
-                        cudaGetErrorString(e));
-        }
-        p->pd.hist = p->hist;
-    }
-    msqoc_status st = stage_inputs(p, alpha, W, s);
+    msqoc_status st = ensure_gradient_buffers(p, s);
     if (st) return st;
-    st = launch_forward_part(p, true, s);
+    st = stage_inputs(p, alpha, W, s);
     if (st) return st;
     const ProbDev& pd = p->pd;
+    // one history segment: every midpoint state in the forward sweep; otherwise checkpoints
+    // at the segment starts, and each segment is recomputed before its adjoint sweep
+    st = launch_forward_part(p, pd.nseg == 1 ? SWEEP_HISTORY : SWEEP_CKPT, s);
+    if (st) return st;
     {
         Mark mk(p, MSQOC_KERNEL_ADJOINT, s);
-        CUDA_TRY(launch_sweep(pd, true, false, s));
+        for (int seg = pd.nseg - 1; seg >= 0; --seg) {
+            if (pd.nseg > 1) {
+                st = sweep(p, SWEEP_RECOMPUTE, seg, s);
+                if (st) return st;
+            }
+            st = sweep(p, SWEEP_ADJOINT, seg, s);
+            if (st) return st;
+        }
     }
     const bool dP = !P_out || is_device_ptr(P_out), dga = is_device_ptr(grad_alpha),
                dgw = pd.M == 1 || is_device_ptr(grad_W);
@@ -610,9 +758,7 @@ msqoc_status msqoc_eval_gradient(msqoc_problem* p, const double* alpha, const do
     return check_status_sync(p, s);
 }
 
-}  // extern "C"
-
-extern "C" msqoc_status msqoc_kernel_times(msqoc_problem* p, float* ms) {
+msqoc_status msqoc_kernel_times(msqoc_problem* p, float* ms) {
     if (!p || !ms) return fail(MSQOC_ERR_INVALID_ARG, "problem or ms is NULL");
     if (!p->profile) return fail(MSQOC_ERR_INVALID_ARG, "problem was created without options.profile = 1");
     for (int k = 0; k < MSQOC_NKERNELS; ++k) {
@@ -624,6 +770,7 @@ extern "C" msqoc_status msqoc_kernel_times(msqoc_problem* p, float* ms) {
     return MSQOC_OK;
 }
 
+}  // extern "C"
 // ------------------------------------------------------------------ objective without allocation
 // Scratch of msqoc_eval_objective_noalloc: every table and intermediate of one objective
 // evaluation, carved into 256-byte-aligned regions.  Static device storage: the module holds
@@ -692,12 +839,14 @@ extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H,
     // ---- scratch layout; the limit depends on the problem's size only
     const size_t N = pd.N, E = pd.E, ne = N * E, M = pd.M, nt = size_t(nsteps);
     const size_t nW = 2 * ne * (M - 1);
+    const size_t nmap = size_t(pd.cb + 1) * pd.nthreads;
     Carve cv;
     const size_t o_status = cv.take<int>(1), o_term = cv.take<double>(M), o_out = cv.take<double>(M + 1),
-                 o_P = cv.take<double2>(N), o_order = cv.take<int>(pd.F), o_emb = cv.take<int>(E),
-                 o_V = cv.take<double2>(ne), o_alpha = cv.take<double>(pd.d), o_W = cv.take<double>(nW),
-                 o_ctrl = cv.take<double2>(nt * pd.q), o_spl = cv.take<Spline4>(nt),
-                 o_phase = cv.take<double2>(nt * pd.nfsum), o_Uend = cv.take<double2>(M * ne);
+                 o_pd = cv.take<ProbDev>(1), o_tiles = cv.take<Tile>(pd.ntiles), o_map = cv.take<int>(nmap),
+                 o_P = cv.take<double2>(N), o_emb = cv.take<int>(E), o_V = cv.take<double2>(ne),
+                 o_alpha = cv.take<double>(pd.d), o_W = cv.take<double>(nW), o_ctrl = cv.take<double2>(nt * pd.q),
+                 o_spl = cv.take<Spline4>(nt), o_phase = cv.take<double2>(nt * pd.nfsum),
+                 o_Uend = cv.take<double2>(M * ne);
     if (cv.off > MSQOC_NOALLOC_SCRATCH_BYTES)
         return fail(MSQOC_ERR_INVALID_ARG,
                     "problem needs %zu bytes of scratch; the allocation-free objective holds at most %zu "
@@ -710,11 +859,12 @@ extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H,
     pd.status = reinterpret_cast<int*>(base + o_status);
     pd.term = reinterpret_cast<double*>(base + o_term);
     double2* Pd = reinterpret_cast<double2*>(base + o_P);
-    int* order_d = reinterpret_cast<int*>(base + o_order);
     int* emb_d = reinterpret_cast<int*>(base + o_emb);
     double2* V_d = reinterpret_cast<double2*>(base + o_V);
+    ProbDev* pd_d = reinterpret_cast<ProbDev*>(base + o_pd);
+    Tile* tiles_d = reinterpret_cast<Tile*>(base + o_tiles);
+    int* map_d = reinterpret_cast<int*>(base + o_map);
     pd.P = Pd;
-    pd.fiber_order = order_d;
     pd.emb = emb_d;
     pd.V = V_d;
     pd.ctrl = reinterpret_cast<double2*>(base + o_ctrl);
@@ -723,29 +873,6 @@ extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H,
     pd.Uend = reinterpret_cast<double2*>(base + o_Uend);
     double* outs = reinterpret_cast<double*>(base + o_out);   // P, J, pen[M-1]
 
-    // ---- model tables, built in small host buffers and copied in (a pageable host-to-device
-    // copy has consumed its source when cudaMemcpyAsync returns, so the buffers are reused)
-    CUDA_TRY(cudaMemsetAsync(pd.status, 0, sizeof(int), s));
-    {
-        double2 rows[kMaxRows];
-        for (size_t i = 0; i < N; ++i) rows[i] = precond_entry(pd.h, drift_entry(H, pd.q, pd.L, int(i)));
-        CUDA_TRY(cudaMemcpyAsync(Pd, rows, N * sizeof(double2), cudaMemcpyHostToDevice, s));
-        int order[kMaxFibers];
-        fiber_order_into(pd.L, pd.q, order);
-        CUDA_TRY(cudaMemcpyAsync(order_d, order, pd.F * sizeof(int), cudaMemcpyHostToDevice, s));
-        int emb[kMaxRows];
-        for (size_t e = 0; e < E; ++e) emb[e] = essential_row(pd.q, pd.L, pd.ness, int(e));
-        CUDA_TRY(cudaMemcpyAsync(emb_d, emb, E * sizeof(int), cudaMemcpyHostToDevice, s));
-        if (target) {
-            CUDA_TRY(cudaMemcpyAsync(V_d, target, ne * sizeof(double2), cudaMemcpyDefault, s));
-        } else {
-            for (size_t j = 0; j < E; ++j) {   // QFT_E on the essential rows, one column at a time
-                for (size_t i = 0; i < N; ++i) rows[i] = make_double2(0.0, 0.0);
-                for (size_t e = 0; e < E; ++e) rows[emb[e]] = qft_entry(int(E), int(e), int(j));
-                CUDA_TRY(cudaMemcpyAsync(V_d + j * N, rows, N * sizeof(double2), cudaMemcpyHostToDevice, s));
-            }
-        }
-    }
     // ---- inputs: device arrays in place, host arrays copied into the scratch
     if (is_device_ptr(alpha)) {
         pd.alpha = alpha;
@@ -763,6 +890,42 @@ extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H,
         }
     }
 
+    // ---- model tables, tiles and lane maps, built in small host buffers and copied in (a
+    // pageable host-to-device copy has consumed its source when cudaMemcpyAsync returns, so the
+    // buffers are reused)
+    CUDA_TRY(cudaMemsetAsync(pd.status, 0, sizeof(int), s));
+    CUDA_TRY(cudaMemcpyAsync(pd_d, &pd, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
+    {
+        double2 rows[kMaxRows];
+        for (size_t i = 0; i < N; ++i) rows[i] = precond_entry(pd.h, drift_entry(H, pd.q, pd.L, int(i)));
+        CUDA_TRY(cudaMemcpyAsync(Pd, rows, N * sizeof(double2), cudaMemcpyHostToDevice, s));
+        int emb[kMaxRows];
+        for (size_t e = 0; e < E; ++e) emb[e] = essential_row(pd.q, pd.L, pd.ness, int(e));
+        CUDA_TRY(cudaMemcpyAsync(emb_d, emb, E * sizeof(int), cudaMemcpyHostToDevice, s));
+        if (target) {
+            CUDA_TRY(cudaMemcpyAsync(V_d, target, ne * sizeof(double2), cudaMemcpyDefault, s));
+        } else {
+            for (size_t j = 0; j < E; ++j) {   // QFT_E on the essential rows, one column at a time
+                for (size_t i = 0; i < N; ++i) rows[i] = make_double2(0.0, 0.0);
+                for (size_t e = 0; e < E; ++e) rows[emb[e]] = qft_entry(int(E), int(e), int(j));
+                CUDA_TRY(cudaMemcpyAsync(V_d + j * N, rows, N * sizeof(double2), cudaMemcpyHostToDevice, s));
+            }
+        }
+        Tile chunk[128];
+        for (long t0 = 0; t0 < pd.ntiles; t0 += 128) {
+            const long n = std::min<long>(128, pd.ntiles - t0);
+            for (long t = 0; t < n; ++t) chunk[t] = tile_at(t0 + t, pd.M, pd.E, pd.cb, 0);
+            CUDA_TRY(cudaMemcpyAsync(tiles_d + t0, chunk, n * sizeof(Tile), cudaMemcpyHostToDevice, s));
+        }
+        int map[MAX_TILE_THREADS];
+        const Tile last = tile_at(pd.ntiles - 1, pd.M, pd.E, pd.cb, 0);
+        for (int k = 0; k <= pd.cb; ++k) {
+            build_lanemap(pd.L, pd.q, k < pd.cb ? pd.cb : last.ncol, k < pd.cb ? k + 1 : last.ncol0, pd.nthreads, map);
+            CUDA_TRY(cudaMemcpyAsync(map_d + size_t(k) * pd.nthreads, map, pd.nthreads * sizeof(int),
+                                     cudaMemcpyHostToDevice, s));
+        }
+    }
+
     // ---- the objective's kernels (controls, forward sweep, terminal terms, reduction)
     {
         const int threads = 256;
@@ -770,7 +933,7 @@ extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H,
         k_controls<<<blocks, threads, 0, s>>>(pd);
         CUDA_TRY(cudaGetLastError());
     }
-    CUDA_TRY(launch_sweep(pd, false, false, s));
+    CUDA_TRY(launch_sweep(sweep_args(pd, pd_d, tiles_d, map_d, SWEEP_OBJECTIVE, 0), pd.ntiles, s));
     k_terminal<<<pd.M, TERM_THREADS, 0, s>>>(pd, 0);
     CUDA_TRY(cudaGetLastError());
     k_finalize_scalars<<<1, 32, 0, s>>>(pd, outs, outs + 1, M > 1 ? outs + 2 : nullptr, nullptr);
@@ -783,9 +946,6 @@ extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H,
     int status_word = 0;
     CUDA_TRY(cudaMemcpyAsync(&status_word, pd.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    if (status_word & ST_TIMEOUT) return fail(MSQOC_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", status_word);
-    if (status_word & ST_SOLVER_RANGE)
-        return fail(MSQOC_ERR_UNSUPPORTED, "time step too large for the step solver (h*|H_c|/2 >= 0.5)");
-    if (status_word) return fail(MSQOC_ERR_INTERNAL, "device status %d", status_word);
+    if (status_word) return status_error(status_word);
     return MSQOC_OK;
 }

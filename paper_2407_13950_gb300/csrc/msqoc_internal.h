@@ -24,15 +24,18 @@ struct __align__(16) Spline4 {
     double w0, w1, w2;
 };
 
-// Everything a kernel needs about one problem and one evaluation.  Passed by value.
+// Everything a kernel needs about one problem.  The small kernels take it by value; the sweep
+// kernels read it from a device copy (several problems share a batched sweep launch).
 struct ProbDev {
     // shape
     int q, L, N, E, F, ness, d1, M, nfsum, d;
-    int cb;        // columns per tile
-    int nblk;      // E / cb
+    int cb;        // columns of a full tile
     int nthreads;  // threads per tile (multiple of 32)
-    int ntiles;    // M * nblk
+    int ntiles;    // tiles of the problem's sweeps
     int solver;
+    int kseg;      // steps per history segment (checkpoint interval; >= the longest window when
+                   // every midpoint state is kept)
+    int nseg;      // segments per window: ceil(longest window / kseg)
     int64_t nsteps;
     double T, h, mu, dtau;
     double lam;    // ||a + a^+|| on L levels (bound of the ladder-term norm per unit |d|)
@@ -43,7 +46,6 @@ struct ProbDev {
     double wsq[2 * MAXL];        // sqrt(l+1) [dir +] and sqrt(l) [dir -]: product weights
     // constant tables
     const double2* P;            // [N] (1 + i h/2 D_i)^-1
-    const int* fiber_order;      // [F] fibers sorted by neighbour class
     const int* emb;              // [E] full row index of essential column e
     const double2* V;            // [E][N] target
     // inputs of this evaluation (device memory)
@@ -53,19 +55,54 @@ struct ProbDev {
     double2* ctrl;               // [nsteps][q] d_k(t_{n+1/2})
     Spline4* spl;                // [nsteps] (first spline index, solver counts, w0, w1, w2)
     double2* phase;              // [nsteps][nfsum] exp(i Omega t_{n+1/2})
-    double2* hist;               // [nsteps][nblk][cb][N] midpoint states Ubar_n
+    double2* hist;               // [M][kseg][E][N] midpoint states Ubar of one segment of every window
+    double2* ckpt;               // [M][nseg][E][N] states at the segment starts (kseg < longest window)
     double2* Uend;               // [M][E][N] U^m(t_m)
     double2* Lterm;              // [M][E][N] Lambda^m(t_m)
     double2* Lam0;               // [M][E][N] Lambda^m(t_{m-1})
+    double2* Lstate;             // [M][E][N] adjoint state between segments
     double* term;                // [M] pen_m (m < M), J (m = M)
     double* gpart;               // [ntiles][d] per-tile alpha-gradient partials
     int* status;                 // status word (ST_* bits)
 };
 
-// shared-memory bytes of a sweep launch
-size_t sweep_smem_bytes(const ProbDev& pd, bool bwd);
+// One sweep tile (one CTA): `ncol` consecutive columns of problem `prob` in window-major column
+// order, starting at column c0 of window m0 (1-based).  The first `ncol0` columns belong to
+// window m0, the rest to window m0 + 1 (a tile covers at most two windows).  `map` selects the
+// thread -> (column, fiber) assignment in the launch's lane maps; `tloc` is the tile's index
+// among its problem's tiles (row of the problem's gradient partials).
+struct Tile {
+    int prob, m0, c0, ncol, ncol0, map, tloc, pad;
+};
 
-// launchers (defined per subsystem count in inst_q*.cu); return cudaError_t
-cudaError_t launch_sweep(const ProbDev& pd, bool bwd, bool want_hist, cudaStream_t s);
+// What a sweep launch does.
+enum SweepMode {
+    SWEEP_OBJECTIVE = 0,  // forward over whole windows; end states U^m(t_m)
+    SWEEP_HISTORY = 1,    // forward over whole windows; also every midpoint state (one segment)
+    SWEEP_CKPT = 2,       // forward over whole windows; also the states at segment starts
+    SWEEP_RECOMPUTE = 3,  // forward over segment `seg` from its checkpoint; midpoint states
+    SWEEP_ADJOINT = 4     // adjoint over segment `seg` with the fused gradient quadrature
+};
+
+// Arguments of one sweep launch (uniform over its tiles; problems share shape and solver).
+struct SweepArgs {
+    const ProbDev* pds;   // [problems] device copies
+    const Tile* tiles;    // [tiles] one per CTA
+    const int* lanemap;   // [maps][threads]: (column << 16 | fiber), ~value for idle lanes
+    int cpt;              // columns of the widest tile (shared-memory sizing)
+    int dmax;             // largest d over the problems
+    int mode;             // SweepMode
+    int seg;              // segment (SWEEP_RECOMPUTE, SWEEP_ADJOINT)
+    int L, q, solver, nthreads;
+};
+
+// shared-memory bytes of a sweep launch
+size_t sweep_smem_bytes(const SweepArgs& a);
+
+// launcher (dispatches on L, q, solver, direction); returns cudaError_t
+cudaError_t launch_sweep(const SweepArgs& a, int ntiles, cudaStream_t s);
+
+// resident CTAs per SM of a sweep kernel at this launch shape (0 on error)
+int sweep_ctas_per_sm(const SweepArgs& a);
 
 }  // namespace msqoc

@@ -272,27 +272,29 @@ __device__ __forceinline__ void apply_off(const T2* __restrict__ buf, const T2* 
 }
 
 // ------------------------------------------------------------------ shared memory layout
+// Per-slot arrays are sized for the two windows a tile can cover.
 struct SweepSmem {
     size_t coef_d, coef_f, params, mbar, red, zy, galpha, D0, D1, FA, FB, H, UB0, UB1, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cb, int nthreads, int d, int solver,
+__host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cpt, int nthreads, int dmax, int solver,
                                                   bool bwd) {
     SweepSmem s{};
     const int nslot = q * L * 2;
     const int nwarps = nthreads / 32;
-    const int V = next_pow2_c(4 * q);
-    const size_t buf_d = size_t(cb) * N * 16, buf_f = size_t(cb) * N * 8;
+    int V = 1;
+    while (V < 4 * q) V <<= 1;
+    const size_t buf_d = size_t(cpt) * N * 16, buf_f = size_t(cpt) * N * 8;
     size_t o = 0;
-    s.coef_d = o; o = align16(o + 2 * nslot * 16);
-    s.coef_f = o; o = align16(o + 2 * nslot * 8);
-    s.params = o; o = align16(o + 2 * 4 * 4);
+    s.coef_d = o; o = align16(o + 2 * 2 * nslot * 16);                 // [parity][slot][NSLOT]
+    s.coef_f = o; o = align16(o + 2 * 2 * nslot * 8);
+    s.params = o; o = align16(o + 2 * 2 * 4 * 4);                      // [parity][slot][4]
     s.mbar = o;   o = align16(o + 2 * 8);
-    s.red = o;    o = align16(o + (bwd ? size_t(2) * nwarps * V * 8 : 0));
-    s.zy = o;     o = align16(o + (bwd ? size_t(2) * 4 * q * 8 : 0));
-    s.galpha = o; o = align16(o + (bwd ? size_t(d) * 8 : 0));
+    s.red = o;    o = align16(o + (bwd ? size_t(2) * 2 * nwarps * V * 8 : 0));   // [parity][slot][warp][V]
+    s.zy = o;     o = align16(o + (bwd ? size_t(2) * 2 * 4 * q * 8 : 0));        // [parity][slot][4q]
+    s.galpha = o; o = align16(o + (bwd ? size_t(2) * dmax * 8 : 0));             // [slot][d]
     s.D0 = o;     o = align16(o + buf_d);
     s.D1 = o;     o = align16(o + (solver == SOLVER_FP64 ? buf_d : 0));
     s.FA = o;     o = align16(o + (solver == SOLVER_MIXED ? buf_f : 0));
@@ -343,18 +345,55 @@ __device__ __forceinline__ int tile_sync_or(int p) {
     return __syncthreads_or(p);
 }
 
+
+// first global step of window m (1-based); window m owns [win_start(m), win_start(m + 1))
+__device__ __forceinline__ int64_t win_start(const ProbDev& pd, int m) {
+    return (static_cast<int64_t>(m - 1) * pd.nsteps) / pd.M;
+}
+
+// warp reduce-scatter of V values: lane ends with value (lane >> (5 - NH)) summed over the warp
+template <int V, int NH>
+__device__ __forceinline__ double warp_reduce_scatter(double (&acc)[V], int lane) {
+    int cnt = V;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if (cnt > 1) {
+            const int half = cnt >> 1;
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int q2 = 0; q2 < V / 2; ++q2) {
+                if (q2 < half) {
+                    const double send = upper ? acc[q2] : acc[q2 + half];
+                    const double keep = upper ? acc[q2 + half] : acc[q2];
+                    acc[q2] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            cnt = half;
+        } else {
+            acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+        }
+    }
+    return acc[0];
+}
+
 // ------------------------------------------------------------------ the sweep kernel
+// One CTA per tile.  A tile covers one or two windows ("slots"); each slot has its own step
+// range, per-step coefficients, iteration counts and gradient fold, computed by warp `slot`
+// (the host only builds two-slot tiles with at least two warps).  Loops run to the longer of
+// the slots' ranges; a thread whose slot has no step at an iteration keeps its state.
 template <int L, int Q, int SOLVER, bool BWD>
-__global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const ProbDev pd, const int want_hist) {
+__global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a) {
     constexpr int N = ipow_c(L, Q);
-    constexpr int F = N / L;
     constexpr int NSLOT = Q * L * 2;
     constexpr int S = BWD ? +1 : -1;       // sign of the preconditioned off-diagonal term
     constexpr int V = next_pow2_c(4 * Q);  // padded count of reduced gradient values
     constexpr int NH = log2_c(V);          // halving levels of the warp reduce-scatter
 
+    const Tile tile = a.tiles[blockIdx.x];
+    const ProbDev& pd = a.pds[tile.prob];
+
     extern __shared__ __align__(128) unsigned char smem[];
-    const SweepSmem lay = sweep_layout(Q, L, N, pd.cb, pd.nthreads, pd.d, SOLVER, BWD);
+    const SweepSmem lay = sweep_layout(Q, L, N, a.cpt, blockDim.x, a.dmax, SOLVER, BWD);
     double2* coef_d = reinterpret_cast<double2*>(smem + lay.coef_d);
     float2* coef_f = reinterpret_cast<float2*>(smem + lay.coef_f);
     int* params = reinterpret_cast<int*>(smem + lay.params);
@@ -374,21 +413,45 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const ProbDev pd,
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int cb = pd.cb;
-    const int tile = blockIdx.x;
-    const int m = tile / pd.nblk + 1;               // window, 1-based
-    const int blk = tile % pd.nblk;
-    const int64_t n0 = ((int64_t)(m - 1) * pd.nsteps) / pd.M;
-    const int64_t n1 = ((int64_t)m * pd.nsteps) / pd.M;
-    const int ns = static_cast<int>(n1 - n0);
-    const int nact = cb * F;
-    const bool act = tid < nact;
-    const int tt = act ? tid : nact - 1;            // inactive lanes mirror a valid fiber, store nothing
-    const int c = tt % cb;
-    const int f = pd.fiber_order[tt / cb];
-    const int col = blk * cb + c;
-    const size_t blk_elems = size_t(cb) * N;
-    const uint32_t blk_bytes = static_cast<uint32_t>(blk_elems * sizeof(double2));
+    const int E = pd.E;
+    const int ncol = tile.ncol, ncol0 = tile.ncol0;
+    const int nslot = ncol0 < ncol ? 2 : 1;
+    const bool segmented = a.mode == SWEEP_RECOMPUTE || a.mode == SWEEP_ADJOINT;
+
+    // ---- the slots' windows and step ranges (local step indices [lo, lo + cnt) of the window)
+    const int64_t wn0_0 = win_start(pd, tile.m0);
+    const int wns_0 = static_cast<int>(win_start(pd, tile.m0 + 1) - wn0_0);
+    const int64_t wn0_1 = nslot > 1 ? win_start(pd, tile.m0 + 1) : 0;
+    const int wns_1 = nslot > 1 ? static_cast<int>(win_start(pd, tile.m0 + 2) - wn0_1) : 0;
+    const int lo_0 = segmented ? a.seg * pd.kseg : 0;
+    const int lo_1 = lo_0;
+    const int cnt_0 = max(0, (segmented ? min(wns_0, lo_0 + pd.kseg) : wns_0) - lo_0);
+    const int cnt_1 = nslot > 1 ? max(0, (segmented ? min(wns_1, lo_1 + pd.kseg) : wns_1) - lo_1) : 0;
+    const int nit = max(cnt_0, cnt_1);
+    // global step of slot s at iteration jj, clamped into the slot's range (a slot without steps
+    // in this launch maps to its window's first step, which exists)
+    auto step_of = [&](int s, int jj) -> int64_t {
+        const int cnt = s ? cnt_1 : cnt_0;
+        const int lo = s ? lo_1 : lo_0;
+        const int64_t n0 = s ? wn0_1 : wn0_0;
+        if (cnt <= 0) return n0;
+        const int jc = min(jj, cnt - 1);
+        return BWD ? n0 + lo + cnt - 1 - jc : n0 + lo + jc;
+    };
+
+    // ---- this thread's fiber
+    const int lm = a.lanemap[tile.map * static_cast<int>(blockDim.x) + tid];
+    const bool act = lm >= 0;                       // idle lanes mirror an active one, store nothing
+    const int lmv = act ? lm : ~lm;
+    const int c = lmv >> 16;                        // tile column
+    const int f = lmv & 0xffff;                     // fiber
+    const int slot = c < ncol0 ? 0 : 1;
+    const int m = tile.m0 + slot;                   // window, 1-based
+    const int col = slot == 0 ? tile.c0 + c : c - ncol0;
+    const int my_cnt = slot ? cnt_1 : cnt_0;
+    const int my_lo = slot ? lo_1 : lo_0;
+    const int my_ns = slot ? wns_1 : wns_0;
+    const size_t wcol = (size_t(m - 1) * E + col) * N;   // (window, column) in [M][E][N] arrays
 
     Fiber<L, Q> fb;
     fb.init(c, f, pd);
@@ -404,77 +467,146 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const ProbDev pd,
         Pf[l] = f32_of(p);
     }
 
-    // initial state: forward U^m(t_{m-1}) = W^{m-1} (identity embedding for m = 1);
-    // adjoint Lambda^m(t_m) from the terminal kernel
+    // ---- initial state
+    //   forward, whole window : U^m(t_{m-1}) = W^{m-1} (identity embedding for m = 1)
+    //   forward, recompute    : the segment's checkpoint
+    //   adjoint               : Lambda^m(t_m) for the window's last segment, else the state the
+    //                           previous (later) segment left
     double2 u[L];
 #pragma unroll
     for (int l = 0; l < L; ++l) {
         const int i = f * L + l;
-        if (BWD) {
-            u[l] = pd.Lterm[(size_t(m - 1) * pd.E + col) * N + i];
+        if (my_cnt == 0) {
+            u[l] = make_double2(0.0, 0.0);
+        } else if (BWD) {
+            u[l] = (my_lo + my_cnt == my_ns) ? pd.Lterm[wcol + i] : pd.Lstate[wcol + i];
+        } else if (a.mode == SWEEP_RECOMPUTE) {
+            u[l] = pd.ckpt[((size_t(m - 1) * pd.nseg + a.seg) * E + col) * N + i];
         } else if (m == 1) {
             u[l] = make_double2(pd.emb[col] == i ? 1.0 : 0.0, 0.0);
         } else {
-            u[l] = pd.W[(size_t(m - 2) * pd.E + col) * N + i];
+            u[l] = pd.W[(size_t(m - 2) * E + col) * N + i];
         }
     }
 
+    // ---- history blocks: slot s of a tile covers a contiguous column range of its window
+    const bool want_hist = !BWD && (a.mode == SWEEP_HISTORY || a.mode == SWEEP_RECOMPUTE);
+    const uint32_t bytes_0 = static_cast<uint32_t>(size_t(ncol0) * N * sizeof(double2));
+    const uint32_t bytes_1 = static_cast<uint32_t>(size_t(ncol - ncol0) * N * sizeof(double2));
+    auto hist_ptr = [&](int s, int jj) -> double2* {
+        const int64_t n0 = s ? wn0_1 : wn0_0;
+        const int lo = s ? lo_1 : lo_0;
+        const int jr = static_cast<int>(step_of(s, jj) - n0) - lo;   // step within the segment
+        return pd.hist + ((size_t(tile.m0 + s - 1) * pd.kseg + jr) * E + (s ? 0 : tile.c0)) * N;
+    };
+    // forward (thread 0): store the staged midpoints of iteration jj of every slot that had a step
+    auto publish = [&](int jj) {
+        if (jj < cnt_0) bulk_s2g(hist_ptr(0, jj), H, bytes_0);
+        if (jj < cnt_1) bulk_s2g(hist_ptr(1, jj), H + size_t(ncol0) * N, bytes_1);
+    };
+    // adjoint (thread 0): fetch the midpoints of iteration jj into dst, completing on bar
+    auto fetch = [&](double2* dst, int jj, uint64_t* bar) {
+        const uint32_t b0 = jj < cnt_0 ? bytes_0 : 0u, b1 = jj < cnt_1 ? bytes_1 : 0u;
+        mbar_expect_tx(bar, b0 + b1);
+        if (b0) bulk_g2s(dst, hist_ptr(0, jj), b0, bar);
+        if (b1) bulk_g2s(dst + size_t(ncol0) * N, hist_ptr(1, jj), b1, bar);
+    };
+
     if (BWD) {
-        for (int j = tid; j < pd.d; j += blockDim.x) galpha[j] = 0.0;
+        for (int j = tid; j < 2 * a.dmax; j += blockDim.x) galpha[j] = 0.0;
         if (tid == 0) {
             mbar_init(&mbar[0], 1);
             mbar_init(&mbar[1], 1);
             fence_mbar_init();
         }
         tile_sync();
-        if (tid == 0 && ns > 0) {
-            const int64_t n = n0 + ns - 1;
-            mbar_expect_tx(&mbar[0], blk_bytes);
-            bulk_g2s(UB0, pd.hist + (size_t(n) * pd.nblk + blk) * blk_elems, blk_bytes, &mbar[0]);
-        }
+        if (tid == 0 && nit > 0) fetch(UB0, 0, &mbar[0]);
     }
 
-    // warp 0 keeps d_k of the next step in registers (lane -> subsystem of its slot)
+    // warp s < nslot computes slot s's coefficients and folds its gradient; it keeps d_k and
+    // the iteration counts of the slot's next step in registers (lane -> subsystem of its slot)
+    const bool coef_warp = warp < nslot;
+    const int cslot = coef_warp ? warp : 0;
     const int my_k = (lane < NSLOT) ? (lane / (2 * L)) : 0;
     double2 dk_next = make_double2(0.0, 0.0);
     int cnt_next = 0;
-    auto load_ctrl = [&](int64_t n) {
-        if (warp == 0) {
+    auto load_ctrl = [&](int jj) {
+        if (coef_warp) {
+            const int64_t n = step_of(cslot, jj);
             dk_next = lane < NSLOT ? pd.ctrl[size_t(n) * pd.q + my_k] : make_double2(0.0, 0.0);
             cnt_next = pd.spl[n].cnt;
         }
     };
-    // warp 0 lanes that scatter gradient entries: (k, f, j) with 3 active splines per carrier
+    // gradient entries of a step: (carrier, spline of the 3 active) pairs, one per lane
     const int nscat = pd.nfsum * 3;
+    // warps whose lanes belong to both slots reduce each slot separately
+    const unsigned mask1 = __ballot_sync(0xffffffffu, act && slot == 1);
+    const unsigned mask0 = __ballot_sync(0xffffffffu, act && slot == 0);
+
+    // fold slot s's reduced products of step np (parity pp of the reduction buffers) into the
+    // slot's alpha-gradient: dP/dalpha1_kfs += -2h B_s Im(e^{iWt} z_k + e^{-iWt} y_k),
+    // dP/dalpha2_kfs += -2h B_s Re(e^{iWt} z_k - e^{-iWt} y_k)  (Eq. grad-int at the midpoint)
+    auto fold = [&](int s, int pp, int64_t np, const Spline4& sp, double2 ph_lane, bool prefetched) {
+        if (lane < 4 * Q) {
+            double sum = 0.0;
+            for (int w2 = 0; w2 < nwarps; ++w2) sum += red[((pp * 2 + s) * nwarps + w2) * V + lane];
+            zy[(pp * 2 + s) * 4 * Q + lane] = sum;
+        }
+        __syncwarp();
+        const int s0 = sp.s;
+        double* ga = galpha + size_t(s) * a.dmax;
+        for (int i = lane; i < nscat; i += 32) {
+            const int kf = i / 3, jw = i % 3;
+            int k = 0;
+            while (k + 1 < Q && pd.cof[k + 1] <= kf) ++k;
+            const double* zyk = zy + (pp * 2 + s) * 4 * Q + 4 * k;
+            const double2 zk = make_double2(zyk[0], zyk[1]);
+            const double2 yk = make_double2(zyk[2], zyk[3]);
+            const double2 ph = (prefetched && i == lane) ? ph_lane : pd.phase[size_t(np) * pd.nfsum + kf];
+            const double wgt = -2.0 * pd.h * (jw == 0 ? sp.w0 : (jw == 1 ? sp.w1 : sp.w2));
+            const double A = zk.y + yk.y, B = zk.x - yk.x;
+            const int idx = (kf * pd.d1 + s0 + jw) * 2;
+            ga[idx + 0] += wgt * fma(ph.x, A, ph.y * B);
+            ga[idx + 1] += wgt * fma(ph.x, B, -ph.y * A);
+        }
+    };
 
     bool timed_out = false;
     int fsel = 0;
     double2* Dc = D0;   // FP64-solver ping-pong buffers
     double2* Dn = D1;
-    load_ctrl(BWD ? n0 + ns - 1 : n0);
+    if (nit > 0) load_ctrl(0);
 
-    for (int jj = 0; jj < ns; ++jj) {
-        const int j = BWD ? ns - 1 - jj : jj;      // local step index
-        const int64_t n = n0 + j;                  // global step index
+    for (int jj = 0; jj < nit; ++jj) {
         const int par = jj & 1;
-        double2* cfd = coef_d + par * NSLOT;
-        float2* cff = coef_f + par * NSLOT;
-        int* prm = params + par * 4;
-
-        if (warp == 0) {
+        const bool live = jj < my_cnt;
+        if (coef_warp) {
             const double2 dk = dk_next;
             const int cnt = cnt_next;
-            if (jj + 1 < ns) load_ctrl(BWD ? n - 1 : n + 1);
-            step_coefficients<L, Q>(pd, lane, dk, cnt, cfd, cff, prm);
+            if (jj + 1 < nit) load_ctrl(jj + 1);
+            step_coefficients<L, Q>(pd, lane, dk, cnt, coef_d + (par * 2 + cslot) * NSLOT,
+                                    coef_f + (par * 2 + cslot) * NSLOT, params + (par * 2 + cslot) * 4);
         }
-        // adjoint: warp 0 fetches what the gradient fold of the previous step (n + 1) needs
-        // now, so the loads are in flight during the solve
+        // adjoint: the folding warps fetch what the fold of iteration jj - 1 needs now, so the
+        // loads are in flight during the solve
         Spline4 sp_prev{};
         double2 ph_prev = make_double2(0.0, 0.0);
-        if (BWD && jj > 0 && warp == 0) {
-            sp_prev = pd.spl[n + 1];
-            if (lane < nscat) ph_prev = pd.phase[size_t(n + 1) * pd.nfsum + lane / 3];
+        if (BWD && jj > 0 && coef_warp && jj - 1 < (cslot ? cnt_1 : cnt_0)) {
+            const int64_t np = step_of(cslot, jj - 1);
+            sp_prev = pd.spl[np];
+            if (lane < nscat) ph_prev = pd.phase[size_t(np) * pd.nfsum + lane / 3];
         }
+        // checkpoint: the state at the start of every segment (forward over whole windows)
+        if (!BWD && a.mode == SWEEP_CKPT && live && act && jj % pd.kseg == 0) {
+            double2* ck = pd.ckpt + ((size_t(m - 1) * pd.nseg + jj / pd.kseg) * E + col) * N + f * L;
+#pragma unroll
+            for (int l = 0; l < L; ++l) ck[l] = u[l];
+        }
+        const double2* cfd = coef_d + (par * 2 + slot) * NSLOT;
+        const float2* cff = coef_f + (par * 2 + slot) * NSLOT;
+        const int* prm = params + (par * 2 + slot) * 4;          // this thread's slot
+        const int* prm0 = params + (par * 2) * 4;
+        const int* prm1 = params + (par * 2 + 1) * 4;
 
         // right-hand side of the preconditioned step equation: b = P u (conj(P) for the adjoint)
         double2 b[L];
@@ -482,6 +614,19 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const ProbDev pd,
         for (int l = 0; l < L; ++l) b[l] = cmul(Pd[l], u[l]);
 
         double2 z[L];   // the midpoint state being solved for (Ubar or Lbar)
+
+        // first barrier of the step: the coefficients are published; thread 0 stores the
+        // previous iteration's midpoints (forward) or fetches the next iteration's (adjoint)
+        auto first_sync_work = [&]() {
+            if (!BWD && want_hist && tid == 0 && jj > 0) {
+                fence_proxy_async_smem();
+                publish(jj - 1);
+            }
+            if (BWD && tid == 0 && jj + 1 < nit) {
+                const int nx = (jj + 1) & 1;
+                fetch(nx ? UB1 : UB0, jj + 1, &mbar[nx]);
+            }
+        };
 
         if constexpr (SOLVER == SOLVER_FP64) {
             // Dc/Dn alternate on every write (persisting across steps): a buffer is never
@@ -493,19 +638,10 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const ProbDev pd,
                 for (int l = 0; l < L; ++l) Dc[fb.xo + l] = z[l];
             }
             tile_sync();
-            // first sync of the step: publish the previous step's history block / issue prefetch
-            if (!BWD && want_hist && tid == 0 && jj > 0) {
-                fence_proxy_async_smem();
-                bulk_s2g(pd.hist + (size_t(n - 1) * pd.nblk + blk) * blk_elems, H, blk_bytes);
-            }
-            if (BWD && tid == 0 && jj + 1 < ns) {
-                const int nx = (jj + 1) & 1;
-                mbar_expect_tx(&mbar[nx], blk_bytes);
-                bulk_g2s(nx ? UB1 : UB0, pd.hist + (size_t(n - 1) * pd.nblk + blk) * blk_elems, blk_bytes,
-                         &mbar[nx]);
-            }
-            const int K = prm[0];
-            for (int it = 0; it < K; ++it) {
+            first_sync_work();
+            const int Kown = prm[0];
+            const int Kmax = nslot > 1 ? max(prm0[0], prm1[0]) : prm0[0];
+            for (int it = 0; it < Kmax; ++it) {
                 if (it > 0) {
                     if (act) {
 #pragma unroll
@@ -515,13 +651,14 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const ProbDev pd,
                 }
                 double2 w[L];
                 apply_off<L, Q, double2>(Dc, cfd, fb, z, w);
+                if (it < Kown) {
 #pragma unroll
-                for (int l = 0; l < L; ++l) z[l] = cadd_scaled<S>(b[l], Pd[l], w[l]);
+                    for (int l = 0; l < L; ++l) z[l] = cadd_scaled<S>(b[l], Pd[l], w[l]);
+                }
                 double2* tmp = Dc;
                 Dc = Dn;
                 Dn = tmp;
             }
-            (void)Dn;
         } else {
             // ---- FP32 stage: d = Ubar - b from the preconditioned fixed point d = s P w(b + d)
             float2 bf[L], df[L], y[L];
@@ -538,23 +675,17 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const ProbDev pd,
                     for (int l = 0; l < L; ++l) Fb[fb.xo + l] = y[l];
                 }
                 tile_sync();
-                if (!BWD && want_hist && tid == 0 && jj > 0) {
-                    fence_proxy_async_smem();
-                    bulk_s2g(pd.hist + (size_t(n - 1) * pd.nblk + blk) * blk_elems, H, blk_bytes);
-                }
-                if (BWD && tid == 0 && jj + 1 < ns) {
-                    const int nx = (jj + 1) & 1;
-                    mbar_expect_tx(&mbar[nx], blk_bytes);
-                    bulk_g2s(nx ? UB1 : UB0, pd.hist + (size_t(n - 1) * pd.nblk + blk) * blk_elems, blk_bytes,
-                             &mbar[nx]);
-                }
+                first_sync_work();
                 float2 w[L];
                 apply_off<L, Q, float2>(Fb, cff, fb, y, w);
 #pragma unroll
                 for (int l = 0; l < L; ++l) df[l] = cadd_scaled<S>(make_float2(0.f, 0.f), Pf[l], w[l]);
             }
             const int j1 = prm[0], j2 = prm[1], R = prm[2];
-            for (int it = 1; it < j1; ++it) {
+            const int j1max = nslot > 1 ? max(prm0[0], prm1[0]) : prm0[0];
+            const int j2max = nslot > 1 ? max(prm0[1], prm1[1]) : prm0[1];
+            const int Rmax = nslot > 1 ? max(prm0[2], prm1[2]) : prm0[2];
+            for (int it = 1; it < j1max; ++it) {
 #pragma unroll
                 for (int l = 0; l < L; ++l) y[l] = make_float2(bf[l].x + df[l].x, bf[l].y + df[l].y);
                 float2* Fb = fsel ? FB : FA;
@@ -566,8 +697,10 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const ProbDev pd,
                 tile_sync();
                 float2 w[L];
                 apply_off<L, Q, float2>(Fb, cff, fb, y, w);
+                if (it < j1) {
 #pragma unroll
-                for (int l = 0; l < L; ++l) df[l] = cadd_scaled<S>(make_float2(0.f, 0.f), Pf[l], w[l]);
+                    for (int l = 0; l < L; ++l) df[l] = cadd_scaled<S>(make_float2(0.f, 0.f), Pf[l], w[l]);
+                }
             }
             // ---- FP64 refinement: z = b + d, residual r = (b - z) + s P w(z), correction in FP32.
             // dacc accumulates z - b (= d, then d + e, ...); b - z = -dacc up to the rounding of z.
@@ -592,7 +725,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const ProbDev pd,
                     rf[l] = f32_of(r);
                     e[l] = rf[l];
                 }
-                for (int it = 0; it < j2; ++it) {
+                for (int it = 0; it < j2max; ++it) {
                     float2* Fb = fsel ? FB : FA;
                     fsel ^= 1;
                     if (act) {
@@ -602,44 +735,50 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const ProbDev pd,
                     tile_sync();
                     float2 wf[L];
                     apply_off<L, Q, float2>(Fb, cff, fb, e, wf);
+                    if (it < j2) {
 #pragma unroll
-                    for (int l = 0; l < L; ++l) e[l] = cadd_scaled<S>(rf[l], Pf[l], wf[l]);
+                        for (int l = 0; l < L; ++l) e[l] = cadd_scaled<S>(rf[l], Pf[l], wf[l]);
+                    }
                 }
                 double2 ed[L];
 #pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    ed[l] = f64_of(e[l]);
-                    z[l] = make_double2(z[l].x + ed[l].x, z[l].y + ed[l].y);
+                for (int l = 0; l < L; ++l) ed[l] = f64_of(e[l]);
+                if (pass < R) {
+#pragma unroll
+                    for (int l = 0; l < L; ++l) z[l] = make_double2(z[l].x + ed[l].x, z[l].y + ed[l].y);
                 }
-                if (pass + 1 >= R) break;
+                if (pass + 1 >= Rmax) break;
                 // another pass: dacc accumulates the correction; it rewrites D0, so every thread
                 // must be done reading it
+                if (pass + 1 < R) {
 #pragma unroll
-                for (int l = 0; l < L; ++l) dacc[l] = make_double2(dacc[l].x + ed[l].x, dacc[l].y + ed[l].y);
+                    for (int l = 0; l < L; ++l) dacc[l] = make_double2(dacc[l].x + ed[l].x, dacc[l].y + ed[l].y);
+                }
                 tile_sync();
             }
         }
 
-        if (tid == 0 && prm[3]) atomicOr(pd.status, ST_SOLVER_RANGE);
+        if (tid == 0 && (prm0[3] || (nslot > 1 && prm1[3]))) atomicOr(pd.status, ST_SOLVER_RANGE);
 
         if constexpr (!BWD) {
-            // ---- history of midpoint states for the adjoint sweep (async bulk store)
+            // ---- midpoint states for the adjoint sweep (async bulk store at the next step)
             if (want_hist) {
                 if (tid == 0) bulk_wait_read_all();
                 tile_sync();
-                if (act) {
+                if (act && live) {
 #pragma unroll
                     for (int l = 0; l < L; ++l) H[fb.xo + l] = z[l];
                 }
                 fence_proxy_async_smem();
             }
+            if (live) {
 #pragma unroll
-            for (int l = 0; l < L; ++l) u[l] = reflect(z[l], u[l]);
+                for (int l = 0; l < L; ++l) u[l] = reflect(z[l], u[l]);
+            }
         } else {
             // ---- gradient quadrature on the midpoints (fused): needs Ubar_n of the tile
-            const int slot = jj & 1;
-            double2* UB = slot ? UB1 : UB0;
-            const bool ok = mbar_wait(&mbar[slot], (jj >> 1) & 1);
+            double2* UB = par ? UB1 : UB0;
+            const bool ok = mbar_wait(&mbar[par], (jj >> 1) & 1);
             if (tile_sync_or(!ok)) {
                 timed_out = true;
                 break;
@@ -702,115 +841,88 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const ProbDev pd,
                     acc[4 * k + 3] = fb.w2[k] * p2.y;
                 }
             }
-            if (!act) {
+            if (!act || !live) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc[v] = 0.0;
             }
-            // warp reduce-scatter: lane ends with value (lane >> (5 - NH)) summed over the warp
+            // per-slot warp sums: lane (lane >> (5 - NH)) == v holds value v
             {
-                int cnt = V;
+                const int vi = lane >> (5 - NH);
+                const bool writer = (lane & ((1 << (5 - NH)) - 1)) == 0;
+                double* r0 = red + ((par * 2 + 0) * nwarps + warp) * V;
+                double* r1 = red + ((par * 2 + 1) * nwarps + warp) * V;
+                if (mask0 && mask1) {
+                    // lanes of both windows: reduce the window-1 lanes on a copy first
+                    double t[V];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    if (cnt > 1) {
-                        const int half = cnt >> 1;
-                        const bool upper = (lane & o) != 0;
+                    for (int v = 0; v < V; ++v) t[v] = slot == 1 ? acc[v] : 0.0;
+                    const double s1 = warp_reduce_scatter<V, NH>(t, lane);
 #pragma unroll
-                        for (int q2 = 0; q2 < V / 2; ++q2) {
-                            if (q2 < half) {
-                                const double send = upper ? acc[q2] : acc[q2 + half];
-                                const double keep = upper ? acc[q2 + half] : acc[q2];
-                                acc[q2] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-                            }
-                        }
-                        cnt = half;
-                    } else {
-                        acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+                    for (int v = 0; v < V; ++v) acc[v] = slot == 0 ? acc[v] : 0.0;
+                    const double s0 = warp_reduce_scatter<V, NH>(acc, lane);
+                    if (writer) {
+                        r0[vi] = s0;
+                        r1[vi] = s1;
+                    }
+                } else {
+                    const double sv = warp_reduce_scatter<V, NH>(acc, lane);
+                    if (writer) {
+                        r0[vi] = mask1 ? 0.0 : sv;
+                        if (nslot > 1) r1[vi] = mask1 ? sv : 0.0;
                     }
                 }
-                const int vi = lane >> (5 - NH);
-                if ((lane & ((1 << (5 - NH)) - 1)) == 0) red[(par * nwarps + warp) * V + vi] = acc[0];
             }
             // Lambda_n = 2 Lbar - Lambda_{n+1}
+            if (live) {
 #pragma unroll
-            for (int l = 0; l < L; ++l) u[l] = reflect(z[l], u[l]);
+                for (int l = 0; l < L; ++l) u[l] = reflect(z[l], u[l]);
+            }
         }
 
-        // warp 0 folds the previous step's reduced products into the alpha-gradient
-        if (BWD && jj > 0 && warp == 0) {
-            // (the sync that published red[par ^ 1] was this step's first sync)
-            const int pp = par ^ 1;
-            const int64_t np = n + 1;   // global step of the previous iteration
-            if (lane < 4 * Q) {
-                double s = 0.0;
-                for (int w2 = 0; w2 < nwarps; ++w2) s += red[(pp * nwarps + w2) * V + lane];
-                zy[pp * 4 * Q + lane] = s;
-            }
-            __syncwarp();
-            const Spline4 sp = sp_prev;
-            const int s0 = sp.s;
-            for (int i = lane; i < nscat; i += 32) {
-                const int kf = i / 3, jw = i % 3;
-                int k = 0;
-                while (k + 1 < Q && pd.cof[k + 1] <= kf) ++k;
-                const double2 zk = make_double2(zy[pp * 4 * Q + 4 * k + 0], zy[pp * 4 * Q + 4 * k + 1]);
-                const double2 yk = make_double2(zy[pp * 4 * Q + 4 * k + 2], zy[pp * 4 * Q + 4 * k + 3]);
-                const double2 ph = i == lane ? ph_prev : pd.phase[size_t(np) * pd.nfsum + kf];
-                const double wgt = -2.0 * pd.h * (jw == 0 ? sp.w0 : (jw == 1 ? sp.w1 : sp.w2));
-                const double A = zk.y + yk.y, B = zk.x - yk.x;
-                const int idx = (kf * pd.d1 + s0 + jw) * 2;
-                galpha[idx + 0] += wgt * fma(ph.x, A, ph.y * B);
-                galpha[idx + 1] += wgt * fma(ph.x, B, -ph.y * A);
-            }
-        }
+        // the folding warps add iteration jj - 1's reduced products into the alpha-gradient
+        // (the barrier that published red[par ^ 1] was this iteration's first one)
+        if (BWD && jj > 0 && coef_warp && jj - 1 < (cslot ? cnt_1 : cnt_0))
+            fold(cslot, par ^ 1, step_of(cslot, jj - 1), sp_prev, ph_prev, true);
     }
 
     if (!timed_out) {
         tile_sync();
-        if (!BWD) {
-            if (want_hist && tid == 0 && ns > 0) {
+        if constexpr (!BWD) {
+            if (want_hist && tid == 0 && nit > 0) {
                 fence_proxy_async_smem();
-                bulk_s2g(pd.hist + (size_t(n0 + ns - 1) * pd.nblk + blk) * blk_elems, H, blk_bytes);
+                publish(nit - 1);
                 bulk_wait_all();
             }
-            if (act) {
+            if (a.mode != SWEEP_RECOMPUTE && act && my_cnt > 0) {
 #pragma unroll
-                for (int l = 0; l < L; ++l) pd.Uend[(size_t(m - 1) * pd.E + col) * N + f * L + l] = u[l];
+                for (int l = 0; l < L; ++l) pd.Uend[wcol + f * L + l] = u[l];
             }
         } else {
-            if (warp == 0 && ns > 0) {
-                const int pp = (ns - 1) & 1;
-                const int64_t np = n0;
-                if (lane < 4 * Q) {
-                    double s = 0.0;
-                    for (int w2 = 0; w2 < nwarps; ++w2) s += red[(pp * nwarps + w2) * V + lane];
-                    zy[pp * 4 * Q + lane] = s;
-                }
-                __syncwarp();
-                const Spline4 sp = pd.spl[np];
-                const int s0 = sp.s;
-                for (int i = lane; i < nscat; i += 32) {
-                    const int kf = i / 3, jw = i % 3;
-                    int k = 0;
-                    while (k + 1 < Q && pd.cof[k + 1] <= kf) ++k;
-                    const double2 zk = make_double2(zy[pp * 4 * Q + 4 * k + 0], zy[pp * 4 * Q + 4 * k + 1]);
-                    const double2 yk = make_double2(zy[pp * 4 * Q + 4 * k + 2], zy[pp * 4 * Q + 4 * k + 3]);
-                    const double2 ph = pd.phase[size_t(np) * pd.nfsum + kf];
-                    const double wgt = -2.0 * pd.h * (jw == 0 ? sp.w0 : (jw == 1 ? sp.w1 : sp.w2));
-                    const double A = zk.y + yk.y, B = zk.x - yk.x;
-                    const int idx = (kf * pd.d1 + s0 + jw) * 2;
-                    galpha[idx + 0] += wgt * fma(ph.x, A, ph.y * B);
-                    galpha[idx + 1] += wgt * fma(ph.x, B, -ph.y * A);
-                }
+            // the last fold of every slot whose range ends at the last iteration
+            if (coef_warp && nit > 0 && (cslot ? cnt_1 : cnt_0) == nit) {
+                const int64_t np = step_of(cslot, nit - 1);
+                fold(cslot, (nit - 1) & 1, np, pd.spl[np], make_double2(0.0, 0.0), false);
             }
             tile_sync();
-            for (int jx = tid; jx < pd.d; jx += blockDim.x) pd.gpart[size_t(tile) * pd.d + jx] = galpha[jx];
-            if (act) {
+            // the tile's alpha-gradient partial, accumulated over the segment launches (the first
+            // adjoint launch is the last segment's)
+            double* gp = pd.gpart + size_t(tile.tloc) * pd.d;
+            const bool first_launch = a.seg == pd.nseg - 1;
+            for (int jx = tid; jx < pd.d; jx += blockDim.x) {
+                const double v = galpha[jx] + galpha[a.dmax + jx];
+                gp[jx] = first_launch ? v : gp[jx] + v;
+            }
+            // Lambda at the segment start: Lambda^m(t_{m-1}) for the window's first segment
+            if (act && my_cnt > 0) {
+                double2* dst = my_lo == 0 ? pd.Lam0 : pd.Lstate;
 #pragma unroll
-                for (int l = 0; l < L; ++l) pd.Lam0[(size_t(m - 1) * pd.E + col) * N + f * L + l] = u[l];
+                for (int l = 0; l < L; ++l) dst[wcol + f * L + l] = u[l];
             }
         }
     } else if (tid == 0) {
         atomicOr(pd.status, ST_TIMEOUT);
+        // let the bulk copies this tile issued land before its shared memory is released
+        for (int p2 = 0; p2 < 2; ++p2) (void)mbar_wait(&mbar[p2], 0), (void)mbar_wait(&mbar[p2], 1);
     }
 }
 

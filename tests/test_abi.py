@@ -77,8 +77,8 @@ def test_validation_rejects_malformed_descriptions_without_a_gpu():
     assert _create(H, C, T=-1.0)[0] == -1
     assert _create(H, C, nsteps=10, M=11)[0] == -1  # more windows than steps
     assert _create(H, C, M=0)[0] == -1
-    opt = msqoc.Options(0, 0, 7)
-    assert _create(H, C, opt=opt)[0] == -6     # checkpoint interval not implemented
+    opt = msqoc.Options(0, 0, -1)
+    assert _create(H, C, opt=opt)[0] == -1     # negative checkpoint interval
     assert "checkpoint" in msqoc.last_error()
     lib = msqoc.load()
     assert lib.msqoc_create_problem(None, None, None, 1.0, 1, 1, 0.0, None, None) == -1

@@ -20,16 +20,16 @@ pytestmark = pytest.mark.gpu
 SOLVERS = {"mixed": msqoc.SOLVER_MIXED, "fp64": msqoc.SOLVER_FP64}
 
 
-def run_both(spec, alpha, W, solver, col_block=0, grad=True):
+def run_both(spec, alpha, W, solver, col_block=0, grad=True, ckpt_interval=0):
     want = oracle.evaluate(spec, alpha, W, grad=grad)
-    with msqoc.Problem(spec, solver=solver, col_block=col_block) as p:
+    with msqoc.Problem(spec, solver=solver, col_block=col_block, ckpt_interval=ckpt_interval) as p:
         got = p.eval_gradient(alpha, W) if grad else p.eval_objective(alpha, W)
         obj = p.eval_objective(alpha, W)
     return got, obj, want
 
 
-def check(spec, alpha, W, solver, col_block=0):
-    got, obj, want = run_both(spec, alpha, W, solver, col_block)
+def check(spec, alpha, W, solver, col_block=0, ckpt_interval=0):
+    got, obj, want = run_both(spec, alpha, W, solver, col_block, ckpt_interval=ckpt_interval)
     assert_objective_close(got["P"], want["P"])
     assert_objective_close(obj["P"], want["P"])
     if spec.M > 1:
@@ -58,11 +58,28 @@ def test_parity_small(case, solver):
     check(spec, alpha, W, SOLVERS[solver])
 
 
-@pytest.mark.parametrize("cb", [1, 2, 4, 8])
+@pytest.mark.parametrize("cb", [1, 2, 3, 4, 5, 7, 8])
 def test_parity_column_blocks_4q(cb):
-    spec = S.transmon_spec(4, 0.6, 100, 2, 4)
+    """Tiles of cb columns run along the window-major column list; widths that do not divide
+    E = 16 give tiles covering two windows (3, 5 and 7 here, 7 being the benchmark's width)."""
+    spec = S.transmon_spec(4, 1.2, 200, 3, 4)
     alpha, W = S.random_alpha(spec, 7), S.random_W(spec, 7)
     check(spec, alpha, W, msqoc.SOLVER_MIXED, col_block=cb)
+
+
+@pytest.mark.parametrize("solver", list(SOLVERS))
+@pytest.mark.parametrize("cb", [5, 7])
+def test_parity_tiles_over_ragged_windows_3q(cb, solver):
+    """Two-window tiles whose windows differ in length by one step (2001 steps over 7 windows)."""
+    spec = S.transmon_spec(3, 30.0, 2001, 7, 8)
+    alpha, W = S.random_alpha(spec, 8), S.random_W(spec, 8)
+    check(spec, alpha, W, SOLVERS[solver], col_block=cb)
+
+
+def test_one_warp_tiles_must_not_cover_two_windows():
+    spec = S.transmon_spec(3, 3.0, 200, 4, 5)     # 9 fibers a column: 3 columns = one warp
+    with pytest.raises(msqoc.MsqocError):
+        msqoc.Problem(spec, col_block=3)
 
 
 def test_column_block_beyond_the_tile_limit_is_rejected():
