@@ -167,6 +167,47 @@ msqoc_status msqoc_kernel_times(msqoc_problem* p, float* ms);
 msqoc_status msqoc_measure_fp64_peak(double* tflops);
 
 /* ---------------------------------------------------------------------------------------
+ * Batched evaluation (many problems per launch).
+ *
+ * Not an operation of the paper: it packs the independent evaluations of many problems (the
+ * paper's method applied to many pulses at once) into few kernel launches.  Problems of one
+ * shape (levels, subsystems) and solver share each sweep launch, whose CTAs take the tiles of
+ * all of them, so small problems no longer leave most of the GPU idle.
+ *
+ * A batch refers to problems created on the current device; they must outlive it and must
+ * not be evaluated on their own while a batched evaluation of them is in flight (they share
+ * buffers).  flags:
+ *   MSQOC_BATCH_GRADIENT: allocate every problem's history buffers now (needed by
+ *                         msqoc_batch_eval_gradient);
+ *   MSQOC_BATCH_GRAPH   : capture each kind of evaluation into a CUDA graph on its first use
+ *                         and replay the graph afterwards (one launch per evaluation).
+ * Inputs are staged per problem with msqoc_set_inputs; a batched evaluation computes every
+ * problem on its staged inputs and leaves the results in the problem's output buffers, read
+ * with msqoc_get_objective / msqoc_get_gradient.  All calls are stream-ordered on `stream`;
+ * msqoc_get_* synchronize it (and report a device status error) when any output is host
+ * memory.  A problem's numbers are the same alone and in any batch up to rounding: each
+ * problem's tiles are its own, only their scheduling changes. */
+#define MSQOC_BATCH_GRADIENT 1
+#define MSQOC_BATCH_GRAPH 2
+
+typedef struct msqoc_batch msqoc_batch;
+
+msqoc_status msqoc_batch_create(msqoc_problem* const* problems, int32_t n, int32_t flags,
+                                msqoc_batch** out);
+/* Stage alpha (d doubles) and W (2 N E (M-1) doubles; NULL when M = 1) for the next batched
+ * evaluation of p: stream-ordered copies from host or device arrays. */
+msqoc_status msqoc_set_inputs(msqoc_problem* p, const double* alpha, const double* W, void* stream);
+msqoc_status msqoc_batch_eval_objective(msqoc_batch* b, void* stream);
+msqoc_status msqoc_batch_eval_gradient(msqoc_batch* b, void* stream);
+/* Results of p's last batched evaluation (J_out and pen_out may be NULL; P_out may be NULL
+ * for the gradient). */
+msqoc_status msqoc_get_objective(msqoc_problem* p, double* P_out, double* J_out, double* pen_out,
+                                 void* stream);
+msqoc_status msqoc_get_gradient(msqoc_problem* p, double* P_out, double* grad_alpha,
+                                double* grad_W, void* stream);
+msqoc_status msqoc_batch_destroy(msqoc_batch* b);
+
+/* ---------------------------------------------------------------------------------------
  * Objective evaluation that allocates no device memory.
  *
  * The paper has no counterpart to this entry point; it exists for callers that cannot

@@ -12,11 +12,12 @@
 #include "../../include/msqoc.h"
 #include "msqoc_aux.cuh"
 #include "msqoc_internal.h"
+#include "msqoc_host.h"
 #include "msqoc_sweep.cuh"
 
 using namespace msqoc;
 
-namespace {
+namespace msqoc {
 
 thread_local std::string g_last_error;
 
@@ -30,13 +31,6 @@ msqoc_status fail(msqoc_status code, const char* fmt, ...) {
     return code;
 }
 
-#define CUDA_TRY(expr)                                                                              \
-    do {                                                                                            \
-        cudaError_t _e = (expr);                                                                    \
-        if (_e != cudaSuccess)                                                                      \
-            return fail(_e == cudaErrorMemoryAllocation ? MSQOC_ERR_OUT_OF_MEMORY : MSQOC_ERR_CUDA, \
-                        "%s failed: %s", #expr, cudaGetErrorString(_e));                           \
-    } while (0)
 
 int ipow_i(int b, int e) {
     int r = 1;
@@ -339,11 +333,6 @@ SweepArgs sweep_args(const ProbDev& pd, const ProbDev* pds_dev, const Tile* tile
     return a;
 }
 
-// Output staging layout in out_dev (doubles): P, J, pen[M-1], grad_alpha[d], grad_W[nW].
-// grad_alpha and grad_W start at even offsets: grad_W is written as double2 (16-byte aligned).
-struct OutLayout {
-    size_t pen, ga, gw, total;
-};
 OutLayout out_layout(int M, int d, size_t nW) {
     OutLayout o;
     o.pen = 2;
@@ -353,44 +342,7 @@ OutLayout out_layout(int M, int d, size_t nW) {
     return o;
 }
 
-}  // namespace
-
-struct msqoc_problem {
-    ProbDev pd{};
-    int device = 0;
-    int ckpt_interval = 1;   // K (1 = every midpoint state kept)
-    size_t nW = 0;           // doubles in W
-    size_t ne = 0;           // N*E
-    // owned device buffers
-    ProbDev* pds = nullptr;        // device copy of pd (read by the sweeps)
-    Tile* tiles = nullptr;
-    int* lanemap = nullptr;
-    double2* P = nullptr;
-    int* emb = nullptr;
-    double2* V = nullptr;
-    double* alpha_dev = nullptr;   // the evaluation's inputs (copied from the caller's arrays)
-    double* W_dev = nullptr;
-    double2* ctrl = nullptr;
-    Spline4* spl = nullptr;
-    double2* phase = nullptr;
-    double2* hist = nullptr;       // allocated by the first gradient evaluation
-    double2* ckpt = nullptr;       // (with hist, when K > 1)
-    double2* Lstate = nullptr;     // (with hist, when K > 1)
-    double2* Uend = nullptr;
-    double2* Lterm = nullptr;
-    double2* Lam0 = nullptr;
-    double* term = nullptr;
-    double* gpart = nullptr;
-    int* status = nullptr;
-    double* out_dev = nullptr;     // staging of outputs: P, J, pen[M-1], galpha[d], gW[nW]
-    int* status_host = nullptr;    // pinned
-    size_t bytes = 0;              // device bytes held now
-    size_t grad_bytes = 0;         // bytes the first gradient evaluation adds
-    // profiling: CUDA events around each kernel of an evaluation
-    bool profile = false;
-    cudaEvent_t ev[MSQOC_NKERNELS][2] = {};
-    bool ran[MSQOC_NKERNELS] = {};
-};
+}  // namespace msqoc
 
 namespace {
 
@@ -590,7 +542,7 @@ msqoc_status msqoc_destroy_problem(msqoc_problem* p) {
 
 }  // extern "C"
 
-namespace {
+namespace msqoc {
 
 // copy the evaluation's inputs into the problem's input buffers (stream-ordered)
 msqoc_status stage_inputs(msqoc_problem* p, const double* alpha, const double* W, cudaStream_t s) {
@@ -632,28 +584,55 @@ msqoc_status sweep(msqoc_problem* p, int mode, int seg, cudaStream_t s) {
     return MSQOC_OK;
 }
 
-// controls, forward sweep over whole windows, terminal conditions
-msqoc_status launch_forward_part(msqoc_problem* p, int mode, cudaStream_t s) {
-    ProbDev& pd = p->pd;
-    for (bool& r : p->ran) r = false;
-    {
-        Mark mk(p, MSQOC_KERNEL_CONTROLS, s);
-        const int threads = 256;
-        int blocks = static_cast<int>(std::min<int64_t>((pd.nsteps + threads - 1) / threads, 4096));
-        k_controls<<<blocks, threads, 0, s>>>(pd);
-        CUDA_TRY(cudaGetLastError());
-    }
-    {
-        Mark mk(p, MSQOC_KERNEL_FORWARD, s);
-        const msqoc_status st = sweep(p, mode, 0, s);
-        if (st) return st;
-    }
-    {
-        Mark mk(p, MSQOC_KERNEL_TERMINAL, s);
-        k_terminal<<<pd.M, TERM_THREADS, 0, s>>>(pd, mode == SWEEP_OBJECTIVE ? 0 : 1);
+msqoc_status launch_controls(msqoc_problem* p, cudaStream_t s) {
+    const ProbDev& pd = p->pd;
+    Mark mk(p, MSQOC_KERNEL_CONTROLS, s);
+    const int threads = 256;
+    const int blocks = static_cast<int>(std::min<int64_t>((pd.nsteps + threads - 1) / threads, 4096));
+    k_controls<<<blocks, threads, 0, s>>>(pd);
+    CUDA_TRY(cudaGetLastError());
+    return MSQOC_OK;
+}
+
+msqoc_status launch_terminal(msqoc_problem* p, bool want_lambda, cudaStream_t s) {
+    Mark mk(p, MSQOC_KERNEL_TERMINAL, s);
+    k_terminal<<<p->pd.M, TERM_THREADS, 0, s>>>(p->pd, want_lambda ? 1 : 0);
+    CUDA_TRY(cudaGetLastError());
+    return MSQOC_OK;
+}
+
+msqoc_status launch_objective_outputs(msqoc_problem* p, double* P, double* J, double* pen, cudaStream_t s) {
+    Mark mk(p, MSQOC_KERNEL_FINALIZE, s);
+    k_finalize_scalars<<<1, 32, 0, s>>>(p->pd, P, J, p->pd.M > 1 ? pen : nullptr, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    return MSQOC_OK;
+}
+
+msqoc_status launch_gradient_outputs(msqoc_problem* p, double* P, double* ga, double* gw, cudaStream_t s) {
+    const ProbDev& pd = p->pd;
+    Mark mk(p, MSQOC_KERNEL_FINALIZE, s);
+    k_finalize_scalars<<<std::max(1, (pd.d + 255) / 256), 256, 0, s>>>(pd, P, nullptr, nullptr, ga);
+    CUDA_TRY(cudaGetLastError());
+    if (pd.M > 1) {
+        const size_t total = p->ne * (pd.M - 1);
+        const int blocks = static_cast<int>(std::min<size_t>((total + 255) / 256, 8192));
+        k_grad_W<<<blocks, 256, 0, s>>>(pd, reinterpret_cast<double2*>(gw));
         CUDA_TRY(cudaGetLastError());
     }
     return MSQOC_OK;
+}
+
+// controls, forward sweep over whole windows, terminal conditions
+msqoc_status launch_forward_part(msqoc_problem* p, int mode, cudaStream_t s) {
+    for (bool& r : p->ran) r = false;
+    msqoc_status st = launch_controls(p, s);
+    if (st) return st;
+    {
+        Mark mk(p, MSQOC_KERNEL_FORWARD, s);
+        st = sweep(p, mode, 0, s);
+        if (st) return st;
+    }
+    return launch_terminal(p, mode != SWEEP_OBJECTIVE, s);
 }
 
 msqoc_status status_error(int st) {
@@ -674,7 +653,7 @@ msqoc_status check_status_sync(msqoc_problem* p, cudaStream_t s) {
     return MSQOC_OK;
 }
 
-}  // namespace
+}  // namespace msqoc
 
 extern "C" {
 
@@ -690,12 +669,9 @@ msqoc_status msqoc_eval_objective(msqoc_problem* p, const double* alpha, const d
     const ProbDev& pd = p->pd;
     const bool dP = is_device_ptr(P_out), dJ = !J_out || is_device_ptr(J_out), dpen = !pen_out || is_device_ptr(pen_out);
     double* o = p->out_dev;
-    {
-        Mark mk(p, MSQOC_KERNEL_FINALIZE, s);
-        k_finalize_scalars<<<1, 32, 0, s>>>(pd, dP ? P_out : o, J_out ? (dJ ? J_out : o + 1) : nullptr,
-                                           pen_out && pd.M > 1 ? (dpen ? pen_out : o + 2) : nullptr, nullptr);
-        CUDA_TRY(cudaGetLastError());
-    }
+    st = launch_objective_outputs(p, dP ? P_out : o, J_out ? (dJ ? J_out : o + 1) : nullptr,
+                                  pen_out ? (dpen ? pen_out : o + 2) : nullptr, s);
+    if (st) return st;
     const bool all_dev = dP && dJ && dpen;
     if (all_dev) return MSQOC_OK;
     if (!dP) CUDA_TRY(cudaMemcpyAsync(P_out, o, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -718,7 +694,7 @@ msqoc_status msqoc_eval_gradient(msqoc_problem* p, const double* alpha, const do
     const ProbDev& pd = p->pd;
     // one history segment: every midpoint state in the forward sweep; otherwise checkpoints
     // at the segment starts, and each segment is recomputed before its adjoint sweep
-    st = launch_forward_part(p, pd.nseg == 1 ? SWEEP_HISTORY : SWEEP_CKPT, s);
+    st = launch_forward_part(p, SWEEP_HISTORY, s);
     if (st) return st;
     {
         Mark mk(p, MSQOC_KERNEL_ADJOINT, s);
@@ -739,18 +715,8 @@ msqoc_status msqoc_eval_gradient(msqoc_problem* p, const double* alpha, const do
         return fail(MSQOC_ERR_INVALID_ARG, "device grad_W must be 16-byte aligned");
     double* ga_dst = dga ? grad_alpha : o + ol.ga;
     double* gw_dst = pd.M == 1 ? nullptr : (dgw ? grad_W : o + ol.gw);
-    {
-        Mark mk(p, MSQOC_KERNEL_FINALIZE, s);
-        k_finalize_scalars<<<std::max(1, (pd.d + 255) / 256), 256, 0, s>>>(pd, P_out ? (dP ? P_out : o) : nullptr,
-                                                                          nullptr, nullptr, ga_dst);
-        CUDA_TRY(cudaGetLastError());
-        if (pd.M > 1) {
-            const size_t total = p->ne * (pd.M - 1);
-            const int blocks = static_cast<int>(std::min<size_t>((total + 255) / 256, 8192));
-            k_grad_W<<<blocks, 256, 0, s>>>(pd, reinterpret_cast<double2*>(gw_dst));
-            CUDA_TRY(cudaGetLastError());
-        }
-    }
+    st = launch_gradient_outputs(p, P_out ? (dP ? P_out : o) : nullptr, ga_dst, gw_dst, s);
+    if (st) return st;
     if (dP && dga && dgw) return MSQOC_OK;
     if (P_out && !dP) CUDA_TRY(cudaMemcpyAsync(P_out, o, sizeof(double), cudaMemcpyDeviceToHost, s));
     if (!dga) CUDA_TRY(cudaMemcpyAsync(grad_alpha, ga_dst, pd.d * sizeof(double), cudaMemcpyDeviceToHost, s));

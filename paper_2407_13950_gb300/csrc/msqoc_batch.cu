@@ -1,0 +1,274 @@
+// Batched evaluation: many problems per sweep launch, optionally replayed as a CUDA graph.
+//
+// Problems of one shape (levels, subsystems) and solver form a group; a group's sweep launch
+// takes the concatenation of its problems' tile lists (each tile names its problem), so
+// problems of different durations and window counts share every wave of the GPU instead of
+// each filling a fraction of it.  The per-problem steps (controls, terminal conditions, final
+// reductions) stay per problem.  With MSQOC_BATCH_GRAPH the whole sequence is captured once
+// into a CUDA graph and replayed; every buffer it touches belongs to the problems and stays
+// where it is, so replays only need the problems' inputs staged with msqoc_set_inputs.
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "msqoc_host.h"
+
+using namespace msqoc;
+
+struct msqoc_batch {
+    struct Group {
+        int L = 0, q = 0, solver = 0;
+        std::vector<int> members;     // indices into probs
+        SweepArgs args{};             // pds / tiles / lanemap / geometry of the group's launches
+        int ntiles = 0;
+        int nseg_max = 1;
+        ProbDev* pds = nullptr;
+        Tile* tiles = nullptr;
+        int* lanemap = nullptr;
+    };
+    std::vector<msqoc_problem*> probs;
+    std::vector<Group> groups;
+    int flags = 0;
+    int device = 0;
+    cudaStream_t cap = nullptr;                   // capture stream (graph mode)
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};  // [objective, gradient]
+};
+
+namespace {
+
+void free_batch(msqoc_batch* b) {
+    for (auto& g : b->groups) {
+        if (g.pds) cudaFree(g.pds);
+        if (g.tiles) cudaFree(g.tiles);
+        if (g.lanemap) cudaFree(g.lanemap);
+    }
+    for (auto& e : b->exec)
+        if (e) cudaGraphExecDestroy(e);
+    if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+// the launch sequence of one batched evaluation
+msqoc_status enqueue(msqoc_batch* b, bool grad, cudaStream_t s) {
+    msqoc_status st;
+    for (msqoc_problem* p : b->probs)
+        if ((st = launch_controls(p, s))) return st;
+    for (auto& g : b->groups) {
+        SweepArgs a = g.args;
+        a.mode = grad ? SWEEP_HISTORY : SWEEP_OBJECTIVE;
+        a.seg = 0;
+        CUDA_TRY(launch_sweep(a, g.ntiles, s));
+    }
+    for (msqoc_problem* p : b->probs)
+        if ((st = launch_terminal(p, grad, s))) return st;
+    if (!grad) {
+        for (msqoc_problem* p : b->probs) {
+            double* o = p->out_dev;
+            if ((st = launch_objective_outputs(p, o, o + 1, o + 2, s))) return st;
+        }
+        return MSQOC_OK;
+    }
+    for (auto& g : b->groups) {
+        for (int seg = g.nseg_max - 1; seg >= 0; --seg) {
+            SweepArgs a = g.args;
+            a.seg = seg;
+            if (g.nseg_max > 1) {
+                a.mode = SWEEP_RECOMPUTE;
+                CUDA_TRY(launch_sweep(a, g.ntiles, s));
+            }
+            a.mode = SWEEP_ADJOINT;
+            CUDA_TRY(launch_sweep(a, g.ntiles, s));
+        }
+    }
+    for (msqoc_problem* p : b->probs) {
+        const OutLayout ol = out_layout(p->pd.M, p->pd.d, p->nW);
+        double* o = p->out_dev;
+        if ((st = launch_gradient_outputs(p, o, o + ol.ga, p->pd.M > 1 ? o + ol.gw : nullptr, s))) return st;
+    }
+    return MSQOC_OK;
+}
+
+msqoc_status eval(msqoc_batch* b, bool grad, cudaStream_t s) {
+    if (grad && !(b->flags & MSQOC_BATCH_GRADIENT))
+        return fail(MSQOC_ERR_INVALID_ARG, "batch was created without MSQOC_BATCH_GRADIENT");
+    if (!(b->flags & MSQOC_BATCH_GRAPH)) return enqueue(b, grad, s);
+    cudaGraphExec_t& ex = b->exec[grad ? 1 : 0];
+    if (!ex) {
+        // capture on a private stream; the first replay below runs it
+        CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+        const msqoc_status st = enqueue(b, grad, b->cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+        if (st) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        CUDA_TRY(e);
+        const cudaError_t ei = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        CUDA_TRY(ei);
+    }
+    CUDA_TRY(cudaGraphLaunch(ex, s));
+    return MSQOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+msqoc_status msqoc_batch_create(msqoc_problem* const* problems, int32_t n, int32_t flags, msqoc_batch** out) {
+    if (!out) return fail(MSQOC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!problems || n < 1) return fail(MSQOC_ERR_INVALID_ARG, "no problems");
+    if (flags & ~(MSQOC_BATCH_GRADIENT | MSQOC_BATCH_GRAPH)) return fail(MSQOC_ERR_INVALID_ARG, "unknown flags %d", flags);
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    for (int i = 0; i < n; ++i) {
+        if (!problems[i]) return fail(MSQOC_ERR_INVALID_ARG, "problem %d is NULL", i);
+        if (problems[i]->device != dev) return fail(MSQOC_ERR_INVALID_ARG, "problem %d lives on another device", i);
+        for (int j = 0; j < i; ++j)
+            if (problems[j] == problems[i]) return fail(MSQOC_ERR_INVALID_ARG, "problem %d appears twice", i);
+    }
+    auto* b = new (std::nothrow) msqoc_batch();
+    if (!b) return fail(MSQOC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    b->flags = flags;
+    b->device = dev;
+    b->probs.assign(problems, problems + n);
+    msqoc_status st = MSQOC_OK;
+    // the history buffers first: the problems' device records then hold their final pointers
+    if (flags & MSQOC_BATCH_GRADIENT)
+        for (msqoc_problem* p : b->probs)
+            if (!st) st = ensure_gradient_buffers(p, nullptr);
+    if (!st && cudaDeviceSynchronize() != cudaSuccess) st = fail(MSQOC_ERR_CUDA, "synchronize failed");
+    // groups by (levels, subsystems, solver)
+    for (int i = 0; i < n && !st; ++i) {
+        const ProbDev& pd = b->probs[i]->pd;
+        auto it = std::find_if(b->groups.begin(), b->groups.end(), [&](const msqoc_batch::Group& g) {
+            return g.L == pd.L && g.q == pd.q && g.solver == pd.solver;
+        });
+        if (it == b->groups.end()) {
+            b->groups.emplace_back();
+            it = b->groups.end() - 1;
+            it->L = pd.L;
+            it->q = pd.q;
+            it->solver = pd.solver;
+        }
+        it->members.push_back(i);
+    }
+    for (auto& g : b->groups) {
+        if (st) break;
+        int nthreads = 32, cpt = 1, dmax = 1;
+        for (int i : g.members) {
+            const ProbDev& pd = b->probs[i]->pd;
+            nthreads = std::max(nthreads, pd.nthreads);
+            cpt = std::max(cpt, pd.cb);
+            dmax = std::max(dmax, pd.d);
+            g.nseg_max = std::max(g.nseg_max, pd.nseg);
+        }
+        std::vector<ProbDev> pds;
+        std::vector<Tile> tiles;
+        std::vector<int> maps;
+        for (size_t k = 0; k < g.members.size(); ++k) {
+            const ProbDev& pd = b->probs[g.members[k]]->pd;
+            const int map_base = static_cast<int>(maps.size() / nthreads);
+            for (int t = 0; t < pd.ntiles; ++t) {
+                Tile x = tile_at(t, pd.M, pd.E, pd.cb, static_cast<int>(k));
+                x.map += map_base;
+                tiles.push_back(x);
+            }
+            const Tile last = tile_at(pd.ntiles - 1, pd.M, pd.E, pd.cb, 0);
+            maps.resize(maps.size() + size_t(pd.cb + 1) * nthreads);
+            int* mp = maps.data() + size_t(map_base) * nthreads;
+            for (int j = 0; j <= pd.cb; ++j)
+                build_lanemap(pd.L, pd.q, j < pd.cb ? pd.cb : last.ncol, j < pd.cb ? j + 1 : last.ncol0, nthreads,
+                              mp + size_t(j) * nthreads);
+            pds.push_back(pd);
+        }
+        g.ntiles = static_cast<int>(tiles.size());
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&g.pds), pds.size() * sizeof(ProbDev));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&g.tiles), tiles.size() * sizeof(Tile));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&g.lanemap), maps.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(g.pds, pds.data(), pds.size() * sizeof(ProbDev), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g.tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g.lanemap, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            st = fail(e == cudaErrorMemoryAllocation ? MSQOC_ERR_OUT_OF_MEMORY : MSQOC_ERR_CUDA, "batch tables: %s",
+                      cudaGetErrorString(e));
+            break;
+        }
+        const ProbDev& p0 = b->probs[g.members[0]]->pd;
+        g.args = sweep_args(p0, g.pds, g.tiles, g.lanemap, SWEEP_OBJECTIVE, 0);
+        g.args.cpt = cpt;
+        g.args.dmax = dmax;
+        g.args.nthreads = nthreads;
+        SweepArgs adj = g.args;
+        adj.mode = SWEEP_ADJOINT;
+        if (std::max(sweep_smem_bytes(g.args), sweep_smem_bytes(adj)) > 227 * 1024) {
+            st = fail(MSQOC_ERR_UNSUPPORTED, "batched tiles need too much shared memory");
+            break;
+        }
+        // set the kernels' shared-memory limits now (a launch of no tiles only does that), so
+        // that a graph capture later makes no attribute calls
+        if (launch_sweep(g.args, 0, nullptr) != cudaSuccess || launch_sweep(adj, 0, nullptr) != cudaSuccess)
+            st = fail(MSQOC_ERR_CUDA, "sweep kernel attributes could not be set");
+    }
+    if (!st && (flags & MSQOC_BATCH_GRAPH) && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+        st = fail(MSQOC_ERR_CUDA, "capture stream creation failed");
+    if (st) {
+        free_batch(b);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return MSQOC_OK;
+}
+
+msqoc_status msqoc_batch_eval_objective(msqoc_batch* b, void* stream) {
+    if (!b) return fail(MSQOC_ERR_INVALID_ARG, "batch is NULL");
+    return eval(b, false, static_cast<cudaStream_t>(stream));
+}
+
+msqoc_status msqoc_batch_eval_gradient(msqoc_batch* b, void* stream) {
+    if (!b) return fail(MSQOC_ERR_INVALID_ARG, "batch is NULL");
+    return eval(b, true, static_cast<cudaStream_t>(stream));
+}
+
+msqoc_status msqoc_batch_destroy(msqoc_batch* b) {
+    if (!b) return MSQOC_OK;
+    cudaDeviceSynchronize();
+    free_batch(b);
+    delete b;
+    return MSQOC_OK;
+}
+
+msqoc_status msqoc_set_inputs(msqoc_problem* p, const double* alpha, const double* W, void* stream) {
+    if (!p) return fail(MSQOC_ERR_INVALID_ARG, "problem is NULL");
+    return stage_inputs(p, alpha, W, static_cast<cudaStream_t>(stream));
+}
+
+msqoc_status msqoc_get_objective(msqoc_problem* p, double* P_out, double* J_out, double* pen_out, void* stream) {
+    if (!p || !P_out) return fail(MSQOC_ERR_INVALID_ARG, "problem or P_out is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double* o = p->out_dev;
+    CUDA_TRY(cudaMemcpyAsync(P_out, o, sizeof(double), cudaMemcpyDefault, s));
+    if (J_out) CUDA_TRY(cudaMemcpyAsync(J_out, o + 1, sizeof(double), cudaMemcpyDefault, s));
+    if (pen_out && p->pd.M > 1)
+        CUDA_TRY(cudaMemcpyAsync(pen_out, o + 2, (p->pd.M - 1) * sizeof(double), cudaMemcpyDefault, s));
+    const bool host = !is_device_ptr(P_out) || (J_out && !is_device_ptr(J_out)) || (pen_out && !is_device_ptr(pen_out));
+    return host ? check_status_sync(p, s) : MSQOC_OK;
+}
+
+msqoc_status msqoc_get_gradient(msqoc_problem* p, double* P_out, double* grad_alpha, double* grad_W, void* stream) {
+    if (!p || !grad_alpha) return fail(MSQOC_ERR_INVALID_ARG, "problem or grad_alpha is NULL");
+    if (p->pd.M > 1 && !grad_W) return fail(MSQOC_ERR_INVALID_ARG, "grad_W is NULL but M > 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double* o = p->out_dev;
+    const OutLayout ol = out_layout(p->pd.M, p->pd.d, p->nW);
+    if (P_out) CUDA_TRY(cudaMemcpyAsync(P_out, o, sizeof(double), cudaMemcpyDefault, s));
+    CUDA_TRY(cudaMemcpyAsync(grad_alpha, o + ol.ga, p->pd.d * sizeof(double), cudaMemcpyDefault, s));
+    if (p->pd.M > 1) CUDA_TRY(cudaMemcpyAsync(grad_W, o + ol.gw, p->nW * sizeof(double), cudaMemcpyDefault, s));
+    const bool host = (P_out && !is_device_ptr(P_out)) || !is_device_ptr(grad_alpha) ||
+                      (p->pd.M > 1 && !is_device_ptr(grad_W));
+    return host ? check_status_sync(p, s) : MSQOC_OK;
+}
+
+}  // extern "C"

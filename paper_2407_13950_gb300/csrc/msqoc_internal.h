@@ -78,9 +78,11 @@ struct Tile {
 // What a sweep launch does.
 enum SweepMode {
     SWEEP_OBJECTIVE = 0,  // forward over whole windows; end states U^m(t_m)
-    SWEEP_HISTORY = 1,    // forward over whole windows; also every midpoint state (one segment)
-    SWEEP_CKPT = 2,       // forward over whole windows; also the states at segment starts
+    SWEEP_HISTORY = 1,    // forward over whole windows for a gradient; also every midpoint state
+                          // (a problem with one history segment) or the states at the segment
+                          // starts (checkpoints, more segments)
     SWEEP_RECOMPUTE = 3,  // forward over segment `seg` from its checkpoint; midpoint states
+                          // (no work for a problem with one segment)
     SWEEP_ADJOINT = 4     // adjoint over segment `seg` with the fused gradient quadrature
 };
 

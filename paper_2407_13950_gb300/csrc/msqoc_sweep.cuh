@@ -417,6 +417,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
     const int ncol = tile.ncol, ncol0 = tile.ncol0;
     const int nslot = ncol0 < ncol ? 2 : 1;
     const bool segmented = a.mode == SWEEP_RECOMPUTE || a.mode == SWEEP_ADJOINT;
+    const bool idle_launch = a.mode == SWEEP_RECOMPUTE && pd.nseg == 1;   // nothing to recompute
 
     // ---- the slots' windows and step ranges (local step indices [lo, lo + cnt) of the window)
     const int64_t wn0_0 = win_start(pd, tile.m0);
@@ -425,8 +426,8 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
     const int wns_1 = nslot > 1 ? static_cast<int>(win_start(pd, tile.m0 + 2) - wn0_1) : 0;
     const int lo_0 = segmented ? a.seg * pd.kseg : 0;
     const int lo_1 = lo_0;
-    const int cnt_0 = max(0, (segmented ? min(wns_0, lo_0 + pd.kseg) : wns_0) - lo_0);
-    const int cnt_1 = nslot > 1 ? max(0, (segmented ? min(wns_1, lo_1 + pd.kseg) : wns_1) - lo_1) : 0;
+    const int cnt_0 = idle_launch ? 0 : max(0, (segmented ? min(wns_0, lo_0 + pd.kseg) : wns_0) - lo_0);
+    const int cnt_1 = nslot > 1 && !idle_launch ? max(0, (segmented ? min(wns_1, lo_1 + pd.kseg) : wns_1) - lo_1) : 0;
     const int nit = max(cnt_0, cnt_1);
     // global step of slot s at iteration jj, clamped into the slot's range (a slot without steps
     // in this launch maps to its window's first step, which exists)
@@ -490,7 +491,8 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
     }
 
     // ---- history blocks: slot s of a tile covers a contiguous column range of its window
-    const bool want_hist = !BWD && (a.mode == SWEEP_HISTORY || a.mode == SWEEP_RECOMPUTE);
+    const bool want_hist = !BWD && ((a.mode == SWEEP_HISTORY && pd.nseg == 1) || a.mode == SWEEP_RECOMPUTE);
+    const bool want_ckpt = !BWD && a.mode == SWEEP_HISTORY && pd.nseg > 1;
     const uint32_t bytes_0 = static_cast<uint32_t>(size_t(ncol0) * N * sizeof(double2));
     const uint32_t bytes_1 = static_cast<uint32_t>(size_t(ncol - ncol0) * N * sizeof(double2));
     auto hist_ptr = [&](int s, int jj) -> double2* {
@@ -597,7 +599,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
             if (lane < nscat) ph_prev = pd.phase[size_t(np) * pd.nfsum + lane / 3];
         }
         // checkpoint: the state at the start of every segment (forward over whole windows)
-        if (!BWD && a.mode == SWEEP_CKPT && live && act && jj % pd.kseg == 0) {
+        if (want_ckpt && live && act && jj % pd.kseg == 0) {
             double2* ck = pd.ckpt + ((size_t(m - 1) * pd.nseg + jj / pd.kseg) * E + col) * N + f * L;
 #pragma unroll
             for (int l = 0; l < L; ++l) ck[l] = u[l];

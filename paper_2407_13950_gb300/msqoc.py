@@ -23,7 +23,10 @@ SOLVER_DEFAULT, SOLVER_FP64, SOLVER_MIXED = 0, 1, 2
 
 EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_eval_objective", "msqoc_eval_gradient",
             "msqoc_destroy_problem", "msqoc_last_error", "msqoc_version", "msqoc_kernel_times",
-            "msqoc_measure_fp64_peak", "msqoc_eval_objective_noalloc"]
+            "msqoc_measure_fp64_peak", "msqoc_eval_objective_noalloc", "msqoc_batch_create",
+            "msqoc_batch_eval_objective", "msqoc_batch_eval_gradient", "msqoc_batch_destroy", "msqoc_set_inputs",
+            "msqoc_get_objective", "msqoc_get_gradient"]
+BATCH_GRADIENT, BATCH_GRAPH = 1, 2
 KERNEL_NAMES = ["controls", "forward", "terminal", "adjoint", "finalize"]
 
 
@@ -79,6 +82,13 @@ def load(build_if_missing: bool = True):
             "msqoc_measure_fp64_peak": (i32, [vp]),
             "msqoc_eval_objective_noalloc": (i32, [vp, vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, i32,
                                                    vp, vp, vp, vp, vp, vp]),
+            "msqoc_batch_create": (i32, [vp, i32, i32, vp]),
+            "msqoc_batch_eval_objective": (i32, [vp, vp]),
+            "msqoc_batch_eval_gradient": (i32, [vp, vp]),
+            "msqoc_batch_destroy": (i32, [vp]),
+            "msqoc_set_inputs": (i32, [vp, vp, vp, vp]),
+            "msqoc_get_objective": (i32, [vp, vp, vp, vp, vp]),
+            "msqoc_get_gradient": (i32, [vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -263,3 +273,62 @@ def eval_objective_noalloc(spec, alpha, W=None, target=None, solver: int = SOLVE
     if P_out is not None:
         return {"P": P_out, "J": J_out, "pen": pen_out}
     return {"P": float(P[0]), "J": float(J[0]), "pen": pen[:M - 1].copy()}
+
+
+class Batch:
+    """Problems evaluated together (msqoc_batch_*): one sweep launch per shape for all of them,
+    optionally replayed as a CUDA graph.  The problems must outlive the batch."""
+
+    def __init__(self, problems, gradient: bool = True, graph: bool = False):
+        lib = load()
+        self.problems = list(problems)
+        arr = (ctypes.c_void_p * len(self.problems))(*[p.handle.value for p in self.problems])
+        flags = (BATCH_GRADIENT if gradient else 0) | (BATCH_GRAPH if graph else 0)
+        h = ctypes.c_void_p()
+        _check(lib.msqoc_batch_create(arr, len(self.problems), flags, ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().msqoc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_inputs(self, i: int, alpha, W=None, stream=None):
+        p = self.problems[i]
+        _check(load().msqoc_set_inputs(p.handle, _ptr(alpha), _ptr(W if p.spec.M > 1 else None),
+                                       _stream_handle(stream)))
+
+    def eval_gradient(self, stream=None):
+        _check(load().msqoc_batch_eval_gradient(self.handle, _stream_handle(stream)))
+
+    def eval_objective(self, stream=None):
+        _check(load().msqoc_batch_eval_objective(self.handle, _stream_handle(stream)))
+
+    def get_gradient(self, i: int, stream=None) -> dict:
+        p = self.problems[i]
+        P = np.zeros(1)
+        ga = np.zeros(p.d)
+        gW = np.zeros(max(p.nW, 1))
+        _check(load().msqoc_get_gradient(p.handle, _ptr(P), _ptr(ga), _ptr(gW) if p.spec.M > 1 else None,
+                                         _stream_handle(stream)))
+        return {"P": float(P[0]), "grad_alpha": ga, "grad_W": gW[:p.nW].copy()}
+
+    def get_objective(self, i: int, stream=None) -> dict:
+        p = self.problems[i]
+        P, J = np.zeros(1), np.zeros(1)
+        pen = np.zeros(max(p.spec.M - 1, 1))
+        _check(load().msqoc_get_objective(p.handle, _ptr(P), _ptr(J), _ptr(pen) if p.spec.M > 1 else None,
+                                          _stream_handle(stream)))
+        return {"P": float(P[0]), "J": float(J[0]), "pen": pen[:p.spec.M - 1].copy()}
