@@ -253,6 +253,119 @@ def run_ours(args, spec):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """Config of the batched launch: 32 x 2 transmons + 32 x 3 + 32 x 4 (durations uniform in
+    [0.5 T, 1.5 T] at the base step size, windows drawn from {8, 32, 64, 128}), one
+    objective+gradient evaluation of all 96 per step, as one batch replayed from a CUDA graph,
+    against the same problems evaluated one after another (one problem per launch sequence)."""
+    import torch
+    from paper_2407_13950_gb300 import msqoc
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    specs = S.mixed_batch_specs(seed=1, n_per_shape=args.batch_per_shape,
+                                shapes=[S.config_2q(), S.config_3q(), S.config_4q()])
+    nprob = len(specs)
+    probs = [msqoc.Problem(sp) for sp in specs]
+    host_in = [(S.random_alpha(sp, 1, problem=i), S.random_W(sp, 1, problem=i)) for i, sp in enumerate(specs)]
+    dev_in = [(torch.tensor(a, device=dev, dtype=torch.float64), torch.tensor(W, device=dev, dtype=torch.float64))
+              for a, W in host_in]
+    outs = [(torch.zeros(1, device=dev, dtype=torch.float64), torch.zeros(p.d, device=dev, dtype=torch.float64),
+             torch.zeros(max(p.nW, 2), device=dev, dtype=torch.float64)) for p in probs]
+    stream = torch.cuda.current_stream(dev)
+    batch = msqoc.Batch(probs, gradient=True, graph=True)
+
+    def batched_step():
+        for i, (a, W) in enumerate(dev_in):
+            batch.set_inputs(i, a, W, stream=stream)
+        batch.eval_gradient(stream=stream)
+
+    def plain_step(ev=None):
+        for i, p in enumerate(probs):
+            a, W = dev_in[i]
+            P, ga, gW = outs[i]
+            p.eval_gradient_into(a, W if p.spec.M > 1 else None, P, ga, gW if p.spec.M > 1 else None, stream=stream)
+            if ev is not None:
+                ev[i].record(stream)
+
+    def timed(fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    for _ in range(args.warmup):
+        batched_step()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms_b = timed(batched_step, args.steps)
+    clocks = sampler.stop()
+    for _ in range(max(1, args.warmup // 2)):
+        plain_step()
+    ms_p = timed(plain_step, args.steps)
+    # completion times when all requests are submitted together: the batch finishes them all at
+    # once; one after another, request i waits for the ones before it
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(nprob)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plain_step(ev)
+    torch.cuda.synchronize()
+    done_p = np.array([e0.elapsed_time(e) for e in ev])
+    # end to end through host buffers: inputs copied from host memory, results read back
+    res = [(np.zeros(1), np.zeros(p.d), np.zeros(max(p.nW, 1))) for p in probs]
+
+    def e2e_step():
+        for i, (a, W) in enumerate(host_in):
+            batch.set_inputs(i, a, W, stream=stream)
+        batch.eval_gradient(stream=stream)
+        for i, p in enumerate(probs):
+            P, ga, gW = res[i]
+            msqoc.load().msqoc_get_gradient(p.handle, msqoc._ptr(P), msqoc._ptr(ga),
+                                           msqoc._ptr(gW) if p.spec.M > 1 else None, msqoc._stream_handle(stream))
+        torch.cuda.synchronize()
+
+    e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    h2d = sum(8 * (sp.d + (sp.nW if sp.M > 1 else 0)) for sp in specs)
+    d2h = sum(8 * (1 + sp.d + (sp.nW if sp.M > 1 else 0)) for sp in specs)
+    fl = sum(flops_model(sp)["total"] for sp in specs)
+    peak = msqoc.measure_fp64_peak()
+    line = {
+        "metric": "mixed-batch objective+gradient evals/s", "value": nprob / (ms_b * 1e-3), "unit": "evals/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batched-{nprob}: {args.batch_per_shape}x2q + {args.batch_per_shape}x3q + "
+                               f"{args.batch_per_shape}x4q, durations U[0.5T,1.5T], windows in {{8,32,64,128}}",
+                   "launch": "one CUDA graph per step (shared sweep launches per shape)",
+                   "l2": "inputs larger than L2 (midpoint histories of GBs per step)"},
+        "plain": {"value": nprob / (ms_p * 1e-3), "unit": "evals/s", "ms_per_step": ms_p,
+                  "launch": "one problem after another, each its own launch sequence"},
+        "speedup_vs_plain": ms_p / ms_b,
+        "latency_ms": {"batched": {"p50": ms_b, "p99": ms_b},
+                       "plain": {"p50": float(np.percentile(done_p, 50)), "p99": float(np.percentile(done_p, 99))},
+                       "note": "all requests submitted at once; completion time of each"},
+        "whole_step": {"algorithmic_tflops": fl / (ms_b * 1e-3) / 1e12,
+                       "frac_of_fp64_peak": fl / (ms_b * 1e-3) / 1e12 / peak, "peak_tflops": peak},
+        "e2e": {"value": nprob / (e2e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "clocks": clocks,
+    }
+    batch.close()
+    for p in probs:
+        p.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -265,7 +378,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nsteps", type=int, default=0,
                     help="shorter time grid with the same step size (small profiling case); 0 = 100000 steps")
+    ap.add_argument("--workload", choices=["4q", "batched"], default="4q",
+                    help="4q: the benchmark workload (one 4-transmon problem); batched: 96 mixed problems")
+    ap.add_argument("--batch-per-shape", type=int, default=32)
     args = ap.parse_args()
+    if args.workload == "batched":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no CPU reference run"}))
+            return
+        run_batched(args)
+        return
     spec = S.config_4q(M=args.windows)
     if args.nsteps:
         spec = spec.replace(nsteps=args.nsteps, T=spec.T * args.nsteps / spec.nsteps,

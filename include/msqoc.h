@@ -189,6 +189,7 @@ msqoc_status msqoc_measure_fp64_peak(double* tflops);
  * problem's tiles are its own, only their scheduling changes. */
 #define MSQOC_BATCH_GRADIENT 1
 #define MSQOC_BATCH_GRAPH 2
+#define MSQOC_BATCH_SLOTS 4   /* concurrent subset evaluations (msqoc_batch_eval_subset) */
 
 typedef struct msqoc_batch msqoc_batch;
 
@@ -199,6 +200,15 @@ msqoc_status msqoc_batch_create(msqoc_problem* const* problems, int32_t n, int32
 msqoc_status msqoc_set_inputs(msqoc_problem* p, const double* alpha, const double* W, void* stream);
 msqoc_status msqoc_batch_eval_objective(msqoc_batch* b, void* stream);
 msqoc_status msqoc_batch_eval_gradient(msqoc_batch* b, void* stream);
+/* Evaluate only the problems members[0..n-1] (indices into the batch's problem array; objective
+ * or, with gradient != 0, objective and gradient) in shared launches, without a graph: the
+ * continuous-batching step of a server, where the set of ready problems changes every time.
+ * slot (0 <= slot < MSQOC_BATCH_SLOTS) selects the staging buffers of the subset's tile list;
+ * evaluations in flight at the same time must use different slots (and, to overlap on the
+ * device, different streams); a slot is reused once its previous tile list has been copied
+ * (the call waits for that).  A problem must not be in two evaluations in flight. */
+msqoc_status msqoc_batch_eval_subset(msqoc_batch* b, const int32_t* members, int32_t n,
+                                     int32_t gradient, int32_t slot, void* stream);
 /* Results of p's last batched evaluation (J_out and pen_out may be NULL; P_out may be NULL
  * for the gradient). */
 msqoc_status msqoc_get_objective(msqoc_problem* p, double* P_out, double* J_out, double* pen_out,

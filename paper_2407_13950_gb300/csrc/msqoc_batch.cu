@@ -25,13 +25,19 @@ struct msqoc_batch {
         ProbDev* pds = nullptr;
         Tile* tiles = nullptr;
         int* lanemap = nullptr;
+        std::vector<Tile> host_tiles;         // the group's tiles, longest windows first
+        std::vector<int> first, count;        // per member: its tiles in host_tiles (by member k)
+        Tile* slot_tiles[MSQOC_BATCH_SLOTS] = {};   // per slot: the tiles of a subset evaluation
+        Tile* slot_host[MSQOC_BATCH_SLOTS] = {};    // pinned staging of those tiles
     };
     std::vector<msqoc_problem*> probs;
+    std::vector<int> group_of, member_of;   // per problem: its group and index within it
     std::vector<Group> groups;
     int flags = 0;
     int device = 0;
     cudaStream_t cap = nullptr;                   // capture stream (graph mode)
     cudaGraphExec_t exec[2] = {nullptr, nullptr};  // [objective, gradient]
+    cudaEvent_t slot_done[MSQOC_BATCH_SLOTS] = {};  // the slot's staging copies have been read
 };
 
 namespace {
@@ -41,45 +47,56 @@ void free_batch(msqoc_batch* b) {
         if (g.pds) cudaFree(g.pds);
         if (g.tiles) cudaFree(g.tiles);
         if (g.lanemap) cudaFree(g.lanemap);
+        for (int k = 0; k < MSQOC_BATCH_SLOTS; ++k) {
+            if (g.slot_tiles[k]) cudaFree(g.slot_tiles[k]);
+            if (g.slot_host[k]) cudaFreeHost(g.slot_host[k]);
+        }
     }
+    for (auto& e : b->slot_done)
+        if (e) cudaEventDestroy(e);
     for (auto& e : b->exec)
         if (e) cudaGraphExecDestroy(e);
     if (b->cap) cudaStreamDestroy(b->cap);
 }
 
-// the launch sequence of one batched evaluation
-msqoc_status enqueue(msqoc_batch* b, bool grad, cudaStream_t s) {
+// The launch sequence of one batched evaluation of the problems `sel` (all when sel is empty);
+// tiles[g] / ntiles[g] are the tiles of group g to launch.
+msqoc_status enqueue(msqoc_batch* b, const std::vector<msqoc_problem*>& sel, Tile* const* tiles, const int* ntiles,
+                     bool grad, cudaStream_t s) {
     msqoc_status st;
-    for (msqoc_problem* p : b->probs)
+    for (msqoc_problem* p : sel)
         if ((st = launch_controls(p, s))) return st;
-    for (auto& g : b->groups) {
-        SweepArgs a = g.args;
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        SweepArgs a = b->groups[gi].args;
+        a.tiles = tiles[gi];
         a.mode = grad ? SWEEP_HISTORY : SWEEP_OBJECTIVE;
         a.seg = 0;
-        CUDA_TRY(launch_sweep(a, g.ntiles, s));
+        CUDA_TRY(launch_sweep(a, ntiles[gi], s));
     }
-    for (msqoc_problem* p : b->probs)
+    for (msqoc_problem* p : sel)
         if ((st = launch_terminal(p, grad, s))) return st;
     if (!grad) {
-        for (msqoc_problem* p : b->probs) {
+        for (msqoc_problem* p : sel) {
             double* o = p->out_dev;
             if ((st = launch_objective_outputs(p, o, o + 1, o + 2, s))) return st;
         }
         return MSQOC_OK;
     }
-    for (auto& g : b->groups) {
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        const auto& g = b->groups[gi];
         for (int seg = g.nseg_max - 1; seg >= 0; --seg) {
             SweepArgs a = g.args;
+            a.tiles = tiles[gi];
             a.seg = seg;
             if (g.nseg_max > 1) {
                 a.mode = SWEEP_RECOMPUTE;
-                CUDA_TRY(launch_sweep(a, g.ntiles, s));
+                CUDA_TRY(launch_sweep(a, ntiles[gi], s));
             }
             a.mode = SWEEP_ADJOINT;
-            CUDA_TRY(launch_sweep(a, g.ntiles, s));
+            CUDA_TRY(launch_sweep(a, ntiles[gi], s));
         }
     }
-    for (msqoc_problem* p : b->probs) {
+    for (msqoc_problem* p : sel) {
         const OutLayout ol = out_layout(p->pd.M, p->pd.d, p->nW);
         double* o = p->out_dev;
         if ((st = launch_gradient_outputs(p, o, o + ol.ga, p->pd.M > 1 ? o + ol.gw : nullptr, s))) return st;
@@ -87,15 +104,25 @@ msqoc_status enqueue(msqoc_batch* b, bool grad, cudaStream_t s) {
     return MSQOC_OK;
 }
 
+msqoc_status enqueue_all(msqoc_batch* b, bool grad, cudaStream_t s) {
+    std::vector<Tile*> tiles;
+    std::vector<int> ntiles;
+    for (auto& g : b->groups) {
+        tiles.push_back(g.tiles);
+        ntiles.push_back(g.ntiles);
+    }
+    return enqueue(b, b->probs, tiles.data(), ntiles.data(), grad, s);
+}
+
 msqoc_status eval(msqoc_batch* b, bool grad, cudaStream_t s) {
     if (grad && !(b->flags & MSQOC_BATCH_GRADIENT))
         return fail(MSQOC_ERR_INVALID_ARG, "batch was created without MSQOC_BATCH_GRADIENT");
-    if (!(b->flags & MSQOC_BATCH_GRAPH)) return enqueue(b, grad, s);
+    if (!(b->flags & MSQOC_BATCH_GRAPH)) return enqueue_all(b, grad, s);
     cudaGraphExec_t& ex = b->exec[grad ? 1 : 0];
     if (!ex) {
         // capture on a private stream; the first replay below runs it
         CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
-        const msqoc_status st = enqueue(b, grad, b->cap);
+        const msqoc_status st = enqueue_all(b, grad, b->cap);
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
         if (st) {
@@ -154,6 +181,13 @@ msqoc_status msqoc_batch_create(msqoc_problem* const* problems, int32_t n, int32
         }
         it->members.push_back(i);
     }
+    b->group_of.assign(n, 0);
+    b->member_of.assign(n, 0);
+    for (size_t gi = 0; gi < b->groups.size(); ++gi)
+        for (size_t k = 0; k < b->groups[gi].members.size(); ++k) {
+            b->group_of[b->groups[gi].members[k]] = static_cast<int>(gi);
+            b->member_of[b->groups[gi].members[k]] = static_cast<int>(k);
+        }
     for (auto& g : b->groups) {
         if (st) break;
         int nthreads = 32, cpt = 1, dmax = 1;
@@ -170,6 +204,8 @@ msqoc_status msqoc_batch_create(msqoc_problem* const* problems, int32_t n, int32
         for (size_t k = 0; k < g.members.size(); ++k) {
             const ProbDev& pd = b->probs[g.members[k]]->pd;
             const int map_base = static_cast<int>(maps.size() / nthreads);
+            g.first.push_back(static_cast<int>(tiles.size()));
+            g.count.push_back(pd.ntiles);
             for (int t = 0; t < pd.ntiles; ++t) {
                 Tile x = tile_at(t, pd.M, pd.E, pd.cb, static_cast<int>(k));
                 x.map += map_base;
@@ -183,6 +219,13 @@ msqoc_status msqoc_batch_create(msqoc_problem* const* problems, int32_t n, int32
                               mp + size_t(j) * nthreads);
             pds.push_back(pd);
         }
+        // longest windows first: the CTAs that take longest start in the first wave
+        auto tile_len = [&](const Tile& x) {
+            const ProbDev& pd = b->probs[g.members[x.prob]]->pd;
+            return (pd.nsteps + pd.M - 1) / pd.M;
+        };
+        g.host_tiles = tiles;
+        std::stable_sort(tiles.begin(), tiles.end(), [&](const Tile& x, const Tile& y) { return tile_len(x) > tile_len(y); });
         g.ntiles = static_cast<int>(tiles.size());
         cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&g.pds), pds.size() * sizeof(ProbDev));
         if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&g.tiles), tiles.size() * sizeof(Tile));
@@ -190,6 +233,10 @@ msqoc_status msqoc_batch_create(msqoc_problem* const* problems, int32_t n, int32
         if (e == cudaSuccess) e = cudaMemcpy(g.pds, pds.data(), pds.size() * sizeof(ProbDev), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(g.tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(g.lanemap, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice);
+        for (int k = 0; k < MSQOC_BATCH_SLOTS && e == cudaSuccess; ++k) {
+            e = cudaMalloc(reinterpret_cast<void**>(&g.slot_tiles[k]), tiles.size() * sizeof(Tile));
+            if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&g.slot_host[k]), tiles.size() * sizeof(Tile));
+        }
         if (e != cudaSuccess) {
             st = fail(e == cudaErrorMemoryAllocation ? MSQOC_ERR_OUT_OF_MEMORY : MSQOC_ERR_CUDA, "batch tables: %s",
                       cudaGetErrorString(e));
@@ -213,6 +260,9 @@ msqoc_status msqoc_batch_create(msqoc_problem* const* problems, int32_t n, int32
     }
     if (!st && (flags & MSQOC_BATCH_GRAPH) && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
         st = fail(MSQOC_ERR_CUDA, "capture stream creation failed");
+    for (int k = 0; k < MSQOC_BATCH_SLOTS && !st; ++k)
+        if (cudaEventCreateWithFlags(&b->slot_done[k], cudaEventDisableTiming) != cudaSuccess)
+            st = fail(MSQOC_ERR_CUDA, "event creation failed");
     if (st) {
         free_batch(b);
         delete b;
@@ -230,6 +280,48 @@ msqoc_status msqoc_batch_eval_objective(msqoc_batch* b, void* stream) {
 msqoc_status msqoc_batch_eval_gradient(msqoc_batch* b, void* stream) {
     if (!b) return fail(MSQOC_ERR_INVALID_ARG, "batch is NULL");
     return eval(b, true, static_cast<cudaStream_t>(stream));
+}
+
+msqoc_status msqoc_batch_eval_subset(msqoc_batch* b, const int32_t* members, int32_t n, int32_t gradient,
+                                     int32_t slot, void* stream) {
+    if (!b || !members || n < 1) return fail(MSQOC_ERR_INVALID_ARG, "batch or members is NULL / empty");
+    if (slot < 0 || slot >= MSQOC_BATCH_SLOTS) return fail(MSQOC_ERR_INVALID_ARG, "slot %d out of range", slot);
+    if (gradient && !(b->flags & MSQOC_BATCH_GRADIENT))
+        return fail(MSQOC_ERR_INVALID_ARG, "batch was created without MSQOC_BATCH_GRADIENT");
+    const int np = static_cast<int>(b->probs.size());
+    std::vector<char> seen(np, 0);
+    for (int i = 0; i < n; ++i) {
+        if (members[i] < 0 || members[i] >= np) return fail(MSQOC_ERR_INVALID_ARG, "member %d out of range", members[i]);
+        if (seen[members[i]]++) return fail(MSQOC_ERR_INVALID_ARG, "member %d listed twice", members[i]);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the slot's staging buffers are rewritten only after its previous copies were read
+    CUDA_TRY(cudaEventSynchronize(b->slot_done[slot]));
+    std::vector<msqoc_problem*> sel;
+    std::vector<Tile*> tiles(b->groups.size());
+    std::vector<int> ntiles(b->groups.size(), 0);
+    for (int i = 0; i < n; ++i) sel.push_back(b->probs[members[i]]);
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        auto& g = b->groups[gi];
+        Tile* h = g.slot_host[slot];
+        int cnt = 0;
+        for (int i = 0; i < n; ++i) {
+            if (b->group_of[members[i]] != static_cast<int>(gi)) continue;
+            const int k = b->member_of[members[i]];
+            std::copy(g.host_tiles.begin() + g.first[k], g.host_tiles.begin() + g.first[k] + g.count[k], h + cnt);
+            cnt += g.count[k];
+        }
+        auto tile_len = [&](const Tile& x) {
+            const ProbDev& pd = b->probs[g.members[x.prob]]->pd;
+            return (pd.nsteps + pd.M - 1) / pd.M;
+        };
+        std::stable_sort(h, h + cnt, [&](const Tile& x, const Tile& y) { return tile_len(x) > tile_len(y); });
+        if (cnt) CUDA_TRY(cudaMemcpyAsync(g.slot_tiles[slot], h, cnt * sizeof(Tile), cudaMemcpyHostToDevice, s));
+        tiles[gi] = g.slot_tiles[slot];
+        ntiles[gi] = cnt;
+    }
+    CUDA_TRY(cudaEventRecord(b->slot_done[slot], s));
+    return enqueue(b, sel, tiles.data(), ntiles.data(), gradient != 0, s);
 }
 
 msqoc_status msqoc_batch_destroy(msqoc_batch* b) {

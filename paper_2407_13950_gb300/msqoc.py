@@ -25,7 +25,7 @@ EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_eval_objective", "msqo
             "msqoc_destroy_problem", "msqoc_last_error", "msqoc_version", "msqoc_kernel_times",
             "msqoc_measure_fp64_peak", "msqoc_eval_objective_noalloc", "msqoc_batch_create",
             "msqoc_batch_eval_objective", "msqoc_batch_eval_gradient", "msqoc_batch_destroy", "msqoc_set_inputs",
-            "msqoc_get_objective", "msqoc_get_gradient"]
+            "msqoc_get_objective", "msqoc_get_gradient", "msqoc_batch_eval_subset"]
 BATCH_GRADIENT, BATCH_GRAPH = 1, 2
 KERNEL_NAMES = ["controls", "forward", "terminal", "adjoint", "finalize"]
 
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
             "msqoc_set_inputs": (i32, [vp, vp, vp, vp]),
             "msqoc_get_objective": (i32, [vp, vp, vp, vp, vp]),
             "msqoc_get_gradient": (i32, [vp, vp, vp, vp, vp]),
+            "msqoc_batch_eval_subset": (i32, [vp, vp, i32, i32, i32, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -315,6 +316,12 @@ class Batch:
 
     def eval_objective(self, stream=None):
         _check(load().msqoc_batch_eval_objective(self.handle, _stream_handle(stream)))
+
+    def eval_subset(self, members, gradient: bool = True, slot: int = 0, stream=None):
+        """Evaluate only the listed problems (indices into the batch) in shared launches."""
+        arr = (ctypes.c_int32 * len(members))(*[int(m) for m in members])
+        _check(load().msqoc_batch_eval_subset(self.handle, arr, len(members), 1 if gradient else 0, int(slot),
+                                              _stream_handle(stream)))
 
     def get_gradient(self, i: int, stream=None) -> dict:
         p = self.problems[i]
