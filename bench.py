@@ -366,6 +366,74 @@ def run_batched(args):
         print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Serving loop: sessions of 2/3/4/5 transmons (the 5-transmon ones with forced
+    checkpointing), a Poisson stream of objective/gradient requests over them, served with
+    continuous batching and, on the same request stream, one request at a time."""
+    import torch
+    from paper_2407_13950_gb300 import msqoc, serving
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    per = args.sessions_per_shape
+    shapes = [(S.config_2q(), 0), (S.config_3q(), 0), (S.config_4q(), 0), (S.config_5q(), 64)]
+    free, _ = torch.cuda.mem_get_info()
+    srv = serving.Server(device_budget_bytes=int(0.85 * free))
+    specs, refused = [], 0
+    for k in range(per):
+        for base, K in shapes:
+            try:
+                srv.admit(base, ckpt_interval=K)
+                specs.append(base)
+            except serving.NotAdmitted:
+                refused += 1
+    # warm-up: one gradient request per session (kernel set-up, first-touch of the histories)
+    warm = [serving.Request(session=i, gradient=True, alpha=S.random_alpha(sp, 7, problem=i),
+                            W=S.random_W(sp, 7, problem=i) if sp.M > 1 else None) for i, sp in enumerate(specs)]
+    srv.run(warm)
+    reqs = serving.poisson_requests(specs, rate=args.rate, duration=args.serve_seconds, seed=1)
+    sampler = ClockSampler(local)
+    sampler.start()
+    done = srv.run(reqs, duration=args.serve_seconds)
+    clocks = sampler.stop()
+    reqs_p = serving.poisson_requests(specs, rate=args.rate, duration=args.serve_seconds, seed=1)
+    done_p = srv.run_plain(reqs_p, duration=args.serve_seconds)
+
+    def by_shape(dn):
+        c = {}
+        for r in dn:
+            q = specs[r.session].q
+            c[f"{q}q"] = c.get(f"{q}q", 0) + 1
+        return c
+
+    def lat_by_shape(dn):
+        out = {}
+        for q in sorted({sp.q for sp in specs}):
+            sub = [r for r in dn if specs[r.session].q == q]
+            if sub:
+                out[f"{q}q"] = serving.latency_summary(sub)["from_ready"]
+        return out
+
+    line = {
+        "metric": "served objective/gradient evals/s", "value": len(done) / args.serve_seconds, "unit": "evals/s",
+        "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": args.serve_seconds * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"serving: {len(specs)} sessions ({per} each of 2q, 3q, 4q, 5q; 5q with checkpoint "
+                               f"interval 64), Poisson {args.rate:.0f} requests/s for {args.serve_seconds:.0f} s, "
+                               f"half gradients", "admitted": len(specs), "refused": refused,
+                   "budget_bytes": srv.budget, "used_bytes": srv.used},
+        "offered": len(reqs), "completed": len(done), "completed_by_shape": by_shape(done),
+        "latency_ms": serving.latency_summary(done), "latency_from_ready_by_shape_ms": lat_by_shape(done),
+        "plain": {"value": len(done_p) / args.serve_seconds, "unit": "evals/s", "completed": len(done_p),
+                  "completed_by_shape": by_shape(done_p), "latency_ms": serving.latency_summary(done_p),
+                  "latency_from_ready_by_shape_ms": lat_by_shape(done_p)},
+        "clocks": clocks,
+    }
+    srv.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -378,10 +446,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nsteps", type=int, default=0,
                     help="shorter time grid with the same step size (small profiling case); 0 = 100000 steps")
-    ap.add_argument("--workload", choices=["4q", "batched"], default="4q",
-                    help="4q: the benchmark workload (one 4-transmon problem); batched: 96 mixed problems")
+    ap.add_argument("--workload", choices=["4q", "batched", "serving"], default="4q",
+                    help="4q: the benchmark workload (one 4-transmon problem); batched: 96 mixed problems; "
+                         "serving: continuous batching of a Poisson request stream")
     ap.add_argument("--batch-per-shape", type=int, default=32)
+    ap.add_argument("--sessions-per-shape", type=int, default=16)
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: offered requests per second")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
     args = ap.parse_args()
+    if args.workload == "serving":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no CPU reference run"}))
+            return
+        run_serving(args)
+        return
     if args.workload == "batched":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no CPU reference run"}))

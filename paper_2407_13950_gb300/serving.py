@@ -1,0 +1,260 @@
+"""Continuous-batching evaluation server for many concurrent pulse optimisations.
+
+Each session (one optimiser) owns a resident problem: its model tables, its controls and window
+states and its scratch stay on the device between optimiser iterations; a request carries the
+optimiser's new iterate (alpha, W) and asks for the objective or the objective and gradient.
+Sessions are admitted while their device memory (including the midpoint history a gradient
+needs) fits the server's budget; a session that does not fit raises ``NotAdmitted``.
+
+Scheduling (host side, this module): requests join their session's queue on arrival; a session
+has at most one request on the GPU (an optimiser needs the previous result before its next
+step), so the head of every idle session's queue is *ready*.  Whenever one of the
+``MSQOC_BATCH_SLOTS`` dispatch slots is free, the scheduler takes the (shape, kind) class of the
+oldest ready request and dispatches every ready request of that class as one subset of the
+server's batch (``msqoc_batch_eval_subset``): their sweeps share launches.  Each class has at
+most one dispatch in flight and each slot its own CUDA stream, with smaller shapes on
+higher-priority streams, so requests that arrive while others run are admitted as slots free
+up and their kernels overlap on the device.  All arithmetic runs in the library's kernels;
+this module only moves pointers, streams and events.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import msqoc
+
+SLOTS = 4   # MSQOC_BATCH_SLOTS
+
+
+class NotAdmitted(RuntimeError):
+    """The session's device memory does not fit the server's budget."""
+
+
+@dataclasses.dataclass
+class Request:
+    session: int
+    gradient: bool
+    alpha: np.ndarray
+    W: Optional[np.ndarray]
+    arrival: float = 0.0          # seconds from the start of Server.run
+    ready: float = math.nan       # reached the head of an idle session's queue
+    dispatched: float = math.nan
+    done: float = math.nan
+    result: Optional[dict] = None
+
+
+def eval_flops(spec, gradient: bool) -> float:
+    """Algorithmic FP64 flops of one evaluation (one H-apply per implicit step, the 2Ubar - U
+    update, and for the gradient the adjoint sweep and its inner products): the scheduler's
+    cost estimate of a request."""
+    nnz = spec.q * 2 * spec.N * (spec.L - 1) // spec.L
+    f_step = 8 * nnz + 6 * spec.N
+    fwd = spec.E * spec.nsteps * f_step
+    return float(fwd + (spec.E * spec.nsteps * (f_step + 8 * nnz) if gradient else 0))
+
+
+class Server:
+    """Sessions and the continuous-batching loop.
+
+    Dispatch policy: a dispatch takes the ready requests of one (shape, kind) class, oldest
+    first, up to `dispatch_flops` of estimated work (at least one request), so that one
+    dispatch of a large shape holds the GPU for a bounded time.  Classes whose requests cost
+    less than `cheap_flops` each run on high-priority streams (their CTAs are scheduled ahead
+    of the large shapes' pending ones); a class whose oldest ready request has waited longer
+    than `age_limit` seconds is promoted to a high-priority stream too, so large shapes are not
+    starved under a stream of small requests."""
+
+    def __init__(self, device_budget_bytes: int, dispatch_flops: float = 2e11, cheap_flops: float = 1e10,
+                 age_limit: float = 1.0):
+        self.budget = int(device_budget_bytes)
+        self.used = 0
+        self.sessions: List[msqoc.Problem] = []
+        self.batch: Optional[msqoc.Batch] = None
+        self.dispatch_flops = dispatch_flops
+        self.cheap_flops = cheap_flops
+        self.age_limit = age_limit
+
+    # ------------------------------------------------------------------ sessions
+    def admit(self, spec, ckpt_interval: int = 0, solver: int = msqoc.SOLVER_DEFAULT) -> int:
+        """Create a session for `spec` if its device memory fits; returns the session id."""
+        p = msqoc.Problem(spec, ckpt_interval=ckpt_interval, solver=solver)
+        if self.used + p.device_bytes > self.budget:
+            need = p.device_bytes
+            p.close()
+            raise NotAdmitted(f"session needs {need} bytes; {self.budget - self.used} of {self.budget} free")
+        self.used += p.device_bytes
+        self.sessions.append(p)
+        if self.batch is not None:
+            self.batch.close()
+            self.batch = None
+        return len(self.sessions) - 1
+
+    def close(self):
+        if self.batch is not None:
+            self.batch.close()
+            self.batch = None
+        for p in self.sessions:
+            p.close()
+        self.sessions = []
+        self.used = 0
+
+    def _shape(self, sid: int):
+        sp = self.sessions[sid].spec
+        return (sp.L, sp.q)
+
+    # ------------------------------------------------------------------ serving
+    def run(self, requests: Sequence[Request], duration: Optional[float] = None) -> List[Request]:
+        """Serve `requests` (sorted by arrival time, seconds from now).  Stops when all are done,
+        or at `duration` seconds (requests then still queued or in flight are not completed).
+        Returns the completed requests with their results and timestamps."""
+        import torch
+        if self.batch is None:
+            self.batch = msqoc.Batch(self.sessions, gradient=True)
+        b = self.batch
+        # per slot a normal and a high-priority stream (a lower number is a higher priority;
+        # CUDA clamps values beyond the device's range)
+        streams = [(torch.cuda.Stream(priority=0), torch.cuda.Stream(priority=-8)) for _ in range(SLOTS)]
+        cost = [(eval_flops(p.spec, False), eval_flops(p.spec, True)) for p in self.sessions]
+        queues: Dict[int, collections.deque] = {s: collections.deque() for s in range(len(self.sessions))}
+        busy = [False] * len(self.sessions)
+        inflight = {}            # slot -> (event, class, [requests])
+        busy_class = set()
+        free_slots = list(range(SLOTS))
+        done: List[Request] = []
+        t0 = time.perf_counter()
+        nxt = 0
+        n = len(requests)
+        while len(done) < n:
+            now = time.perf_counter() - t0
+            if duration is not None and now >= duration:
+                break
+            progressed = False
+            while nxt < n and requests[nxt].arrival <= now:
+                r = requests[nxt]
+                queues[r.session].append(r)
+                nxt += 1
+                progressed = True
+            # completions
+            for slot in list(inflight):
+                ev, cls, reqs = inflight[slot]
+                if ev.query():
+                    tdone = time.perf_counter() - t0
+                    for r in reqs:
+                        r.result = b.get_gradient(r.session) if r.gradient else b.get_objective(r.session)
+                        r.done = tdone
+                        busy[r.session] = False
+                    done.extend(reqs)
+                    del inflight[slot]
+                    busy_class.discard(cls)
+                    free_slots.append(slot)
+                    progressed = True
+            # dispatch: oldest ready request's class, all ready requests of that class
+            while free_slots:
+                ready = []
+                for s, q in queues.items():
+                    if q and not busy[s]:
+                        r = q[0]
+                        if math.isnan(r.ready):
+                            r.ready = max(r.arrival, now)
+                        ready.append(r)
+                ready = [r for r in ready if (self._shape(r.session), r.gradient) not in busy_class]
+                if not ready:
+                    break
+                oldest = min(ready, key=lambda r: r.arrival)
+                cls = (self._shape(oldest.session), oldest.gradient)
+                sel, work = [], 0.0
+                for r in sorted((r for r in ready if (self._shape(r.session), r.gradient) == cls),
+                                key=lambda r: r.arrival):
+                    c = cost[r.session][1 if r.gradient else 0]
+                    if sel and work + c > self.dispatch_flops:
+                        break
+                    sel.append(r)
+                    work += c
+                slot = free_slots.pop()
+                cheap = cost[oldest.session][1 if oldest.gradient else 0] < self.cheap_flops
+                aged = now - oldest.ready > self.age_limit
+                stream = streams[slot][1 if (cheap or aged) else 0]
+                for r in sel:
+                    queues[r.session].popleft()
+                    busy[r.session] = True
+                    r.dispatched = now
+                    b.set_inputs(r.session, r.alpha, r.W, stream=stream)
+                b.eval_subset([r.session for r in sel], gradient=cls[1], slot=slot, stream=stream)
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                inflight[slot] = (ev, cls, sel)
+                busy_class.add(cls)
+                progressed = True
+            if not progressed:
+                time.sleep(0.0002)
+        torch.cuda.synchronize()
+        return done
+
+    def run_plain(self, requests: Sequence[Request], duration: Optional[float] = None) -> List[Request]:
+        """The same requests one at a time in arrival order, each its own synchronous
+        evaluation (one problem per launch sequence, nothing overlapped)."""
+        t0 = time.perf_counter()
+        done: List[Request] = []
+        for r in requests:
+            now = time.perf_counter() - t0
+            if duration is not None and now >= duration:
+                break
+            if r.arrival > now:
+                time.sleep(r.arrival - now)
+                now = time.perf_counter() - t0
+            r.ready = r.dispatched = now
+            p = self.sessions[r.session]
+            r.result = p.eval_gradient(r.alpha, r.W) if r.gradient else p.eval_objective(r.alpha, r.W)
+            r.done = time.perf_counter() - t0
+            done.append(r)
+        return done
+
+
+def poisson_requests(sessions: Sequence, rate: float, duration: float, seed: int,
+                     gradient_fraction: float = 0.5, inputs=None, variants: int = 2) -> List[Request]:
+    """A Poisson stream of `rate` requests/s for `duration` s over the given sessions (uniformly
+    drawn), objective or gradient with the given split.  inputs(session, k) gives the k-th
+    iterate (alpha, W) of a session; by default each session cycles through `variants` seeded
+    synthetic iterates, generated once (an iterate of the 5-transmon workload is 32 MB, so a
+    long stream must not hold one per request)."""
+    from . import synthetic as S
+    rng = np.random.default_rng(seed)
+    cache = {}
+
+    def default_inputs(s, k):
+        key = (s, k % variants)
+        if key not in cache:
+            sp = sessions[s]
+            v = seed + 1000 * key[1]
+            cache[key] = (S.random_alpha(sp, v, problem=s), S.random_W(sp, v, problem=s) if sp.M > 1 else None)
+        return cache[key]
+
+    get = inputs if inputs is not None else default_inputs
+    t, out, count = 0.0, [], collections.Counter()
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        s = int(rng.integers(len(sessions)))
+        k = count[s]
+        count[s] += 1
+        a, W = get(s, k)
+        out.append(Request(session=s, gradient=bool(rng.random() < gradient_fraction), alpha=a,
+                           W=W if sessions[s].M > 1 else None, arrival=t))
+    return out
+
+
+def latency_summary(done: Sequence[Request]) -> dict:
+    """p50/p99 (ms) from arrival and from readiness (head of an idle session's queue)."""
+    if not done:
+        return {}
+    arr = np.array([r.done - r.arrival for r in done]) * 1e3
+    rdy = np.array([r.done - r.ready for r in done]) * 1e3
+    return {"from_arrival": {"p50": float(np.percentile(arr, 50)), "p99": float(np.percentile(arr, 99))},
+            "from_ready": {"p50": float(np.percentile(rdy, 50)), "p99": float(np.percentile(rdy, 99))}}
