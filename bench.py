@@ -177,7 +177,10 @@ def run_ours(args, spec):
     gW_d = torch.zeros(spec.nW, device=dev, dtype=torch.float64)
     stream = torch.cuda.current_stream(dev)
     solver = msqoc.SOLVER_FP64 if args.solver == "fp64" else msqoc.SOLVER_MIXED
-    prob = msqoc.Problem(spec, solver=solver, col_block=args.col_block, profile=True)
+    # tile width: the library's model (0), a given width, or measured by the autotuner (-1)
+    tuned, tune_ms = msqoc.autotune(spec, alpha=alpha, probe_steps=64, solver=solver)
+    col_block = tuned if args.col_block < 0 else args.col_block
+    prob = msqoc.Problem(spec, solver=solver, col_block=col_block, profile=True)
     peak_tflops = msqoc.measure_fp64_peak()
 
     for _ in range(args.warmup):
@@ -229,7 +232,9 @@ def run_ours(args, spec):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": spec.name, "N": spec.N, "E": spec.E, "nsteps": spec.nsteps, "windows": spec.M,
-                   "T_ns": spec.T, "d": spec.d, "solver": args.solver, "col_block": args.col_block or "auto",
+                   "T_ns": spec.T, "d": spec.d, "solver": args.solver,
+                   "col_block": col_block if col_block > 0 else f"model ({prob.col_block})",
+                   "autotune": {"best": tuned, "ms_per_probe_eval": tune_ms},
                    "l2": "inputs larger than L2 (2 GB midpoint history per evaluation)",
                    "parallelism": f"independent problem per GPU x{world}"},
         "roofline": {"bound": "alu", "kernel": f"k_sweep ({dom})", "achieved": achieved, "peak": peak_tflops,
@@ -442,7 +447,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--windows", type=int, default=64)
     ap.add_argument("--solver", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--col-block", type=int, default=0)
+    ap.add_argument("--col-block", type=int, default=0,
+                    help="columns per sweep tile: 0 = the library's model, -1 = measured by the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nsteps", type=int, default=0,
                     help="shorter time grid with the same step size (small profiling case); 0 = 100000 steps")

@@ -136,6 +136,12 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
  * NULL. */
 msqoc_status msqoc_query(const msqoc_problem* p, int64_t* d, int64_t* nW, size_t* device_bytes);
 
+/* Sweep layout of a problem: columns per tile, tiles (CTAs) per sweep launch, threads per
+ * tile, and the checkpoint interval K in use (after automatic choices).  Any pointer may be
+ * NULL. */
+msqoc_status msqoc_query_layout(const msqoc_problem* p, int32_t* col_block, int32_t* tiles,
+                                int32_t* threads, int32_t* ckpt_interval);
+
 /* Objective only (forward sweep of every window, Eq. penalty-fcn).  P_out: 1 double;
  * J_out (1 double) and pen_out (M-1 doubles) may be NULL. */
 msqoc_status msqoc_eval_objective(msqoc_problem* p, const double* alpha, const double* W,
@@ -256,6 +262,21 @@ msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H, const msqo
                                           int32_t nwindows, double mu, int32_t solver,
                                           const double* alpha, const double* W, double* P_out,
                                           double* J_out, double* pen_out, void* stream);
+
+/* Tile width by measurement (not an operation of the paper): for every admissible number of
+ * columns per sweep tile, a problem of the same description, step size and window count but
+ * only probe_steps steps per window is created with that width and its objective + gradient is
+ * timed (one warm-up, two timed evaluations, CUDA events on the default stream).  *col_block
+ * receives the fastest width (use it as msqoc_options.col_block); widths[i], ms[i] (i <
+ * *n_out <= max_out; may be NULL) the widths tried and their milliseconds per evaluation.
+ * alpha: d control coefficients (host) of a typical iterate (the iteration counts of the step
+ * solver depend on the control amplitude); NULL = alternating +-2 pi 0.002 rad/ns.  opt:
+ * solver and checkpoint interval as for msqoc_create_problem (col_block is ignored).
+ * Allocates and frees temporary problems; synchronizes the device. */
+msqoc_status msqoc_autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, double T,
+                            int64_t nsteps, int32_t nwindows, double mu, const msqoc_options* opt,
+                            const double* alpha, int32_t probe_steps, int32_t* col_block,
+                            int32_t* widths, float* ms, int32_t max_out, int32_t* n_out);
 
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t msqoc_version(void);

@@ -532,6 +532,16 @@ msqoc_status msqoc_query(const msqoc_problem* p, int64_t* d, int64_t* nW, size_t
     return MSQOC_OK;
 }
 
+msqoc_status msqoc_query_layout(const msqoc_problem* p, int32_t* col_block, int32_t* tiles, int32_t* threads,
+                                int32_t* ckpt_interval) {
+    if (!p) return fail(MSQOC_ERR_INVALID_ARG, "problem is NULL");
+    if (col_block) *col_block = p->pd.cb;
+    if (tiles) *tiles = p->pd.ntiles;
+    if (threads) *threads = p->pd.nthreads;
+    if (ckpt_interval) *ckpt_interval = p->ckpt_interval;
+    return MSQOC_OK;
+}
+
 msqoc_status msqoc_destroy_problem(msqoc_problem* p) {
     if (!p) return MSQOC_OK;
     cudaDeviceSynchronize();
@@ -737,6 +747,103 @@ msqoc_status msqoc_kernel_times(msqoc_problem* p, float* ms) {
 }
 
 }  // extern "C"
+// ------------------------------------------------------------------ autotuning the tile width
+extern "C" msqoc_status msqoc_autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps,
+                                       int32_t nwindows, double mu, const msqoc_options* opt, const double* alpha,
+                                       int32_t probe_steps, int32_t* col_block, int32_t* widths, float* ms,
+                                       int32_t max_out, int32_t* n_out) {
+    if (!col_block) return fail(MSQOC_ERR_INVALID_ARG, "col_block is NULL");
+    *col_block = 0;
+    if (n_out) *n_out = 0;
+    msqoc_status st = check_description(H, C, T, nsteps, nwindows);
+    if (st != MSQOC_OK) return st;
+    if (probe_steps < 1) return fail(MSQOC_ERR_INVALID_ARG, "probe_steps %d < 1", probe_steps);
+    msqoc_options o{};
+    if (opt) o = *opt;
+    o.profile = 0;
+    const int solver = o.solver == MSQOC_SOLVER_FP64 ? SOLVER_FP64 : SOLVER_MIXED;
+    // the probe: same shape, step size and window count, probe_steps steps per window
+    const int64_t psteps = std::min<int64_t>(nsteps, int64_t(nwindows) * probe_steps);
+    const double pT = T * double(psteps) / double(nsteps);
+    ProbDev pd{};
+    st = shape_problem(H, C, pT, psteps, nwindows, mu, solver, 1, 1, pd);
+    if (st != MSQOC_OK && st != MSQOC_ERR_INVALID_ARG) return st;
+    std::vector<double> a(static_cast<size_t>(pd.d));
+    for (int j = 0; j < pd.d; ++j)   // default iterate: alternating amplitudes of the workloads' scale
+        a[j] = alpha ? alpha[j] : ((j & 1) ? -1.0 : 1.0) * 2.0 * M_PI * 0.002;
+    const size_t nW = 2 * size_t(pd.N) * pd.E * size_t(nwindows - 1);
+    std::vector<double> W(std::max<size_t>(nW, 2), 0.0), ga(pd.d), gW(std::max<size_t>(nW, 2));
+    double* dbuf = nullptr;
+    CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&dbuf), (pd.d + nW + 2) * sizeof(double)));
+    double* d_alpha = dbuf;
+    double* d_W = dbuf + pd.d;
+    double* d_out = nullptr;
+    cudaError_t ce = cudaMalloc(reinterpret_cast<void**>(&d_out), (1 + pd.d + nW + 2) * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMemcpy(d_alpha, a.data(), pd.d * sizeof(double), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemset(d_W, 0, (nW + 2) * sizeof(double));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaFree(dbuf);
+        if (d_out) cudaFree(d_out);
+        if (e0) cudaEventDestroy(e0);
+        return fail(MSQOC_ERR_CUDA, "autotune buffers: %s", cudaGetErrorString(ce));
+    }
+    double* o_P = d_out;
+    double* o_ga = d_out + 2;   // keep grad_W 16-byte aligned: it starts at an even offset
+    double* o_gW = o_ga + ((pd.d + 1) & ~1);
+    float best_ms = 0.f;
+    int best = 0, nrec = 0;
+    for (int cb = std::min(pd.E, MAX_TILE_THREADS / pd.F); cb >= 1 && st == MSQOC_OK; --cb) {
+        if (!tile_width_ok(cb, pd.E, pd.F, pd.q, pd.L, pd.N, pd.d, solver)) continue;
+        msqoc_options oc = o;
+        oc.col_block = cb;
+        msqoc_problem* p = nullptr;
+        msqoc_status cs = msqoc_create_problem(H, C, nullptr, pT, psteps, nwindows, mu, &oc, &p);
+        if (cs != MSQOC_OK) {
+            st = cs;
+            break;
+        }
+        float t = 0.f;
+        for (int it = 0; it < 3 && cs == MSQOC_OK; ++it) {   // one warm-up, two timed
+            if (it == 1) cudaEventRecord(e0, nullptr);
+            cs = msqoc_eval_gradient(p, d_alpha, nwindows > 1 ? d_W : nullptr, o_P, o_ga, nwindows > 1 ? o_gW : nullptr,
+                                     nullptr);
+        }
+        if (cs == MSQOC_OK) {
+            cudaEventRecord(e1, nullptr);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&t, e0, e1);
+            t *= 0.5f;
+            cs = check_status_sync(p, nullptr);
+        }
+        msqoc_destroy_problem(p);
+        if (cs != MSQOC_OK) {
+            st = cs;
+            break;
+        }
+        if (widths && ms && nrec < max_out) {
+            widths[nrec] = cb;
+            ms[nrec] = t;
+        }
+        ++nrec;
+        if (best == 0 || t < best_ms) {
+            best = cb;
+            best_ms = t;
+        }
+    }
+    cudaFree(dbuf);
+    cudaFree(d_out);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != MSQOC_OK) return st;
+    if (best == 0) return fail(MSQOC_ERR_UNSUPPORTED, "no admissible tile width");
+    *col_block = best;
+    if (n_out) *n_out = std::min(nrec, max_out);
+    return MSQOC_OK;
+}
+
 // ------------------------------------------------------------------ objective without allocation
 // Scratch of msqoc_eval_objective_noalloc: every table and intermediate of one objective
 // evaluation, carved into 256-byte-aligned regions.  Static device storage: the module holds

@@ -21,11 +21,11 @@ STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OUT_OF_MEMORY", -3: "NOT_ADMITT
                 -5: "TIMEOUT", -6: "UNSUPPORTED", -7: "INTERNAL"}
 SOLVER_DEFAULT, SOLVER_FP64, SOLVER_MIXED = 0, 1, 2
 
-EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_eval_objective", "msqoc_eval_gradient",
+EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_query_layout", "msqoc_eval_objective", "msqoc_eval_gradient",
             "msqoc_destroy_problem", "msqoc_last_error", "msqoc_version", "msqoc_kernel_times",
             "msqoc_measure_fp64_peak", "msqoc_eval_objective_noalloc", "msqoc_batch_create",
             "msqoc_batch_eval_objective", "msqoc_batch_eval_gradient", "msqoc_batch_destroy", "msqoc_set_inputs",
-            "msqoc_get_objective", "msqoc_get_gradient", "msqoc_batch_eval_subset"]
+            "msqoc_get_objective", "msqoc_get_gradient", "msqoc_batch_eval_subset", "msqoc_autotune"]
 BATCH_GRADIENT, BATCH_GRAPH = 1, 2
 KERNEL_NAMES = ["controls", "forward", "terminal", "adjoint", "finalize"]
 
@@ -73,6 +73,7 @@ def load(build_if_missing: bool = True):
         sigs = {
             "msqoc_create_problem": (i32, [vp, vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, vp, vp]),
             "msqoc_query": (i32, [vp, vp, vp, vp]),
+            "msqoc_query_layout": (i32, [vp, vp, vp, vp, vp]),
             "msqoc_eval_objective": (i32, [vp, vp, vp, vp, vp, vp, vp]),
             "msqoc_eval_gradient": (i32, [vp, vp, vp, vp, vp, vp, vp]),
             "msqoc_destroy_problem": (i32, [vp]),
@@ -90,6 +91,8 @@ def load(build_if_missing: bool = True):
             "msqoc_get_objective": (i32, [vp, vp, vp, vp, vp]),
             "msqoc_get_gradient": (i32, [vp, vp, vp, vp, vp]),
             "msqoc_batch_eval_subset": (i32, [vp, vp, i32, i32, i32, vp]),
+            "msqoc_autotune": (i32, [vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, vp, vp, i32, vp, vp, vp,
+                                     i32, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -169,6 +172,9 @@ class Problem:
                                         float(spec.T), int(spec.nsteps), int(spec.M), float(spec.mu),
                                         ctypes.byref(O), ctypes.byref(h)))
         self.handle = h
+        cb, nt, th, K = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.msqoc_query_layout(h, ctypes.byref(cb), ctypes.byref(nt), ctypes.byref(th), ctypes.byref(K)))
+        self.col_block, self.tiles, self.threads, self.ckpt_interval = cb.value, nt.value, th.value, K.value
         d, nW, nbytes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
         _check(lib.msqoc_query(h, ctypes.byref(d), ctypes.byref(nW), ctypes.byref(nbytes)))
         self.d, self.nW, self.device_bytes = d.value, nW.value, nbytes.value
@@ -339,3 +345,20 @@ class Batch:
         _check(load().msqoc_get_objective(p.handle, _ptr(P), _ptr(J), _ptr(pen) if p.spec.M > 1 else None,
                                           _stream_handle(stream)))
         return {"P": float(P[0]), "J": float(J[0]), "pen": pen[:p.spec.M - 1].copy()}
+
+
+def autotune(spec, alpha=None, probe_steps: int = 64, solver: int = SOLVER_DEFAULT, ckpt_interval: int = 0):
+    """Columns per sweep tile by measurement (msqoc_autotune): returns (best width,
+    {width: ms per probe evaluation})."""
+    lib = load()
+    desc = _Description(spec)
+    O = Options(solver, 0, ckpt_interval, 0)
+    a = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float64)
+    best = ctypes.c_int32()
+    widths = (ctypes.c_int32 * 64)()
+    ms = (ctypes.c_float * 64)()
+    n = ctypes.c_int32()
+    _check(lib.msqoc_autotune(ctypes.byref(desc.H), ctypes.byref(desc.C), float(spec.T), int(spec.nsteps),
+                              int(spec.M), float(spec.mu), ctypes.byref(O), None if a is None else a.ctypes.data,
+                              int(probe_steps), ctypes.byref(best), widths, ms, 64, ctypes.byref(n)))
+    return best.value, {int(widths[i]): float(ms[i]) for i in range(n.value)}

@@ -1,0 +1,26 @@
+"""The tile-width autotuner: it times every admissible width on a probe of the problem and
+returns one of them; a problem built with the returned width evaluates correctly."""
+import pytest
+
+import oracle
+from paper_2407_13950_gb300 import msqoc
+from paper_2407_13950_gb300 import synthetic as S
+
+from gpu_helpers import assert_grad_close, assert_objective_close
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_returns_a_measured_admissible_width():
+    spec = S.transmon_spec(3, 30.0, 2001, 7, 8)
+    alpha, W = S.random_alpha(spec, 61), S.random_W(spec, 61)
+    best, times = msqoc.autotune(spec, alpha=alpha, probe_steps=16)
+    assert best in times and len(times) >= 3
+    assert all(t > 0 for t in times.values())
+    assert times[best] == min(times.values())
+    with msqoc.Problem(spec, col_block=best) as p:
+        got = p.eval_gradient(alpha, W)
+    want = oracle.evaluate(spec, alpha, W)
+    assert_objective_close(got["P"], want["P"])
+    assert_grad_close(got["grad_alpha"], want["grad_alpha"])
+    assert_grad_close(got["grad_W"], want["grad_W"])
