@@ -14,8 +14,9 @@ namespace msqoc {
 //     |P rhs| (FP32 rounding of the right-hand side and of the sweeps, times the contraction,
 //     plus truncation); each FP64 residual + FP32 correction multiplies it by
 //     phi = c u32 + rho^(j2+1).  c = 4 rounding units per FP32 sweep output; target: the FP64
-//     unit roundoff 2^-53.  Extra FP32 sweeps are cheaper than an FP64 pass, so j1 and j2 grow
-//     (by up to 2) before a second refinement pass is added.
+//     unit roundoff 2^-53.  An FP64 pass costs far more than FP32 sweeps, so the fewest passes R
+//     are taken first, then the fewest FP32 sweeps j1 + j2 (each sweep is a barrier of the
+//     tile), then the smaller j2.
 //   bad: rho >= 1/2, outside the range the counts are derived for.
 __device__ inline int step_counts(int solver, float rho) {
     int a = 1, b = 1, r = 1, bad = 0;
@@ -26,21 +27,24 @@ __device__ inline int step_counts(int solver, float rho) {
             a = a < 1 ? 1 : (a > 60 ? 60 : a);
         } else {
             const float u32 = 5.9604645e-8f, c = 4.f, target = 1.1102230e-16f;
-            const int j0 = max(1, min(30, int(ceilf(logf(u32) / lr))));
+            const int j0 = max(1, min(30, int(ceilf(logf(u32) / lr))));   // rho^j0 <= u32
             r = 0;
             for (int pass = 1; pass <= 6 && r == 0; ++pass) {
-                for (int extra = 0; extra <= 2 && r == 0; ++extra) {
-                    const int ja = min(30, j0 + extra), jb = max(1, min(30, j0 - 1 + extra));
+                int best = 0;
+                for (int ja = 1; ja <= j0 + 2; ++ja) {
                     const float e1 = c * u32 * rho + __powf(rho, float(ja + 1));
-                    const float phi = c * u32 + __powf(rho, float(jb + 1));
-                    float e = e1;
-                    for (int t = 0; t < pass; ++t) e *= phi;
-                    if (e <= target) {
-                        a = ja;
-                        b = jb;
-                        r = pass;
+                    for (int jb = 1; jb <= j0 + 1; ++jb) {
+                        const float phi = c * u32 + __powf(rho, float(jb + 1));
+                        float e = e1;
+                        for (int t = 0; t < pass; ++t) e *= phi;
+                        if (e <= target && (best == 0 || ja + jb < best || (ja + jb == best && jb < b))) {
+                            best = ja + jb;
+                            a = ja;
+                            b = jb;
+                        }
                     }
                 }
+                if (best) r = pass;
             }
             if (r == 0) {
                 a = min(30, j0 + 2);
