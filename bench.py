@@ -97,6 +97,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+SWEEP_SOURCES = ["msqoc_sweep.cuh", "inst_sweep.cu", "msqoc_internal.h"]
+PROFILE = os.path.join(ROOT, "profiles", "k_sweep_4q_small_full.md")
+
+
+def sweep_traffic(kernel: str):
+    """DRAM bytes per launch of a sweep kernel from the committed ncu summary, or None when the
+    kernel sources changed since that capture (their digest differs)."""
+    import hashlib
+    import re
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    h = hashlib.sha256()
+    for fn in SWEEP_SOURCES:
+        h.update(fn.encode())
+        with open(os.path.join(ROOT, "paper_2407_13950_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    m = re.search(r"sources_sha256: ([0-9a-f]+)", text)
+    t = re.search(rf"{kernel}=([0-9.e+]+)", text)
+    if not m or not t or m.group(1) != h.hexdigest()[:16]:
+        return None
+    return float(t.group(1))
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -178,7 +203,8 @@ def run_ours(args, spec):
     stream = torch.cuda.current_stream(dev)
     solver = msqoc.SOLVER_FP64 if args.solver == "fp64" else msqoc.SOLVER_MIXED
     # tile width: the library's model (0), a given width, or measured by the autotuner (-1)
-    tuned, tune_ms = msqoc.autotune(spec, alpha=alpha, probe_steps=64, solver=solver)
+    tuned, tune_ms = (msqoc.autotune(spec, alpha=alpha, probe_steps=64, solver=solver) if args.col_block < 0
+                      else (None, None))
     col_block = tuned if args.col_block < 0 else args.col_block
     prob = msqoc.Problem(spec, solver=solver, col_block=col_block, profile=True)
     peak_tflops = msqoc.measure_fp64_peak()
@@ -234,11 +260,14 @@ def run_ours(args, spec):
         "config": {"workload": spec.name, "N": spec.N, "E": spec.E, "nsteps": spec.nsteps, "windows": spec.M,
                    "T_ns": spec.T, "d": spec.d, "solver": args.solver,
                    "col_block": col_block if col_block > 0 else f"model ({prob.col_block})",
-                   "autotune": {"best": tuned, "ms_per_probe_eval": tune_ms},
+                   **({"autotune": {"best": tuned, "ms_per_probe_eval": tune_ms}} if tuned else {}),
                    "l2": "inputs larger than L2 (2 GB midpoint history per evaluation)",
                    "parallelism": f"independent problem per GPU x{world}"},
         "roofline": {"bound": "alu", "kernel": f"k_sweep ({dom})", "achieved": achieved, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "traffic": sweep_traffic(dom) if spec.nsteps == 100000 and spec.M == 64 else None,
+                     "traffic_note": "DRAM bytes per launch from profiles/k_sweep_4q_small_full.md (6400-step capture "
+                                     "x 15.625); null when the sweep sources changed since",
                      "peak_source": "measured FP64 FMA microbenchmark (msqoc_measure_fp64_peak), same run",
                      "algorithmic_flops_per_launch": fl[dom], "avg_launch_ms": dom_ms},
         "kernel_ms": {k: v / args.steps for k, v in kt.items()},
