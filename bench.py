@@ -122,6 +122,21 @@ def sweep_traffic(kernel: str):
     return float(t.group(1))
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest of every rank's value (timings: the job is as slow as its slowest rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_inputs(spec, rank: int):
+    """Each rank evaluates its own independent problem: the seeded inputs of problem `rank`."""
+    return S.random_alpha(spec, 1, problem=rank), S.random_W(spec, 1, problem=rank)
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -193,7 +208,7 @@ def run_ours(args, spec):
             dist.barrier()
         torch.cuda.synchronize()
 
-    alpha, W = S.random_alpha(spec, 1, problem=rank), S.random_W(spec, 1, problem=rank)
+    alpha, W = rank_inputs(spec, rank)
     dev = torch.device("cuda", local)
     a_d = torch.tensor(alpha, device=dev, dtype=torch.float64)
     W_d = torch.tensor(W, device=dev, dtype=torch.float64)
@@ -227,11 +242,7 @@ def run_ours(args, spec):
     e1.record(stream)
     barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
     value = world / (ms * 1e-3)
 
     # end to end through the C ABI with host buffers (H2D of alpha and W, D2H of P and gradients)
@@ -242,11 +253,7 @@ def run_ours(args, spec):
         prob.eval_gradient(alpha, W)
         if it >= args.warmup:
             e2e_times.append(time.perf_counter() - t0)
-    e2e_ms = float(np.mean(e2e_times)) * 1e3
-    if dist is not None:
-        tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(float(np.mean(e2e_times)) * 1e3, dist, dev)
 
     fl = flops_model(spec)
     dom = max(("forward", "adjoint"), key=lambda k: kt[k])

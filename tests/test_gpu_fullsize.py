@@ -29,3 +29,37 @@ def test_fullsize_4q(M):
     np.testing.assert_allclose(obj["pen"], want["pen"], rtol=1e-12, atol=0)
     assert_grad_close(got["grad_alpha"], want["grad_alpha"], what="grad_alpha")
     assert_grad_close(got["grad_W"], want["grad_W"], what="grad_W")
+
+
+def test_fullsize_5q_sampled_windows_and_directional_derivatives():
+    """The 5-transmon serving workload at full size (N=243, E=32, T=800 ns, 150000 steps,
+    M=256, d=1060) with the forced checkpoint interval 64.  The oracle's cost per step is too
+    high for all windows, so it evaluates the last two: J, pen_255 and dP/dW^255 (which needs
+    Lambda^256 at t_255) are compared element by element.  The alpha- and W-gradients as a
+    whole are checked by the property that holds at any size: central differences of the GPU
+    objective along seeded random directions equal the gradient's projections."""
+    spec = S.config_5q()
+    alpha, W = S.random_alpha(spec, 3), S.random_W(spec, 3)
+    M = spec.M
+    with msqoc.Problem(spec, ckpt_interval=64) as p:
+        got = p.eval_gradient(alpha, W)
+        obj = p.eval_objective(alpha, W)
+        rng = np.random.default_rng(17)
+        va = rng.standard_normal(spec.d)
+        vw = rng.standard_normal(spec.nW)
+        eps_a, eps_w = 1e-6, 1e-7
+        fd_a = (p.eval_objective(alpha + eps_a * va, W)["P"] - p.eval_objective(alpha - eps_a * va, W)["P"]) / (2 * eps_a)
+        fd_w = (p.eval_objective(alpha, W + eps_w * vw)["P"] - p.eval_objective(alpha, W - eps_w * vw)["P"]) / (2 * eps_w)
+    assert_objective_close(obj["P"], got["P"])
+    want = oracle.evaluate(spec, alpha, W, windows=(M - 1, M), nthreads=os.cpu_count())
+    assert_objective_close(obj["J"], want["J"])
+    np.testing.assert_allclose(obj["pen"][M - 2], want["pen"][M - 2], rtol=1e-12, atol=0)
+    ne2 = 2 * spec.N * spec.E
+    sl = slice((M - 2) * ne2, (M - 1) * ne2)     # W^{M-1}
+    assert_grad_close(got["grad_W"][sl], want["grad_W"][sl], what="grad_W^{M-1}")
+    # directional derivatives: round-off of P over the step, plus the truncation bound
+    ga_v, gw_v = float(got["grad_alpha"] @ va), float(got["grad_W"] @ vw)
+    tol_a = 1e-6 * abs(ga_v) + 16 * np.finfo(float).eps * abs(got["P"]) / eps_a
+    tol_w = 1e-6 * abs(gw_v) + 16 * np.finfo(float).eps * abs(got["P"]) / eps_w
+    assert abs(fd_a - ga_v) <= tol_a, (fd_a, ga_v)
+    assert abs(fd_w - gw_v) <= tol_w, (fd_w, gw_v)
