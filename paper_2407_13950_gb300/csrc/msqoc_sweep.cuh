@@ -573,6 +573,10 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
         }
     };
 
+    __shared__ int tflag_s;   // a bounded history wait gave up (adjoint)
+    int* tflag = &tflag_s;
+    if (tid == 0) tflag_s = 0;
+    // (the first barrier of the loop orders this store before every read of the flag)
     bool timed_out = false;
     int fsel = 0;
     double2* Dc = D0;   // FP64-solver ping-pong buffers
@@ -620,6 +624,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
         // first barrier of the step: the coefficients are published; thread 0 stores the
         // previous iteration's midpoints (forward) or fetches the next iteration's (adjoint)
         auto first_sync_work = [&]() {
+            if (BWD && *tflag) timed_out = true;   // uniform: read after a barrier
             if (!BWD && want_hist && tid == 0 && jj > 0) {
                 fence_proxy_async_smem();
                 publish(jj - 1);
@@ -641,6 +646,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
             }
             tile_sync();
             first_sync_work();
+            if (timed_out) break;
             const int Kown = prm[0];
             const int Kmax = nslot > 1 ? max(prm0[0], prm1[0]) : prm0[0];
             for (int it = 0; it < Kmax; ++it) {
@@ -678,6 +684,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
                 }
                 tile_sync();
                 first_sync_work();
+                if (timed_out) break;
                 float2 w[L];
                 apply_off<L, Q, float2>(Fb, cff, fb, y, w);
 #pragma unroll
@@ -717,6 +724,10 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
 #pragma unroll
                     for (int l = 0; l < L; ++l) D0[fb.xo + l] = z[l];
                 }
+                // forward: the staged midpoints of the previous step must have been read by their
+                // bulk store (issued at this step's first barrier) before this step's are staged;
+                // waiting here, ahead of a barrier every step has, makes the staging barrier-free
+                if (!BWD && want_hist && pass == 0 && tid == 0) bulk_wait_read_all();
                 tile_sync();
                 double2 w[L];
                 apply_off<L, Q, double2>(D0, cfd, fb, z, w);
@@ -765,8 +776,11 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
         if constexpr (!BWD) {
             // ---- midpoint states for the adjoint sweep (async bulk store at the next step)
             if (want_hist) {
-                if (tid == 0) bulk_wait_read_all();
-                tile_sync();
+                if constexpr (SOLVER == SOLVER_FP64) {
+                    // (the FP64 solver's step may have no barrier after the first one)
+                    if (tid == 0) bulk_wait_read_all();
+                    tile_sync();
+                }
                 if (act && live) {
 #pragma unroll
                     for (int l = 0; l < L; ++l) H[fb.xo + l] = z[l];
@@ -780,11 +794,9 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
         } else {
             // ---- gradient quadrature on the midpoints (fused): needs Ubar_n of the tile
             double2* UB = par ? UB1 : UB0;
-            const bool ok = mbar_wait(&mbar[par], (jj >> 1) & 1);
-            if (tile_sync_or(!ok)) {
-                timed_out = true;
-                break;
-            }
+            // a wait that gives up raises the tile's flag, read after the next barrier (the
+            // products below then use whatever landed; the evaluation reports the timeout)
+            if (!mbar_wait(&mbar[par], (jj >> 1) & 1)) *tflag = 1;
             double acc[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = 0.0;
@@ -889,6 +901,9 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
 
     if (!timed_out) {
         tile_sync();
+        if (BWD && *tflag) timed_out = true;   // the last step's wait (uniform: after the barrier)
+    }
+    if (!timed_out) {
         if constexpr (!BWD) {
             if (want_hist && tid == 0 && nit > 0) {
                 fence_proxy_async_smem();
