@@ -153,6 +153,21 @@ msqoc_status msqoc_eval_objective(msqoc_problem* p, const double* alpha, const d
 msqoc_status msqoc_eval_gradient(msqoc_problem* p, const double* alpha, const double* W,
                                  double* P_out, double* grad_alpha, double* grad_W, void* stream);
 
+/* Roll-out (Sec. 5, initialisation of the window states): propagate the identity embedding
+ * W^0 over the whole time grid [0, T] as one window under the controls alpha, sequentially in
+ * time, and store the state at every window boundary: W_out^m = U(t_m), m = 1..M-1 (layout of
+ * W).  With these window states every continuity penalty vanishes (to rounding) and the
+ * objective equals the single-shooting infidelity.  This sweep cannot be parallelised over the
+ * windows: it runs E / col_block tiles for all N_T steps.  W_out: host or device. */
+msqoc_status msqoc_rollout(msqoc_problem* p, const double* alpha, double* W_out, void* stream);
+
+/* Roll-out infidelity estimate (Eq. rollout-infid-est) from the problem's last evaluation
+ * (objective or gradient): J + (2/sqrt(E)) sqrt(J) S + S^2/E with S = sum_m ||C^m||_F and
+ * ||C^m||_F = sqrt(2 pen_m / mu), an upper bound of the infidelity of the rolled-out state
+ * that needs no sequential sweep (the paper's stopping criterion).  est_out: 1 double, host
+ * or device. */
+msqoc_status msqoc_rollout_estimate(msqoc_problem* p, double* est_out, void* stream);
+
 /* Release every resource of the problem (synchronizes the device first). NULL is a no-op. */
 msqoc_status msqoc_destroy_problem(msqoc_problem* p);
 

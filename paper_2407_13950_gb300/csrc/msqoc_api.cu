@@ -347,7 +347,8 @@ OutLayout out_layout(int M, int d, size_t nW) {
 namespace {
 
 void free_problem(msqoc_problem* p) {
-    void* bufs[] = {p->pds,   p->tiles, p->lanemap, p->P,     p->emb,   p->V,     p->alpha_dev, p->W_dev,
+    void* bufs[] = {p->tiles_ro, p->lanemap_ro,
+                    p->pds,   p->tiles, p->lanemap, p->P,     p->emb,   p->V,     p->alpha_dev, p->W_dev,
                     p->ctrl,  p->spl,   p->phase,   p->hist,  p->ckpt,  p->Lstate, p->Uend,     p->Lterm,
                     p->Lam0,  p->term,  p->gpart,   p->status, p->out_dev};
     for (void* b : bufs)
@@ -455,6 +456,12 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
     for (int t = 0; t < pd.ntiles; ++t) tiles[t] = tile_at(t, pd.M, E, pd.cb, 0);
     std::vector<int> maps(size_t(pd.cb + 1) * pd.nthreads);
     build_lanemaps(L, q, pd.M, E, pd.cb, pd.nthreads, maps.data());
+    // the roll-out sweep's tiles: the same widths over a single window
+    p->ntiles_ro = static_cast<int>(tile_count(1, E, pd.cb));
+    std::vector<Tile> tiles_ro(p->ntiles_ro);
+    for (int t = 0; t < p->ntiles_ro; ++t) tiles_ro[t] = tile_at(t, 1, E, pd.cb, 0);
+    std::vector<int> maps_ro(size_t(pd.cb + 1) * pd.nthreads);
+    build_lanemaps(L, q, 1, E, pd.cb, pd.nthreads, maps_ro.data());
 
     // ---- device buffers
     const size_t M = pd.M;
@@ -467,6 +474,8 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
     A(dalloc(&p->pds, 1), "problem record");
     A(dalloc(&p->tiles, tiles.size()), "tiles");
     A(dalloc(&p->lanemap, maps.size()), "lane maps");
+    A(dalloc(&p->tiles_ro, tiles_ro.size()), "roll-out tiles");
+    A(dalloc(&p->lanemap_ro, maps_ro.size()), "roll-out lane maps");
     A(dalloc(&p->P, N), "P");
     A(dalloc(&p->emb, E), "embedding");
     A(dalloc(&p->V, p->ne), "target");
@@ -504,6 +513,10 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
         pd.status = p->status;
         A(cudaMemcpy(p->tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice), "tiles copy");
         A(cudaMemcpy(p->lanemap, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice), "lane map copy");
+        A(cudaMemcpy(p->tiles_ro, tiles_ro.data(), tiles_ro.size() * sizeof(Tile), cudaMemcpyHostToDevice),
+          "roll-out tiles copy");
+        A(cudaMemcpy(p->lanemap_ro, maps_ro.data(), maps_ro.size() * sizeof(int), cudaMemcpyHostToDevice),
+          "roll-out lane map copy");
         A(cudaMemcpy(p->P, P.data(), N * sizeof(double2), cudaMemcpyHostToDevice), "P copy");
         A(cudaMemcpy(p->emb, emb.data(), E * sizeof(int), cudaMemcpyHostToDevice), "emb copy");
         A(cudaMemcpy(p->V, Vh.data(), p->ne * sizeof(double2), cudaMemcpyHostToDevice), "target copy");
@@ -518,7 +531,8 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
     }
     p->bytes = sizeof(double2) * (N + p->ne * (1 + 3 * M) + size_t(nsteps) * (q + nfsum)) +
                sizeof(Spline4) * size_t(nsteps) + sizeof(double) * (pd.d + p->nW + M + size_t(pd.ntiles) * pd.d) +
-               sizeof(int) * (E + 1 + maps.size()) + sizeof(Tile) * tiles.size() + sizeof(ProbDev);
+               sizeof(int) * (E + 1 + maps.size() + maps_ro.size()) + sizeof(Tile) * (tiles.size() + tiles_ro.size()) +
+               sizeof(ProbDev);
     p->grad_bytes = gradient_bytes(pd);
     *out = p;
     return MSQOC_OK;
@@ -731,6 +745,42 @@ msqoc_status msqoc_eval_gradient(msqoc_problem* p, const double* alpha, const do
     if (P_out && !dP) CUDA_TRY(cudaMemcpyAsync(P_out, o, sizeof(double), cudaMemcpyDeviceToHost, s));
     if (!dga) CUDA_TRY(cudaMemcpyAsync(grad_alpha, ga_dst, pd.d * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (!dgw) CUDA_TRY(cudaMemcpyAsync(grad_W, gw_dst, p->nW * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return check_status_sync(p, s);
+}
+
+msqoc_status msqoc_rollout(msqoc_problem* p, const double* alpha, double* W_out, void* stream) {
+    if (!p) return fail(MSQOC_ERR_INVALID_ARG, "problem is NULL");
+    if (p->pd.M > 1 && !W_out) return fail(MSQOC_ERR_INVALID_ARG, "W_out is NULL but M > 1");
+    if (!alpha) return fail(MSQOC_ERR_INVALID_ARG, "alpha is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->pd.M == 1) return MSQOC_OK;
+    CUDA_TRY(cudaMemcpyAsync(p->alpha_dev, alpha, p->pd.d * sizeof(double), cudaMemcpyDefault, s));
+    msqoc_status st;
+    const bool dev = is_device_ptr(W_out) && reinterpret_cast<uintptr_t>(W_out) % 16 == 0;
+    double* dst = dev ? W_out : p->out_dev + out_layout(p->pd.M, p->pd.d, p->nW).gw;
+    for (bool& r : p->ran) r = false;
+    if ((st = launch_controls(p, s))) return st;
+    SweepArgs a = sweep_args(p->pd, p->pds, p->tiles_ro, p->lanemap_ro, SWEEP_ROLLOUT, 0);
+    a.out = reinterpret_cast<double2*>(dst);
+    {
+        Mark mk(p, MSQOC_KERNEL_FORWARD, s);
+        CUDA_TRY(launch_sweep(a, p->ntiles_ro, s));
+    }
+    if (dev) return MSQOC_OK;
+    CUDA_TRY(cudaMemcpyAsync(W_out, dst, p->nW * sizeof(double), cudaMemcpyDefault, s));
+    return check_status_sync(p, s);
+}
+
+msqoc_status msqoc_rollout_estimate(msqoc_problem* p, double* est_out, void* stream) {
+    if (!p || !est_out) return fail(MSQOC_ERR_INVALID_ARG, "problem or est_out is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool dev = is_device_ptr(est_out);
+    // a spare slot at the end of the output staging (the other slots hold the last results)
+    double* dst = dev ? est_out : p->out_dev + out_layout(p->pd.M, p->pd.d, p->nW).total - 1;
+    k_rollout_estimate<<<1, 32, 0, s>>>(p->pd, dst);
+    CUDA_TRY(cudaGetLastError());
+    if (dev) return MSQOC_OK;
+    CUDA_TRY(cudaMemcpyAsync(est_out, dst, sizeof(double), cudaMemcpyDeviceToHost, s));
     return check_status_sync(p, s);
 }
 

@@ -178,6 +178,19 @@ __global__ void k_finalize_scalars(const ProbDev pd, double* P_out, double* J_ou
     }
 }
 
+// Roll-out infidelity estimate (Eq. rollout-infid-est) from the last evaluation's window terms:
+//   J + (2 / sqrt(n)) sqrt(J) S + S^2 / n,  S = sum_{m<M} ||C^m||_F,  ||C^m||_F = sqrt(2 pen_m / mu),
+// with n := E (as in the generalized infidelity).  Window order sum (deterministic).
+__global__ void k_rollout_estimate(const ProbDev pd, double* est) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double S = 0.0;
+        for (int m = 1; m < pd.M; ++m) S += sqrt(2.0 * pd.term[m - 1] / pd.mu);
+        const double J = pd.term[pd.M - 1];
+        const double n = pd.E;
+        *est = J + 2.0 / sqrt(n) * sqrt(fmax(J, 0.0)) * S + S * S / n;
+    }
+}
+
 // dP/dW^m = mu (W^m - U^m(t_m)) - 2 Lambda^{m+1}(t_m) = 2 (Lambda^m(t_m) - Lambda^{m+1}(t_m))
 // (Eq. dP-dW with the factor of Appendix B, Eq. dT-dW-j), m = 1..M-1.
 __global__ void k_grad_W(const ProbDev pd, double2* gW) {

@@ -19,6 +19,9 @@ struct msqoc_problem {
     msqoc::ProbDev* pds = nullptr;   // device copy of pd (read by the sweeps)
     msqoc::Tile* tiles = nullptr;
     int* lanemap = nullptr;
+    msqoc::Tile* tiles_ro = nullptr;   // the roll-out sweep: one window over the whole grid
+    int* lanemap_ro = nullptr;
+    int ntiles_ro = 0;
     double2* P = nullptr;
     int* emb = nullptr;
     double2* V = nullptr;

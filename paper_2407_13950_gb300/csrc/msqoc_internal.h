@@ -83,7 +83,9 @@ enum SweepMode {
                           // starts (checkpoints, more segments)
     SWEEP_RECOMPUTE = 3,  // forward over segment `seg` from its checkpoint; midpoint states
                           // (no work for a problem with one segment)
-    SWEEP_ADJOINT = 4     // adjoint over segment `seg` with the fused gradient quadrature
+    SWEEP_ADJOINT = 4,    // adjoint over segment `seg` with the fused gradient quadrature
+    SWEEP_ROLLOUT = 5     // forward over the whole time grid as one window from the identity
+                          // embedding; the state at every window boundary t_m into `out`
 };
 
 // Arguments of one sweep launch (uniform over its tiles; problems share shape and solver).
@@ -96,6 +98,7 @@ struct SweepArgs {
     int mode;             // SweepMode
     int seg;              // segment (SWEEP_RECOMPUTE, SWEEP_ADJOINT)
     int L, q, solver, nthreads;
+    double2* out;         // SWEEP_ROLLOUT: [M-1][E][N] states at the window boundaries
 };
 
 // shared-memory bytes of a sweep launch

@@ -418,10 +418,11 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
     const int nslot = ncol0 < ncol ? 2 : 1;
     const bool segmented = a.mode == SWEEP_RECOMPUTE || a.mode == SWEEP_ADJOINT;
     const bool idle_launch = a.mode == SWEEP_RECOMPUTE && pd.nseg == 1;   // nothing to recompute
+    const bool rollout = !BWD && a.mode == SWEEP_ROLLOUT;                 // one window: the whole grid
 
     // ---- the slots' windows and step ranges (local step indices [lo, lo + cnt) of the window)
-    const int64_t wn0_0 = win_start(pd, tile.m0);
-    const int wns_0 = static_cast<int>(win_start(pd, tile.m0 + 1) - wn0_0);
+    const int64_t wn0_0 = rollout ? 0 : win_start(pd, tile.m0);
+    const int wns_0 = rollout ? static_cast<int>(pd.nsteps) : static_cast<int>(win_start(pd, tile.m0 + 1) - wn0_0);
     const int64_t wn0_1 = nslot > 1 ? win_start(pd, tile.m0 + 1) : 0;
     const int wns_1 = nslot > 1 ? static_cast<int>(win_start(pd, tile.m0 + 2) - wn0_1) : 0;
     const int lo_0 = segmented ? a.seg * pd.kseg : 0;
@@ -577,6 +578,9 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
     int* tflag = &tflag_s;
     if (tid == 0) tflag_s = 0;
     // (the first barrier of the loop orders this store before every read of the flag)
+    // roll-out: the next window boundary (global step index after which U(t_boundary) is stored)
+    int boundary = 1;
+    int64_t next_boundary = (rollout && pd.M > 1) ? win_start(pd, 2) : -1;
     bool timed_out = false;
     int fsel = 0;
     double2* Dc = D0;   // FP64-solver ping-pong buffers
@@ -791,6 +795,16 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
 #pragma unroll
                 for (int l = 0; l < L; ++l) u[l] = reflect(z[l], u[l]);
             }
+            // roll-out: U(t_m) at every window boundary the step reached (t_m = t_{n+1})
+            if (rollout && live && (wn0_0 + jj + 1) == next_boundary) {
+                if (act) {
+                    double2* dst = a.out + (size_t(boundary - 1) * E + col) * N + f * L;
+#pragma unroll
+                    for (int l = 0; l < L; ++l) dst[l] = u[l];
+                }
+                ++boundary;
+                next_boundary = boundary < pd.M ? win_start(pd, boundary + 1) : -1;
+            }
         } else {
             // ---- gradient quadrature on the midpoints (fused): needs Ubar_n of the tile
             double2* UB = par ? UB1 : UB0;
@@ -910,7 +924,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
                 publish(nit - 1);
                 bulk_wait_all();
             }
-            if (a.mode != SWEEP_RECOMPUTE && act && my_cnt > 0) {
+            if (a.mode != SWEEP_RECOMPUTE && !rollout && act && my_cnt > 0) {
 #pragma unroll
                 for (int l = 0; l < L; ++l) pd.Uend[wcol + f * L + l] = u[l];
             }

@@ -25,7 +25,8 @@ EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_query_layout", "msqoc_
             "msqoc_destroy_problem", "msqoc_last_error", "msqoc_version", "msqoc_kernel_times",
             "msqoc_measure_fp64_peak", "msqoc_eval_objective_noalloc", "msqoc_batch_create",
             "msqoc_batch_eval_objective", "msqoc_batch_eval_gradient", "msqoc_batch_destroy", "msqoc_set_inputs",
-            "msqoc_get_objective", "msqoc_get_gradient", "msqoc_batch_eval_subset", "msqoc_autotune"]
+            "msqoc_get_objective", "msqoc_get_gradient", "msqoc_batch_eval_subset", "msqoc_autotune",
+            "msqoc_rollout", "msqoc_rollout_estimate"]
 BATCH_GRADIENT, BATCH_GRAPH = 1, 2
 KERNEL_NAMES = ["controls", "forward", "terminal", "adjoint", "finalize"]
 
@@ -91,6 +92,8 @@ def load(build_if_missing: bool = True):
             "msqoc_get_objective": (i32, [vp, vp, vp, vp, vp]),
             "msqoc_get_gradient": (i32, [vp, vp, vp, vp, vp]),
             "msqoc_batch_eval_subset": (i32, [vp, vp, i32, i32, i32, vp]),
+            "msqoc_rollout": (i32, [vp, vp, vp, vp]),
+            "msqoc_rollout_estimate": (i32, [vp, vp, vp]),
             "msqoc_autotune": (i32, [vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, vp, vp, i32, vp, vp, vp,
                                      i32, vp]),
         }
@@ -221,6 +224,19 @@ class Problem:
         _check(load().msqoc_eval_gradient(self.handle, _ptr(alpha), _ptr(w), _ptr(P), _ptr(ga),
                                           _ptr(gW) if M > 1 else None, _stream_handle(stream)))
         return {"P": float(P[0]), "grad_alpha": ga, "grad_W": gW[:self.nW].copy()}
+
+    def rollout(self, alpha, stream=None) -> np.ndarray:
+        """Window states from a sequential roll-out of the identity under alpha (W^m = U(t_m))."""
+        W = np.zeros(max(self.nW, 1))
+        _check(load().msqoc_rollout(self.handle, _ptr(alpha), _ptr(W) if self.spec.M > 1 else None,
+                                    _stream_handle(stream)))
+        return W[:self.nW].copy()
+
+    def rollout_estimate(self, stream=None) -> float:
+        """Roll-out infidelity estimate from the last evaluation (objective or gradient)."""
+        est = np.zeros(1)
+        _check(load().msqoc_rollout_estimate(self.handle, _ptr(est), _stream_handle(stream)))
+        return float(est[0])
 
     # ---- pointer-level API (device tensors; asynchronous on the stream)
     def eval_gradient_into(self, alpha, W, P_out, grad_alpha, grad_W, stream=None):

@@ -1,0 +1,47 @@
+"""Roll-out (the paper's initialisation of the window states, Sec. 5) and the roll-out
+infidelity estimate (Eq. rollout-infid-est) on the GPU, against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_13950_gb300 import msqoc
+from paper_2407_13950_gb300 import synthetic as S
+
+from gpu_helpers import assert_objective_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("solver", [msqoc.SOLVER_MIXED, msqoc.SOLVER_FP64])
+def test_rollout_matches_oracle_and_zeroes_the_penalties(solver):
+    spec = S.transmon_spec(3, 30.0, 2001, 7, 8)            # ragged windows
+    alpha = S.random_alpha(spec, 71)
+    want = oracle.rollout(spec, alpha)
+    with msqoc.Problem(spec, solver=solver, col_block=5) as p:
+        W = p.rollout(alpha)
+        np.testing.assert_allclose(W, want, rtol=0, atol=1e-12)
+        obj = p.eval_objective(alpha, W)
+    assert np.all(np.abs(obj["pen"]) < 1e-22)
+    single = oracle.evaluate(spec.replace(M=1), alpha, np.zeros(0), grad=False)
+    assert_objective_close(obj["J"], single["P"], rtol=1e-11)
+
+
+def test_rollout_estimate_is_the_formula_and_bounds_the_rollout_infidelity():
+    spec = S.transmon_spec(2, 16.0, 320, 4, 6)
+    alpha = S.random_alpha(spec, 72)
+    with msqoc.Problem(spec) as p:
+        W = p.rollout(alpha) + 0.05 * S.random_W(spec, 72)     # perturbed boundary states
+        obj = p.eval_objective(alpha, W)
+        est = p.rollout_estimate()
+        g = p.eval_gradient(alpha, W)
+        est_g = p.rollout_estimate()
+    J, pen, mu, n = obj["J"], obj["pen"], 2.0 / spec.E, spec.E
+    S_ = sum(math.sqrt(2 * x / mu) for x in pen)
+    want = J + 2 / math.sqrt(n) * math.sqrt(J) * S_ + S_ ** 2 / n
+    assert est == pytest.approx(want, rel=1e-13)
+    assert est_g == pytest.approx(want, rel=1e-12)
+    J_ro = oracle.evaluate(spec.replace(M=1), alpha, np.zeros(0), grad=False)["P"]
+    assert J_ro <= est * (1 + 1e-12)
+    assert g["P"] == pytest.approx(obj["P"], rel=1e-12)
