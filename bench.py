@@ -407,6 +407,62 @@ def run_batched(args):
         print(json.dumps(line), flush=True)
 
 
+def run_paper(args):
+    """The paper's own test cases (Table 1-2: QFT-4/8/16 on 2/3/4 qubits with exchange coupling,
+    full time grids): objective+gradient evaluations per second for each window count, and the
+    speedup of the multiple-window evaluation over single shooting (M = 1), the quantity the
+    paper reports (8x / 31x / 80x at M = 16 / 128 / 256 on 64 / 1024 / 4096 CPU processes)."""
+    import torch
+    from paper_2407_13950_gb300 import msqoc
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for q, Ms in ((2, (1, 16)), (3, (1, 128)), (4, (1, 256))):
+        row = {}
+        for M in Ms:
+            spec = S.paper_qft_spec(q, M=M)
+            alpha, W = S.random_alpha(spec, 1), S.random_W(spec, 1)
+            a_d = torch.tensor(alpha, device=dev, dtype=torch.float64)
+            W_d = torch.tensor(W if M > 1 else np.zeros(2), device=dev, dtype=torch.float64)
+            P_d = torch.zeros(1, device=dev, dtype=torch.float64)
+            ga_d = torch.zeros(spec.d, device=dev, dtype=torch.float64)
+            gW_d = torch.zeros(max(spec.nW, 2), device=dev, dtype=torch.float64)
+            with msqoc.Problem(spec) as p:
+                def step():
+                    p.eval_gradient_into(a_d, W_d if M > 1 else None, P_d, ga_d, gW_d if M > 1 else None,
+                                         stream=stream)
+                for _ in range(args.warmup):
+                    step()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(args.steps):
+                    step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+            row[M] = ms
+        Mbig = Ms[-1]
+        out[f"QFT-{2 ** q}"] = {"n_steps": S.PAPER_NSTEPS[q], "ms_per_eval": {str(k): v for k, v in row.items()},
+                                "evals_per_s": {str(k): 1e3 / v for k, v in row.items()},
+                                f"speedup_M{Mbig}_over_M1": row[1] / row[Mbig]}
+    q16 = out["QFT-16"]
+    line = {"metric": "QFT-16 objective+gradient evals/s (paper model, M=256)", "value": q16["evals_per_s"]["256"],
+            "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": q16["ms_per_eval"]["256"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper's QFT-4/8/16 (Table 1 parameters, Table 2 step counts, exchange coupling)"},
+            "cases": out,
+            "paper_context": "paper: gradient-evaluation speedup over M=1 of 8x (QFT-4, 16 windows x 4 columns = 64 "
+                             "processes), 31x (QFT-8, 1024 processes), 80x (QFT-16, 4096 processes) on Intel "
+                             "Sapphire Rapids"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_serving(args):
     """Serving loop: sessions of 2/3/4/5 transmons (the 5-transmon ones with forced
     checkpointing), a Poisson stream of objective/gradient requests over them, served with
@@ -488,14 +544,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nsteps", type=int, default=0,
                     help="shorter time grid with the same step size (small profiling case); 0 = 100000 steps")
-    ap.add_argument("--workload", choices=["4q", "batched", "serving"], default="4q",
+    ap.add_argument("--workload", choices=["4q", "batched", "serving", "paper"], default="4q",
                     help="4q: the benchmark workload (one 4-transmon problem); batched: 96 mixed problems; "
-                         "serving: continuous batching of a Poisson request stream")
+                         "serving: continuous batching of a Poisson request stream; paper: the paper's QFT cases")
     ap.add_argument("--batch-per-shape", type=int, default=32)
     ap.add_argument("--sessions-per-shape", type=int, default=16)
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: offered requests per second")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     args = ap.parse_args()
+    if args.workload == "paper":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the paper workloads have no CPU reference run"}))
+            return
+        run_paper(args)
+        return
     if args.workload == "serving":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no CPU reference run"}))

@@ -18,10 +18,10 @@
  *   - q subsystems, L levels each (the first `ness` essential); N = L^q rows, E = ness^q
  *     columns.  Full index i = sum_k l_k L^(q-1-k) (subsystem 0 most significant); essential
  *     column e = sum_k b_k ness^(q-1-k).
- *   - Drift (diagonal): H_s = sum_k -xi_k/2 a_k^+a_k^+a_k a_k - sum_{k<l} xi_kl a_k^+a_k a_l^+a_l
- *     (transmons with self- and cross-Kerr in per-qubit rotating frames), optionally
- *     + sum_k detune_k a_k^+ a_k.  The paper's dipole exchange (Eq. sys-ham, J_kl) is not
- *     supported by this library: jx must be NULL or all zero (MSQOC_ERR_UNSUPPORTED).
+ *   - Drift: H_s = sum_k -xi_k/2 a_k^+a_k^+a_k a_k - sum_{k<l} xi_kl a_k^+a_k a_l^+a_l
+ *     (transmons with self- and cross-Kerr in per-qubit rotating frames)
+ *     + sum_k detune_k a_k^+ a_k + sum_{k<l} J_kl (a_l^+ a_k + a_l a_k^+) (the paper's
+ *     Eq. sys-ham: detuning omega_k - omega_rot and dipole exchange).
  *   - Controls: d_k(t) = sum_f exp(i Omega_kf t) sum_s (alpha1_kfs + i alpha2_kfs) B_s(t),
  *     quadratic cardinal B-splines on knots j*dtau, dtau = T/(d1-2), spline s centred at
  *     (s - 1/2) dtau (Sec. 2 and Sec. 5: d1 = T/dtau + 2).  alpha layout [k][f][s][2],
@@ -86,7 +86,8 @@ typedef struct msqoc_hamiltonian {
     const double* xi;       /* [q] self-Kerr xi_k (rad/ns); host memory */
     const double* xi_cross; /* [q*q] row-major, entry (k,l) with k<l used; NULL = 0; host */
     const double* detune;   /* [q] or NULL; host */
-    const double* jx;       /* must be NULL or zero (see above); host */
+    const double* jx;       /* [q*q] row-major dipole exchange J_kl, (k,l) with k<l used; NULL = 0;
+                               nonzero only with nlevels = 2 (else MSQOC_ERR_UNSUPPORTED); host */
 } msqoc_hamiltonian;
 
 typedef struct msqoc_controls {

@@ -239,8 +239,11 @@ msqoc_status check_description(const msqoc_hamiltonian* H, const msqoc_controls*
     if (!shape_supported(L, q))
         return fail(MSQOC_ERR_UNSUPPORTED, "no kernel for L=%d levels and q=%d subsystems", L, q);
     if (H->jx)
-        for (int e = 0; e < q * q; ++e)
-            if (H->jx[e] != 0.0) return fail(MSQOC_ERR_UNSUPPORTED, "dipole exchange (jx) is not supported");
+        for (int e = 0; e < q * q; ++e) {
+            if (!std::isfinite(H->jx[e])) return fail(MSQOC_ERR_INVALID_ARG, "dipole exchange jx[%d] is not finite", e);
+            if (H->jx[e] != 0.0 && L != 2)
+                return fail(MSQOC_ERR_UNSUPPORTED, "dipole exchange is implemented for 2-level subsystems only");
+        }
     if (!C->ncarriers || !C->carriers || C->nsplines < 3)
         return fail(MSQOC_ERR_INVALID_ARG, "invalid control description");
     if (!(T > 0) || !std::isfinite(T) || nsteps < 1 || nwindows < 1 || nwindows > nsteps)
@@ -285,6 +288,20 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
         pd.cof[k + 1] = pd.cof[k] + C->ncarriers[k];
     }
     for (int i = 0; i < nfsum; ++i) pd.omega[i] = C->carriers[i];
+    // dipole exchange pairs (j < k): constant off-diagonal terms of the step operator; their norm
+    // joins the contraction bound (||a_k^+ a_j|| <= L - 1, two terms per pair)
+    pd.nex = 0;
+    pd.rho_ex = 0.0;
+    if (H->jx)
+        for (int j = 0; j < q; ++j)
+            for (int k = j + 1; k < q; ++k)
+                if (H->jx[j * q + k] != 0.0) {
+                    pd.ex_j[pd.nex] = j;
+                    pd.ex_k[pd.nex] = k;
+                    pd.ex_c[pd.nex] = 0.5 * pd.h * H->jx[j * q + k];
+                    pd.rho_ex += pd.h * (L - 1) * std::fabs(H->jx[j * q + k]);
+                    ++pd.nex;
+                }
     for (int l = 0; l < MAXL; ++l) {
         pd.sc[2 * l + 0] = 0.5 * pd.h * std::sqrt(double(l + 1));
         pd.sc[2 * l + 1] = 0.5 * pd.h * std::sqrt(double(l));

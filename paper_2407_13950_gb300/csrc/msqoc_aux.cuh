@@ -90,7 +90,7 @@ __global__ void k_controls(const ProbDev pd) {
             pd.ctrl[size_t(n) * pd.q + k] = dk;
             mag += sqrt(dk.x * dk.x + dk.y * dk.y);
         }
-        const float rho = float(0.5 * pd.h * pd.lam * mag) * 1.0001f;
+        const float rho = float(0.5 * pd.h * pd.lam * mag + pd.rho_ex) * 1.0001f;
         pd.spl[n] = Spline4{s0, step_counts(pd.solver, rho), w0, w1, w2};
     }
 }

@@ -7,6 +7,7 @@
 namespace msqoc {
 
 constexpr int MAXQ = 6;       // subsystems
+constexpr int MAXEX = 15;     // exchange-coupled pairs (q (q - 1) / 2)
 constexpr int MAXNF = 64;     // carriers over all subsystems
 constexpr int MAXL = 4;       // levels per subsystem handled by the sweep kernels
 constexpr int MAX_TILE_THREADS = 256;  // threads of one sweep tile (leaves 255 registers a thread)
@@ -43,6 +44,12 @@ struct ProbDev {
     int cof[MAXQ + 1];           // carrier offsets
     double omega[MAXNF];
     double sc[2 * MAXL];         // (h/2) sqrt(l+1) [dir +] and (h/2) sqrt(l) [dir -], index 2l+dir
+    // dipole exchange J_jk (a_k^+ a_j + a_k a_j^+), j < k, a constant part of the off-diagonal
+    // operator of the step: pairs, (h/2) J_jk, and its contribution to the contraction bound
+    int nex;
+    int ex_j[MAXEX], ex_k[MAXEX];
+    double ex_c[MAXEX];
+    double rho_ex;
     double wsq[2 * MAXL];        // sqrt(l+1) [dir +] and sqrt(l) [dir -]: product weights
     // constant tables
     const double2* P;            // [N] (1 + i h/2 D_i)^-1

@@ -200,6 +200,7 @@ template <int L, int Q>
 struct Fiber {
     static constexpr int NFIX = Q - 1;
     static constexpr int NA = NFIX > 0 ? NFIX : 1;
+    int f;             // fiber index
     int xo;            // offset of the fiber's first entry in a [cb][N] buffer
     int nb1[NA];       // offset of neighbour fiber (first entry) for subsystem k, entry 1
     int nb2[NA];       // entry 2 (exists when the level is interior)
@@ -212,6 +213,7 @@ struct Fiber {
 
     __device__ void init(int c, int f, const ProbDev& pd) {
         constexpr int N = ipow_c(L, Q);
+        this->f = f;
         xo = c * N + f * L;
 #pragma unroll
         for (int k = 0; k < NFIX; ++k) {
@@ -240,11 +242,72 @@ struct Fiber {
     }
 };
 
+// Dipole exchange on the fiber (fiber index f, entries at fb.xo of a [cols][N] buffer):
+// w += i (h/2) J_jk (a_k^+ a_j + a_k a_j^+) x for every coupled pair j < k.  a_k^+ a_j moves one
+// quantum from j to k: the source has l_j + 1 and l_k - 1, weight sqrt(l_k) sqrt(l_j + 1); a_k a_j^+
+// the opposite, weight sqrt(l_k + 1) sqrt(l_j).  When k is the last subsystem the source is an
+// entry of the neighbour fiber in subsystem j at the shifted level; otherwise a fiber that
+// differs in both digits, at the same level.  The pairs are warp-uniform; the level tests are
+// per lane.
+template <int L, int Q, typename T2>
+__device__ __forceinline__ void apply_exchange(const T2* __restrict__ buf, const ProbDev& pd, int f, int xo,
+                                               T2 (&w)[L]) {
+    using R = typename cx<T2>::T;
+    for (int e = 0; e < pd.nex; ++e) {
+        const int j = pd.ex_j[e], k = pd.ex_k[e];
+        int sfj = 1, sfk = 1;                                  // fiber strides (j is never the last)
+        for (int t = j; t < Q - 2; ++t) sfj *= L;
+        for (int t = k; t < Q - 2; ++t) sfk *= L;
+        const int lj = (f / sfj) % L;
+        const R c = static_cast<R>(pd.ex_c[e]);
+        if (k == Q - 1) {
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                // a_k^+ a_j: from (l_j + 1, l - 1)
+                if (l >= 1 && lj <= L - 2) {
+                    const R wt = c * static_cast<R>(sqrt_small(l) * sqrt_small(lj + 1));
+                    const T2 x = buf[xo + sfj * L + (l - 1)];
+                    w[l].x -= wt * x.y;
+                    w[l].y += wt * x.x;
+                }
+                // a_k a_j^+: from (l_j - 1, l + 1)
+                if (l <= L - 2 && lj >= 1) {
+                    const R wt = c * static_cast<R>(sqrt_small(l + 1) * sqrt_small(lj));
+                    const T2 x = buf[xo - sfj * L + (l + 1)];
+                    w[l].x -= wt * x.y;
+                    w[l].y += wt * x.x;
+                }
+            }
+        } else {
+            const int lk = (f / sfk) % L;
+            if (lk >= 1 && lj <= L - 2) {
+                const R wt = c * static_cast<R>(sqrt_small(lk) * sqrt_small(lj + 1));
+                const T2* src = buf + xo + (sfj - sfk) * L;
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    w[l].x -= wt * src[l].y;
+                    w[l].y += wt * src[l].x;
+                }
+            }
+            if (lk <= L - 2 && lj >= 1) {
+                const R wt = c * static_cast<R>(sqrt_small(lk + 1) * sqrt_small(lj));
+                const T2* src = buf + xo + (sfk - sfj) * L;
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    w[l].x -= wt * src[l].y;
+                    w[l].y += wt * src[l].x;
+                }
+            }
+        }
+    }
+}
+
 // w = (iX_C x) on the fiber: ladder terms of the last subsystem from registers (xr), the
 // others from the shared buffer.  cf: per-slot coefficients i(h/2)sqrt(.)d_k for this step.
 template <int L, int Q, typename T2>
 __device__ __forceinline__ void apply_off(const T2* __restrict__ buf, const T2* __restrict__ cf,
-                                          const Fiber<L, Q>& fb, const T2 (&xr)[L], T2 (&w)[L]) {
+                                          const Fiber<L, Q>& fb, const T2 (&xr)[L], T2 (&w)[L],
+                                          const ProbDev& pd) {
 #pragma unroll
     for (int l = 0; l < L; ++l) {
         w[l].x = 0;
@@ -268,6 +331,10 @@ __device__ __forceinline__ void apply_off(const T2* __restrict__ buf, const T2* 
 #pragma unroll
             for (int l = 0; l < L; ++l) cmac(w[l], c2, p2[l]);
         }
+    }
+    // exchange-coupled problems are 2-level qubit models (the only shapes compiled with it)
+    if constexpr (L == 2 && Q >= 2) {
+        if (pd.nex) apply_exchange<L, Q, T2>(buf, pd, fb.f, fb.xo, w);
     }
 }
 
@@ -662,7 +729,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
                     tile_sync();
                 }
                 double2 w[L];
-                apply_off<L, Q, double2>(Dc, cfd, fb, z, w);
+                apply_off<L, Q, double2>(Dc, cfd, fb, z, w, pd);
                 if (it < Kown) {
 #pragma unroll
                     for (int l = 0; l < L; ++l) z[l] = cadd_scaled<S>(b[l], Pd[l], w[l]);
@@ -690,7 +757,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
                 first_sync_work();
                 if (timed_out) break;
                 float2 w[L];
-                apply_off<L, Q, float2>(Fb, cff, fb, y, w);
+                apply_off<L, Q, float2>(Fb, cff, fb, y, w, pd);
 #pragma unroll
                 for (int l = 0; l < L; ++l) df[l] = cadd_scaled<S>(make_float2(0.f, 0.f), Pf[l], w[l]);
             }
@@ -709,7 +776,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
                 }
                 tile_sync();
                 float2 w[L];
-                apply_off<L, Q, float2>(Fb, cff, fb, y, w);
+                apply_off<L, Q, float2>(Fb, cff, fb, y, w, pd);
                 if (it < j1) {
 #pragma unroll
                     for (int l = 0; l < L; ++l) df[l] = cadd_scaled<S>(make_float2(0.f, 0.f), Pf[l], w[l]);
@@ -734,7 +801,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
                 if (!BWD && want_hist && pass == 0 && tid == 0) bulk_wait_read_all();
                 tile_sync();
                 double2 w[L];
-                apply_off<L, Q, double2>(D0, cfd, fb, z, w);
+                apply_off<L, Q, double2>(D0, cfd, fb, z, w, pd);
                 float2 rf[L], e[L];
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
@@ -751,7 +818,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
                     }
                     tile_sync();
                     float2 wf[L];
-                    apply_off<L, Q, float2>(Fb, cff, fb, e, wf);
+                    apply_off<L, Q, float2>(Fb, cff, fb, e, wf, pd);
                     if (it < j2) {
 #pragma unroll
                         for (int l = 0; l < L; ++l) e[l] = cadd_scaled<S>(rf[l], Pf[l], wf[l]);

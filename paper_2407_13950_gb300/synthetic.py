@@ -148,6 +148,35 @@ def config_5q(M: int = 256) -> ProblemSpec:
     return transmon_spec(5, 800.0, 150000, M, 53, name="5q-N243-E32")
 
 
+# The paper's own test cases (Table 1): q qubits (2 levels, all essential) in a linear chain,
+# rotating frame at the mean transition frequency, dipole exchange between neighbours, the
+# listed carrier frequencies, B-spline spacing 3 ns; durations and step counts of Table 2.
+PAPER_OMEGA_GHZ = [5.18, 5.12, 5.06, 5.0]
+PAPER_J_GHZ = 0.005
+PAPER_CARRIERS_MHZ = {
+    2: [[-30.41, 30.41], [-30.41, 30.41]],
+    3: [[0.0, -60.4], [60.4, 0.0, -60.4], [60.4, 0.0]],
+    4: [[-30.0, -90.41], [30.0, -30.0, -90.41], [90.41, 30.0, -30.0], [90.41, -30.0]],
+}
+PAPER_T_NS = {2: 190.0, 3: 500.0, 4: 900.0}
+PAPER_NSTEPS = {2: 2252, 3: 19806, 4: 106072}
+
+
+def paper_qft_spec(q: int, M: int = 1, nsteps: Optional[int] = None) -> ProblemSpec:
+    """QFT-2^q on q qubits with the paper's system parameters (Table 1) and time grid (Table 2).
+    nsteps, if given, replaces the table's step count with the same duration."""
+    om = PAPER_OMEGA_GHZ[:q]
+    rot = sum(om) / q
+    detune = [TWO_PI * (w - rot) for w in om]
+    jx = [[(TWO_PI * PAPER_J_GHZ if l == k + 1 else 0.0) for l in range(q)] for k in range(q)]
+    omega = [[TWO_PI * f * 1e-3 for f in fs] for fs in PAPER_CARRIERS_MHZ[q]]
+    T = PAPER_T_NS[q]
+    d1 = int(math.ceil(T / 3.0)) + 2
+    return ProblemSpec(q=q, L=2, ness=2, xi=[0.0] * q, xi_cross=[[0.0] * q for _ in range(q)], omega=omega,
+                       d1=d1, T=T, nsteps=nsteps or PAPER_NSTEPS[q], M=M, detune=detune, jx=jx,
+                       name=f"QFT-{2 ** q}")
+
+
 ALPHA_AMP = TWO_PI * 0.004  # rad/ns: control coefficients are uniform in +-ALPHA_AMP
 
 

@@ -68,8 +68,10 @@ def test_validation_rejects_malformed_descriptions_without_a_gpu():
     assert _create(Hb, Cb)[0] == -1
     Hb, Cb, k3 = _desc(L=5, q=2)
     assert _create(Hb, Cb)[0] == -6            # no kernel for 5 levels
-    Hb, Cb, k4 = _desc(jx=np.eye(2))
-    assert _create(Hb, Cb)[0] == -6            # dipole exchange not supported
+    Hb, Cb, k4 = _desc(jx=np.array([[0.0, 0.1], [0.0, 0.0]]))
+    assert _create(Hb, Cb)[0] == -6            # dipole exchange needs 2-level subsystems
+    Hb, Cb, k4b = _desc(jx=np.array([[0.0, np.nan], [0.0, 0.0]]))
+    assert _create(Hb, Cb)[0] == -1            # non-finite exchange
     Hb, Cb, k5 = _desc(d1=2)
     assert _create(Hb, Cb)[0] == -1            # fewer than 3 splines
     Hb, Cb, k6 = _desc(ncar=[2, 0])

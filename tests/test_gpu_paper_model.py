@@ -1,0 +1,81 @@
+"""The paper's own model (Eq. sys-ham, Table 1): 2-level qubits in a linear chain with
+detuning and dipole exchange, QFT-4/8/16 targets, the paper's carriers and B-spline spacing.
+The exchange is a constant off-diagonal part of the implicit step; parity against the oracle
+(whose exchange construction is pinned by a kron-built Hamiltonian and finite differences)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_13950_gb300 import msqoc
+from paper_2407_13950_gb300 import synthetic as S
+
+from gpu_helpers import assert_grad_close, assert_objective_close
+
+pytestmark = pytest.mark.gpu
+
+SOLVERS = {"mixed": msqoc.SOLVER_MIXED, "fp64": msqoc.SOLVER_FP64}
+
+
+def check(spec, seed, solver=msqoc.SOLVER_DEFAULT, ckpt_interval=0):
+    alpha, W = S.random_alpha(spec, seed), S.random_W(spec, seed)
+    want = oracle.evaluate(spec, alpha, W, nthreads=os.cpu_count())
+    with msqoc.Problem(spec, solver=solver, ckpt_interval=ckpt_interval) as p:
+        got = p.eval_gradient(alpha, W)
+        obj = p.eval_objective(alpha, W)
+    assert_objective_close(got["P"], want["P"])
+    assert_objective_close(obj["J"], want["J"])
+    assert_grad_close(got["grad_alpha"], want["grad_alpha"], what="grad_alpha")
+    if spec.M > 1:
+        np.testing.assert_allclose(obj["pen"], want["pen"], rtol=1e-12, atol=1e-24)
+        assert_grad_close(got["grad_W"], want["grad_W"], what="grad_W")
+
+
+@pytest.mark.parametrize("M", [1, 8, 64])
+def test_qft4_full_time_grid(M):
+    check(S.paper_qft_spec(2, M=M), 81)
+
+
+def test_qft8_ragged_windows_and_checkpoints():
+    spec = S.paper_qft_spec(3, M=13, nsteps=4001)
+    check(spec, 82)
+    check(spec, 82, ckpt_interval=7)
+
+
+@pytest.mark.parametrize("solver", list(SOLVERS))
+def test_qft16_short(solver):
+    check(S.paper_qft_spec(4, M=4, nsteps=2000), 83, solver=SOLVERS[solver])
+
+
+def test_qft16_full_size_sampled_windows():
+    """QFT-16 at the paper's full size (106072 steps) over 256 windows (the paper's largest
+    run): the last two windows against the oracle (J, pen_255, dP/dW^255), the gradients as a
+    whole by central differences along seeded random directions."""
+    spec = S.paper_qft_spec(4, M=256)
+    alpha, W = S.random_alpha(spec, 84), S.random_W(spec, 84)
+    M = spec.M
+    with msqoc.Problem(spec) as p:
+        got = p.eval_gradient(alpha, W)
+        obj = p.eval_objective(alpha, W)
+        rng = np.random.default_rng(19)
+        va, vw = rng.standard_normal(spec.d), rng.standard_normal(spec.nW)
+        ea, ew = 1e-6, 1e-7
+        fd_a = (p.eval_objective(alpha + ea * va, W)["P"] - p.eval_objective(alpha - ea * va, W)["P"]) / (2 * ea)
+        fd_w = (p.eval_objective(alpha, W + ew * vw)["P"] - p.eval_objective(alpha, W - ew * vw)["P"]) / (2 * ew)
+    want = oracle.evaluate(spec, alpha, W, windows=(M - 1, M), nthreads=os.cpu_count())
+    assert_objective_close(obj["J"], want["J"])
+    np.testing.assert_allclose(obj["pen"][M - 2], want["pen"][M - 2], rtol=1e-12, atol=0)
+    ne2 = 2 * spec.N * spec.E
+    sl = slice((M - 2) * ne2, (M - 1) * ne2)
+    assert_grad_close(got["grad_W"][sl], want["grad_W"][sl], what="grad_W^{M-1}")
+    ga_v, gw_v = float(got["grad_alpha"] @ va), float(got["grad_W"] @ vw)
+    assert abs(fd_a - ga_v) <= 1e-6 * abs(ga_v) + 16 * np.finfo(float).eps * abs(got["P"]) / ea, (fd_a, ga_v)
+    assert abs(fd_w - gw_v) <= 1e-6 * abs(gw_v) + 16 * np.finfo(float).eps * abs(got["P"]) / ew, (fd_w, gw_v)
+
+
+def test_exchange_on_three_levels_is_rejected():
+    spec = S.transmon_spec(2, 10.0, 100, 2, 5).replace(jx=[[0.0, 0.03], [0.0, 0.0]])
+    with pytest.raises(msqoc.MsqocError) as err:
+        msqoc.Problem(spec)
+    assert err.value.status == -6
