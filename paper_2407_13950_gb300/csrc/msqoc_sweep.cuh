@@ -645,9 +645,6 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
     int* tflag = &tflag_s;
     if (tid == 0) tflag_s = 0;
     // (the first barrier of the loop orders this store before every read of the flag)
-    // roll-out: the next window boundary (global step index after which U(t_boundary) is stored)
-    int boundary = 1;
-    int64_t next_boundary = (rollout && pd.M > 1) ? win_start(pd, 2) : -1;
     bool timed_out = false;
     int fsel = 0;
     double2* Dc = D0;   // FP64-solver ping-pong buffers
@@ -862,15 +859,16 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
 #pragma unroll
                 for (int l = 0; l < L; ++l) u[l] = reflect(z[l], u[l]);
             }
-            // roll-out: U(t_m) at every window boundary the step reached (t_m = t_{n+1})
-            if (rollout && live && (wn0_0 + jj + 1) == next_boundary) {
-                if (act) {
-                    double2* dst = a.out + (size_t(boundary - 1) * E + col) * N + f * L;
+            // roll-out: U(t_m) when the step ends on a window boundary t_m, i.e. when n + 1 =
+            // floor(m N_T / M) for some 1 <= m < M; the only candidate is m = ceil((n+1) M / N_T)
+            if (rollout && live && act) {
+                const int64_t n1 = wn0_0 + jj + 1;
+                const int64_t mb = (n1 * pd.M + pd.nsteps - 1) / pd.nsteps;
+                if (mb >= 1 && mb < pd.M && (mb * pd.nsteps) / pd.M == n1) {
+                    double2* dst = a.out + (size_t(mb - 1) * E + col) * N + f * L;
 #pragma unroll
                     for (int l = 0; l < L; ++l) dst[l] = u[l];
                 }
-                ++boundary;
-                next_boundary = boundary < pd.M ? win_start(pd, boundary + 1) : -1;
             }
         } else {
             // ---- gradient quadrature on the midpoints (fused): needs Ubar_n of the tile

@@ -1,0 +1,38 @@
+"""The multiple-shooting optimiser (L-BFGS over alpha and the window states, roll-out start,
+roll-out-estimate stopping rule) on the GPU objective and gradient."""
+import numpy as np
+import pytest
+
+from paper_2407_13950_gb300 import msqoc, optimize
+from paper_2407_13950_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+def test_optimiser_decreases_the_penalty_objective_and_respects_bounds():
+    spec = S.paper_qft_spec(2, M=4)                       # QFT-4, the paper's full time grid
+    alpha0 = S.random_alpha(spec, 91)
+    bound = 2 * np.pi * 0.02
+    with msqoc.Problem(spec) as p:
+        res = optimize.optimize(p, alpha0, tol=1e-3, max_iter=40, bound=bound)
+        check = p.eval_objective(res.alpha, res.W)
+    Ps = [h["P"] for h in res.history]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(Ps, Ps[1:]))     # Armijo: monotone
+    assert res.P < 0.5 * Ps[0]
+    assert res.estimate < res.history[0]["estimate"]
+    assert np.all(np.abs(res.alpha) <= bound * (1 + 1e-15))
+    assert check["P"] == pytest.approx(res.P, rel=1e-12)
+    print(f"QFT-4 M=4: P {Ps[0]:.4e} -> {res.P:.4e}, estimate {res.history[0]['estimate']:.3e} -> "
+          f"{res.estimate:.3e} in {res.iterations} iterations, {res.evaluations} evaluations")
+
+
+def test_optimiser_starts_from_the_rollout():
+    spec = S.transmon_spec(2, 20.0, 800, 4, 6)
+    alpha0 = S.random_alpha(spec, 92)
+    with msqoc.Problem(spec) as p:
+        res = optimize.optimize(p, alpha0, max_iter=0)
+        single = msqoc.Problem(spec.replace(M=1))
+        want = single.eval_objective(alpha0)["P"]
+        single.close()
+    assert res.iterations == 0
+    assert res.P == pytest.approx(want, rel=1e-11)          # all penalties zero at the roll-out
