@@ -14,9 +14,9 @@
 
 namespace msqoc {
 
-template <int SOLVER, bool BWD>
+template <int SOLVER, bool BWD, bool ROLLOUT = false>
 static cudaError_t launch_one(const SweepArgs& a, int ntiles, cudaStream_t s) {
-    auto kern = k_sweep<MSQOC_L, MSQOC_Q, SOLVER, BWD>;
+    auto kern = k_sweep<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT>;
     const size_t smem = sweep_smem_bytes(a);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -40,6 +40,9 @@ static int occupancy_one(const SweepArgs& a) {
 }
 
 cudaError_t MSQOC_CAT(launch_sweep, MSQOC_L, MSQOC_Q)(const SweepArgs& a, int ntiles, cudaStream_t s) {
+    if (a.mode == SWEEP_ROLLOUT)
+        return a.solver == SOLVER_FP64 ? launch_one<SOLVER_FP64, false, true>(a, ntiles, s)
+                                       : launch_one<SOLVER_MIXED, false, true>(a, ntiles, s);
     const bool bwd = a.mode == SWEEP_ADJOINT;
     if (a.solver == SOLVER_FP64)
         return bwd ? launch_one<SOLVER_FP64, true>(a, ntiles, s) : launch_one<SOLVER_FP64, false>(a, ntiles, s);

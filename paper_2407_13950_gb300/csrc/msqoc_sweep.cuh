@@ -448,8 +448,9 @@ __device__ __forceinline__ double warp_reduce_scatter(double (&acc)[V], int lane
 // range, per-step coefficients, iteration counts and gradient fold, computed by warp `slot`
 // (the host only builds two-slot tiles with at least two warps).  Loops run to the longer of
 // the slots' ranges; a thread whose slot has no step at an iteration keeps its state.
-template <int L, int Q, int SOLVER, bool BWD>
+template <int L, int Q, int SOLVER, bool BWD, bool ROLLOUT = false>
 __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a) {
+    static_assert(!(BWD && ROLLOUT), "the roll-out is a forward sweep");
     constexpr int N = ipow_c(L, Q);
     constexpr int NSLOT = Q * L * 2;
     constexpr int S = BWD ? +1 : -1;       // sign of the preconditioned off-diagonal term
@@ -485,7 +486,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
     const int nslot = ncol0 < ncol ? 2 : 1;
     const bool segmented = a.mode == SWEEP_RECOMPUTE || a.mode == SWEEP_ADJOINT;
     const bool idle_launch = a.mode == SWEEP_RECOMPUTE && pd.nseg == 1;   // nothing to recompute
-    const bool rollout = !BWD && a.mode == SWEEP_ROLLOUT;                 // one window: the whole grid
+    constexpr bool rollout = ROLLOUT;   // one window over the whole grid (compiled separately)
 
     // ---- the slots' windows and step ranges (local step indices [lo, lo + cnt) of the window)
     const int64_t wn0_0 = rollout ? 0 : win_start(pd, tile.m0);
