@@ -415,9 +415,29 @@ int32_t msqoc_last_error(char* buf, size_t len) {
     return static_cast<int32_t>(g_last_error.size());
 }
 
-msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, const double* target,
-                                  double T, int64_t nsteps, int32_t nwindows, double mu,
-                                  const msqoc_options* opt, msqoc_problem** out) {
+}  // extern "C"
+
+namespace {
+
+// frees a problem under construction unless released
+struct ProblemOwner {
+    msqoc_problem* p = nullptr;
+    ~ProblemOwner() {
+        if (p) {
+            free_problem(p);
+            delete p;
+        }
+    }
+    msqoc_problem* release() {
+        msqoc_problem* q = p;
+        p = nullptr;
+        return q;
+    }
+};
+
+msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, const double* target, double T,
+                            int64_t nsteps, int32_t nwindows, double mu, const msqoc_options* opt,
+                            msqoc_problem** out) {
     if (!out) return fail(MSQOC_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     msqoc_status st0 = check_description(H, C, T, nsteps, nwindows);
@@ -429,7 +449,8 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
     if (o.ckpt_interval < 0) return fail(MSQOC_ERR_INVALID_ARG, "checkpoint interval %d < 0", o.ckpt_interval);
     if (o.profile != 0 && o.profile != 1) return fail(MSQOC_ERR_INVALID_ARG, "profile must be 0 or 1");
 
-    auto* p = new (std::nothrow) msqoc_problem();
+    ProblemOwner owner{new (std::nothrow) msqoc_problem()};
+    msqoc_problem* p = owner.p;
     if (!p) return fail(MSQOC_ERR_OUT_OF_MEMORY, "host allocation failed");
     ProbDev& pd = p->pd;
     cudaGetDevice(&p->device);
@@ -437,10 +458,7 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     if (sms <= 0) sms = 1;
     st0 = shape_problem(H, C, T, nsteps, nwindows, mu, solver, o.col_block, sms, pd);
-    if (st0 != MSQOC_OK) {
-        delete p;
-        return st0;
-    }
+    if (st0 != MSQOC_OK) return st0;
     const int q = pd.q, L = pd.L, nfsum = pd.nfsum;
     // checkpoint interval: 0 = automatic (every midpoint state unless that history would take
     // more than a quarter of the device memory, else every 64 steps)
@@ -541,18 +559,25 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
         A(cudaMemset(p->status, 0, sizeof(int)), "status init");
         A(cudaMemcpy(p->pds, &pd, sizeof(ProbDev), cudaMemcpyHostToDevice), "problem record copy");
     }
-    if (st != MSQOC_OK) {
-        free_problem(p);
-        delete p;
-        return st;
-    }
+    if (st != MSQOC_OK) return st;
     p->bytes = sizeof(double2) * (N + p->ne * (1 + 3 * M) + size_t(nsteps) * (q + nfsum)) +
                sizeof(Spline4) * size_t(nsteps) + sizeof(double) * (pd.d + p->nW + M + size_t(pd.ntiles) * pd.d) +
                sizeof(int) * (E + 1 + maps.size() + maps_ro.size()) + sizeof(Tile) * (tiles.size() + tiles_ro.size()) +
                sizeof(ProbDev);
     p->grad_bytes = gradient_bytes(pd);
-    *out = p;
+    *out = owner.release();
     return MSQOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, const double* target,
+                                  double T, int64_t nsteps, int32_t nwindows, double mu,
+                                  const msqoc_options* opt, msqoc_problem** out) {
+    if (out) *out = nullptr;
+    return guarded([&] { return create_problem(H, C, target, T, nsteps, nwindows, mu, opt, out); });
 }
 
 msqoc_status msqoc_query(const msqoc_problem* p, int64_t* d, int64_t* nW, size_t* device_bytes) {
@@ -815,10 +840,11 @@ msqoc_status msqoc_kernel_times(msqoc_problem* p, float* ms) {
 
 }  // extern "C"
 // ------------------------------------------------------------------ autotuning the tile width
-extern "C" msqoc_status msqoc_autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps,
-                                       int32_t nwindows, double mu, const msqoc_options* opt, const double* alpha,
-                                       int32_t probe_steps, int32_t* col_block, int32_t* widths, float* ms,
-                                       int32_t max_out, int32_t* n_out) {
+namespace {
+
+msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps, int32_t nwindows,
+                      double mu, const msqoc_options* opt, const double* alpha, int32_t probe_steps,
+                      int32_t* col_block, int32_t* widths, float* ms, int32_t max_out, int32_t* n_out) {
     if (!col_block) return fail(MSQOC_ERR_INVALID_ARG, "col_block is NULL");
     *col_block = 0;
     if (n_out) *n_out = 0;
@@ -909,6 +935,17 @@ extern "C" msqoc_status msqoc_autotune(const msqoc_hamiltonian* H, const msqoc_c
     *col_block = best;
     if (n_out) *n_out = std::min(nrec, max_out);
     return MSQOC_OK;
+}
+
+}  // namespace
+
+extern "C" msqoc_status msqoc_autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps,
+                                       int32_t nwindows, double mu, const msqoc_options* opt, const double* alpha,
+                                       int32_t probe_steps, int32_t* col_block, int32_t* widths, float* ms,
+                                       int32_t max_out, int32_t* n_out) {
+    return guarded([&] {
+        return autotune(H, C, T, nsteps, nwindows, mu, opt, alpha, probe_steps, col_block, widths, ms, max_out, n_out);
+    });
 }
 
 // ------------------------------------------------------------------ objective without allocation

@@ -138,11 +138,18 @@ msqoc_status eval(msqoc_batch* b, bool grad, cudaStream_t s) {
     return MSQOC_OK;
 }
 
-}  // namespace
+// frees a batch under construction unless released
+struct BatchOwner {
+    msqoc_batch* b = nullptr;
+    ~BatchOwner() {
+        if (b) {
+            free_batch(b);
+            delete b;
+        }
+    }
+};
 
-extern "C" {
-
-msqoc_status msqoc_batch_create(msqoc_problem* const* problems, int32_t n, int32_t flags, msqoc_batch** out) {
+msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t flags, msqoc_batch** out) {
     if (!out) return fail(MSQOC_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!problems || n < 1) return fail(MSQOC_ERR_INVALID_ARG, "no problems");
@@ -155,7 +162,8 @@ msqoc_status msqoc_batch_create(msqoc_problem* const* problems, int32_t n, int32
         for (int j = 0; j < i; ++j)
             if (problems[j] == problems[i]) return fail(MSQOC_ERR_INVALID_ARG, "problem %d appears twice", i);
     }
-    auto* b = new (std::nothrow) msqoc_batch();
+    BatchOwner owner{new (std::nothrow) msqoc_batch()};
+    msqoc_batch* b = owner.b;
     if (!b) return fail(MSQOC_ERR_OUT_OF_MEMORY, "host allocation failed");
     b->flags = flags;
     b->device = dev;
@@ -263,27 +271,14 @@ msqoc_status msqoc_batch_create(msqoc_problem* const* problems, int32_t n, int32
     for (int k = 0; k < MSQOC_BATCH_SLOTS && !st; ++k)
         if (cudaEventCreateWithFlags(&b->slot_done[k], cudaEventDisableTiming) != cudaSuccess)
             st = fail(MSQOC_ERR_CUDA, "event creation failed");
-    if (st) {
-        free_batch(b);
-        delete b;
-        return st;
-    }
+    if (st) return st;
     *out = b;
+    owner.b = nullptr;
     return MSQOC_OK;
 }
 
-msqoc_status msqoc_batch_eval_objective(msqoc_batch* b, void* stream) {
-    if (!b) return fail(MSQOC_ERR_INVALID_ARG, "batch is NULL");
-    return eval(b, false, static_cast<cudaStream_t>(stream));
-}
-
-msqoc_status msqoc_batch_eval_gradient(msqoc_batch* b, void* stream) {
-    if (!b) return fail(MSQOC_ERR_INVALID_ARG, "batch is NULL");
-    return eval(b, true, static_cast<cudaStream_t>(stream));
-}
-
-msqoc_status msqoc_batch_eval_subset(msqoc_batch* b, const int32_t* members, int32_t n, int32_t gradient,
-                                     int32_t slot, void* stream) {
+msqoc_status batch_eval_subset(msqoc_batch* b, const int32_t* members, int32_t n, int32_t gradient, int32_t slot,
+                               void* stream) {
     if (!b || !members || n < 1) return fail(MSQOC_ERR_INVALID_ARG, "batch or members is NULL / empty");
     if (slot < 0 || slot >= MSQOC_BATCH_SLOTS) return fail(MSQOC_ERR_INVALID_ARG, "slot %d out of range", slot);
     if (gradient && !(b->flags & MSQOC_BATCH_GRADIENT))
@@ -322,6 +317,30 @@ msqoc_status msqoc_batch_eval_subset(msqoc_batch* b, const int32_t* members, int
     }
     CUDA_TRY(cudaEventRecord(b->slot_done[slot], s));
     return enqueue(b, sel, tiles.data(), ntiles.data(), gradient != 0, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+msqoc_status msqoc_batch_create(msqoc_problem* const* problems, int32_t n, int32_t flags, msqoc_batch** out) {
+    if (out) *out = nullptr;
+    return guarded([&] { return batch_create(problems, n, flags, out); });
+}
+
+msqoc_status msqoc_batch_eval_objective(msqoc_batch* b, void* stream) {
+    if (!b) return fail(MSQOC_ERR_INVALID_ARG, "batch is NULL");
+    return guarded([&] { return eval(b, false, static_cast<cudaStream_t>(stream)); });
+}
+
+msqoc_status msqoc_batch_eval_gradient(msqoc_batch* b, void* stream) {
+    if (!b) return fail(MSQOC_ERR_INVALID_ARG, "batch is NULL");
+    return guarded([&] { return eval(b, true, static_cast<cudaStream_t>(stream)); });
+}
+
+msqoc_status msqoc_batch_eval_subset(msqoc_batch* b, const int32_t* members, int32_t n, int32_t gradient,
+                                     int32_t slot, void* stream) {
+    return guarded([&] { return batch_eval_subset(b, members, n, gradient, slot, stream); });
 }
 
 msqoc_status msqoc_batch_destroy(msqoc_batch* b) {

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <new>
 
 #include "../../include/msqoc.h"
 #include "msqoc_internal.h"
@@ -64,6 +65,19 @@ msqoc_status fail(msqoc_status code, const char* fmt, ...);
     } while (0)
 
 bool is_device_ptr(const void* p);
+
+// Runs f and turns a C++ exception (a failed host allocation in a std container) into a status:
+// nothing may unwind across the C ABI.
+template <class F>
+msqoc_status guarded(F&& f) noexcept {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return fail(MSQOC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail(MSQOC_ERR_INTERNAL, "unexpected C++ exception");
+    }
+}
 
 // tile layout (see msqoc_api.cu)
 void build_lanemap(int L, int q, int ncol, int ncol0, int nthreads, int* out);
