@@ -70,6 +70,7 @@ def lib():
                 "oracle_propagate": (ci, [P, vp, i64, i64, vp, vp, ci]),
                 "oracle_propagate_adjoint": (ci, [P, vp, i64, i64, vp, vp, ci]),
                 "oracle_rollout": (ci, [P, vp, vp]),
+                "oracle_regularization": (cd, [P, vp, cd, cd, vp]),
                 "oracle_eval_windows": (ci, [P, vp, vp, ci, ci, ci, vp, vp, vp, vp, vp, vp, vp]),
                 "oracle_eval": (ci, [P, vp, vp, ci, vp, vp, vp, vp, vp]),
             }
@@ -232,6 +233,16 @@ def rollout(spec, alpha) -> np.ndarray:
     if lib().oracle_rollout(p.ref, _ptr(a), _ptr(out)):
         raise RuntimeError("oracle_rollout failed")
     return out
+
+
+def regularization(spec, alpha, gamma_tik: float, gamma_energy: float):
+    """(R, dR/dalpha): (gamma_tik/2)||alpha||^2 + gamma_energy * midpoint-rule integral of
+    sum_k |d_k(t)|^2 over [0, T] (Sec. 5 regularization)."""
+    p = _as_problem(spec)
+    a = _f64(alpha)
+    g = np.zeros(a.size)
+    R = lib().oracle_regularization(p.ref, _ptr(a), float(gamma_tik), float(gamma_energy), _ptr(g))
+    return R, g
 
 
 def default_threads() -> int:

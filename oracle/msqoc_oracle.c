@@ -507,6 +507,57 @@ int oracle_rollout(const oracle_problem* p, const double* alpha, double* W_out) 
     return rc;
 }
 
+/* Regularization of the optimisation problem (Sec. 5): a Tikhonov term (gamma_tik/2)||alpha||^2
+ * on the control vector plus gamma_energy times the control-pulse energy
+ * int_0^T sum_k |d_k(t)|^2 dt.  The integral is the midpoint rule on the time grid (the
+ * quadrature of the gradient integral, Eq. grad-int).  The gradient differentiates each
+ * term literally: with d_k = sum_f exp(i Omega_kf t) sum_s (alpha1 + i alpha2)_kfs B_s(t),
+ *   d|d_k|^2 / d alpha1_kfs = 2 Re(conj(d_k) exp(i Omega_kf t) B_s(t)),
+ *   d|d_k|^2 / d alpha2_kfs = 2 Re(conj(d_k) i exp(i Omega_kf t) B_s(t)).
+ * Step sums are accumulated in blocks of BLOCK_REG steps.  grad may be NULL. */
+#define BLOCK_REG 256
+double oracle_regularization(const oracle_problem* p, const double* alpha, double gamma_tik, double gamma_energy,
+                             double* grad) {
+    int N, E, d;
+    dims(p, &N, &E, &d);
+    double h = p->T / (double)p->nsteps;
+    double* dk = malloc(sizeof(double) * 2 * p->q);
+    double* gblk = calloc((size_t)d, sizeof(double));
+    double* gsum = calloc((size_t)d, sizeof(double));
+    double energy = 0.0, eblk = 0.0;
+    for (int64_t n = 0; n < p->nsteps; ++n) {
+        double t = ((double)n + 0.5) * h;
+        oracle_controls(p, alpha, t, dk);
+        int off = 0;
+        for (int k = 0; k < p->q; ++k) {
+            cplx dkc = dk[2 * k] + I * dk[2 * k + 1];
+            eblk += creal(dkc) * creal(dkc) + cimag(dkc) * cimag(dkc);
+            for (int f = 0; f < p->nf[k]; ++f) {
+                cplx e = cexp(I * p->omega[off + f] * t);
+                for (int s = 0; s < p->d1; ++s) {
+                    double B = basis(p, s, t);
+                    size_t j = (size_t)2 * ((size_t)(off + f) * p->d1 + s);
+                    gblk[j] += 2.0 * creal(conj(dkc) * e * B);
+                    gblk[j + 1] += 2.0 * creal(conj(dkc) * I * e * B);
+                }
+            }
+            off += p->nf[k];
+        }
+        if ((n + 1) % BLOCK_REG == 0 || n + 1 == p->nsteps) {
+            energy += eblk;
+            eblk = 0.0;
+            for (int j = 0; j < d; ++j) { gsum[j] += gblk[j]; gblk[j] = 0.0; }
+        }
+    }
+    double tik = 0.0;
+    for (int j = 0; j < d; ++j) tik += alpha[j] * alpha[j];
+    double R = 0.5 * gamma_tik * tik + gamma_energy * h * energy;
+    if (grad)
+        for (int j = 0; j < d; ++j) grad[j] = gamma_tik * alpha[j] + gamma_energy * h * gsum[j];
+    free(dk); free(gblk); free(gsum);
+    return R;
+}
+
 /* ------------------------------------------------------------------ one window's work */
 
 typedef struct {

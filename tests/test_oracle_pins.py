@@ -452,3 +452,65 @@ def test_initial_adjoint_norm_is_terminal_norm():
             g = np.vdot(V, Uend)
             xi_norm = np.linalg.norm(g * V - sp.E * Uend) / sp.E ** 2
         assert np.linalg.norm(Lam0) == pytest.approx(xi_norm, rel=1e-12)
+
+
+# ----------------------------------------------------------------------------- regularization
+def _constant_envelope_alpha(spec, coeffs):
+    """alpha whose every spline coefficient of carrier (k, f) is coeffs[(k, f)] (complex):
+    by the partition of unity the envelope of that carrier is the constant coeffs[(k, f)]."""
+    a = np.zeros(spec.d)
+    fi = 0
+    for k in range(spec.q):
+        for f in range(len(spec.omega[k])):
+            c = coeffs.get((k, f), 0.0)
+            blk = a[2 * spec.d1 * fi: 2 * spec.d1 * (fi + 1)]
+            blk[0::2], blk[1::2] = c.real if c else 0.0, c.imag if c else 0.0
+            fi += 1
+    return a
+
+
+def test_control_energy_of_constant_envelopes_is_T_times_amplitude_squared():
+    sp = S.transmon_spec(2, 12.0, 300, 1, 7)
+    c = {(0, 0): 0.3 - 0.2j, (1, 0): -0.1 + 0.05j}          # carrier 0 has Omega = 0
+    R, _ = oracle.regularization(sp, _constant_envelope_alpha(sp, c), 0.0, 1.0)
+    want = sp.T * sum(abs(v) ** 2 for v in c.values())
+    assert R == pytest.approx(want, rel=1e-13)
+
+
+def test_control_energy_two_carriers_geometric_sum():
+    # |c0 + c1 e^{i D t}|^2 = |c0|^2 + |c1|^2 + 2 Re(conj(c0) c1 e^{i D t}); the midpoint sum of
+    # the oscillating term is a geometric series with a closed form
+    sp = S.transmon_spec(1, 10.0, 250, 1, 6)
+    c0, c1 = 0.4 + 0.1j, -0.2 + 0.3j
+    R, _ = oracle.regularization(sp, _constant_envelope_alpha(sp, {(0, 0): c0, (0, 1): c1}), 0.0, 1.0)
+    D = sp.omega[0][1] - sp.omega[0][0]
+    h, n = sp.T / sp.nsteps, sp.nsteps
+    geo = h * np.exp(0.5j * D * h) * (1 - np.exp(1j * D * h * n)) / (1 - np.exp(1j * D * h))
+    want = sp.T * (abs(c0) ** 2 + abs(c1) ** 2) + 2 * (np.conj(c0) * c1 * geo).real
+    assert R == pytest.approx(want, rel=1e-12)
+
+
+def test_tikhonov_term_closed_form():
+    sp = S.transmon_spec(2, 8.0, 100, 2, 5)
+    a = S.random_alpha(sp, 3)
+    R, g = oracle.regularization(sp, a, 0.7, 0.0)
+    assert R == pytest.approx(0.35 * float(a @ a), rel=1e-14)
+    np.testing.assert_allclose(g, 0.7 * a, rtol=1e-15)
+
+
+def test_regularization_gradient_central_differences_and_euler_identity():
+    # R is a quadratic in alpha: central differences are exact up to rounding, and for the
+    # homogeneous energy term alpha . grad E = 2 E
+    sp = S.paper_qft_spec(2, nsteps=240).replace(T=20.0, d1=9)
+    a = S.random_alpha(sp, 5, amp=2 * np.pi * 0.01)
+    gt, ge = 1e-3 / sp.d, 1e-3
+    R, g = oracle.regularization(sp, a, gt, ge)
+    fd = np.empty(sp.d)
+    eps = 1e-3
+    for j in range(sp.d):
+        e = np.zeros(sp.d)
+        e[j] = eps
+        fd[j] = (oracle.regularization(sp, a + e, gt, ge)[0] - oracle.regularization(sp, a - e, gt, ge)[0]) / (2 * eps)
+    np.testing.assert_allclose(g, fd, rtol=1e-8, atol=1e-10 * np.max(np.abs(g)))
+    E, gE = oracle.regularization(sp, a, 0.0, 1.0)
+    assert float(a @ gE) == pytest.approx(2 * E, rel=1e-12)
