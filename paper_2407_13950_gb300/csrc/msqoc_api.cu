@@ -367,7 +367,7 @@ void free_problem(msqoc_problem* p) {
     void* bufs[] = {p->tiles_ro, p->lanemap_ro,
                     p->pds,   p->tiles, p->lanemap, p->P,     p->emb,   p->V,     p->alpha_dev, p->W_dev,
                     p->ctrl,  p->spl,   p->phase,   p->hist,  p->ckpt,  p->Lstate, p->Uend,     p->Lterm,
-                    p->Lam0,  p->term,  p->gpart,   p->status, p->out_dev};
+                    p->Lam0,  p->term,  p->gpart,   p->status, p->out_dev, p->reg_dev};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->status_host) cudaFreeHost(p->status_host);
@@ -391,6 +391,9 @@ struct Mark {
         if (p->profile) cudaEventRecord(p->ev[k][1], s);
     }
 };
+
+// doubles of the regularization scratch: alpha[d], gradient[d], energy shares[q d1], R
+size_t reg_doubles(const ProbDev& pd) { return 2 * size_t(pd.d) + size_t(pd.q) * pd.d1 + 2; }
 
 // device bytes of the history, checkpoints and segment state of one problem
 size_t gradient_bytes(const ProbDev& pd) {
@@ -526,6 +529,7 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
     A(dalloc(&p->gpart, size_t(pd.ntiles) * pd.d), "gradient partials");
     A(dalloc(&p->status, 1), "status");
     A(dalloc(&p->out_dev, out_layout(pd.M, pd.d, p->nW).total), "outputs");
+    A(dalloc(&p->reg_dev, reg_doubles(pd)), "regularization scratch");
     A(cudaMallocHost(reinterpret_cast<void**>(&p->status_host), sizeof(int)), "pinned status");
     p->profile = o.profile == 1;
     if (p->profile)
@@ -561,7 +565,8 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
     }
     if (st != MSQOC_OK) return st;
     p->bytes = sizeof(double2) * (N + p->ne * (1 + 3 * M) + size_t(nsteps) * (q + nfsum)) +
-               sizeof(Spline4) * size_t(nsteps) + sizeof(double) * (pd.d + p->nW + M + size_t(pd.ntiles) * pd.d) +
+               sizeof(Spline4) * size_t(nsteps) + sizeof(double) * (pd.d + p->nW + M + size_t(pd.ntiles) * pd.d + out_layout(pd.M, pd.d, p->nW).total +
+                                reg_doubles(pd)) +
                sizeof(int) * (E + 1 + maps.size() + maps_ro.size()) + sizeof(Tile) * (tiles.size() + tiles_ro.size()) +
                sizeof(ProbDev);
     p->grad_bytes = gradient_bytes(pd);
@@ -824,6 +829,33 @@ msqoc_status msqoc_rollout_estimate(msqoc_problem* p, double* est_out, void* str
     if (dev) return MSQOC_OK;
     CUDA_TRY(cudaMemcpyAsync(est_out, dst, sizeof(double), cudaMemcpyDeviceToHost, s));
     return check_status_sync(p, s);
+}
+
+msqoc_status msqoc_eval_regularization(msqoc_problem* p, const double* alpha, double gamma_tik,
+                                       double gamma_energy, double* R_out, double* grad_alpha, void* stream) {
+    if (!p) return fail(MSQOC_ERR_INVALID_ARG, "problem is NULL");
+    if (!alpha || !R_out) return fail(MSQOC_ERR_INVALID_ARG, "alpha or R_out is NULL");
+    if (!(gamma_tik >= 0.0) || !(gamma_energy >= 0.0) || std::isinf(gamma_tik) || std::isinf(gamma_energy))
+        return fail(MSQOC_ERR_INVALID_ARG, "gamma_tik %g and gamma_energy %g must be finite and >= 0", gamma_tik,
+                    gamma_energy);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const ProbDev& pd = p->pd;
+    double* a = p->reg_dev;
+    double* g = a + pd.d;
+    double* ep = g + pd.d;
+    double* R = ep + size_t(pd.q) * pd.d1;
+    const bool dR = is_device_ptr(R_out);
+    const bool dg = grad_alpha && is_device_ptr(grad_alpha);
+    CUDA_TRY(cudaMemcpyAsync(a, alpha, pd.d * sizeof(double), cudaMemcpyDefault, s));
+    k_regularization<<<pd.q * pd.d1, REG_THREADS, 0, s>>>(pd, a, gamma_tik, gamma_energy, dg ? grad_alpha : g, ep);
+    CUDA_TRY(cudaGetLastError());
+    k_regularization_total<<<1, REG_THREADS, 0, s>>>(pd, a, gamma_tik, gamma_energy, ep, dR ? R_out : R);
+    CUDA_TRY(cudaGetLastError());
+    if (dR && (dg || !grad_alpha)) return MSQOC_OK;
+    if (!dR) CUDA_TRY(cudaMemcpyAsync(R_out, R, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (grad_alpha && !dg) CUDA_TRY(cudaMemcpyAsync(grad_alpha, g, pd.d * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return MSQOC_OK;
 }
 
 msqoc_status msqoc_kernel_times(msqoc_problem* p, float* ms) {

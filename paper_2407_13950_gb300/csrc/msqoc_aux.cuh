@@ -57,23 +57,31 @@ __device__ inline int step_counts(int solver, float rho) {
     return a | (b << 8) | (r << 16) | (bad << 24);
 }
 
+// The quadratic cardinal B-splines active at time t: on [j dtau, (j+1) dtau) the three
+// non-zero splines are s = j, j+1, j+2 with weights (1-x)^2/2, 3/4 - (x-1/2)^2, x^2/2
+// (x = t/dtau - j); j is clamped to [0, d1 - 3].
+struct SplineAt {
+    int s0;
+    double w0, w1, w2;
+};
+
+__device__ __forceinline__ SplineAt spline_at(const ProbDev& pd, double t) {
+    const double tau = t / pd.dtau;
+    int s0 = static_cast<int>(floor(tau));
+    s0 = s0 < 0 ? 0 : (s0 > pd.d1 - 3 ? pd.d1 - 3 : s0);
+    const double x = tau - s0;
+    return SplineAt{s0, 0.5 * (1.0 - x) * (1.0 - x), 0.75 - (x - 0.5) * (x - 0.5), 0.5 * x * x};
+}
+
 // Controls at every step midpoint t_{n+1/2} = (n + 1/2) h (Eq. dj-ctrl with the quadratic
 // B-spline envelope of Sec. 2): d_k(t) = sum_f e^{i Omega_kf t} sum_s (a1 + i a2)_kfs B_s(t),
-// and the step solver's iteration counts (step_counts).
-// On [j dtau, (j+1) dtau) the three non-zero splines are s = j, j+1, j+2 with weights
-// (1-x)^2/2, 3/4 - (x-1/2)^2, x^2/2 (x = t/dtau - j).  Also stores the spline weights and the
-// carrier phases for the gradient quadrature of the adjoint sweep.
+// and the step solver's iteration counts (step_counts).  Also stores the spline weights and
+// the carrier phases for the gradient quadrature of the adjoint sweep.
 __global__ void k_controls(const ProbDev pd) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; n < pd.nsteps; n += stride) {
         const double t = (double(n) + 0.5) * pd.h;
-        const double tau = t / pd.dtau;
-        int s0 = static_cast<int>(floor(tau));
-        s0 = s0 < 0 ? 0 : (s0 > pd.d1 - 3 ? pd.d1 - 3 : s0);
-        const double x = tau - s0;
-        const double w0 = 0.5 * (1.0 - x) * (1.0 - x);
-        const double w1 = 0.75 - (x - 0.5) * (x - 0.5);
-        const double w2 = 0.5 * x * x;
+        const SplineAt sp = spline_at(pd, t);
         double mag = 0.0;   // sum_k |d_k| for the contraction bound
         for (int k = 0; k < pd.q; ++k) {
             double2 dk = make_double2(0.0, 0.0);
@@ -81,9 +89,9 @@ __global__ void k_controls(const ProbDev pd) {
                 double sn, cs;
                 sincos(pd.omega[fi] * t, &sn, &cs);
                 pd.phase[size_t(n) * pd.nfsum + fi] = make_double2(cs, sn);
-                const double* a = pd.alpha + (size_t(fi) * pd.d1 + s0) * 2;
-                const double er = a[0] * w0 + a[2] * w1 + a[4] * w2;
-                const double ei = a[1] * w0 + a[3] * w1 + a[5] * w2;
+                const double* a = pd.alpha + (size_t(fi) * pd.d1 + sp.s0) * 2;
+                const double er = a[0] * sp.w0 + a[2] * sp.w1 + a[4] * sp.w2;
+                const double ei = a[1] * sp.w0 + a[3] * sp.w1 + a[5] * sp.w2;
                 dk.x += cs * er - sn * ei;
                 dk.y += cs * ei + sn * er;
             }
@@ -91,7 +99,7 @@ __global__ void k_controls(const ProbDev pd) {
             mag += sqrt(dk.x * dk.x + dk.y * dk.y);
         }
         const float rho = float(0.5 * pd.h * pd.lam * mag + pd.rho_ex) * 1.0001f;
-        pd.spl[n] = Spline4{s0, step_counts(pd.solver, rho), w0, w1, w2};
+        pd.spl[n] = Spline4{sp.s0, step_counts(pd.solver, rho), sp.w0, sp.w1, sp.w2};
     }
 }
 
@@ -201,6 +209,80 @@ __global__ void k_grad_W(const ProbDev pd, double2* gW) {
         const double2 l0 = pd.Lam0[e + ne];
         gW[e] = make_double2(2.0 * (lt.x - l0.x), 2.0 * (lt.y - l0.y));
     }
+}
+
+constexpr int REG_THREADS = 256;
+
+// Regularization of the optimisation problem (Sec. 5): R = (gamma_tik/2) ||alpha||^2 +
+// gamma_energy E with the control-pulse energy E = h sum_n sum_k |d_k(t_{n+1/2})|^2 (the
+// midpoint rule of int_0^T sum_k |d_k|^2 dt on the time grid).  One block per (subsystem k,
+// spline s), over the steps where spline s is active (its weight B = w_{s - s0}):
+//   dR/d alpha1_kfs = gamma_tik alpha1_kfs + 2 gamma_energy h sum_n B Re(conj(d_k) e^{i Omega_kf t}),
+//   dR/d alpha2_kfs = gamma_tik alpha2_kfs - 2 gamma_energy h sum_n B Im(conj(d_k) e^{i Omega_kf t}),
+// and the block's share of the energy, h sum |d_k|^2 over the steps whose first active spline
+// is s (each step is counted by exactly one block per k).  Every sum has a fixed order.
+__global__ void __launch_bounds__(REG_THREADS) k_regularization(const ProbDev pd, const double* alpha,
+                                                                 double gamma_tik, double gamma_energy,
+                                                                 double* grad, double* epart) {
+    __shared__ double sh[REG_THREADS];
+    const int k = blockIdx.x / pd.d1, s = blockIdx.x % pd.d1;
+    // steps whose midpoint lies in [(s - 2) dtau, (s + 1) dtau), widened by two steps on each side
+    // (membership is decided exactly by spline_at below)
+    const double r = pd.dtau / pd.h;
+    const int64_t lo = max(int64_t(0), int64_t(floor((s - 2) * r - 0.5)) - 2);
+    const int64_t hi = min(pd.nsteps, int64_t(ceil((s + 1) * r)) + 2);
+    for (int fi = pd.cof[k] - 1; fi < pd.cof[k + 1]; ++fi) {   // fi = cof[k] - 1: the energy
+        double acc_re = 0.0, acc_im = 0.0;
+        for (int64_t n = lo + threadIdx.x; n < hi; n += REG_THREADS) {
+            const double t = (double(n) + 0.5) * pd.h;
+            const SplineAt sp = spline_at(pd, t);
+            const int j = s - sp.s0;
+            if (j < 0 || j > 2 || (fi < pd.cof[k] && j != 0)) continue;
+            double2 dk = make_double2(0.0, 0.0), ph = make_double2(0.0, 0.0);
+            for (int g = pd.cof[k]; g < pd.cof[k + 1]; ++g) {
+                double sn, cs;
+                sincos(pd.omega[g] * t, &sn, &cs);
+                const double* a = alpha + (size_t(g) * pd.d1 + sp.s0) * 2;
+                const double er = a[0] * sp.w0 + a[2] * sp.w1 + a[4] * sp.w2;
+                const double ei = a[1] * sp.w0 + a[3] * sp.w1 + a[5] * sp.w2;
+                dk.x += cs * er - sn * ei;
+                dk.y += cs * ei + sn * er;
+                if (g == fi) ph = make_double2(cs, sn);
+            }
+            if (fi < pd.cof[k]) {
+                acc_re += dk.x * dk.x + dk.y * dk.y;
+            } else {
+                const double B = j == 0 ? sp.w0 : (j == 1 ? sp.w1 : sp.w2);
+                // conj(d_k) e^{i Omega t}
+                acc_re += B * (dk.x * ph.x + dk.y * ph.y);
+                acc_im += B * (dk.x * ph.y - dk.y * ph.x);
+            }
+        }
+        const double sre = block_sum<REG_THREADS>(acc_re, sh);
+        const double sim = block_sum<REG_THREADS>(acc_im, sh);
+        if (threadIdx.x == 0) {
+            if (fi < pd.cof[k]) {
+                epart[blockIdx.x] = pd.h * sre;
+            } else {
+                const size_t i = (size_t(fi) * pd.d1 + s) * 2;
+                grad[i] = gamma_tik * alpha[i] + 2.0 * gamma_energy * pd.h * sre;
+                grad[i + 1] = gamma_tik * alpha[i + 1] - 2.0 * gamma_energy * pd.h * sim;
+            }
+        }
+    }
+}
+
+// R from the energy shares of k_regularization and ||alpha||^2 (one block, fixed order)
+__global__ void __launch_bounds__(REG_THREADS) k_regularization_total(const ProbDev pd, const double* alpha,
+                                                                       double gamma_tik, double gamma_energy,
+                                                                       const double* epart, double* R) {
+    __shared__ double sh[REG_THREADS];
+    double a2 = 0.0, en = 0.0;
+    for (int i = threadIdx.x; i < pd.d; i += REG_THREADS) a2 += alpha[i] * alpha[i];
+    for (int i = threadIdx.x; i < pd.q * pd.d1; i += REG_THREADS) en += epart[i];
+    a2 = block_sum<REG_THREADS>(a2, sh);
+    en = block_sum<REG_THREADS>(en, sh);
+    if (threadIdx.x == 0) *R = 0.5 * gamma_tik * a2 + gamma_energy * en;
 }
 
 }  // namespace msqoc

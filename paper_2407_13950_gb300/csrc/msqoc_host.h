@@ -41,6 +41,7 @@ struct msqoc_problem {
     double* gpart = nullptr;
     int* status = nullptr;
     double* out_dev = nullptr;     // outputs of the last evaluation: P, J, pen[M-1], galpha[d], gW[nW]
+    double* reg_dev = nullptr;     // regularization: alpha[d], gradient[d], energy shares[q d1], R
     int* status_host = nullptr;    // pinned
     size_t bytes = 0;              // device bytes held now
     size_t grad_bytes = 0;         // bytes the first gradient evaluation adds

@@ -26,7 +26,7 @@ EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_query_layout", "msqoc_
             "msqoc_measure_fp64_peak", "msqoc_eval_objective_noalloc", "msqoc_batch_create",
             "msqoc_batch_eval_objective", "msqoc_batch_eval_gradient", "msqoc_batch_destroy", "msqoc_set_inputs",
             "msqoc_get_objective", "msqoc_get_gradient", "msqoc_batch_eval_subset", "msqoc_autotune",
-            "msqoc_rollout", "msqoc_rollout_estimate"]
+            "msqoc_rollout", "msqoc_rollout_estimate", "msqoc_eval_regularization"]
 BATCH_GRADIENT, BATCH_GRAPH = 1, 2
 KERNEL_NAMES = ["controls", "forward", "terminal", "adjoint", "finalize"]
 
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
             "msqoc_batch_eval_subset": (i32, [vp, vp, i32, i32, i32, vp]),
             "msqoc_rollout": (i32, [vp, vp, vp, vp]),
             "msqoc_rollout_estimate": (i32, [vp, vp, vp]),
+            "msqoc_eval_regularization": (i32, [vp, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp]),
             "msqoc_autotune": (i32, [vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, vp, vp, i32, vp, vp, vp,
                                      i32, vp]),
         }
@@ -238,7 +239,20 @@ class Problem:
         _check(load().msqoc_rollout_estimate(self.handle, _ptr(est), _stream_handle(stream)))
         return float(est[0])
 
+    def eval_regularization(self, alpha, gamma_tik: float, gamma_energy: float, stream=None) -> dict:
+        """Tikhonov + control-energy regularization (Sec. 5) and its alpha-gradient."""
+        R = np.zeros(1)
+        g = np.zeros(self.d)
+        _check(load().msqoc_eval_regularization(self.handle, _ptr(alpha), float(gamma_tik), float(gamma_energy),
+                                                _ptr(R), _ptr(g), _stream_handle(stream)))
+        return {"R": float(R[0]), "grad_alpha": g}
+
     # ---- pointer-level API (device tensors; asynchronous on the stream)
+    def eval_regularization_into(self, alpha, gamma_tik: float, gamma_energy: float, R_out, grad_alpha,
+                                 stream=None):
+        _check(load().msqoc_eval_regularization(self.handle, _ptr(alpha), float(gamma_tik), float(gamma_energy),
+                                                _ptr(R_out), _ptr(grad_alpha), _stream_handle(stream)))
+
     def eval_gradient_into(self, alpha, W, P_out, grad_alpha, grad_W, stream=None):
         _check(load().msqoc_eval_gradient(self.handle, _ptr(alpha), _ptr(W), _ptr(P_out), _ptr(grad_alpha),
                                           _ptr(grad_W), _stream_handle(stream)))

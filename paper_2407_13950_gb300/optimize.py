@@ -2,20 +2,30 @@
 
 The optimisation variables are the control coefficients alpha and the window states
 W^1..W^{M-1} (Sec. 3: the penalty objective P(alpha, W) is minimised over both).  Following
-Sec. 5, the window states start from a roll-out of the initial controls (all continuity
-penalties zero), the penalty weight is fixed (mu = 2/E, the problem's default), and the
-iteration stops once the estimate of the roll-out infidelity (Eq. rollout-infid-est) falls
-below a tolerance.  The minimiser is L-BFGS (two-loop recursion, limited memory) with a
-backtracking Armijo line search; optional box bounds on alpha are kept by projection (the
-search direction is built from the projected gradient and steps are clipped).
+Sec. 5:
+- the window states start from a roll-out of the initial controls (all continuity penalties
+  zero);
+- the penalty weight is fixed (mu = 2/E, the problem's default);
+- the objective may carry the paper's regularization: a Tikhonov term (gamma_tik/2)||alpha||^2
+  and the control-pulse energy gamma_energy int sum_k |d_k|^2 dt (msqoc_eval_regularization);
+- the window states may enter the optimisation scaled, W~ = sigma W, which balances the
+  alpha- and W-parts of the gradient (the paper scans sigma in [0.05, 0.15]);
+- box bounds on alpha keep the pulse amplitudes below a limit (`amplitude_bound`);
+- the iteration stops once the estimate of the roll-out infidelity (Eq. rollout-infid-est)
+  falls below a tolerance.
 
-Every objective and gradient comes from the library's kernels through the C ABI; the vectors
-of the recursion live on the GPU as torch tensors (FP64) and only scalars cross to the host.
+The minimiser is L-BFGS (two-loop recursion, limited memory) with a backtracking Armijo line
+search; the box bounds are kept by projection: an alpha at its bound whose gradient pushes it
+outward is held fixed for the iteration (its gradient and search-direction components are
+zeroed) and steps are clipped to the box.  Every objective and gradient comes from the
+library's kernels through the C ABI; the vectors of the recursion live on the GPU as torch
+tensors (FP64) and only scalars cross to the host.
 """
 from __future__ import annotations
 
 import dataclasses
-from typing import List, Optional
+import math
+from typing import List, Union
 
 import numpy as np
 
@@ -25,115 +35,154 @@ from . import msqoc
 @dataclasses.dataclass
 class Result:
     alpha: np.ndarray
-    W: np.ndarray
-    P: float
+    W: np.ndarray                   # unscaled window states
+    P: float                        # penalty objective at the end (without the regularization)
+    F: float                        # minimised objective P + R
     estimate: float                 # roll-out infidelity estimate at the end
     iterations: int
     evaluations: int
     converged: bool
-    history: List[dict]             # per iteration: P, J, estimate, step
+    history: List[dict]             # per iteration: F, P, estimate, step
+
+
+def amplitude_bound(spec, max_amplitude: float) -> np.ndarray:
+    """Per-coefficient box bound b (layout of alpha) such that |alpha1|, |alpha2| <= b keeps
+    |d_k(t)| <= max_amplitude (rad/ns) at every t.  The B-splines are non-negative and sum
+    to one, so |d_k(t)| <= sum_f max_s |alpha1 + i alpha2|_kfs <= sqrt(2) N_f(k) b_k:
+    b_k = max_amplitude / (sqrt(2) N_f(k))."""
+    out = []
+    for k in range(spec.q):
+        nf = len(spec.omega[k])
+        out.extend([max_amplitude / (math.sqrt(2.0) * nf)] * (2 * spec.d1 * nf))
+    return np.asarray(out, dtype=np.float64)
+
+
+def paper_settings(spec) -> dict:
+    """The optimisation settings of Sec. 5: amplitudes below 2 pi x 25 MHz, gamma_tik = 1e-3/d,
+    gamma_energy = 1e-3, roll-out estimate below 1e-3."""
+    return {"bound": amplitude_bound(spec, 2 * math.pi * 0.025), "gamma_tik": 1e-3 / spec.d,
+            "gamma_energy": 1e-3, "tol": 1e-3}
 
 
 def optimize(problem: msqoc.Problem, alpha0, W0=None, *, tol: float = 1e-3, max_iter: int = 200,
-             memory: int = 10, bound: Optional[float] = None, c1: float = 1e-4, max_backtracks: int = 30,
+             memory: int = 10, bound: Union[None, float, np.ndarray] = None, gamma_tik: float = 0.0,
+             gamma_energy: float = 0.0, sigma: float = 1.0, c1: float = 1e-4, max_backtracks: int = 30,
              stream=None) -> Result:
-    """Minimise P(alpha, W) of `problem` from alpha0 (and W0, default: the roll-out of alpha0).
-    bound: |alpha_i| <= bound when given.  Stops when the roll-out estimate is below tol."""
+    """Minimise P(alpha, W) + R(alpha) of `problem` from alpha0 (and W0, default: the roll-out
+    of alpha0).  bound: |alpha_i| <= bound (a scalar or one bound per coefficient).  Stops when
+    the roll-out estimate is below tol."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     spec = problem.spec
     d, nW = problem.d, problem.nW
+    if not sigma > 0:
+        raise ValueError("sigma must be > 0")
+    regularized = gamma_tik > 0 or gamma_energy > 0
     a0 = np.asarray(alpha0, dtype=np.float64)
+    lim = None
     if bound is not None:
-        a0 = np.clip(a0, -bound, bound)
+        lim_h = np.broadcast_to(np.asarray(bound, dtype=np.float64), (d,))
+        a0 = np.clip(a0, -lim_h, lim_h)
+        lim = torch.tensor(lim_h, device=dev, dtype=torch.float64)
     if W0 is None:
         W0 = problem.rollout(a0) if spec.M > 1 else np.zeros(0)
-    x = torch.tensor(np.concatenate([a0, np.asarray(W0, dtype=np.float64)]), device=dev, dtype=torch.float64)
+    x = torch.tensor(np.concatenate([a0, sigma * np.asarray(W0, dtype=np.float64)]), device=dev,
+                     dtype=torch.float64)
     g = torch.zeros_like(x)
-    P = torch.zeros(1, device=dev, dtype=torch.float64)
+    Pv = torch.zeros(1, device=dev, dtype=torch.float64)
+    Rv = torch.zeros(1, device=dev, dtype=torch.float64)
+    rg = torch.zeros(d, device=dev, dtype=torch.float64)
+    w_unscaled = torch.zeros(nW, device=dev, dtype=torch.float64)
     nev = 0
 
-    def evaluate(xv, gv, Pv):
+    def evaluate(xv, gv):
+        """P into Pv, R into Rv and the gradient of F = P + R in the optimisation variables into
+        gv (asynchronous: nothing is read back here)."""
         nonlocal nev
         nev += 1
-        a, w = xv[:d], xv[d:]
-        problem.eval_gradient_into(a, w if spec.M > 1 else None, Pv, gv[:d], gv[d:] if spec.M > 1 else None,
-                                   stream=stream)
+        a, wt = xv[:d], xv[d:]
+        w = None
+        if spec.M > 1:
+            w = wt if sigma == 1.0 else torch.div(wt, sigma, out=w_unscaled)
+        problem.eval_gradient_into(a, w, Pv, gv[:d], gv[d:] if spec.M > 1 else None, stream=stream)
+        if sigma != 1.0 and spec.M > 1:
+            gv[d:].div_(sigma)
+        if regularized:
+            problem.eval_regularization_into(a, gamma_tik, gamma_energy, Rv, rg, stream=stream)
+            gv[:d].add_(rg)
+
+    def scalars(*ts):
+        """device scalars to host floats in one transfer"""
+        return torch.cat([t.reshape(1) for t in ts]).tolist()
 
     def project(xv):
-        if bound is not None:
-            xv[:d].clamp_(-bound, bound)
+        if lim is not None:
+            torch.minimum(torch.maximum(xv[:d], -lim), lim, out=xv[:d])
         return xv
 
-    def projected_gradient(xv, gv):
-        # zero the components that push an alpha at its bound outward
-        if bound is None:
-            return gv
-        pg = gv.clone()
-        a, ga = xv[:d], pg[:d]
-        ga[(a >= bound) & (ga < 0)] = 0.0
-        ga[(a <= -bound) & (ga > 0)] = 0.0
-        return pg
+    def active_set(xv, gv):
+        """alphas at a bound whose gradient pushes them outward (held fixed this iteration)"""
+        act = torch.zeros_like(xv, dtype=torch.bool)
+        if lim is not None:
+            a, ga = xv[:d], gv[:d]
+            act[:d] = ((a >= lim) & (ga < 0)) | ((a <= -lim) & (ga > 0))
+        return act
 
-    evaluate(x, g, P)
-    f = float(P.item())
+    evaluate(x, g)
+    P, R = scalars(Pv, Rv)
+    f = P + R
     est = problem.rollout_estimate()
-    S_mem, Y_mem = [], []
-    history = [{"P": f, "estimate": est, "step": 0.0}]
+    mem = []            # (s, y, 1 / <y, s>) pairs, oldest first
+    history = [{"F": f, "P": P, "estimate": est, "step": 0.0}]
     it = 0
     while est >= tol and it < max_iter:
-        pg = projected_gradient(x, g)
-        # two-loop recursion
+        act = active_set(x, g)
+        pg = g.masked_fill(act, 0.0)
+        # two-loop recursion; the scalars stay on the device (no host round trip per product)
         q = pg.clone()
-        alphas = []
-        for s, y in reversed(list(zip(S_mem, Y_mem))):
-            rho = 1.0 / float(torch.dot(y, s))
-            a_i = rho * float(torch.dot(s, q))
-            q -= a_i * y
-            alphas.append((rho, a_i))
-        if S_mem:
-            s, y = S_mem[-1], Y_mem[-1]
-            q *= float(torch.dot(s, y)) / float(torch.dot(y, y))
+        coef = []
+        for s, y, rho in reversed(mem):
+            a_i = rho * torch.dot(s, q)
+            q.sub_(a_i * y)
+            coef.append(a_i)
+        if mem:
+            s, y, _ = mem[-1]
+            q.mul_(torch.dot(s, y) / torch.dot(y, y))
         else:
-            q /= max(float(torch.linalg.norm(q)), 1e-300)      # first step: unit length
-        for (s, y), (rho, a_i) in zip(zip(S_mem, Y_mem), reversed(alphas)):
-            b = rho * float(torch.dot(y, q))
-            q += (a_i - b) * s
-        direction = -q
-        slope = float(torch.dot(pg, direction))
-        if slope >= 0:                                          # not a descent direction: restart
-            S_mem.clear()
-            Y_mem.clear()
-            direction = -pg / max(float(torch.linalg.norm(pg)), 1e-300)
-            slope = float(torch.dot(pg, direction))
+            q.div_(torch.linalg.norm(q).clamp_min(1e-300))      # first step: unit length
+        for (s, y, rho), a_i in zip(mem, reversed(coef)):
+            q.add_((a_i - rho * torch.dot(y, q)) * s)
+        direction = q.neg_().masked_fill_(act, 0.0)
+        if float(torch.dot(pg, direction)) >= 0:                # not a descent direction: restart
+            mem.clear()
+            direction = -pg / torch.linalg.norm(pg).clamp_min(1e-300)
         # backtracking Armijo line search on the projected path
         t = 1.0
         x_new = torch.empty_like(x)
         g_new = torch.empty_like(g)
-        P_new = torch.zeros_like(P)
         accepted = False
         for _ in range(max_backtracks):
             x_new.copy_(x).add_(direction, alpha=t)
             project(x_new)
-            evaluate(x_new, g_new, P_new)
-            f_new = float(P_new.item())
-            if f_new <= f + c1 * float(torch.dot(pg, x_new - x)):
+            evaluate(x_new, g_new)
+            P_new, R_new, decrease = scalars(Pv, Rv, torch.dot(g, x_new - x))
+            f_new = P_new + R_new
+            if f_new <= f + c1 * decrease:
                 accepted = True
                 break
             t *= 0.5
         if not accepted:
             break
         s_vec, y_vec = x_new - x, g_new - g
-        if float(torch.dot(s_vec, y_vec)) > 1e-12 * float(torch.dot(y_vec, y_vec)):
-            S_mem.append(s_vec)
-            Y_mem.append(y_vec)
-            if len(S_mem) > memory:
-                S_mem.pop(0)
-                Y_mem.pop(0)
-        x, g, f = x_new.clone(), g_new.clone(), f_new
+        sy, yy = torch.stack([torch.dot(s_vec, y_vec), torch.dot(y_vec, y_vec)]).tolist()
+        if sy > 1e-12 * yy:
+            mem.append((s_vec, y_vec, torch.tensor(1.0 / sy, device=dev, dtype=torch.float64)))
+            if len(mem) > memory:
+                mem.pop(0)
+        x, g, f, P = x_new, g_new, f_new, P_new
         est = problem.rollout_estimate()
         it += 1
-        history.append({"P": f, "estimate": est, "step": t})
+        history.append({"F": f, "P": P, "estimate": est, "step": t})
     xh = x.cpu().numpy()
-    return Result(alpha=xh[:d], W=xh[d:], P=f, estimate=est, iterations=it, evaluations=nev,
+    return Result(alpha=xh[:d], W=xh[d:] / sigma, P=P, F=f, estimate=est, iterations=it, evaluations=nev,
                   converged=est < tol, history=history)

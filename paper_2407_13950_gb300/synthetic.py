@@ -178,6 +178,7 @@ def paper_qft_spec(q: int, M: int = 1, nsteps: Optional[int] = None) -> ProblemS
 
 
 ALPHA_AMP = TWO_PI * 0.004  # rad/ns: control coefficients are uniform in +-ALPHA_AMP
+PAPER_ALPHA0_AMP = TWO_PI * 0.010  # rad/ns: the paper's initial guess, uniform in +-10 MHz (Sec. 5)
 
 
 def random_alpha(spec: ProblemSpec, seed: int, problem: int = 0, amp: float = ALPHA_AMP) -> np.ndarray:
