@@ -236,8 +236,8 @@ def rollout(spec, alpha) -> np.ndarray:
 
 
 def regularization(spec, alpha, gamma_tik: float, gamma_energy: float):
-    """(R, dR/dalpha): (gamma_tik/2)||alpha||^2 + gamma_energy * midpoint-rule integral of
-    sum_k |d_k(t)|^2 over [0, T] (Sec. 5 regularization)."""
+    """(R, dR/dalpha): (gamma_tik/2)||alpha||^2 + gamma_energy * the midpoint-rule time average
+    (1/T) int_0^T sum_k |d_k(t)|^2 dt (Sec. 5 regularization)."""
     p = _as_problem(spec)
     a = _f64(alpha)
     g = np.zeros(a.size)

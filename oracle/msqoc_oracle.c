@@ -508,10 +508,11 @@ int oracle_rollout(const oracle_problem* p, const double* alpha, double* W_out) 
 }
 
 /* Regularization of the optimisation problem (Sec. 5): a Tikhonov term (gamma_tik/2)||alpha||^2
- * on the control vector plus gamma_energy times the control-pulse energy
- * int_0^T sum_k |d_k(t)|^2 dt.  The integral is the midpoint rule on the time grid (the
- * quadrature of the gradient integral, Eq. grad-int).  The gradient differentiates each
- * term literally: with d_k = sum_f exp(i Omega_kf t) sum_s (alpha1 + i alpha2)_kfs B_s(t),
+ * on the control vector plus gamma_energy times the time-averaged control-pulse energy
+ * (1/T) int_0^T sum_k |d_k(t)|^2 dt.  The integral is the midpoint rule on the time grid (the
+ * quadrature of the gradient integral, Eq. grad-int), so h/T = 1/nsteps weights each step.  The
+ * gradient differentiates each term literally: with
+ * d_k = sum_f exp(i Omega_kf t) sum_s (alpha1 + i alpha2)_kfs B_s(t),
  *   d|d_k|^2 / d alpha1_kfs = 2 Re(conj(d_k) exp(i Omega_kf t) B_s(t)),
  *   d|d_k|^2 / d alpha2_kfs = 2 Re(conj(d_k) i exp(i Omega_kf t) B_s(t)).
  * Step sums are accumulated in blocks of BLOCK_REG steps.  grad may be NULL. */
@@ -551,9 +552,10 @@ double oracle_regularization(const oracle_problem* p, const double* alpha, doubl
     }
     double tik = 0.0;
     for (int j = 0; j < d; ++j) tik += alpha[j] * alpha[j];
-    double R = 0.5 * gamma_tik * tik + gamma_energy * h * energy;
+    double wt = h / p->T;   /* midpoint weight of the time average */
+    double R = 0.5 * gamma_tik * tik + gamma_energy * wt * energy;
     if (grad)
-        for (int j = 0; j < d; ++j) grad[j] = gamma_tik * alpha[j] + gamma_energy * h * gsum[j];
+        for (int j = 0; j < d; ++j) grad[j] = gamma_tik * alpha[j] + gamma_energy * wt * gsum[j];
     free(dk); free(gblk); free(gsum);
     return R;
 }

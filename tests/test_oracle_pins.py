@@ -469,11 +469,12 @@ def _constant_envelope_alpha(spec, coeffs):
     return a
 
 
-def test_control_energy_of_constant_envelopes_is_T_times_amplitude_squared():
+def test_control_energy_of_constant_envelopes_is_the_amplitude_squared():
+    # the time average of a constant |d_k|^2
     sp = S.transmon_spec(2, 12.0, 300, 1, 7)
     c = {(0, 0): 0.3 - 0.2j, (1, 0): -0.1 + 0.05j}          # carrier 0 has Omega = 0
     R, _ = oracle.regularization(sp, _constant_envelope_alpha(sp, c), 0.0, 1.0)
-    want = sp.T * sum(abs(v) ** 2 for v in c.values())
+    want = sum(abs(v) ** 2 for v in c.values())
     assert R == pytest.approx(want, rel=1e-13)
 
 
@@ -486,7 +487,7 @@ def test_control_energy_two_carriers_geometric_sum():
     D = sp.omega[0][1] - sp.omega[0][0]
     h, n = sp.T / sp.nsteps, sp.nsteps
     geo = h * np.exp(0.5j * D * h) * (1 - np.exp(1j * D * h * n)) / (1 - np.exp(1j * D * h))
-    want = sp.T * (abs(c0) ** 2 + abs(c1) ** 2) + 2 * (np.conj(c0) * c1 * geo).real
+    want = (sp.T * (abs(c0) ** 2 + abs(c1) ** 2) + 2 * (np.conj(c0) * c1 * geo).real) / sp.T
     assert R == pytest.approx(want, rel=1e-12)
 
 
