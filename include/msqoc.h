@@ -171,9 +171,9 @@ msqoc_status msqoc_rollout_estimate(msqoc_problem* p, double* est_out, void* str
 
 /* Regularization of the optimisation problem (Sec. 5: a Tikhonov term and a control-pulse
  * energy penalty):
- *   R = (gamma_tik / 2) ||alpha||^2 + gamma_energy * h sum_n sum_k |d_k(t_{n+1/2})|^2,
- * the energy integral int_0^T sum_k |d_k(t)|^2 dt taken with the midpoint rule on the problem's
- * time grid (the quadrature of the gradient, Eq. grad-int), and its gradient dR/dalpha
+ *   R = (gamma_tik / 2) ||alpha||^2 + gamma_energy * (h/T) sum_n sum_k |d_k(t_{n+1/2})|^2,
+ * the time-averaged energy (1/T) int_0^T sum_k |d_k(t)|^2 dt taken with the midpoint rule on
+ * the problem's time grid (the quadrature of the gradient, Eq. grad-int), and its gradient dR/dalpha
  * (d doubles, layout of alpha; may be NULL).  The paper uses gamma_tik = 1e-3/d and
  * gamma_energy = 1e-3.  Independent of W and of the problem's last evaluation (neither is
  * read or changed).  alpha, R_out, grad_alpha: host or device; the gammas must be finite and

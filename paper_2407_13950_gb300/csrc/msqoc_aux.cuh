@@ -214,13 +214,14 @@ __global__ void k_grad_W(const ProbDev pd, double2* gW) {
 constexpr int REG_THREADS = 256;
 
 // Regularization of the optimisation problem (Sec. 5): R = (gamma_tik/2) ||alpha||^2 +
-// gamma_energy E with the control-pulse energy E = h sum_n sum_k |d_k(t_{n+1/2})|^2 (the
-// midpoint rule of int_0^T sum_k |d_k|^2 dt on the time grid).  One block per (subsystem k,
-// spline s), over the steps where spline s is active (its weight B = w_{s - s0}):
-//   dR/d alpha1_kfs = gamma_tik alpha1_kfs + 2 gamma_energy h sum_n B Re(conj(d_k) e^{i Omega_kf t}),
-//   dR/d alpha2_kfs = gamma_tik alpha2_kfs - 2 gamma_energy h sum_n B Im(conj(d_k) e^{i Omega_kf t}),
-// and the block's share of the energy, h sum |d_k|^2 over the steps whose first active spline
-// is s (each step is counted by exactly one block per k).  Every sum has a fixed order.
+// gamma_energy E with the time-averaged control-pulse energy E = (h/T) sum_n sum_k
+// |d_k(t_{n+1/2})|^2 (the midpoint rule of (1/T) int_0^T sum_k |d_k|^2 dt on the time grid).
+// One block per (subsystem k, spline s), over the steps where spline s is active (its weight
+// B = w_{s - s0}):
+//   dR/d alpha1_kfs = gamma_tik alpha1_kfs + 2 gamma_energy (h/T) sum_n B Re(conj(d_k) e^{i Omega_kf t}),
+//   dR/d alpha2_kfs = gamma_tik alpha2_kfs - 2 gamma_energy (h/T) sum_n B Im(conj(d_k) e^{i Omega_kf t}),
+// and the block's share of the energy, (h/T) sum |d_k|^2 over the steps whose first active
+// spline is s (each step is counted by exactly one block per k).  Every sum has a fixed order.
 __global__ void __launch_bounds__(REG_THREADS) k_regularization(const ProbDev pd, const double* alpha,
                                                                  double gamma_tik, double gamma_energy,
                                                                  double* grad, double* epart) {
@@ -261,12 +262,13 @@ __global__ void __launch_bounds__(REG_THREADS) k_regularization(const ProbDev pd
         const double sre = block_sum<REG_THREADS>(acc_re, sh);
         const double sim = block_sum<REG_THREADS>(acc_im, sh);
         if (threadIdx.x == 0) {
+            const double wt = pd.h / pd.T;   // midpoint weight of the time average
             if (fi < pd.cof[k]) {
-                epart[blockIdx.x] = pd.h * sre;
+                epart[blockIdx.x] = wt * sre;
             } else {
                 const size_t i = (size_t(fi) * pd.d1 + s) * 2;
-                grad[i] = gamma_tik * alpha[i] + 2.0 * gamma_energy * pd.h * sre;
-                grad[i + 1] = gamma_tik * alpha[i + 1] - 2.0 * gamma_energy * pd.h * sim;
+                grad[i] = gamma_tik * alpha[i] + 2.0 * gamma_energy * wt * sre;
+                grad[i + 1] = gamma_tik * alpha[i + 1] - 2.0 * gamma_energy * wt * sim;
             }
         }
     }

@@ -240,7 +240,7 @@ class Problem:
         return float(est[0])
 
     def eval_regularization(self, alpha, gamma_tik: float, gamma_energy: float, stream=None) -> dict:
-        """Tikhonov + control-energy regularization (Sec. 5) and its alpha-gradient."""
+        """Tikhonov + time-averaged control-energy regularization (Sec. 5) and its alpha-gradient."""
         R = np.zeros(1)
         g = np.zeros(self.d)
         _check(load().msqoc_eval_regularization(self.handle, _ptr(alpha), float(gamma_tik), float(gamma_energy),

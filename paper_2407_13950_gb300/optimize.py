@@ -7,7 +7,8 @@ Sec. 5:
   zero);
 - the penalty weight is fixed (mu = 2/E, the problem's default);
 - the objective may carry the paper's regularization: a Tikhonov term (gamma_tik/2)||alpha||^2
-  and the control-pulse energy gamma_energy int sum_k |d_k|^2 dt (msqoc_eval_regularization);
+  and the time-averaged control-pulse energy gamma_energy (1/T) int sum_k |d_k|^2 dt
+  (msqoc_eval_regularization);
 - the window states may enter the optimisation scaled, W~ = sigma W, which balances the
   alpha- and W-parts of the gradient (the paper scans sigma in [0.05, 0.15]);
 - box bounds on alpha keep the pulse amplitudes below a limit (`amplitude_bound`);
