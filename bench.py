@@ -97,8 +97,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-SWEEP_SOURCES = ["msqoc_sweep.cuh", "inst_sweep.cu", "msqoc_internal.h"]
+SWEEP_SOURCES = ["msqoc_sweep.cuh", "msqoc_sweep_pair.cuh", "msqoc_sweep_common.cuh", "inst_sweep.cu",
+                 "msqoc_internal.h"]
 PROFILE = os.path.join(ROOT, "profiles", "k_sweep_4q_small_full.md")
+LAYOUTS = {"auto": 0, "fiber": 1, "pair": 2}
 
 
 def sweep_traffic(kernel: str):
@@ -221,7 +223,7 @@ def run_ours(args, spec):
     tuned, tune_ms = (msqoc.autotune(spec, alpha=alpha, probe_steps=64, solver=solver) if args.col_block < 0
                       else (None, None))
     col_block = tuned if args.col_block < 0 else args.col_block
-    prob = msqoc.Problem(spec, solver=solver, col_block=col_block, profile=True)
+    prob = msqoc.Problem(spec, solver=solver, col_block=col_block, profile=True, layout=LAYOUTS[args.layout])
     peak_tflops = msqoc.measure_fp64_peak()
 
     for _ in range(args.warmup):
@@ -267,6 +269,7 @@ def run_ours(args, spec):
         "config": {"workload": spec.name, "N": spec.N, "E": spec.E, "nsteps": spec.nsteps, "windows": spec.M,
                    "T_ns": spec.T, "d": spec.d, "solver": args.solver,
                    "col_block": col_block if col_block > 0 else f"model ({prob.col_block})",
+                   "layout": {1: "one thread per fiber", 2: "lane pair per fiber"}[prob.layout],
                    **({"autotune": {"best": tuned, "ms_per_probe_eval": tune_ms}} if tuned else {}),
                    "l2": "inputs larger than L2 (2 GB midpoint history per evaluation)",
                    "parallelism": f"independent problem per GPU x{world}"},
@@ -602,6 +605,8 @@ def main():
     ap.add_argument("--col-block", type=int, default=0,
                     help="columns per sweep tile: 0 = the library's model, -1 = measured by the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--layout", choices=list(LAYOUTS), default="auto",
+                    help="sweep kernel family: one thread or a lane pair per fiber (auto: the library's model)")
     ap.add_argument("--nsteps", type=int, default=0,
                     help="shorter time grid with the same step size (small profiling case); 0 = 100000 steps")
     ap.add_argument("--workload", choices=["4q", "batched", "serving", "paper", "optimize"], default="4q",

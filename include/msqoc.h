@@ -98,9 +98,10 @@ typedef struct msqoc_controls {
 
 typedef struct msqoc_options {
     int32_t solver;        /* MSQOC_SOLVER_* */
-    int32_t col_block;     /* columns per sweep tile (1 <= col_block <= E, col_block * N/L <= 256;
-                              tiles run along the window-major column list and may cover two
-                              windows; a one-warp tile must divide E); 0 = automatic */
+    int32_t col_block;     /* columns per sweep tile (1 <= col_block <= E; col_block N/L <= 256
+                              threads with one thread per fiber, 2 col_block N/L <= 384 with
+                              lane pairs; tiles run along the window-major column list and may
+                              cover two windows; a one-warp tile must divide E); 0 = automatic */
     int32_t ckpt_interval; /* K: forward states kept for the adjoint sweep.  1 = every midpoint
                               state (history of nsteps * E * N complex); K > 1 = the state every
                               K steps of each window, each K-step segment recomputed before its
@@ -108,8 +109,19 @@ typedef struct msqoc_options {
                               unless that history exceeds a quarter of the device memory, then
                               64) */
     int32_t profile;       /* 1 = record CUDA events around every kernel (msqoc_kernel_times) */
-    int32_t reserved[4];
+    int32_t layout;        /* MSQOC_LAYOUT_*: threads per (column, fiber) of the sweep tiles */
+    int32_t reserved[3];
 } msqoc_options;
+
+/* Sweep kernel families.  FIBER: one thread per fiber (the L entries of a column along the last
+ * subsystem), the choice for problems whose tiles fill the GPU.  PAIR: a lane pair per fiber,
+ * one thread computing the real and one the imaginary component of every complex result: half
+ * the FP64 instructions per thread, so steps run faster when the tiles are too few to fill the
+ * GPU (small problems, the paper's QFT cases).  AUTO: chosen with the column block by the
+ * library's makespan model. */
+#define MSQOC_LAYOUT_AUTO 0
+#define MSQOC_LAYOUT_FIBER 1
+#define MSQOC_LAYOUT_PAIR 2
 
 /* Kernels of one evaluation, in launch order, as indexed by msqoc_kernel_times. */
 #define MSQOC_KERNEL_CONTROLS 0  /* control evaluation at the step midpoints */
@@ -138,10 +150,10 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
 msqoc_status msqoc_query(const msqoc_problem* p, int64_t* d, int64_t* nW, size_t* device_bytes);
 
 /* Sweep layout of a problem: columns per tile, tiles (CTAs) per sweep launch, threads per
- * tile, and the checkpoint interval K in use (after automatic choices).  Any pointer may be
- * NULL. */
+ * tile, the checkpoint interval K and the kernel family (MSQOC_LAYOUT_FIBER or
+ * MSQOC_LAYOUT_PAIR) in use (after automatic choices).  Any pointer may be NULL. */
 msqoc_status msqoc_query_layout(const msqoc_problem* p, int32_t* col_block, int32_t* tiles,
-                                int32_t* threads, int32_t* ckpt_interval);
+                                int32_t* threads, int32_t* ckpt_interval, int32_t* layout);
 
 /* Objective only (forward sweep of every window, Eq. penalty-fcn).  P_out: 1 double;
  * J_out (1 double) and pen_out (M-1 doubles) may be NULL. */

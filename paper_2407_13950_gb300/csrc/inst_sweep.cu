@@ -1,6 +1,8 @@
-// Explicit instantiation of the sweep kernels for one (levels, subsystems) shape, selected with
-// -DMSQOC_L=<levels> -DMSQOC_Q=<subsystems>; this file is compiled once per supported shape.
+// Explicit instantiation of the sweep kernels (both families: one thread per fiber and a lane
+// pair per fiber) for one (levels, subsystems) shape, selected with -DMSQOC_L=<levels>
+// -DMSQOC_Q=<subsystems>; this file is compiled once per supported shape.
 #include "msqoc_sweep.cuh"
+#include "msqoc_sweep_pair.cuh"
 
 #ifndef MSQOC_L
 #error "MSQOC_L must be defined"
@@ -14,9 +16,17 @@
 
 namespace msqoc {
 
-template <int SOLVER, bool BWD, bool ROLLOUT = false>
+template <int SOLVER, bool BWD, bool ROLLOUT, bool PAIR>
+static auto kernel_of() {
+    if constexpr (PAIR)
+        return k_sweep_pair<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT>;
+    else
+        return k_sweep<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT>;
+}
+
+template <int SOLVER, bool BWD, bool ROLLOUT, bool PAIR>
 static cudaError_t launch_one(const SweepArgs& a, int ntiles, cudaStream_t s) {
-    auto kern = k_sweep<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT>;
+    auto kern = kernel_of<SOLVER, BWD, ROLLOUT, PAIR>();
     const size_t smem = sweep_smem_bytes(a);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -27,9 +37,9 @@ static cudaError_t launch_one(const SweepArgs& a, int ntiles, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int SOLVER, bool BWD>
+template <int SOLVER, bool BWD, bool PAIR>
 static int occupancy_one(const SweepArgs& a) {
-    auto kern = k_sweep<MSQOC_L, MSQOC_Q, SOLVER, BWD>;
+    auto kern = kernel_of<SOLVER, BWD, false, PAIR>();
     const size_t smem = sweep_smem_bytes(a);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
@@ -39,20 +49,33 @@ static int occupancy_one(const SweepArgs& a) {
     return n;
 }
 
-cudaError_t MSQOC_CAT(launch_sweep, MSQOC_L, MSQOC_Q)(const SweepArgs& a, int ntiles, cudaStream_t s) {
+template <bool PAIR>
+static cudaError_t launch_family(const SweepArgs& a, int ntiles, cudaStream_t s) {
     if (a.mode == SWEEP_ROLLOUT)
-        return a.solver == SOLVER_FP64 ? launch_one<SOLVER_FP64, false, true>(a, ntiles, s)
-                                       : launch_one<SOLVER_MIXED, false, true>(a, ntiles, s);
+        return a.solver == SOLVER_FP64 ? launch_one<SOLVER_FP64, false, true, PAIR>(a, ntiles, s)
+                                       : launch_one<SOLVER_MIXED, false, true, PAIR>(a, ntiles, s);
     const bool bwd = a.mode == SWEEP_ADJOINT;
     if (a.solver == SOLVER_FP64)
-        return bwd ? launch_one<SOLVER_FP64, true>(a, ntiles, s) : launch_one<SOLVER_FP64, false>(a, ntiles, s);
-    return bwd ? launch_one<SOLVER_MIXED, true>(a, ntiles, s) : launch_one<SOLVER_MIXED, false>(a, ntiles, s);
+        return bwd ? launch_one<SOLVER_FP64, true, false, PAIR>(a, ntiles, s)
+                   : launch_one<SOLVER_FP64, false, false, PAIR>(a, ntiles, s);
+    return bwd ? launch_one<SOLVER_MIXED, true, false, PAIR>(a, ntiles, s)
+               : launch_one<SOLVER_MIXED, false, false, PAIR>(a, ntiles, s);
+}
+
+template <bool PAIR>
+static int occupancy_family(const SweepArgs& a) {
+    const bool bwd = a.mode == SWEEP_ADJOINT;
+    if (a.solver == SOLVER_FP64)
+        return bwd ? occupancy_one<SOLVER_FP64, true, PAIR>(a) : occupancy_one<SOLVER_FP64, false, PAIR>(a);
+    return bwd ? occupancy_one<SOLVER_MIXED, true, PAIR>(a) : occupancy_one<SOLVER_MIXED, false, PAIR>(a);
+}
+
+cudaError_t MSQOC_CAT(launch_sweep, MSQOC_L, MSQOC_Q)(const SweepArgs& a, int ntiles, cudaStream_t s) {
+    return a.pair ? launch_family<true>(a, ntiles, s) : launch_family<false>(a, ntiles, s);
 }
 
 int MSQOC_CAT(sweep_occupancy, MSQOC_L, MSQOC_Q)(const SweepArgs& a) {
-    const bool bwd = a.mode == SWEEP_ADJOINT;
-    if (a.solver == SOLVER_FP64) return bwd ? occupancy_one<SOLVER_FP64, true>(a) : occupancy_one<SOLVER_FP64, false>(a);
-    return bwd ? occupancy_one<SOLVER_MIXED, true>(a) : occupancy_one<SOLVER_MIXED, false>(a);
+    return a.pair ? occupancy_family<true>(a) : occupancy_family<false>(a);
 }
 
 }  // namespace msqoc

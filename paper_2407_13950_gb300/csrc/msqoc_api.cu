@@ -13,7 +13,7 @@
 #include "msqoc_aux.cuh"
 #include "msqoc_internal.h"
 #include "msqoc_host.h"
-#include "msqoc_sweep.cuh"
+#include "msqoc_sweep_common.cuh"
 
 using namespace msqoc;
 
@@ -131,9 +131,11 @@ int gray_rank(int g) {
 // Threads of a tile with ncol columns, the first ncol0 of window m0: each window's
 // (column, fiber) pairs are ordered by the Gray rank of the fiber class, so that a warp spans
 // few classes (its branch cost is the union of its lanes' branches); window m0's pairs come
-// first so at most one warp has lanes of both windows.  Idle lanes mirror the last active pair.
-// Writes out[nthreads]; no allocation.
-void build_lanemap(int L, int q, int ncol, int ncol0, int nthreads, int* out) {
+// first so at most one warp has lanes of both windows.  Each (column, fiber) goes to one thread
+// or, for lane-pair tiles (pair = 1), to a lane pair (threads 2i and 2i + 1: the real and the
+// imaginary part).  Idle lanes mirror the last active entry.  Writes out[nthreads]; no
+// allocation.
+void build_lanemap(int L, int q, int ncol, int ncol0, int nthreads, int pair, int* out) {
     const int F = ipow_i(L, q) / L;
     int key[MAX_TILE_THREADS], val[MAX_TILE_THREADS];
     int n = 0;
@@ -154,7 +156,8 @@ void build_lanemap(int L, int q, int ncol, int ncol0, int nthreads, int* out) {
                 val[pos] = (c << 16) | f;
             }
     }
-    for (int t = 0; t < nthreads; ++t) out[t] = t < n ? val[t] : ~val[n - 1];
+    const int sh = pair ? 1 : 0;
+    for (int t = 0; t < nthreads; ++t) out[t] = (t >> sh) < n ? val[t >> sh] : ~val[n - 1];
 }
 
 // Tile t of one problem for `cpt` columns per tile: a consecutive run of the window-major column
@@ -176,54 +179,90 @@ long tile_count(int M, int E, int cpt) { return (long(M) * E + cpt - 1) / cpt; }
 
 // The cpt + 1 lane maps of a problem's tiles (out[(cpt + 1) * nthreads]); map cpt serves the
 // last tile when it is partial.
-void build_lanemaps(int L, int q, int M, int E, int cpt, int nthreads, int* out) {
-    for (int k = 0; k < cpt; ++k) build_lanemap(L, q, cpt, k + 1, nthreads, out + size_t(k) * nthreads);
+void build_lanemaps(int L, int q, int M, int E, int cpt, int nthreads, int pair, int* out) {
+    for (int k = 0; k < cpt; ++k) build_lanemap(L, q, cpt, k + 1, nthreads, pair, out + size_t(k) * nthreads);
     const Tile last = tile_at(tile_count(M, E, cpt) - 1, M, E, cpt, 0);
-    build_lanemap(L, q, last.ncol, last.ncol0, nthreads, out + size_t(cpt) * nthreads);
+    build_lanemap(L, q, last.ncol, last.ncol0, nthreads, pair, out + size_t(cpt) * nthreads);
 }
 
-int tile_threads(int cpt, int F) { return ((cpt * F + 31) / 32) * 32; }
+// one thread, or a lane pair, per (column, fiber)
+int tile_threads(int cpt, int F, int pair) { return (((pair ? 2 : 1) * cpt * F + 31) / 32) * 32; }
+int max_tile_threads(int pair) { return pair ? MAX_PAIR_TILE_THREADS : MAX_TILE_THREADS; }
 
-// Is `cpt` columns per tile usable?  Tiles must fit MAX_TILE_THREADS threads and the shared
-// memory; a tile that covers two windows needs two warps (one per window's coefficients), so a
-// one-warp tile must divide the window's columns.
-bool tile_width_ok(int cpt, int E, int F, int q, int L, int N, int d, int solver) {
-    if (cpt < 1 || cpt > E || cpt * F > MAX_TILE_THREADS) return false;
-    const int nthreads = tile_threads(cpt, F);
+// Is `cpt` columns per tile usable in the given kernel family?  Tiles must fit the family's
+// thread limit and the shared memory; a tile that covers two windows needs two warps (one per
+// window's coefficients), so a one-warp tile must divide the window's columns.
+bool tile_width_ok(int cpt, int E, int F, int q, int L, int N, int d, int solver, int pair) {
+    if (cpt < 1 || cpt > E || (pair ? 2 : 1) * cpt * F > max_tile_threads(pair)) return false;
+    const int nthreads = tile_threads(cpt, F, pair);
     if (nthreads == 32 && E % cpt) return false;
-    const size_t s1 = sweep_layout(q, L, N, cpt, nthreads, d, solver, true).total;
-    const size_t s0 = sweep_layout(q, L, N, cpt, nthreads, d, solver, false).total;
+    const size_t s1 = sweep_layout(q, L, N, cpt, nthreads, d, solver, true, pair).total;
+    const size_t s0 = sweep_layout(q, L, N, cpt, nthreads, d, solver, false, pair).total;
     return std::max(s0, s1) <= 200 * 1024;
 }
 
-// Columns per tile.  Makespan model, from FP64 throughput probes and sweep timings on this GPU:
-// the FP64 units belong to the SM's four sub-partitions and idle lanes cost as much as busy
-// ones; the sweeps' time follows the sub-partition with the most warps.  Candidates are ranked by
-//   1. tiles that stay inside one window (a tile over two windows pays a second gradient
-//      reduction and wider class mixing in its warps: measured slower on the 4-transmon
-//      adjoint at 64, 128 and 256 windows, although it uses more SMs);
-//   2. warps on the busiest sub-partition: ceil(ceil(tiles / SMs) * warps per tile / 4);
+// Kernel family and columns per tile.  Makespan model, from FP64 throughput probes and sweep
+// timings on this GPU: a warp issues one FP64 instruction per 64 cycles on its SM sub-partition,
+// an SM with four or more warps of FP64 work runs at its full rate, and every thread of a tile
+// does the same FP64 work per step (idle lanes cost as much as busy ones).  In units of the
+// step time of one one-thread-per-fiber warp alone on a sub-partition, a step of an SM holding
+// w warps costs max(w c / 4, c0): c = c0 = 1 for that family; for lane pairs (half the FP64
+// instructions a thread, plus shuffles) c = 0.6 at full SM load and c0 = 0.7 alone (measured:
+// equal to the one-thread family on the 4-transmon tiles, 1.4x faster steps on small
+// problems).  Tiles that do not fit at once run in waves of the CTAs an SM holds (the kernels'
+// occupancy at that width).  A tile over two windows pays a second gradient reduction and wider
+// class mixing in its warps: its cost is taken 1.18x (measured on the 4-transmon tiles: the
+// adjoint 9% slower, the forward 3% faster than 8-column one-window tiles, where the warp count
+// alone predicts both 14% faster).  Candidates are ranked by
+//   1. the makespan: an SM's ceil(tiles / SMs) tiles in waves of `resident`, summed over the
+//      waves;
+//   2. tiles that stay inside one window;
 //   3. the idle-lane fraction of a tile.
-int choose_tile_width(int M, int E, int F, int q, int L, int N, int d, int solver, int sms) {
-    int best = -1;
-    long best_a = 0;
+// fixed_cpt > 0 restricts the width, layout (MSQOC_LAYOUT_*) the family.  cpt = -1: none fits.
+TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int d, int solver, int sms, int fixed_cpt,
+                              int layout) {
+    TileChoice best{-1, 0};
+    double best_a = 0.0, best_c = 0.0;
     int best_b = 0;
-    double best_c = 0.0;
-    for (int cpt = std::min(E, MAX_TILE_THREADS / F); cpt >= 1; --cpt) {
-        if (!tile_width_ok(cpt, E, F, q, L, N, d, solver)) continue;
-        const long tiles = (long(M) * E + cpt - 1) / cpt;
-        const int warps = tile_threads(cpt, F) / 32;
-        const long per_sm = (tiles + sms - 1) / sms;
-        const long ca = (per_sm * warps + 3) / 4;
-        const int cb = (E % cpt) ? 1 : 0;
-        const double cc = 1.0 - double(cpt * F) / (32.0 * warps);
-        const bool better =
-            best < 0 || cb < best_b || (cb == best_b && (ca < best_a || (ca == best_a && cc < best_c - 1e-9)));
-        if (better) {
-            best = cpt;
-            best_a = ca;
-            best_b = cb;
-            best_c = cc;
+    for (int pair = 0; pair <= 1; ++pair) {
+        if ((layout == MSQOC_LAYOUT_FIBER && pair) || (layout == MSQOC_LAYOUT_PAIR && !pair)) continue;
+        const double c_load = pair ? 0.6 : 1.0, c_alone = pair ? 0.7 : 1.0;
+        const int hi = fixed_cpt > 0 ? fixed_cpt : std::min(E, max_tile_threads(pair) / ((pair ? 2 : 1) * F));
+        const int lo = fixed_cpt > 0 ? fixed_cpt : 1;
+        for (int cpt = hi; cpt >= lo; --cpt) {
+            if (!tile_width_ok(cpt, E, F, q, L, N, d, solver, pair)) continue;
+            const long tiles = (long(M) * E + cpt - 1) / cpt;
+            const int threads = tile_threads(cpt, F, pair);
+            const int warps = threads / 32;
+            SweepArgs a{};
+            a.cpt = cpt;
+            a.dmax = d;
+            a.L = L;
+            a.q = q;
+            a.solver = solver;
+            a.nthreads = threads;
+            a.pair = pair;
+            a.mode = SWEEP_HISTORY;
+            const int r0 = sweep_ctas_per_sm(a);
+            a.mode = SWEEP_ADJOINT;
+            const int r1 = sweep_ctas_per_sm(a);
+            const long resident = std::max(1, std::min(r0, r1));
+            const long per_sm = (tiles + sms - 1) / sms;
+            const long waves = (per_sm + resident - 1) / resident;
+            const long last = per_sm - (waves - 1) * resident;
+            const int cb = (E % cpt) ? 1 : 0;
+            const double ca = (cb ? 1.18 : 1.0) *
+                              (double(waves - 1) * std::max(double(resident * warps) * c_load / 4.0, c_alone) +
+                               std::max(double(last * warps) * c_load / 4.0, c_alone));
+            const double cc = 1.0 - double((pair ? 2 : 1) * cpt * F) / (32.0 * warps);
+            const bool better = best.cpt < 0 || ca < best_a - 1e-9 ||
+                                (ca < best_a + 1e-9 && (cb < best_b || (cb == best_b && cc < best_c - 1e-9)));
+            if (better) {
+                best = TileChoice{cpt, pair};
+                best_a = ca;
+                best_b = cb;
+                best_c = cc;
+            }
         }
     }
     return best;
@@ -261,7 +300,7 @@ msqoc_status check_description(const msqoc_hamiltonian* H, const msqoc_controls*
 // Shape, time grid, model scalars and tile geometry of a validated description (every field
 // of pd except the device pointers and the history segmentation).  col_block 0 = automatic.
 msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps,
-                           int32_t nwindows, double mu, int solver, int col_block, int sms, ProbDev& pd) {
+                           int32_t nwindows, double mu, int solver, int col_block, int layout, int sms, ProbDev& pd) {
     const int q = H->nqubits, L = H->nlevels, ness = H->ness;
     int nfsum = 0;
     for (int k = 0; k < q; ++k) nfsum += C->ncarriers[k];
@@ -308,15 +347,19 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
         pd.wsq[2 * l + 0] = std::sqrt(double(l + 1));
         pd.wsq[2 * l + 1] = std::sqrt(double(l));
     }
-    int cpt = col_block;
-    if (cpt == 0) cpt = choose_tile_width(pd.M, pd.E, pd.F, q, L, pd.N, pd.d, solver, sms);
-    if (!tile_width_ok(cpt, pd.E, pd.F, q, L, pd.N, pd.d, solver))
+    if (layout < MSQOC_LAYOUT_AUTO || layout > MSQOC_LAYOUT_PAIR)
+        return fail(MSQOC_ERR_INVALID_ARG, "layout %d is not an MSQOC_LAYOUT_* value", layout);
+    if (col_block < 0) return fail(MSQOC_ERR_INVALID_ARG, "column block %d < 0", col_block);
+    const TileChoice tc = choose_tile_layout(pd.M, pd.E, pd.F, q, L, pd.N, pd.d, solver, sms, col_block, layout);
+    if (tc.cpt < 0)
         return fail(MSQOC_ERR_INVALID_ARG,
-                    "column block %d invalid for E=%d (needs 1 <= cb <= E, cb*N/L <= %d, cb | E for one-warp "
-                    "tiles, and the shared memory)",
-                    cpt, pd.E, MAX_TILE_THREADS);
+                    "column block %d invalid for E=%d (needs 1 <= cb <= E, cb N/L <= %d threads with one thread "
+                    "per fiber or 2 cb N/L <= %d with lane pairs, cb | E for one-warp tiles, and the shared memory)",
+                    col_block, pd.E, MAX_TILE_THREADS, MAX_PAIR_TILE_THREADS);
+    const int cpt = tc.cpt;
     pd.cb = cpt;
-    pd.nthreads = tile_threads(cpt, pd.F);
+    pd.pair = tc.pair;
+    pd.nthreads = tile_threads(cpt, pd.F, tc.pair);
     pd.ntiles = static_cast<int>((long(pd.M) * pd.E + cpt - 1) / cpt);
     // whole windows in one history segment unless a checkpoint interval is set later
     const int64_t max_ns = (nsteps + nwindows - 1) / nwindows;
@@ -347,6 +390,7 @@ SweepArgs sweep_args(const ProbDev& pd, const ProbDev* pds_dev, const Tile* tile
     a.q = pd.q;
     a.solver = pd.solver;
     a.nthreads = pd.nthreads;
+    a.pair = pd.pair;
     return a;
 }
 
@@ -460,7 +504,7 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     if (sms <= 0) sms = 1;
-    st0 = shape_problem(H, C, T, nsteps, nwindows, mu, solver, o.col_block, sms, pd);
+    st0 = shape_problem(H, C, T, nsteps, nwindows, mu, solver, o.col_block, o.layout, sms, pd);
     if (st0 != MSQOC_OK) return st0;
     const int q = pd.q, L = pd.L, nfsum = pd.nfsum;
     // checkpoint interval: 0 = automatic (every midpoint state unless that history would take
@@ -493,13 +537,13 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
     std::vector<Tile> tiles(pd.ntiles);
     for (int t = 0; t < pd.ntiles; ++t) tiles[t] = tile_at(t, pd.M, E, pd.cb, 0);
     std::vector<int> maps(size_t(pd.cb + 1) * pd.nthreads);
-    build_lanemaps(L, q, pd.M, E, pd.cb, pd.nthreads, maps.data());
+    build_lanemaps(L, q, pd.M, E, pd.cb, pd.nthreads, pd.pair, maps.data());
     // the roll-out sweep's tiles: the same widths over a single window
     p->ntiles_ro = static_cast<int>(tile_count(1, E, pd.cb));
     std::vector<Tile> tiles_ro(p->ntiles_ro);
     for (int t = 0; t < p->ntiles_ro; ++t) tiles_ro[t] = tile_at(t, 1, E, pd.cb, 0);
     std::vector<int> maps_ro(size_t(pd.cb + 1) * pd.nthreads);
-    build_lanemaps(L, q, 1, E, pd.cb, pd.nthreads, maps_ro.data());
+    build_lanemaps(L, q, 1, E, pd.cb, pd.nthreads, pd.pair, maps_ro.data());
 
     // ---- device buffers
     const size_t M = pd.M;
@@ -594,12 +638,13 @@ msqoc_status msqoc_query(const msqoc_problem* p, int64_t* d, int64_t* nW, size_t
 }
 
 msqoc_status msqoc_query_layout(const msqoc_problem* p, int32_t* col_block, int32_t* tiles, int32_t* threads,
-                                int32_t* ckpt_interval) {
+                                int32_t* ckpt_interval, int32_t* layout) {
     if (!p) return fail(MSQOC_ERR_INVALID_ARG, "problem is NULL");
     if (col_block) *col_block = p->pd.cb;
     if (tiles) *tiles = p->pd.ntiles;
     if (threads) *threads = p->pd.nthreads;
     if (ckpt_interval) *ckpt_interval = p->ckpt_interval;
+    if (layout) *layout = p->pd.pair ? MSQOC_LAYOUT_PAIR : MSQOC_LAYOUT_FIBER;
     return MSQOC_OK;
 }
 
@@ -891,7 +936,7 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
     const int64_t psteps = std::min<int64_t>(nsteps, int64_t(nwindows) * probe_steps);
     const double pT = T * double(psteps) / double(nsteps);
     ProbDev pd{};
-    st = shape_problem(H, C, pT, psteps, nwindows, mu, solver, 1, 1, pd);
+    st = shape_problem(H, C, pT, psteps, nwindows, mu, solver, 1, o.layout, 1, pd);
     if (st != MSQOC_OK && st != MSQOC_ERR_INVALID_ARG) return st;
     std::vector<double> a(static_cast<size_t>(pd.d));
     for (int j = 0; j < pd.d; ++j)   // default iterate: alternating amplitudes of the workloads' scale
@@ -921,7 +966,7 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
     float best_ms = 0.f;
     int best = 0, nrec = 0;
     for (int cb = std::min(pd.E, MAX_TILE_THREADS / pd.F); cb >= 1 && st == MSQOC_OK; --cb) {
-        if (!tile_width_ok(cb, pd.E, pd.F, pd.q, pd.L, pd.N, pd.d, solver)) continue;
+        if (choose_tile_layout(pd.M, pd.E, pd.F, pd.q, pd.L, pd.N, pd.d, solver, 1, cb, o.layout).cpt < 0) continue;
         msqoc_options oc = o;
         oc.col_block = cb;
         msqoc_problem* p = nullptr;
@@ -1042,7 +1087,7 @@ extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H,
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     ProbDev pd{};
     st = shape_problem(H, C, T, nsteps, nwindows, mu, solver == MSQOC_SOLVER_FP64 ? SOLVER_FP64 : SOLVER_MIXED, 0,
-                       std::max(sms, 1), pd);
+                       MSQOC_LAYOUT_AUTO, std::max(sms, 1), pd);
     if (st != MSQOC_OK) return st;
 
     // ---- scratch layout; the limit depends on the problem's size only
@@ -1126,10 +1171,11 @@ extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H,
             for (long t = 0; t < n; ++t) chunk[t] = tile_at(t0 + t, pd.M, pd.E, pd.cb, 0);
             CUDA_TRY(cudaMemcpyAsync(tiles_d + t0, chunk, n * sizeof(Tile), cudaMemcpyHostToDevice, s));
         }
-        int map[MAX_TILE_THREADS];
+        int map[MAX_PAIR_TILE_THREADS > MAX_TILE_THREADS ? MAX_PAIR_TILE_THREADS : MAX_TILE_THREADS];
         const Tile last = tile_at(pd.ntiles - 1, pd.M, pd.E, pd.cb, 0);
         for (int k = 0; k <= pd.cb; ++k) {
-            build_lanemap(pd.L, pd.q, k < pd.cb ? pd.cb : last.ncol, k < pd.cb ? k + 1 : last.ncol0, pd.nthreads, map);
+            build_lanemap(pd.L, pd.q, k < pd.cb ? pd.cb : last.ncol, k < pd.cb ? k + 1 : last.ncol0, pd.nthreads,
+                          pd.pair, map);
             CUDA_TRY(cudaMemcpyAsync(map_d + size_t(k) * pd.nthreads, map, pd.nthreads * sizeof(int),
                                      cudaMemcpyHostToDevice, s));
         }

@@ -17,7 +17,7 @@ using namespace msqoc;
 
 struct msqoc_batch {
     struct Group {
-        int L = 0, q = 0, solver = 0;
+        int L = 0, q = 0, solver = 0, pair = 0;   // shape, solver and kernel family of the group
         std::vector<int> members;     // indices into probs
         SweepArgs args{};             // pds / tiles / lanemap / geometry of the group's launches
         int ntiles = 0;
@@ -178,7 +178,7 @@ msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t fla
     for (int i = 0; i < n && !st; ++i) {
         const ProbDev& pd = b->probs[i]->pd;
         auto it = std::find_if(b->groups.begin(), b->groups.end(), [&](const msqoc_batch::Group& g) {
-            return g.L == pd.L && g.q == pd.q && g.solver == pd.solver;
+            return g.L == pd.L && g.q == pd.q && g.solver == pd.solver && g.pair == pd.pair;
         });
         if (it == b->groups.end()) {
             b->groups.emplace_back();
@@ -186,6 +186,7 @@ msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t fla
             it->L = pd.L;
             it->q = pd.q;
             it->solver = pd.solver;
+            it->pair = pd.pair;
         }
         it->members.push_back(i);
     }
@@ -224,7 +225,7 @@ msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t fla
             int* mp = maps.data() + size_t(map_base) * nthreads;
             for (int j = 0; j <= pd.cb; ++j)
                 build_lanemap(pd.L, pd.q, j < pd.cb ? pd.cb : last.ncol, j < pd.cb ? j + 1 : last.ncol0, nthreads,
-                              mp + size_t(j) * nthreads);
+                              pd.pair, mp + size_t(j) * nthreads);
             pds.push_back(pd);
         }
         // longest windows first: the CTAs that take longest start in the first wave

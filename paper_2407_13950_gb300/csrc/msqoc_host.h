@@ -81,7 +81,11 @@ msqoc_status guarded(F&& f) noexcept {
 }
 
 // tile layout (see msqoc_api.cu)
-void build_lanemap(int L, int q, int ncol, int ncol0, int nthreads, int* out);
+void build_lanemap(int L, int q, int ncol, int ncol0, int nthreads, int pair, int* out);
+// kernel family (pair: 1 = a lane pair per fiber) and columns per tile of a problem
+struct TileChoice {
+    int cpt, pair;
+};
 Tile tile_at(long t, int M, int E, int cpt, int prob);
 long tile_count(int M, int E, int cpt);
 SweepArgs sweep_args(const ProbDev& pd, const ProbDev* pds_dev, const Tile* tiles, const int* lanemap, int mode,

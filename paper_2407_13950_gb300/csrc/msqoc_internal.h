@@ -10,7 +10,8 @@ constexpr int MAXQ = 6;       // subsystems
 constexpr int MAXEX = 15;     // exchange-coupled pairs (q (q - 1) / 2)
 constexpr int MAXNF = 64;     // carriers over all subsystems
 constexpr int MAXL = 4;       // levels per subsystem handled by the sweep kernels
-constexpr int MAX_TILE_THREADS = 256;  // threads of one sweep tile (leaves 255 registers a thread)
+constexpr int MAX_TILE_THREADS = 256;       // threads of a one-thread-per-fiber tile (255 registers a thread)
+constexpr int MAX_PAIR_TILE_THREADS = 384;  // threads of a lane-pair tile (168 registers a thread)
 
 enum Solver { SOLVER_FP64 = 1, SOLVER_MIXED = 2 };
 
@@ -32,6 +33,7 @@ struct ProbDev {
     int q, L, N, E, F, ness, d1, M, nfsum, d;
     int cb;        // columns of a full tile
     int nthreads;  // threads per tile (multiple of 32)
+    int pair;      // 1: a lane pair per fiber (the real and the imaginary part), 0: one thread
     int ntiles;    // tiles of the problem's sweeps
     int solver;
     int kseg;      // steps per history segment (checkpoint interval; >= the longest window when
@@ -105,6 +107,7 @@ struct SweepArgs {
     int mode;             // SweepMode
     int seg;              // segment (SWEEP_RECOMPUTE, SWEEP_ADJOINT)
     int L, q, solver, nthreads;
+    int pair;             // kernel family: 1 = a lane pair per fiber, 0 = one thread per fiber
     double2* out;         // SWEEP_ROLLOUT: [M-1][E][N] states at the window boundaries
 };
 

@@ -1,0 +1,209 @@
+// Pieces shared by the two sweep kernel families (msqoc_sweep.cuh: one thread per fiber;
+// msqoc_sweep_pair.cuh: a lane pair per fiber): precision conversions, 1D bulk async copies
+// and bounded mbarrier waits, the per-thread neighbour lists, the shared-memory layout and
+// the tile barrier.
+#pragma once
+
+#include <cstdint>
+
+#include "msqoc_internal.h"
+
+namespace msqoc {
+
+__host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
+__host__ __device__ constexpr int next_pow2_c(int v) { return v <= 1 ? 1 : 2 * next_pow2_c((v + 1) / 2); }
+__host__ __device__ constexpr int log2_c(int v) { return v <= 1 ? 0 : 1 + log2_c(v / 2); }
+
+// ------------------------------------------------------------------ precision conversions
+// f64 -> f32 rounded to nearest (ties away from zero) for |x| in [2^-126, 2^127); smaller
+// magnitudes become signed zero.  Pure integer operations.
+__device__ __forceinline__ float f32_of(double x) {
+    unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned int ahi = static_cast<unsigned int>(bits >> 32) & 0x7fffffffu;
+    bits += (1ull << 28);
+    const unsigned int hi = static_cast<unsigned int>(bits >> 32);
+    const unsigned int lo = static_cast<unsigned int>(bits);
+    const unsigned int t = __funnelshift_l(lo, hi, 3);
+    unsigned int fb = ((t ^ 0x40000000u) & 0x7fffffffu) | (hi & 0x80000000u);
+    fb = (ahi < 0x38100000u) ? (hi & 0x80000000u) : fb;
+    return __uint_as_float(fb);
+}
+// f32 -> f64 exactly for normal floats (denormals become signed zero).  Integer operations.
+__device__ __forceinline__ double f64_of(float f) {
+    const unsigned int fb = __float_as_uint(f);
+    const unsigned int s = fb & 0x80000000u;
+    const unsigned int a = fb & 0x7fffffffu;
+    unsigned int hi = s | ((a >> 3) + 0x38000000u);
+    unsigned int lo = a << 29;
+    hi = (a < 0x00800000u) ? s : hi;
+    lo = (a < 0x00800000u) ? 0u : lo;
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+__device__ __forceinline__ float2 f32_of(double2 v) { return make_float2(f32_of(v.x), f32_of(v.y)); }
+__device__ __forceinline__ double2 f64_of(float2 v) { return make_double2(f64_of(v.x), f64_of(v.y)); }
+
+template <typename T2> struct cx;
+template <> struct cx<double2> { using T = double; };
+template <> struct cx<float2> { using T = float; };
+
+// sqrt(l) for small l, as compile-time constants
+__host__ __device__ constexpr double sqrt_small(int l) {
+    return l == 0 ? 0.0 : l == 1 ? 1.0 : l == 2 ? 1.4142135623730951 : l == 3 ? 1.7320508075688772 : 2.0;
+}
+
+// ------------------------------------------------------------------ async bulk copies (TMA, 1D)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// global -> shared bulk copy completing on an mbarrier (bytes multiple of 16, 16B-aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// shared -> global bulk copy (bulk-group completion)
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// bounded wait on an mbarrier phase; returns false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------ per-thread neighbour lists
+template <int L, int Q>
+struct Fiber {
+    static constexpr int NFIX = Q - 1;
+    static constexpr int NA = NFIX > 0 ? NFIX : 1;
+    int f;             // fiber index
+    int xo;            // offset of the fiber's first entry in a [cb][N] buffer
+    int nb1[NA];       // offset of neighbour fiber (first entry) for subsystem k, entry 1
+    int nb2[NA];       // entry 2 (exists when the level is interior)
+    int sl1[NA];       // coefficient slot of entry 1
+    int sl2[NA];
+    bool two[NA];      // entry 2 exists (warp-uniform by construction)
+    bool plus1[NA];    // entry 1 is the a_k (lowering, "+") term
+    double w1[NA];     // product weight sqrt(level factor) of entry 1
+    double w2[NA];
+
+    __device__ void init(int c, int f, const ProbDev& pd) {
+        constexpr int N = ipow_c(L, Q);
+        this->f = f;
+        xo = c * N + f * L;
+#pragma unroll
+        for (int k = 0; k < NFIX; ++k) {
+            const int sf = ipow_c(L, Q - 2 - k);   // stride of subsystem k in fiber units
+            const int lk = (f / sf) % L;
+            if (lk < L - 1) {
+                nb1[k] = c * N + (f + sf) * L;
+                sl1[k] = (k * L + lk) * 2 + 0;
+                plus1[k] = true;
+                w1[k] = pd.wsq[2 * lk + 0];
+                two[k] = lk > 0;
+                nb2[k] = c * N + (f - (lk > 0 ? sf : 0)) * L;
+                sl2[k] = (k * L + lk) * 2 + 1;
+                w2[k] = pd.wsq[2 * lk + 1];
+            } else {
+                nb1[k] = c * N + (f - sf) * L;
+                sl1[k] = (k * L + lk) * 2 + 1;
+                plus1[k] = false;
+                w1[k] = pd.wsq[2 * lk + 1];
+                two[k] = false;
+                nb2[k] = nb1[k];
+                sl2[k] = sl1[k];
+                w2[k] = 0.0;
+            }
+        }
+    }
+};
+
+// ------------------------------------------------------------------ shared memory layout
+// Per-slot arrays are sized for the two windows a tile can cover.  Lane-pair tiles (pair = 1)
+// keep each coefficient in the form of either part, so their coefficient arrays are twice as
+// large.
+struct SweepSmem {
+    size_t coef_d, coef_f, params, mbar, red, zy, galpha, D0, D1, FA, FB, H, UB0, UB1, total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cpt, int nthreads, int dmax, int solver,
+                                                  bool bwd, int pair) {
+    SweepSmem s{};
+    const int nslot = q * L * 2;
+    const int nwarps = nthreads / 32;
+    const int ncoef = pair ? 2 : 1;
+    int V = 1;
+    while (V < 4 * q) V <<= 1;
+    const size_t buf_d = size_t(cpt) * N * 16, buf_f = size_t(cpt) * N * 8;
+    size_t o = 0;
+    s.coef_d = o; o = align16(o + size_t(2) * 2 * ncoef * nslot * 16);  // [parity][slot][part][NSLOT]
+    s.coef_f = o; o = align16(o + size_t(2) * 2 * ncoef * nslot * 8);
+    s.params = o; o = align16(o + 2 * 2 * 4 * 4);                      // [parity][slot][4]
+    s.mbar = o;   o = align16(o + 2 * 8);
+    s.red = o;    o = align16(o + (bwd ? size_t(2) * 2 * nwarps * V * 8 : 0));   // [parity][slot][warp][V]
+    s.zy = o;     o = align16(o + (bwd ? size_t(2) * 2 * 4 * q * 8 : 0));        // [parity][slot][4q]
+    s.galpha = o; o = align16(o + (bwd ? size_t(2) * dmax * 8 : 0));             // [slot][d]
+    s.D0 = o;     o = align16(o + buf_d);
+    s.D1 = o;     o = align16(o + (solver == SOLVER_FP64 ? buf_d : 0));
+    s.FA = o;     o = align16(o + (solver == SOLVER_MIXED ? buf_f : 0));
+    s.FB = o;     o = align16(o + (solver == SOLVER_MIXED ? buf_f : 0));
+    s.H = o;      o = align16(o + (bwd ? 0 : buf_d));
+    s.UB0 = o;    o = align16(o + (bwd ? buf_d : 0));
+    s.UB1 = o;    o = align16(o + (bwd ? buf_d : 0));
+    s.total = o;
+    return s;
+}
+
+// Barrier of the tile's threads; a warp barrier when the tile is a single warp (blockDim is
+// uniform, so the branch is too).
+__device__ __forceinline__ void tile_sync() {
+    if (blockDim.x == 32)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+__device__ __forceinline__ int tile_sync_or(int p) {
+    if (blockDim.x == 32) return __any_sync(0xffffffffu, p);
+    return __syncthreads_or(p);
+}
+
+
+// first global step of window m (1-based); window m owns [win_start(m), win_start(m + 1))
+__device__ __forceinline__ int64_t win_start(const ProbDev& pd, int m) {
+    return (static_cast<int64_t>(m - 1) * pd.nsteps) / pd.M;
+}
+
+}  // namespace msqoc

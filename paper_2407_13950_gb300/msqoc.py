@@ -20,6 +20,7 @@ MSQOC_OK = 0
 STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OUT_OF_MEMORY", -3: "NOT_ADMITTED", -4: "CUDA_ERROR",
                 -5: "TIMEOUT", -6: "UNSUPPORTED", -7: "INTERNAL"}
 SOLVER_DEFAULT, SOLVER_FP64, SOLVER_MIXED = 0, 1, 2
+LAYOUT_AUTO, LAYOUT_FIBER, LAYOUT_PAIR = 0, 1, 2
 
 EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_query_layout", "msqoc_eval_objective", "msqoc_eval_gradient",
             "msqoc_destroy_problem", "msqoc_last_error", "msqoc_version", "msqoc_kernel_times",
@@ -49,7 +50,7 @@ class Controls(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int32), ("col_block", ctypes.c_int32), ("ckpt_interval", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("profile", ctypes.c_int32), ("layout", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 _lib = None
@@ -74,7 +75,7 @@ def load(build_if_missing: bool = True):
         sigs = {
             "msqoc_create_problem": (i32, [vp, vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, vp, vp]),
             "msqoc_query": (i32, [vp, vp, vp, vp]),
-            "msqoc_query_layout": (i32, [vp, vp, vp, vp, vp]),
+            "msqoc_query_layout": (i32, [vp, vp, vp, vp, vp, vp]),
             "msqoc_eval_objective": (i32, [vp, vp, vp, vp, vp, vp, vp]),
             "msqoc_eval_gradient": (i32, [vp, vp, vp, vp, vp, vp, vp]),
             "msqoc_destroy_problem": (i32, [vp]),
@@ -166,19 +167,22 @@ class Problem:
     """One multiple-shooting problem living on the current CUDA device."""
 
     def __init__(self, spec, target: Optional[np.ndarray] = None, solver: int = SOLVER_DEFAULT,
-                 col_block: int = 0, ckpt_interval: int = 0, profile: bool = False):
+                 col_block: int = 0, ckpt_interval: int = 0, profile: bool = False, layout: int = 0):
         lib = load()
         self.spec = spec
         self._desc = _Description(spec, target)
-        O = Options(solver, col_block, ckpt_interval, 1 if profile else 0)
+        O = Options(solver, col_block, ckpt_interval, 1 if profile else 0, layout)
         h = ctypes.c_void_p()
         _check(lib.msqoc_create_problem(ctypes.byref(self._desc.H), ctypes.byref(self._desc.C), self._desc.target_ptr,
                                         float(spec.T), int(spec.nsteps), int(spec.M), float(spec.mu),
                                         ctypes.byref(O), ctypes.byref(h)))
         self.handle = h
         cb, nt, th, K = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        _check(lib.msqoc_query_layout(h, ctypes.byref(cb), ctypes.byref(nt), ctypes.byref(th), ctypes.byref(K)))
+        lay = ctypes.c_int32()
+        _check(lib.msqoc_query_layout(h, ctypes.byref(cb), ctypes.byref(nt), ctypes.byref(th), ctypes.byref(K),
+                                      ctypes.byref(lay)))
         self.col_block, self.tiles, self.threads, self.ckpt_interval = cb.value, nt.value, th.value, K.value
+        self.layout = lay.value
         d, nW, nbytes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
         _check(lib.msqoc_query(h, ctypes.byref(d), ctypes.byref(nW), ctypes.byref(nbytes)))
         self.d, self.nW, self.device_bytes = d.value, nW.value, nbytes.value

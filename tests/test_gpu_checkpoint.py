@@ -15,20 +15,22 @@ from gpu_helpers import assert_grad_close, assert_objective_close
 pytestmark = pytest.mark.gpu
 
 
-def evaluate(spec, alpha, W, K, solver=msqoc.SOLVER_DEFAULT, col_block=0):
-    with msqoc.Problem(spec, ckpt_interval=K, solver=solver, col_block=col_block) as p:
+def evaluate(spec, alpha, W, K, solver=msqoc.SOLVER_DEFAULT, col_block=0, layout=msqoc.LAYOUT_AUTO):
+    with msqoc.Problem(spec, ckpt_interval=K, solver=solver, col_block=col_block, layout=layout) as p:
         return p.eval_gradient(alpha, W)
 
 
 @pytest.mark.parametrize("K", [2, 7, 64])
 def test_checkpointed_gradient_matches_oracle_3q(K):
+    """Both sweep kernel families, two-window tiles of 5 columns."""
     spec = S.transmon_spec(3, 30.0, 2001, 7, 8)     # windows of 285 and 286 steps
     alpha, W = S.random_alpha(spec, 21), S.random_W(spec, 21)
     want = oracle.evaluate(spec, alpha, W)
-    got = evaluate(spec, alpha, W, K, col_block=5)
-    assert_objective_close(got["P"], want["P"])
-    assert_grad_close(got["grad_alpha"], want["grad_alpha"], what="grad_alpha")
-    assert_grad_close(got["grad_W"], want["grad_W"], what="grad_W")
+    for layout in (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR):
+        got = evaluate(spec, alpha, W, K, col_block=5, layout=layout)
+        assert_objective_close(got["P"], want["P"])
+        assert_grad_close(got["grad_alpha"], want["grad_alpha"], what=f"grad_alpha (layout {layout})")
+        assert_grad_close(got["grad_W"], want["grad_W"], what=f"grad_W (layout {layout})")
 
 
 @pytest.mark.parametrize("K", [1, 16, 512])

@@ -21,15 +21,16 @@ SOLVERS = {"mixed": msqoc.SOLVER_MIXED, "fp64": msqoc.SOLVER_FP64}
 def check(spec, seed, solver=msqoc.SOLVER_DEFAULT, ckpt_interval=0):
     alpha, W = S.random_alpha(spec, seed), S.random_W(spec, seed)
     want = oracle.evaluate(spec, alpha, W, nthreads=os.cpu_count())
-    with msqoc.Problem(spec, solver=solver, ckpt_interval=ckpt_interval) as p:
-        got = p.eval_gradient(alpha, W)
-        obj = p.eval_objective(alpha, W)
-    assert_objective_close(got["P"], want["P"])
-    assert_objective_close(obj["J"], want["J"])
-    assert_grad_close(got["grad_alpha"], want["grad_alpha"], what="grad_alpha")
-    if spec.M > 1:
-        np.testing.assert_allclose(obj["pen"], want["pen"], rtol=1e-12, atol=1e-24)
-        assert_grad_close(got["grad_W"], want["grad_W"], what="grad_W")
+    for layout in (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR):     # both sweep kernel families
+        with msqoc.Problem(spec, solver=solver, ckpt_interval=ckpt_interval, layout=layout) as p:
+            got = p.eval_gradient(alpha, W)
+            obj = p.eval_objective(alpha, W)
+        assert_objective_close(got["P"], want["P"])
+        assert_objective_close(obj["J"], want["J"])
+        assert_grad_close(got["grad_alpha"], want["grad_alpha"], what=f"grad_alpha (layout {layout})")
+        if spec.M > 1:
+            np.testing.assert_allclose(obj["pen"], want["pen"], rtol=1e-12, atol=1e-24)
+            assert_grad_close(got["grad_W"], want["grad_W"], what=f"grad_W (layout {layout})")
 
 
 @pytest.mark.parametrize("M", [1, 8, 64])

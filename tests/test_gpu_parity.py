@@ -20,25 +20,32 @@ pytestmark = pytest.mark.gpu
 SOLVERS = {"mixed": msqoc.SOLVER_MIXED, "fp64": msqoc.SOLVER_FP64}
 
 
-def run_both(spec, alpha, W, solver, col_block=0, grad=True, ckpt_interval=0):
-    want = oracle.evaluate(spec, alpha, W, grad=grad)
-    with msqoc.Problem(spec, solver=solver, col_block=col_block, ckpt_interval=ckpt_interval) as p:
-        got = p.eval_gradient(alpha, W) if grad else p.eval_objective(alpha, W)
-        obj = p.eval_objective(alpha, W)
-    return got, obj, want
+LAYOUTS = {"fiber": msqoc.LAYOUT_FIBER, "pair": msqoc.LAYOUT_PAIR}
+BOTH = (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR)
 
 
-def check(spec, alpha, W, solver, col_block=0, ckpt_interval=0):
-    got, obj, want = run_both(spec, alpha, W, solver, col_block, ckpt_interval=ckpt_interval)
-    assert_objective_close(got["P"], want["P"])
-    assert_objective_close(obj["P"], want["P"])
-    if spec.M > 1:
-        # a penalty whose residual is at round-off ((1e-14)^2) has no relative accuracy
-        np.testing.assert_allclose(obj["pen"], want["pen"], rtol=1e-12, atol=1e-24)
-    assert_objective_close(obj["J"], want["J"])
-    assert_grad_close(got["grad_alpha"], want["grad_alpha"], what="grad_alpha")
-    if spec.M > 1:
-        assert_grad_close(got["grad_W"], want["grad_W"], what="grad_W")
+def run_gpu(spec, alpha, W, solver, col_block=0, ckpt_interval=0, layout=msqoc.LAYOUT_AUTO):
+    with msqoc.Problem(spec, solver=solver, col_block=col_block, ckpt_interval=ckpt_interval, layout=layout) as p:
+        if layout != msqoc.LAYOUT_AUTO:
+            assert p.layout == layout
+        return p.eval_gradient(alpha, W), p.eval_objective(alpha, W)
+
+
+def check(spec, alpha, W, solver, col_block=0, ckpt_interval=0, layouts=BOTH):
+    """Both sweep kernel families (one thread per fiber, a lane pair per fiber) against one
+    oracle evaluation."""
+    want = oracle.evaluate(spec, alpha, W)
+    for layout in layouts:
+        got, obj = run_gpu(spec, alpha, W, solver, col_block, ckpt_interval, layout)
+        assert_objective_close(got["P"], want["P"])
+        assert_objective_close(obj["P"], want["P"])
+        if spec.M > 1:
+            # a penalty whose residual is at round-off ((1e-14)^2) has no relative accuracy
+            np.testing.assert_allclose(obj["pen"], want["pen"], rtol=1e-12, atol=1e-24)
+        assert_objective_close(obj["J"], want["J"])
+        assert_grad_close(got["grad_alpha"], want["grad_alpha"], what=f"grad_alpha (layout {layout})")
+        if spec.M > 1:
+            assert_grad_close(got["grad_W"], want["grad_W"], what=f"grad_W (layout {layout})")
     return got, want
 
 
@@ -58,13 +65,15 @@ def test_parity_small(case, solver):
     check(spec, alpha, W, SOLVERS[solver])
 
 
-@pytest.mark.parametrize("cb", [1, 2, 3, 4, 5, 7, 8])
-def test_parity_column_blocks_4q(cb):
+@pytest.mark.parametrize("layout,cb", [("fiber", cb) for cb in (1, 2, 3, 4, 5, 7, 8)] +
+                         [("pair", cb) for cb in (1, 2, 3, 4, 5, 6, 7)])
+def test_parity_column_blocks_4q(layout, cb):
     """Tiles of cb columns run along the window-major column list; widths that do not divide
-    E = 16 give tiles covering two windows (3, 5 and 7 here, 7 being the benchmark's width)."""
+    E = 16 give tiles covering two windows (3, 5, 6 and 7 here).  8 columns (224 threads) is the
+    widest one-thread-per-fiber tile, 7 (384 threads) the widest lane-pair tile."""
     spec = S.transmon_spec(4, 1.2, 200, 3, 4)
     alpha, W = S.random_alpha(spec, 7), S.random_W(spec, 7)
-    check(spec, alpha, W, msqoc.SOLVER_MIXED, col_block=cb)
+    check(spec, alpha, W, msqoc.SOLVER_MIXED, col_block=cb, layouts=(LAYOUTS[layout],))
 
 
 @pytest.mark.parametrize("solver", list(SOLVERS))
@@ -79,13 +88,24 @@ def test_parity_tiles_over_ragged_windows_3q(cb, solver):
 def test_one_warp_tiles_must_not_cover_two_windows():
     spec = S.transmon_spec(3, 3.0, 200, 4, 5)     # 9 fibers a column: 3 columns = one warp
     with pytest.raises(msqoc.MsqocError):
-        msqoc.Problem(spec, col_block=3)
+        msqoc.Problem(spec, col_block=3, layout=msqoc.LAYOUT_FIBER)
+    spec = S.transmon_spec(2, 3.0, 200, 4, 5)     # 3 fibers (6 threads) a column: 3 columns = one warp
+    with pytest.raises(msqoc.MsqocError):
+        msqoc.Problem(spec, col_block=3, layout=msqoc.LAYOUT_PAIR)
 
 
 def test_column_block_beyond_the_tile_limit_is_rejected():
     spec = S.transmon_spec(4, 0.6, 100, 2, 4)
+    for cb, layout in ((16, msqoc.LAYOUT_AUTO),     # 16 x 27 fibers > 256 threads, x 2 > 384
+                       (10, msqoc.LAYOUT_FIBER),    # 270 > 256
+                       (8, msqoc.LAYOUT_PAIR)):     # 432 > 384
+        with pytest.raises(msqoc.MsqocError) as err:
+            msqoc.Problem(spec, col_block=cb, layout=layout)
+        assert err.value.status == -1
+    with msqoc.Problem(spec, col_block=8) as p:    # automatic family: only one thread per fiber fits
+        assert p.layout == msqoc.LAYOUT_FIBER
     with pytest.raises(msqoc.MsqocError) as err:
-        msqoc.Problem(spec, col_block=16)     # 16 columns x 27 fibers > 256 threads
+        msqoc.Problem(spec, layout=3)
     assert err.value.status == -1
 
 
