@@ -192,9 +192,26 @@ __device__ __forceinline__ void apply_off(const T2* __restrict__ buf, const T2* 
             for (int l = 0; l < L; ++l) cmac(w[l], c2, p2[l]);
         }
     }
-    // exchange-coupled problems are 2-level qubit models (the only shapes compiled with it)
+    // exchange-coupled problems are 2-level qubit models (the only shapes compiled with it):
+    // w += i (h/2) J x_src from the fiber's precomputed sources, or the general form
     if constexpr (L == 2 && Q >= 2) {
-        if (pd.nex) apply_exchange<L, Q, T2>(buf, pd, fb.f, fb.xo, w);
+        if (pd.nex > MAXEXF) {
+            apply_exchange<L, Q, T2>(buf, pd, fb.f, fb.xo, w);
+        } else if (pd.nex) {
+            using R = typename cx<T2>::T;
+#pragma unroll
+            for (int e = 0; e < MAXEXF; ++e) {
+                if (fb.exs[e] < 0) continue;
+                const R c = static_cast<R>(pd.ex_c[e]);
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    if (fb.ext[e] >= 0 && fb.ext[e] != l) continue;
+                    const T2 x = buf[fb.exs[e] + (fb.ext[e] < 0 ? l : 0)];
+                    w[l].x -= c * x.y;
+                    w[l].y += c * x.x;
+                }
+            }
+        }
     }
 }
 

@@ -103,6 +103,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // ------------------------------------------------------------------ per-thread neighbour lists
+// exchange-coupled pairs whose sources a fiber keeps precomputed (more use the general form)
+constexpr int MAXEXF = 6;
 template <int L, int Q>
 struct Fiber {
     static constexpr int NFIX = Q - 1;
@@ -117,6 +119,11 @@ struct Fiber {
     bool plus1[NA];    // entry 1 is the a_k (lowering, "+") term
     double w1[NA];     // product weight sqrt(level factor) of entry 1
     double w2[NA];
+    // dipole exchange of a 2-level (qubit) problem with at most MAXEXF coupled pairs: the
+    // source of pair e's term (entry index in a [cb][N] buffer, -1: the pair gives this fiber no
+    // term) and its target (a level of the fiber, or -1: every entry from the source fiber)
+    int exs[MAXEXF];
+    int ext[MAXEXF];
 
     __device__ void init(int c, int f, const ProbDev& pd) {
         constexpr int N = ipow_c(L, Q);
@@ -144,6 +151,36 @@ struct Fiber {
                 nb2[k] = nb1[k];
                 sl2[k] = sl1[k];
                 w2[k] = 0.0;
+            }
+        }
+        if constexpr (L == 2 && Q >= 2) init_exchange(pd);
+    }
+
+    // For 2 levels every weight of the exchange terms is 1 and a coupled pair (j, k) gives the
+    // fiber at most one term.  k the last subsystem: level 1 of the fiber takes level 0 of the
+    // fiber with l_j + 1 (a_k^+ a_j, when l_j = 0), or level 0 takes level 1 of the fiber with
+    // l_j - 1 (a_k a_j^+, when l_j = 1).  k not the last: every entry takes the same level of
+    // the fiber with (l_j + 1, l_k - 1) when (l_j, l_k) = (0, 1), or (l_j - 1, l_k + 1) when
+    // (1, 0).  Computed once per launch instead of in every apply.
+    __device__ void init_exchange(const ProbDev& pd) {
+#pragma unroll
+        for (int e = 0; e < MAXEXF; ++e) {
+            exs[e] = -1;
+            ext[e] = -1;
+            if (e < pd.nex) {
+                const int j = pd.ex_j[e], k = pd.ex_k[e];
+                int sfj = 1, sfk = 1;                          // fiber strides (j is never the last)
+                for (int t = j; t < Q - 2; ++t) sfj *= 2;
+                for (int t = k; t < Q - 2; ++t) sfk *= 2;
+                const int lj = (f / sfj) % 2;
+                if (k == Q - 1) {
+                    exs[e] = lj == 0 ? xo + sfj * 2 : xo - sfj * 2 + 1;
+                    ext[e] = lj == 0 ? 1 : 0;
+                } else {
+                    const int lk = (f / sfk) % 2;
+                    if (lk == 1 && lj == 0) exs[e] = xo + (sfj - sfk) * 2;
+                    if (lk == 0 && lj == 1) exs[e] = xo + (sfk - sfj) * 2;
+                }
             }
         }
     }

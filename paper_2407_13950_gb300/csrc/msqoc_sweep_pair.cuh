@@ -120,9 +120,23 @@ __device__ __forceinline__ void apply_off_pair(const T2* __restrict__ buf, const
             for (int l = 0; l < L; ++l) w[l] = pmac(w[l], c2, ba[o2 + 2 * l], bb[o2 + 2 * l]);
         }
     }
-    // exchange-coupled problems are 2-level qubit models (the only shapes compiled with it)
+    // exchange-coupled problems are 2-level qubit models (the only shapes compiled with it):
+    // w += (i (h/2) J x_src)_p from the fiber's precomputed sources, or the general form
     if constexpr (L == 2 && Q >= 2) {
-        if (pd.nex) apply_exchange_pair<L, Q, R>(bb, pd, fb.f, fb.xo, p, w);
+        if (pd.nex > MAXEXF) {
+            apply_exchange_pair<L, Q, R>(bb, pd, fb.f, fb.xo, p, w);
+        } else if (pd.nex) {
+#pragma unroll
+            for (int e = 0; e < MAXEXF; ++e) {
+                if (fb.exs[e] < 0) continue;
+                const R c = static_cast<R>(p ? pd.ex_c[e] : -pd.ex_c[e]);
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    if (fb.ext[e] >= 0 && fb.ext[e] != l) continue;
+                    w[l] += c * bb[2 * (fb.exs[e] + (fb.ext[e] < 0 ? l : 0))];
+                }
+            }
+        }
     }
 }
 
