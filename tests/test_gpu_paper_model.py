@@ -49,6 +49,19 @@ def test_qft16_short(solver):
     check(S.paper_qft_spec(4, M=4, nsteps=2000), 83, solver=SOLVERS[solver])
 
 
+@pytest.mark.parametrize("q", [4, 5])
+def test_all_to_all_exchange(q):
+    """Every pair of qubits coupled, with distinct strengths: 4 qubits give 6 pairs (sources
+    precomputed per fiber, pairs with the last subsystem and pairs between fixed subsystems at
+    every distance), 5 qubits give 10 (more than the per-fiber list holds: the general form)."""
+    base = S.paper_qft_spec(min(q, 4), M=3, nsteps=300)
+    jx = [[(2 * np.pi * 0.004 * (1 + 0.3 * k + 0.1 * l) if l > k else 0.0) for l in range(q)] for k in range(q)]
+    omega = [list(base.omega[min(k, len(base.omega) - 1)]) for k in range(q)]
+    spec = base.replace(q=q, xi=[0.0] * q, xi_cross=[[0.0] * q for _ in range(q)], omega=omega,
+                        detune=[2 * np.pi * 0.06 * (k - (q - 1) / 2) for k in range(q)], jx=jx, T=8.0)
+    check(spec, 85)
+
+
 def test_qft16_full_size_sampled_windows():
     """QFT-16 at the paper's full size (106072 steps) over 256 windows (the paper's largest
     run): the last two windows against the oracle (J, pen_255, dP/dW^255), the gradients as a
