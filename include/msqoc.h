@@ -194,6 +194,39 @@ msqoc_status msqoc_eval_regularization(msqoc_problem* p, const double* alpha, do
                                        double gamma_energy, double* R_out, double* grad_alpha,
                                        void* stream);
 
+/* ---- L-BFGS steps of the client optimiser (Sec. 5 minimises P + R with L-BFGS; the paper uses
+ * PETSc/TAO, this library its own kernels).  The optimisation vector x has n entries; its first
+ * nb entries (the control coefficients) may carry box bounds |x_i| <= lim_i (lim: nb entries,
+ * NULL when nb = 0).  An entry at its bound whose gradient pushes it outward is *active*: held
+ * fixed for the iteration.  The memory is a ring of cap slots (cap <= MSQOC_LBFGS_MAXMEM) of
+ * pairs s_j = x_{j+1} - x_j, y_j = g_{j+1} - g_j, stored as S, Y [cap][n]; rho[slot] =
+ * 1/<s, y>, yy[slot] = <y, y>; the m newest pairs are used, the newest in slot head - 1
+ * (mod cap).  Every array is device memory; each call is one CTA on `stream`, asynchronous,
+ * with sums in a fixed order (bitwise repeatable).  No paper counterpart beyond the choice of
+ * L-BFGS. */
+#define MSQOC_LBFGS_MAXMEM 64
+
+/* Search direction d = -H pg by the two-loop recursion (pg: the gradient g with its active
+ * entries zeroed; H: the limited-memory inverse Hessian with initial scaling <s,y>/<y,y> of the
+ * newest pair; m = 0 gives d = -pg/||pg||), zeroed on the active set; slope_out = <pg, d>
+ * (< 0 for a descent direction).  d_out: n doubles; slope_out: 1 double. */
+msqoc_status msqoc_lbfgs_direction(int64_t n, int64_t nb, const double* x, const double* g,
+                                   const double* lim, const double* S, const double* Y,
+                                   const double* rho, const double* yy, int32_t cap, int32_t m,
+                                   int32_t head, double* d_out, double* slope_out, void* stream);
+
+/* Trial point of the projected line search: x_new = x + step d, the first nb entries clipped to
+ * [-lim, lim]; dec_out = <g, x_new - x> (the first-order change of the objective). */
+msqoc_status msqoc_lbfgs_trial(int64_t n, int64_t nb, const double* x, const double* d, double step,
+                               const double* lim, const double* g, double* x_new, double* dec_out,
+                               void* stream);
+
+/* Memory update: s_out = x_new - x, y_out = g_new - g (n doubles each, e.g. the next ring slot
+ * of S and Y), sy_yy_out = (<s, y>, <y, y>) (2 doubles). */
+msqoc_status msqoc_lbfgs_update(int64_t n, const double* x, const double* x_new, const double* g,
+                                const double* g_new, double* s_out, double* y_out, double* sy_yy_out,
+                                void* stream);
+
 /* Release every resource of the problem (synchronizes the device first). NULL is a no-op. */
 msqoc_status msqoc_destroy_problem(msqoc_problem* p);
 

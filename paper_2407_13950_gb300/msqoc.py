@@ -27,7 +27,8 @@ EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_query_layout", "msqoc_
             "msqoc_measure_fp64_peak", "msqoc_eval_objective_noalloc", "msqoc_batch_create",
             "msqoc_batch_eval_objective", "msqoc_batch_eval_gradient", "msqoc_batch_destroy", "msqoc_set_inputs",
             "msqoc_get_objective", "msqoc_get_gradient", "msqoc_batch_eval_subset", "msqoc_autotune",
-            "msqoc_rollout", "msqoc_rollout_estimate", "msqoc_eval_regularization"]
+            "msqoc_rollout", "msqoc_rollout_estimate", "msqoc_eval_regularization", "msqoc_lbfgs_direction",
+            "msqoc_lbfgs_trial", "msqoc_lbfgs_update"]
 BATCH_GRADIENT, BATCH_GRAPH = 1, 2
 KERNEL_NAMES = ["controls", "forward", "terminal", "adjoint", "finalize"]
 
@@ -96,6 +97,9 @@ def load(build_if_missing: bool = True):
             "msqoc_rollout": (i32, [vp, vp, vp, vp]),
             "msqoc_rollout_estimate": (i32, [vp, vp, vp]),
             "msqoc_eval_regularization": (i32, [vp, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp]),
+            "msqoc_lbfgs_direction": (i32, [i64, i64, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp]),
+            "msqoc_lbfgs_trial": (i32, [i64, i64, vp, vp, ctypes.c_double, vp, vp, vp, vp, vp]),
+            "msqoc_lbfgs_update": (i32, [i64, vp, vp, vp, vp, vp, vp, vp, vp]),
             "msqoc_autotune": (i32, [vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, vp, vp, i32, vp, vp, vp,
                                      i32, vp]),
         }
@@ -379,6 +383,29 @@ class Batch:
         _check(load().msqoc_get_objective(p.handle, _ptr(P), _ptr(J), _ptr(pen) if p.spec.M > 1 else None,
                                           _stream_handle(stream)))
         return {"P": float(P[0]), "J": float(J[0]), "pen": pen[:p.spec.M - 1].copy()}
+
+
+# ---- L-BFGS steps (device arrays; asynchronous on the stream)
+LBFGS_MAXMEM = 64
+
+
+def lbfgs_direction(n, nb, x, g, lim, S, Y, rho, yy, cap, m, head, d_out, slope_out, stream=None):
+    """d_out = -H pg by the two-loop recursion over the m newest ring slots (msqoc_lbfgs_direction)."""
+    _check(load().msqoc_lbfgs_direction(int(n), int(nb), _ptr(x), _ptr(g), _ptr(lim), _ptr(S), _ptr(Y), _ptr(rho),
+                                        _ptr(yy), int(cap), int(m), int(head), _ptr(d_out), _ptr(slope_out),
+                                        _stream_handle(stream)))
+
+
+def lbfgs_trial(n, nb, x, d, step, lim, g, x_new, dec_out, stream=None):
+    """x_new = box projection of x + step d, dec_out = <g, x_new - x> (msqoc_lbfgs_trial)."""
+    _check(load().msqoc_lbfgs_trial(int(n), int(nb), _ptr(x), _ptr(d), float(step), _ptr(lim), _ptr(g), _ptr(x_new),
+                                    _ptr(dec_out), _stream_handle(stream)))
+
+
+def lbfgs_update(n, x, x_new, g, g_new, s_out, y_out, sy_yy_out, stream=None):
+    """s_out = x_new - x, y_out = g_new - g, sy_yy_out = (<s, y>, <y, y>) (msqoc_lbfgs_update)."""
+    _check(load().msqoc_lbfgs_update(int(n), _ptr(x), _ptr(x_new), _ptr(g), _ptr(g_new), _ptr(s_out), _ptr(y_out),
+                                     _ptr(sy_yy_out), _stream_handle(stream)))
 
 
 def autotune(spec, alpha=None, probe_steps: int = 64, solver: int = SOLVER_DEFAULT, ckpt_interval: int = 0):

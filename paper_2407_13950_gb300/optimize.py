@@ -19,8 +19,9 @@ The minimiser is L-BFGS (two-loop recursion, limited memory) with a backtracking
 search; the box bounds are kept by projection: an alpha at its bound whose gradient pushes it
 outward is held fixed for the iteration (its gradient and search-direction components are
 zeroed) and steps are clipped to the box.  Every objective and gradient comes from the
-library's kernels through the C ABI; the vectors of the recursion live on the GPU as torch
-tensors (FP64) and only scalars cross to the host.
+library's kernels through the C ABI, and so do the L-BFGS steps (msqoc_lbfgs_direction, _trial,
+_update: one CTA each); the vectors live on the GPU as torch tensors (FP64) and only scalars
+cross to the host, a few per iteration.
 """
 from __future__ import annotations
 
@@ -116,57 +117,40 @@ def optimize(problem: msqoc.Problem, alpha0, W0=None, *, tol: float = 1e-3, max_
         """device scalars to host floats in one transfer"""
         return torch.cat([t.reshape(1) for t in ts]).tolist()
 
-    def project(xv):
-        if lim is not None:
-            torch.minimum(torch.maximum(xv[:d], -lim), lim, out=xv[:d])
-        return xv
-
-    def active_set(xv, gv):
-        """alphas at a bound whose gradient pushes them outward (held fixed this iteration)"""
-        act = torch.zeros_like(xv, dtype=torch.bool)
-        if lim is not None:
-            a, ga = xv[:d], gv[:d]
-            act[:d] = ((a >= lim) & (ga < 0)) | ((a <= -lim) & (ga > 0))
-        return act
+    n = d + nW
+    nb = d if lim is not None else 0
+    cap = max(1, min(int(memory), msqoc.LBFGS_MAXMEM))
+    S = torch.zeros((cap, n), device=dev, dtype=torch.float64)     # memory ring: s_j, y_j
+    Y = torch.zeros((cap, n), device=dev, dtype=torch.float64)
+    rho = torch.zeros(cap, device=dev, dtype=torch.float64)        # 1 / <s_j, y_j>
+    yy = torch.zeros(cap, device=dev, dtype=torch.float64)         # <y_j, y_j>
+    m = head = 0
+    direction = torch.empty_like(x)
+    slope = torch.zeros(1, device=dev, dtype=torch.float64)
+    dec = torch.zeros(1, device=dev, dtype=torch.float64)
+    sy_yy = torch.zeros(2, device=dev, dtype=torch.float64)
+    x_new = torch.empty_like(x)
+    g_new = torch.empty_like(g)
 
     evaluate(x, g)
     P, R = scalars(Pv, Rv)
     f = P + R
     est = problem.rollout_estimate()
-    mem = []            # (s, y, 1 / <y, s>) pairs, oldest first
     history = [{"F": f, "P": P, "estimate": est, "step": 0.0}]
     it = 0
     while est >= tol and it < max_iter:
-        act = active_set(x, g)
-        pg = g.masked_fill(act, 0.0)
-        # two-loop recursion; the scalars stay on the device (no host round trip per product)
-        q = pg.clone()
-        coef = []
-        for s, y, rho in reversed(mem):
-            a_i = rho * torch.dot(s, q)
-            q.sub_(a_i * y)
-            coef.append(a_i)
-        if mem:
-            s, y, _ = mem[-1]
-            q.mul_(torch.dot(s, y) / torch.dot(y, y))
-        else:
-            q.div_(torch.linalg.norm(q).clamp_min(1e-300))      # first step: unit length
-        for (s, y, rho), a_i in zip(mem, reversed(coef)):
-            q.add_((a_i - rho * torch.dot(y, q)) * s)
-        direction = q.neg_().masked_fill_(act, 0.0)
-        if float(torch.dot(pg, direction)) >= 0:                # not a descent direction: restart
-            mem.clear()
-            direction = -pg / torch.linalg.norm(pg).clamp_min(1e-300)
+        # search direction on the device (two-loop recursion, active set held fixed)
+        msqoc.lbfgs_direction(n, nb, x, g, lim, S, Y, rho, yy, cap, m, head, direction, slope, stream=stream)
+        if slope.item() >= 0:                                   # not a descent direction: restart
+            m = 0
+            msqoc.lbfgs_direction(n, nb, x, g, lim, S, Y, rho, yy, cap, 0, head, direction, slope, stream=stream)
         # backtracking Armijo line search on the projected path
         t = 1.0
-        x_new = torch.empty_like(x)
-        g_new = torch.empty_like(g)
         accepted = False
         for _ in range(max_backtracks):
-            x_new.copy_(x).add_(direction, alpha=t)
-            project(x_new)
+            msqoc.lbfgs_trial(n, nb, x, direction, t, lim, g, x_new, dec, stream=stream)
             evaluate(x_new, g_new)
-            P_new, R_new, decrease = scalars(Pv, Rv, torch.dot(g, x_new - x))
+            P_new, R_new, decrease = scalars(Pv, Rv, dec)
             f_new = P_new + R_new
             if f_new <= f + c1 * decrease:
                 accepted = True
@@ -174,13 +158,16 @@ def optimize(problem: msqoc.Problem, alpha0, W0=None, *, tol: float = 1e-3, max_
             t *= 0.5
         if not accepted:
             break
-        s_vec, y_vec = x_new - x, g_new - g
-        sy, yy = torch.stack([torch.dot(s_vec, y_vec), torch.dot(y_vec, y_vec)]).tolist()
-        if sy > 1e-12 * yy:
-            mem.append((s_vec, y_vec, torch.tensor(1.0 / sy, device=dev, dtype=torch.float64)))
-            if len(mem) > memory:
-                mem.pop(0)
-        x, g, f, P = x_new, g_new, f_new, P_new
+        msqoc.lbfgs_update(n, x, x_new, g, g_new, S[head], Y[head], sy_yy, stream=stream)
+        sy, yyv = sy_yy.tolist()
+        if sy > 1e-12 * yyv:                                    # curvature condition: keep the pair
+            rho[head] = 1.0 / sy
+            yy[head] = yyv
+            head = (head + 1) % cap
+            m = min(m + 1, cap)
+        x, x_new = x_new, x
+        g, g_new = g_new, g
+        f, P = f_new, P_new
         est = problem.rollout_estimate()
         it += 1
         history.append({"F": f, "P": P, "estimate": est, "step": t})
