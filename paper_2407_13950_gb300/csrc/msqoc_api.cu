@@ -217,13 +217,18 @@ bool tile_width_ok(int cpt, int E, int F, int q, int L, int N, int d, int solver
 //   1. the makespan: an SM's ceil(tiles / SMs) tiles in waves of `resident`, summed over the
 //      waves;
 //   2. tiles that stay inside one window;
-//   3. the idle-lane fraction of a tile.
+//   3. where every wave sits at the single-warp floor (problems too small to fill the GPU, whose
+//      candidates all tie there): tiles of 2 or 3 warps, then of 1, then of more (measured
+//      there, 2-3 warp tiles step fastest:
+//      fewer threads meet at each barrier than in wider tiles, and the coefficient and gradient
+//      work of a tile is not serialised with the step as in one-warp tiles);
+//   4. the idle-lane fraction of a tile.
 // fixed_cpt > 0 restricts the width, layout (MSQOC_LAYOUT_*) the family.  cpt = -1: none fits.
 TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int d, int solver, int sms, int fixed_cpt,
                               int layout) {
     TileChoice best{-1, 0};
     double best_a = 0.0, best_c = 0.0;
-    int best_b = 0;
+    int best_b = 0, best_w = 0;
     for (int pair = 0; pair <= 1; ++pair) {
         if ((layout == MSQOC_LAYOUT_FIBER && pair) || (layout == MSQOC_LAYOUT_PAIR && !pair)) continue;
         const double c_load = pair ? 0.6 : 1.0, c_alone = pair ? 0.7 : 1.0;
@@ -255,12 +260,16 @@ TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int d, i
                               (double(waves - 1) * std::max(double(resident * warps) * c_load / 4.0, c_alone) +
                                std::max(double(last * warps) * c_load / 4.0, c_alone));
             const double cc = 1.0 - double((pair ? 2 : 1) * cpt * F) / (32.0 * warps);
+            const bool at_floor = ca <= (cb ? 1.18 : 1.0) * double(waves) * c_alone + 1e-9;
+            const int cw = !at_floor ? 0 : ((warps == 2 || warps == 3) ? 0 : (warps == 1 ? 1 : 2));
+            const bool tie_a = ca < best_a + 1e-9, tie_b = cb == best_b, tie_w = cw == best_w;
             const bool better = best.cpt < 0 || ca < best_a - 1e-9 ||
-                                (ca < best_a + 1e-9 && (cb < best_b || (cb == best_b && cc < best_c - 1e-9)));
+                                (tie_a && (cb < best_b || (tie_b && (cw < best_w || (tie_w && cc < best_c - 1e-9)))));
             if (better) {
                 best = TileChoice{cpt, pair};
                 best_a = ca;
                 best_b = cb;
+                best_w = cw;
                 best_c = cc;
             }
         }
