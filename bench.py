@@ -232,20 +232,25 @@ def run_ours(args, spec):
 
     sampler = ClockSampler(local)
     sampler.start()
-    kt = {k: 0.0 for k in msqoc.KERNEL_NAMES}
+    # timed region: the evaluations back to back, no host synchronisation between them
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
     for _ in range(args.steps):
         prob.eval_gradient_into(a_d, W_d, P_d, ga_d, gW_d, stream=stream)
+    e1.record(stream)
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+    value = world / (ms * 1e-3)
+    # per-kernel CUDA-event times (the library's profiling events) over the same number of
+    # evaluations right after: reading them synchronises every evaluation
+    kt = {k: 0.0 for k in msqoc.KERNEL_NAMES}
+    for _ in range(args.steps):
+        prob.eval_gradient_into(a_d, W_d, P_d, ga_d, gW_d, stream=stream)
         t = prob.kernel_times()
         for k in kt:
             kt[k] += t[k]
-    e1.record(stream)
-    barrier()
     clocks = sampler.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
-    value = world / (ms * 1e-3)
 
     # end to end through the C ABI with host buffers (H2D of alpha and W, D2H of P and gradients)
     e2e_times = []
