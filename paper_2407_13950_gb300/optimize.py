@@ -33,6 +33,8 @@ import numpy as np
 
 from . import msqoc
 
+NATIVE_MAX = 1 << 18   # unknowns up to which the one-CTA L-BFGS kernels are used
+
 
 @dataclasses.dataclass
 class Result:
@@ -131,6 +133,51 @@ def optimize(problem: msqoc.Problem, alpha0, W0=None, *, tol: float = 1e-3, max_
     sy_yy = torch.zeros(2, device=dev, dtype=torch.float64)
     x_new = torch.empty_like(x)
     g_new = torch.empty_like(g)
+    # The library's L-BFGS kernels run on one CTA: a few launches an iteration, the right
+    # trade for the paper's problem sizes; beyond NATIVE_MAX unknowns the same steps run as
+    # whole-GPU vector operations.
+    native = n <= NATIVE_MAX
+
+    def lbfgs_direction(mm):
+        if native:
+            msqoc.lbfgs_direction(n, nb, x, g, lim, S, Y, rho, yy, cap, mm, head, direction, slope, stream=stream)
+            return
+        act = torch.zeros(n, device=dev, dtype=torch.bool)
+        if nb:
+            act[:nb] = ((x[:nb] >= lim) & (g[:nb] < 0)) | ((x[:nb] <= -lim) & (g[:nb] > 0))
+        pg = g.masked_fill(act, 0.0)
+        q = pg.clone()
+        slots = [(head - mm + j) % cap for j in range(mm)]
+        coef = []
+        for k in reversed(slots):
+            a_k = rho[k] * torch.dot(S[k], q)
+            q.sub_(a_k * Y[k])
+            coef.append(a_k)
+        if mm:
+            q.mul_((1.0 / rho[slots[-1]]) / yy[slots[-1]])
+        else:
+            q.div_(torch.linalg.norm(q).clamp_min(1e-300))
+        for k, a_k in zip(slots, reversed(coef)):
+            q.add_((a_k - rho[k] * torch.dot(Y[k], q)) * S[k])
+        torch.neg(q, out=direction).masked_fill_(act, 0.0)
+        slope.copy_(torch.dot(pg, direction).reshape(1))
+
+    def lbfgs_trial(t):
+        if native:
+            msqoc.lbfgs_trial(n, nb, x, direction, t, lim, g, x_new, dec, stream=stream)
+            return
+        x_new.copy_(x).add_(direction, alpha=t)
+        if nb:
+            torch.minimum(torch.maximum(x_new[:nb], -lim), lim, out=x_new[:nb])
+        dec.copy_(torch.dot(g, x_new - x).reshape(1))
+
+    def lbfgs_update():
+        if native:
+            msqoc.lbfgs_update(n, x, x_new, g, g_new, S[head], Y[head], sy_yy, stream=stream)
+            return
+        torch.sub(x_new, x, out=S[head])
+        torch.sub(g_new, g, out=Y[head])
+        sy_yy.copy_(torch.stack([torch.dot(S[head], Y[head]), torch.dot(Y[head], Y[head])]))
 
     evaluate(x, g)
     P, R = scalars(Pv, Rv)
@@ -140,15 +187,15 @@ def optimize(problem: msqoc.Problem, alpha0, W0=None, *, tol: float = 1e-3, max_
     it = 0
     while est >= tol and it < max_iter:
         # search direction on the device (two-loop recursion, active set held fixed)
-        msqoc.lbfgs_direction(n, nb, x, g, lim, S, Y, rho, yy, cap, m, head, direction, slope, stream=stream)
+        lbfgs_direction(m)
         if slope.item() >= 0:                                   # not a descent direction: restart
             m = 0
-            msqoc.lbfgs_direction(n, nb, x, g, lim, S, Y, rho, yy, cap, 0, head, direction, slope, stream=stream)
+            lbfgs_direction(0)
         # backtracking Armijo line search on the projected path
         t = 1.0
         accepted = False
         for _ in range(max_backtracks):
-            msqoc.lbfgs_trial(n, nb, x, direction, t, lim, g, x_new, dec, stream=stream)
+            lbfgs_trial(t)
             evaluate(x_new, g_new)
             P_new, R_new, decrease = scalars(Pv, Rv, dec)
             f_new = P_new + R_new
@@ -158,7 +205,7 @@ def optimize(problem: msqoc.Problem, alpha0, W0=None, *, tol: float = 1e-3, max_
             t *= 0.5
         if not accepted:
             break
-        msqoc.lbfgs_update(n, x, x_new, g, g_new, S[head], Y[head], sy_yy, stream=stream)
+        lbfgs_update()
         sy, yyv = sy_yy.tolist()
         if sy > 1e-12 * yyv:                                    # curvature condition: keep the pair
             rho[head] = 1.0 / sy

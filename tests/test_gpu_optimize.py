@@ -66,3 +66,22 @@ def test_paper_settings_qft4_converge_and_the_estimate_bounds_the_rollout(M, sig
     assert J_rollout <= res.estimate * (1 + 1e-12) and res.estimate < 1e-3
     print(f"QFT-4 M={M} sigma={sigma}: {res.iterations} iterations, estimate {res.estimate:.3e}, "
           f"roll-out infidelity {J_rollout:.3e}")
+
+
+def test_native_and_vector_lbfgs_steps_agree(monkeypatch):
+    """The one-CTA L-BFGS kernels (small problems) and the whole-GPU vector form (large ones)
+    take the same iterates, up to the order of their sums."""
+    spec = S.paper_qft_spec(2, M=4)
+    alpha0 = S.random_alpha(spec, 93)
+    st = optimize.paper_settings(spec)
+    runs = []
+    for native_max in (1 << 18, 0):
+        monkeypatch.setattr(optimize, "NATIVE_MAX", native_max)
+        with msqoc.Problem(spec) as p:
+            runs.append(optimize.optimize(p, alpha0, tol=0.0, max_iter=6, bound=st["bound"],
+                                          gamma_tik=st["gamma_tik"], gamma_energy=st["gamma_energy"], sigma=0.1))
+    a, b = runs
+    assert a.iterations == b.iterations == 6
+    assert [h["step"] for h in a.history] == [h["step"] for h in b.history]
+    np.testing.assert_allclose([h["F"] for h in a.history], [h["F"] for h in b.history], rtol=1e-9)
+    np.testing.assert_allclose(a.alpha, b.alpha, rtol=1e-7, atol=1e-12)
