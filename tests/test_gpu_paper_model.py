@@ -62,11 +62,21 @@ def test_all_to_all_exchange(q):
     check(spec, 85)
 
 
-def test_qft16_full_size_sampled_windows():
-    """QFT-16 at the paper's full size (106072 steps) over 256 windows (the paper's largest
-    run): the last two windows against the oracle (J, pen_255, dP/dW^255), the gradients as a
-    whole by central differences along seeded random directions."""
-    spec = S.paper_qft_spec(4, M=256)
+def test_qft8_full_time_grid_pair_tiles():
+    """QFT-8 on the paper's full grid (19806 steps) at 32 windows, the lane-pair kernels."""
+    spec = S.paper_qft_spec(3, M=32)
+    with msqoc.Problem(spec) as p:
+        assert p.layout == msqoc.LAYOUT_PAIR
+    check(spec, 86)
+
+
+@pytest.mark.parametrize("M", [64, 256])
+def test_qft16_full_size_sampled_windows(M):
+    """QFT-16 at the paper's full size (106072 steps) over 64 windows (lane-pair tiles) and 256
+    (the paper's largest run; one thread per fiber): the last two windows against the oracle (J,
+    pen_{M-1}, dP/dW^{M-1}), the gradients as a whole by central differences along seeded random
+    directions."""
+    spec = S.paper_qft_spec(4, M=M)
     alpha, W = S.random_alpha(spec, 84), S.random_W(spec, 84)
     M = spec.M
     with msqoc.Problem(spec) as p:
