@@ -219,11 +219,15 @@ def run_ours(args, spec):
     gW_d = torch.zeros(spec.nW, device=dev, dtype=torch.float64)
     stream = torch.cuda.current_stream(dev)
     solver = msqoc.SOLVER_FP64 if args.solver == "fp64" else msqoc.SOLVER_MIXED
-    # tile width: the library's model (0), a given width, or measured by the autotuner (-1)
-    tuned, tune_ms = (msqoc.autotune(spec, alpha=alpha, probe_steps=64, solver=solver) if args.col_block < 0
-                      else (None, None))
+    # tile width and kernel family: the library's model (0), a given width, or measured by the
+    # autotuner (-1)
+    layout = LAYOUTS[args.layout]
+    tuned = tune_ms = None
+    if args.col_block < 0:
+        tuned, layout, tune_ms = msqoc.autotune(spec, alpha=alpha, probe_steps=64, solver=solver, layout=layout)
+        tune_ms = {f"{'pair' if lay == 2 else 'fiber'}-{cb}": v for (lay, cb), v in tune_ms.items()}
     col_block = tuned if args.col_block < 0 else args.col_block
-    prob = msqoc.Problem(spec, solver=solver, col_block=col_block, profile=True, layout=LAYOUTS[args.layout])
+    prob = msqoc.Problem(spec, solver=solver, col_block=col_block, profile=True, layout=layout)
     peak_tflops = msqoc.measure_fp64_peak()
 
     for _ in range(args.warmup):

@@ -337,20 +337,22 @@ msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H, const msqo
                                           const double* alpha, const double* W, double* P_out,
                                           double* J_out, double* pen_out, void* stream);
 
-/* Tile width by measurement (not an operation of the paper): for every admissible number of
- * columns per sweep tile, a problem of the same description, step size and window count but
- * only probe_steps steps per window is created with that width and its objective + gradient is
- * timed (one warm-up, two timed evaluations, CUDA events on the default stream).  *col_block
- * receives the fastest width (use it as msqoc_options.col_block); widths[i], ms[i] (i <
- * *n_out <= max_out; may be NULL) the widths tried and their milliseconds per evaluation.
- * alpha: d control coefficients (host) of a typical iterate (the iteration counts of the step
- * solver depend on the control amplitude); NULL = alternating +-2 pi 0.002 rad/ns.  opt:
- * solver and checkpoint interval as for msqoc_create_problem (col_block is ignored).
- * Allocates and frees temporary problems; synchronizes the device. */
+/* Sweep kernel family and tile width by measurement (not an operation of the paper): for every
+ * admissible (family, columns per tile) pair, a problem of the same description, step size and
+ * window count but only probe_steps steps per window is created with it and its objective +
+ * gradient is timed (one warm-up, two timed evaluations, CUDA events on the default stream).
+ * *col_block and *layout (may be NULL) receive the fastest pair (use them as
+ * msqoc_options.col_block and .layout); widths[i], layouts[i], ms[i] (i < *n_out <= max_out;
+ * may be NULL) the pairs tried and their milliseconds per evaluation.  alpha: d control
+ * coefficients (host) of a typical iterate (the iteration counts of the step solver depend on
+ * the control amplitude); NULL = alternating +-2 pi 0.002 rad/ns.  opt: solver, checkpoint
+ * interval and layout as for msqoc_create_problem (layout AUTO tries both families; col_block
+ * is ignored).  Allocates and frees temporary problems; synchronizes the device. */
 msqoc_status msqoc_autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, double T,
                             int64_t nsteps, int32_t nwindows, double mu, const msqoc_options* opt,
                             const double* alpha, int32_t probe_steps, int32_t* col_block,
-                            int32_t* widths, float* ms, int32_t max_out, int32_t* n_out);
+                            int32_t* layout, int32_t* widths, int32_t* layouts, float* ms,
+                            int32_t max_out, int32_t* n_out);
 
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t msqoc_version(void);

@@ -930,9 +930,11 @@ namespace {
 
 msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps, int32_t nwindows,
                       double mu, const msqoc_options* opt, const double* alpha, int32_t probe_steps,
-                      int32_t* col_block, int32_t* widths, float* ms, int32_t max_out, int32_t* n_out) {
+                      int32_t* col_block, int32_t* layout, int32_t* widths, int32_t* layouts, float* ms,
+                      int32_t max_out, int32_t* n_out) {
     if (!col_block) return fail(MSQOC_ERR_INVALID_ARG, "col_block is NULL");
     *col_block = 0;
+    if (layout) *layout = 0;
     if (n_out) *n_out = 0;
     msqoc_status st = check_description(H, C, T, nsteps, nwindows);
     if (st != MSQOC_OK) return st;
@@ -974,10 +976,15 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
     double* o_gW = o_ga + ((pd.d + 1) & ~1);
     float best_ms = 0.f;
     int best = 0, nrec = 0;
+    int best_layout = 0;
+    const int fam_lo = o.layout == MSQOC_LAYOUT_PAIR ? MSQOC_LAYOUT_PAIR : MSQOC_LAYOUT_FIBER;
+    const int fam_hi = o.layout == MSQOC_LAYOUT_FIBER ? MSQOC_LAYOUT_FIBER : MSQOC_LAYOUT_PAIR;
+    for (int fam = fam_lo; fam <= fam_hi && st == MSQOC_OK; ++fam)
     for (int cb = std::min(pd.E, MAX_TILE_THREADS / pd.F); cb >= 1 && st == MSQOC_OK; --cb) {
-        if (choose_tile_layout(pd.M, pd.E, pd.F, pd.q, pd.L, pd.N, pd.d, solver, 1, cb, o.layout).cpt < 0) continue;
+        if (choose_tile_layout(pd.M, pd.E, pd.F, pd.q, pd.L, pd.N, pd.d, solver, 1, cb, fam).cpt < 0) continue;
         msqoc_options oc = o;
         oc.col_block = cb;
+        oc.layout = fam;
         msqoc_problem* p = nullptr;
         msqoc_status cs = msqoc_create_problem(H, C, nullptr, pT, psteps, nwindows, mu, &oc, &p);
         if (cs != MSQOC_OK) {
@@ -1005,10 +1012,12 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
         if (widths && ms && nrec < max_out) {
             widths[nrec] = cb;
             ms[nrec] = t;
+            if (layouts) layouts[nrec] = fam;
         }
         ++nrec;
         if (best == 0 || t < best_ms) {
             best = cb;
+            best_layout = fam;
             best_ms = t;
         }
     }
@@ -1019,6 +1028,7 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
     if (st != MSQOC_OK) return st;
     if (best == 0) return fail(MSQOC_ERR_UNSUPPORTED, "no admissible tile width");
     *col_block = best;
+    if (layout) *layout = best_layout;
     if (n_out) *n_out = std::min(nrec, max_out);
     return MSQOC_OK;
 }
@@ -1027,10 +1037,11 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
 
 extern "C" msqoc_status msqoc_autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps,
                                        int32_t nwindows, double mu, const msqoc_options* opt, const double* alpha,
-                                       int32_t probe_steps, int32_t* col_block, int32_t* widths, float* ms,
-                                       int32_t max_out, int32_t* n_out) {
+                                       int32_t probe_steps, int32_t* col_block, int32_t* layout, int32_t* widths,
+                                       int32_t* layouts, float* ms, int32_t max_out, int32_t* n_out) {
     return guarded([&] {
-        return autotune(H, C, T, nsteps, nwindows, mu, opt, alpha, probe_steps, col_block, widths, ms, max_out, n_out);
+        return autotune(H, C, T, nsteps, nwindows, mu, opt, alpha, probe_steps, col_block, layout, widths, layouts, ms,
+                        max_out, n_out);
     });
 }
 

@@ -100,8 +100,8 @@ def load(build_if_missing: bool = True):
             "msqoc_lbfgs_direction": (i32, [i64, i64, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp]),
             "msqoc_lbfgs_trial": (i32, [i64, i64, vp, vp, ctypes.c_double, vp, vp, vp, vp, vp]),
             "msqoc_lbfgs_update": (i32, [i64, vp, vp, vp, vp, vp, vp, vp, vp]),
-            "msqoc_autotune": (i32, [vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, vp, vp, i32, vp, vp, vp,
-                                     i32, vp]),
+            "msqoc_autotune": (i32, [vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, vp, vp, i32, vp, vp, vp, vp,
+                                     vp, i32, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -408,18 +408,21 @@ def lbfgs_update(n, x, x_new, g, g_new, s_out, y_out, sy_yy_out, stream=None):
                                      _ptr(sy_yy_out), _stream_handle(stream)))
 
 
-def autotune(spec, alpha=None, probe_steps: int = 64, solver: int = SOLVER_DEFAULT, ckpt_interval: int = 0):
-    """Columns per sweep tile by measurement (msqoc_autotune): returns (best width,
-    {width: ms per probe evaluation})."""
+def autotune(spec, alpha=None, probe_steps: int = 64, solver: int = SOLVER_DEFAULT, ckpt_interval: int = 0,
+             layout: int = LAYOUT_AUTO):
+    """Kernel family and columns per sweep tile by measurement (msqoc_autotune): returns
+    (best width, best layout, {(layout, width): ms per probe evaluation})."""
     lib = load()
     desc = _Description(spec)
-    O = Options(solver, 0, ckpt_interval, 0)
+    O = Options(solver, 0, ckpt_interval, 0, layout)
     a = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float64)
-    best = ctypes.c_int32()
-    widths = (ctypes.c_int32 * 64)()
-    ms = (ctypes.c_float * 64)()
+    best, best_layout = ctypes.c_int32(), ctypes.c_int32()
+    widths = (ctypes.c_int32 * 128)()
+    layouts = (ctypes.c_int32 * 128)()
+    ms = (ctypes.c_float * 128)()
     n = ctypes.c_int32()
     _check(lib.msqoc_autotune(ctypes.byref(desc.H), ctypes.byref(desc.C), float(spec.T), int(spec.nsteps),
                               int(spec.M), float(spec.mu), ctypes.byref(O), None if a is None else a.ctypes.data,
-                              int(probe_steps), ctypes.byref(best), widths, ms, 64, ctypes.byref(n)))
-    return best.value, {int(widths[i]): float(ms[i]) for i in range(n.value)}
+                              int(probe_steps), ctypes.byref(best), ctypes.byref(best_layout), widths, layouts, ms, 128,
+                              ctypes.byref(n)))
+    return best.value, best_layout.value, {(int(layouts[i]), int(widths[i])): float(ms[i]) for i in range(n.value)}

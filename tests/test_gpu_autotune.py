@@ -1,5 +1,5 @@
-"""The tile-width autotuner: it times every admissible width on a probe of the problem and
-returns one of them; a problem built with the returned width evaluates correctly."""
+"""The autotuner: it times every admissible (kernel family, tile width) pair on a probe of the
+problem and returns one of them; a problem built with the returned pair evaluates correctly."""
 import pytest
 
 import oracle
@@ -14,11 +14,14 @@ pytestmark = pytest.mark.gpu
 def test_autotune_returns_a_measured_admissible_width():
     spec = S.transmon_spec(3, 30.0, 2001, 7, 8)
     alpha, W = S.random_alpha(spec, 61), S.random_W(spec, 61)
-    best, times = msqoc.autotune(spec, alpha=alpha, probe_steps=16)
-    assert best in times and len(times) >= 3
+    best, layout, times = msqoc.autotune(spec, alpha=alpha, probe_steps=16)
+    assert (layout, best) in times and len(times) >= 6
+    assert {lay for lay, _ in times} == {msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR}   # both families tried
     assert all(t > 0 for t in times.values())
-    assert times[best] == min(times.values())
-    with msqoc.Problem(spec, col_block=best) as p:
+    assert times[(layout, best)] == min(times.values())
+    _, lay1, times1 = msqoc.autotune(spec, alpha=alpha, probe_steps=16, layout=msqoc.LAYOUT_FIBER)
+    assert lay1 == msqoc.LAYOUT_FIBER and {lay for lay, _ in times1} == {msqoc.LAYOUT_FIBER}
+    with msqoc.Problem(spec, col_block=best, layout=layout) as p:
         got = p.eval_gradient(alpha, W)
     want = oracle.evaluate(spec, alpha, W)
     assert_objective_close(got["P"], want["P"])
