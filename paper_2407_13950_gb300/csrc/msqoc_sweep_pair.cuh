@@ -382,8 +382,12 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
             cnt_next = pd.spl[n].cnt;
         }
     };
-    // gradient entries of a step: (carrier, spline of the 3 active) pairs, one per lane
+    // gradient entries of a step: (carrier, spline of the 3 active) pairs, one per lane; the
+    // carrier, spline offset and subsystem of this lane's first entry are fixed for the launch
     const int nscat = pd.nfsum * 3;
+    const int f_kf = lane / 3, f_jw = lane % 3;
+    int f_k = 0;
+    while (f_k + 1 < Q && pd.cof[f_k + 1] <= f_kf) ++f_k;
     // warps whose lanes belong to both slots reduce each slot separately
     const unsigned mask1 = __ballot_sync(0xffffffffu, act && slot == 1);
     const unsigned mask0 = __ballot_sync(0xffffffffu, act && slot == 0);
@@ -404,9 +408,13 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
         const int s0 = sp.s;
         double* ga = galpha + size_t(s) * a.dmax;
         for (int i = lane; i < nscat; i += 32) {
-            const int kf = i / 3, jw = i % 3;
-            int k = 0;
-            while (k + 1 < Q && pd.cof[k + 1] <= kf) ++k;
+            int kf = f_kf, jw = f_jw, k = f_k;   // this lane's first entry, precomputed
+            if (i != lane) {
+                kf = i / 3;
+                jw = i % 3;
+                k = 0;
+                while (k + 1 < Q && pd.cof[k + 1] <= kf) ++k;
+            }
             const double* zyk = zy + (pp * 2 + s) * 4 * Q + 4 * k;
             const double2 zk = make_double2(zyk[0], zyk[1]);
             const double2 yk = make_double2(zyk[2], zyk[3]);
