@@ -119,13 +119,13 @@ struct Fiber {
     bool plus1[NA];    // entry 1 is the a_k (lowering, "+") term
     double w1[NA];     // product weight sqrt(level factor) of entry 1
     double w2[NA];
-    // dipole exchange of a 2-level (qubit) problem with at most MAXEXF coupled pairs: the
-    // source of pair e's term (entry index in a [cb][N] buffer, -1: the pair gives this fiber no
-    // term) and its target (a level of the fiber, or -1: every entry from the source fiber)
-    int exs[MAXEXF];
-    int ext[MAXEXF];
+    // dipole exchange of a 2-level (qubit) problem with at most MAXEXF coupled pairs: the source
+    // of pair e's term for entry l (an entry index in a [cb][N] buffer, or the buffer's zero
+    // entry when the pair gives that entry no term), so the apply is the same for every lane
+    int exs[MAXEXF][L];
 
-    __device__ void init(int c, int f, const ProbDev& pd) {
+    // c: tile column, f: fiber, zero: index of the shared buffers' zero entry
+    __device__ void init(int c, int f, const ProbDev& pd, int zero) {
         constexpr int N = ipow_c(L, Q);
         this->f = f;
         xo = c * N + f * L;
@@ -153,7 +153,7 @@ struct Fiber {
                 w2[k] = 0.0;
             }
         }
-        if constexpr (L == 2 && Q >= 2) init_exchange(pd);
+        if constexpr (L == 2 && Q >= 2) init_exchange(pd, zero);
     }
 
     // For 2 levels every weight of the exchange terms is 1 and a coupled pair (j, k) gives the
@@ -162,11 +162,11 @@ struct Fiber {
     // l_j - 1 (a_k a_j^+, when l_j = 1).  k not the last: every entry takes the same level of
     // the fiber with (l_j + 1, l_k - 1) when (l_j, l_k) = (0, 1), or (l_j - 1, l_k + 1) when
     // (1, 0).  Computed once per launch instead of in every apply.
-    __device__ void init_exchange(const ProbDev& pd) {
+    __device__ void init_exchange(const ProbDev& pd, int zero) {
 #pragma unroll
         for (int e = 0; e < MAXEXF; ++e) {
-            exs[e] = -1;
-            ext[e] = -1;
+#pragma unroll
+            for (int l = 0; l < L; ++l) exs[e][l] = zero;
             if (e < pd.nex) {
                 const int j = pd.ex_j[e], k = pd.ex_k[e];
                 int sfj = 1, sfk = 1;                          // fiber strides (j is never the last)
@@ -174,12 +174,17 @@ struct Fiber {
                 for (int t = k; t < Q - 2; ++t) sfk *= 2;
                 const int lj = (f / sfj) % 2;
                 if (k == Q - 1) {
-                    exs[e] = lj == 0 ? xo + sfj * 2 : xo - sfj * 2 + 1;
-                    ext[e] = lj == 0 ? 1 : 0;
+                    if (lj == 0)
+                        exs[e][1] = xo + sfj * 2;
+                    else
+                        exs[e][0] = xo - sfj * 2 + 1;
                 } else {
                     const int lk = (f / sfk) % 2;
-                    if (lk == 1 && lj == 0) exs[e] = xo + (sfj - sfk) * 2;
-                    if (lk == 0 && lj == 1) exs[e] = xo + (sfk - sfj) * 2;
+#pragma unroll
+                    for (int l = 0; l < L; ++l) {
+                        if (lk == 1 && lj == 0) exs[e][l] = xo + (sfj - sfk) * 2 + l;
+                        if (lk == 0 && lj == 1) exs[e][l] = xo + (sfk - sfj) * 2 + l;
+                    }
                 }
             }
         }
@@ -204,7 +209,9 @@ __host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cpt, 
     const int ncoef = pair ? 2 : 1;
     int V = 1;
     while (V < 4 * q) V <<= 1;
-    const size_t buf_d = size_t(cpt) * N * 16, buf_f = size_t(cpt) * N * 8;
+    // apply buffers hold cpt N entries plus a zero entry (index cpt N, never written by the
+    // sweeps: the source of the exchange terms an entry does not have)
+    const size_t buf_d = (size_t(cpt) * N + 1) * 16, buf_f = (size_t(cpt) * N + 1) * 8;
     size_t o = 0;
     s.coef_d = o; o = align16(o + size_t(2) * 2 * ncoef * nslot * 16);  // [parity][slot][part][NSLOT]
     s.coef_f = o; o = align16(o + size_t(2) * 2 * ncoef * nslot * 8);

@@ -128,13 +128,10 @@ __device__ __forceinline__ void apply_off_pair(const T2* __restrict__ buf, const
         } else if (pd.nex) {
 #pragma unroll
             for (int e = 0; e < MAXEXF; ++e) {
-                if (fb.exs[e] < 0) continue;
+                if (e >= pd.nex) break;                        // warp-uniform
                 const R c = static_cast<R>(p ? pd.ex_c[e] : -pd.ex_c[e]);
 #pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    if (fb.ext[e] >= 0 && fb.ext[e] != l) continue;
-                    w[l] += c * bb[2 * (fb.exs[e] + (fb.ext[e] < 0 ? l : 0))];
-                }
+                for (int l = 0; l < L; ++l) w[l] += c * bb[2 * fb.exs[e][l]];   // zero entry where no term
             }
         }
     }
@@ -290,7 +287,18 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
     const size_t wcol = (size_t(m - 1) * E + col) * N;   // (window, column) in [M][E][N] arrays
 
     Fiber<L, Q> fb;
-    fb.init(c, f, pd);
+    fb.init(c, f, pd, a.cpt * N);
+    // the apply buffers' zero entry (read by the exchange terms a fiber entry does not have; the
+    // first barrier of the time loop orders these stores before any read)
+    if (tid == 0) {
+        const size_t z = size_t(a.cpt) * N;
+        D0[z] = make_double2(0.0, 0.0);
+        if (SOLVER == SOLVER_FP64) D1[z] = make_double2(0.0, 0.0);
+        if (SOLVER == SOLVER_MIXED) {
+            FA[z] = make_float2(0.f, 0.f);
+            FB[z] = make_float2(0.f, 0.f);
+        }
+    }
 
     // preconditioner on the fiber (P forward, conj(P) adjoint) as this part's pairs, times the
     // sign S of the off-diagonal term: (S P w)_p = SP.x w_p + SP.y w_{1-p}
