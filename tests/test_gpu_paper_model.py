@@ -18,11 +18,12 @@ pytestmark = pytest.mark.gpu
 SOLVERS = {"mixed": msqoc.SOLVER_MIXED, "fp64": msqoc.SOLVER_FP64}
 
 
-def check(spec, seed, solver=msqoc.SOLVER_DEFAULT, ckpt_interval=0):
+def check(spec, seed, solver=msqoc.SOLVER_DEFAULT, ckpt_interval=0, col_block=0):
     alpha, W = S.random_alpha(spec, seed), S.random_W(spec, seed)
     want = oracle.evaluate(spec, alpha, W, nthreads=os.cpu_count())
     for layout in (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR):     # both sweep kernel families
-        with msqoc.Problem(spec, solver=solver, ckpt_interval=ckpt_interval, layout=layout) as p:
+        with msqoc.Problem(spec, solver=solver, ckpt_interval=ckpt_interval, layout=layout,
+                           col_block=col_block) as p:
             got = p.eval_gradient(alpha, W)
             obj = p.eval_objective(alpha, W)
         assert_objective_close(got["P"], want["P"])
@@ -47,6 +48,12 @@ def test_qft8_ragged_windows_and_checkpoints():
 @pytest.mark.parametrize("solver", list(SOLVERS))
 def test_qft16_short(solver):
     check(S.paper_qft_spec(4, M=4, nsteps=2000), 83, solver=SOLVERS[solver])
+
+
+def test_qft16_tiles_over_two_windows():
+    """5-column tiles (E = 16): 40 threads (one thread per fiber) or 80 (lane pairs), tiles that
+    cover the end of one window and the start of the next, with exchange coupling."""
+    check(S.paper_qft_spec(4, M=5, nsteps=1001), 87, col_block=5)
 
 
 @pytest.mark.parametrize("q", [4, 5])

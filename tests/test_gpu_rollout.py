@@ -14,12 +14,13 @@ from gpu_helpers import assert_objective_close
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("layout", [msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR])
 @pytest.mark.parametrize("solver", [msqoc.SOLVER_MIXED, msqoc.SOLVER_FP64])
-def test_rollout_matches_oracle_and_zeroes_the_penalties(solver):
+def test_rollout_matches_oracle_and_zeroes_the_penalties(solver, layout):
     spec = S.transmon_spec(3, 30.0, 2001, 7, 8)            # ragged windows
     alpha = S.random_alpha(spec, 71)
     want = oracle.rollout(spec, alpha)
-    with msqoc.Problem(spec, solver=solver, col_block=5) as p:
+    with msqoc.Problem(spec, solver=solver, col_block=5, layout=layout) as p:
         W = p.rollout(alpha)
         np.testing.assert_allclose(W, want, rtol=0, atol=1e-12)
         obj = p.eval_objective(alpha, W)
