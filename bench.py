@@ -100,7 +100,7 @@ class ClockSampler:
 SWEEP_SOURCES = ["msqoc_sweep.cuh", "msqoc_sweep_pair.cuh", "msqoc_sweep_common.cuh", "inst_sweep.cu",
                  "msqoc_internal.h"]
 PROFILE = os.path.join(ROOT, "profiles", "k_sweep_4q_small_full.md")
-LAYOUTS = {"auto": 0, "fiber": 1, "pair": 2}
+LAYOUTS = {"auto": 0, "fiber": 1, "pair": 2, "quad": 3}
 
 
 def sweep_traffic(kernel: str):
@@ -278,7 +278,7 @@ def run_ours(args, spec):
         "config": {"workload": spec.name, "N": spec.N, "E": spec.E, "nsteps": spec.nsteps, "windows": spec.M,
                    "T_ns": spec.T, "d": spec.d, "solver": args.solver,
                    "col_block": col_block if col_block > 0 else f"model ({prob.col_block})",
-                   "layout": {1: "one thread per fiber", 2: "lane pair per fiber"}[prob.layout],
+                   "layout": {1: "one thread per fiber", 2: "lane pair per fiber", 3: "lane quad per fiber"}[prob.layout],
                    **({"autotune": {"best": tuned, "ms_per_probe_eval": tune_ms}} if tuned else {}),
                    "l2": "inputs larger than L2 (2 GB midpoint history per evaluation)",
                    "parallelism": f"independent problem per GPU x{world}"},
@@ -435,8 +435,9 @@ def run_paper(args):
     cases = ((2, (1, 16)), (3, (1, 128)), (4, (1, 256)))
     if args.qft:
         cases = tuple(c for c in cases if 2 ** c[0] == args.qft)
+    fam_names = {1: "fiber", 2: "pair", 3: "quad"}
     for q, Ms in cases:
-        row = {}
+        row, tiles = {}, {}
         for M in Ms:
             spec = S.paper_qft_spec(q, M=M)
             alpha, W = S.random_alpha(spec, 1), S.random_W(spec, 1)
@@ -445,7 +446,8 @@ def run_paper(args):
             P_d = torch.zeros(1, device=dev, dtype=torch.float64)
             ga_d = torch.zeros(spec.d, device=dev, dtype=torch.float64)
             gW_d = torch.zeros(max(spec.nW, 2), device=dev, dtype=torch.float64)
-            with msqoc.Problem(spec) as p:
+            with msqoc.Problem(spec, layout=LAYOUTS[args.layout]) as p:
+                tiles[M] = f"{fam_names[p.layout]} x {p.col_block} columns"
                 def step():
                     p.eval_gradient_into(a_d, W_d if M > 1 else None, P_d, ga_d, gW_d if M > 1 else None,
                                          stream=stream)
@@ -463,6 +465,7 @@ def run_paper(args):
         Mbig = Ms[-1]
         out[f"QFT-{2 ** q}"] = {"n_steps": S.PAPER_NSTEPS[q], "ms_per_eval": {str(k): v for k, v in row.items()},
                                 "evals_per_s": {str(k): 1e3 / v for k, v in row.items()},
+                                "tiles": {str(k): v for k, v in tiles.items()},
                                 f"speedup_M{Mbig}_over_M1": row[1] / row[Mbig]}
     head = list(out)[-1]                       # QFT-16 unless --qft selects another case
     q16 = out[head]
@@ -626,7 +629,8 @@ def main():
                     help="columns per sweep tile: 0 = the library's model, -1 = measured by the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--layout", choices=list(LAYOUTS), default="auto",
-                    help="sweep kernel family: one thread or a lane pair per fiber (auto: the library's model)")
+                    help="sweep kernel family: one thread, a lane pair or (2-level subsystems) a lane quad per fiber "
+                         "(auto: the library's model)")
     ap.add_argument("--nsteps", type=int, default=0,
                     help="shorter time grid with the same step size (small profiling case); 0 = 100000 steps")
     ap.add_argument("--workload", choices=["4q", "batched", "serving", "paper", "optimize"], default="4q",

@@ -100,8 +100,9 @@ typedef struct msqoc_options {
     int32_t solver;        /* MSQOC_SOLVER_* */
     int32_t col_block;     /* columns per sweep tile (1 <= col_block <= E; col_block N/L <= 256
                               threads with one thread per fiber, 2 col_block N/L <= 384 with
-                              lane pairs; tiles run along the window-major column list and may
-                              cover two windows; a one-warp tile must divide E); 0 = automatic */
+                              lane pairs, 4 col_block N/L <= 512 with lane quads; tiles run
+                              along the window-major column list and may cover two windows; a
+                              one-warp tile must divide E); 0 = automatic */
     int32_t ckpt_interval; /* K: forward states kept for the adjoint sweep.  1 = every midpoint
                               state (history of nsteps * E * N complex); K > 1 = the state every
                               K steps of each window, each K-step segment recomputed before its
@@ -117,11 +118,14 @@ typedef struct msqoc_options {
  * subsystem), the choice for problems whose tiles fill the GPU.  PAIR: a lane pair per fiber,
  * one thread computing the real and one the imaginary component of every complex result: half
  * the FP64 instructions per thread, so steps run faster when the tiles are too few to fill the
- * GPU (small problems, the paper's QFT cases).  AUTO: chosen with the column block by the
- * library's makespan model. */
+ * GPU (small problems, the paper's QFT cases).  QUAD: 2-level subsystems only (and at most 6
+ * exchange-coupled pairs): a lane pair per entry of the fiber, four threads per fiber, a
+ * quarter of its work per thread.  AUTO: chosen with the column block by the library's
+ * makespan model.  A family the problem does not admit is rejected (MSQOC_ERR_INVALID_ARG). */
 #define MSQOC_LAYOUT_AUTO 0
 #define MSQOC_LAYOUT_FIBER 1
 #define MSQOC_LAYOUT_PAIR 2
+#define MSQOC_LAYOUT_QUAD 3
 
 /* Kernels of one evaluation, in launch order, as indexed by msqoc_kernel_times. */
 #define MSQOC_KERNEL_CONTROLS 0  /* control evaluation at the step midpoints */
@@ -150,8 +154,8 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
 msqoc_status msqoc_query(const msqoc_problem* p, int64_t* d, int64_t* nW, size_t* device_bytes);
 
 /* Sweep layout of a problem: columns per tile, tiles (CTAs) per sweep launch, threads per
- * tile, the checkpoint interval K and the kernel family (MSQOC_LAYOUT_FIBER or
- * MSQOC_LAYOUT_PAIR) in use (after automatic choices).  Any pointer may be NULL. */
+ * tile, the checkpoint interval K and the kernel family (MSQOC_LAYOUT_FIBER, MSQOC_LAYOUT_PAIR
+ * or MSQOC_LAYOUT_QUAD) in use (after automatic choices).  Any pointer may be NULL. */
 msqoc_status msqoc_query_layout(const msqoc_problem* p, int32_t* col_block, int32_t* tiles,
                                 int32_t* threads, int32_t* ckpt_interval, int32_t* layout);
 
@@ -346,8 +350,9 @@ msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H, const msqo
  * may be NULL) the pairs tried and their milliseconds per evaluation.  alpha: d control
  * coefficients (host) of a typical iterate (the iteration counts of the step solver depend on
  * the control amplitude); NULL = alternating +-2 pi 0.002 rad/ns.  opt: solver, checkpoint
- * interval and layout as for msqoc_create_problem (layout AUTO tries both families; col_block
- * is ignored).  Allocates and frees temporary problems; synchronizes the device. */
+ * interval and layout as for msqoc_create_problem (layout AUTO tries every family the problem
+ * admits; col_block is ignored).  Allocates and frees temporary problems; synchronizes the
+ * device. */
 msqoc_status msqoc_autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, double T,
                             int64_t nsteps, int32_t nwindows, double mu, const msqoc_options* opt,
                             const double* alpha, int32_t probe_steps, int32_t* col_block,

@@ -1,6 +1,7 @@
-// Explicit instantiation of the sweep kernels (both families: one thread per fiber and a lane
-// pair per fiber) for one (levels, subsystems) shape, selected with -DMSQOC_L=<levels>
-// -DMSQOC_Q=<subsystems>; this file is compiled once per supported shape.
+// Explicit instantiation of the sweep kernels (the families: one thread per fiber, a lane pair
+// per fiber and, for 2-level shapes, a lane quad per fiber) for one (levels, subsystems) shape,
+// selected with -DMSQOC_L=<levels> -DMSQOC_Q=<subsystems>; this file is compiled once per
+// supported shape.
 #include "msqoc_sweep.cuh"
 #include "msqoc_sweep_pair.cuh"
 
@@ -16,17 +17,20 @@
 
 namespace msqoc {
 
-template <int SOLVER, bool BWD, bool ROLLOUT, bool PAIR>
+// FAM: log2 of the threads per fiber (0: k_sweep; 1, 2: k_sweep_pair with one or two entry groups)
+template <int SOLVER, bool BWD, bool ROLLOUT, int FAM>
 static auto kernel_of() {
-    if constexpr (PAIR)
-        return k_sweep_pair<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT>;
+    if constexpr (FAM == 2)
+        return k_sweep_pair<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT, 2>;
+    else if constexpr (FAM == 1)
+        return k_sweep_pair<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT, 1>;
     else
         return k_sweep<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT>;
 }
 
-template <int SOLVER, bool BWD, bool ROLLOUT, bool PAIR>
+template <int SOLVER, bool BWD, bool ROLLOUT, int FAM>
 static cudaError_t launch_one(const SweepArgs& a, int ntiles, cudaStream_t s) {
-    auto kern = kernel_of<SOLVER, BWD, ROLLOUT, PAIR>();
+    auto kern = kernel_of<SOLVER, BWD, ROLLOUT, FAM>();
     const size_t smem = sweep_smem_bytes(a);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -37,9 +41,9 @@ static cudaError_t launch_one(const SweepArgs& a, int ntiles, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int SOLVER, bool BWD, bool PAIR>
+template <int SOLVER, bool BWD, int FAM>
 static int occupancy_one(const SweepArgs& a) {
-    auto kern = kernel_of<SOLVER, BWD, false, PAIR>();
+    auto kern = kernel_of<SOLVER, BWD, false, FAM>();
     const size_t smem = sweep_smem_bytes(a);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
@@ -49,33 +53,43 @@ static int occupancy_one(const SweepArgs& a) {
     return n;
 }
 
-template <bool PAIR>
+template <int FAM>
 static cudaError_t launch_family(const SweepArgs& a, int ntiles, cudaStream_t s) {
     if (a.mode == SWEEP_ROLLOUT)
-        return a.solver == SOLVER_FP64 ? launch_one<SOLVER_FP64, false, true, PAIR>(a, ntiles, s)
-                                       : launch_one<SOLVER_MIXED, false, true, PAIR>(a, ntiles, s);
+        return a.solver == SOLVER_FP64 ? launch_one<SOLVER_FP64, false, true, FAM>(a, ntiles, s)
+                                       : launch_one<SOLVER_MIXED, false, true, FAM>(a, ntiles, s);
     const bool bwd = a.mode == SWEEP_ADJOINT;
     if (a.solver == SOLVER_FP64)
-        return bwd ? launch_one<SOLVER_FP64, true, false, PAIR>(a, ntiles, s)
-                   : launch_one<SOLVER_FP64, false, false, PAIR>(a, ntiles, s);
-    return bwd ? launch_one<SOLVER_MIXED, true, false, PAIR>(a, ntiles, s)
-               : launch_one<SOLVER_MIXED, false, false, PAIR>(a, ntiles, s);
+        return bwd ? launch_one<SOLVER_FP64, true, false, FAM>(a, ntiles, s)
+                   : launch_one<SOLVER_FP64, false, false, FAM>(a, ntiles, s);
+    return bwd ? launch_one<SOLVER_MIXED, true, false, FAM>(a, ntiles, s)
+               : launch_one<SOLVER_MIXED, false, false, FAM>(a, ntiles, s);
 }
 
-template <bool PAIR>
+template <int FAM>
 static int occupancy_family(const SweepArgs& a) {
     const bool bwd = a.mode == SWEEP_ADJOINT;
     if (a.solver == SOLVER_FP64)
-        return bwd ? occupancy_one<SOLVER_FP64, true, PAIR>(a) : occupancy_one<SOLVER_FP64, false, PAIR>(a);
-    return bwd ? occupancy_one<SOLVER_MIXED, true, PAIR>(a) : occupancy_one<SOLVER_MIXED, false, PAIR>(a);
+        return bwd ? occupancy_one<SOLVER_FP64, true, FAM>(a) : occupancy_one<SOLVER_FP64, false, FAM>(a);
+    return bwd ? occupancy_one<SOLVER_MIXED, true, FAM>(a) : occupancy_one<SOLVER_MIXED, false, FAM>(a);
 }
 
 cudaError_t MSQOC_CAT(launch_sweep, MSQOC_L, MSQOC_Q)(const SweepArgs& a, int ntiles, cudaStream_t s) {
-    return a.pair ? launch_family<true>(a, ntiles, s) : launch_family<false>(a, ntiles, s);
+    if (a.pair == 0) return launch_family<0>(a, ntiles, s);
+    if (a.pair == 1) return launch_family<1>(a, ntiles, s);
+#if MSQOC_L == 2
+    if (a.pair == 2) return launch_family<2>(a, ntiles, s);
+#endif
+    return cudaErrorInvalidValue;
 }
 
 int MSQOC_CAT(sweep_occupancy, MSQOC_L, MSQOC_Q)(const SweepArgs& a) {
-    return a.pair ? occupancy_family<true>(a) : occupancy_family<false>(a);
+    if (a.pair == 0) return occupancy_family<0>(a);
+    if (a.pair == 1) return occupancy_family<1>(a);
+#if MSQOC_L == 2
+    if (a.pair == 2) return occupancy_family<2>(a);
+#endif
+    return 0;
 }
 
 }  // namespace msqoc

@@ -131,10 +131,10 @@ int gray_rank(int g) {
 // Threads of a tile with ncol columns, the first ncol0 of window m0: each window's
 // (column, fiber) pairs are ordered by the Gray rank of the fiber class, so that a warp spans
 // few classes (its branch cost is the union of its lanes' branches); window m0's pairs come
-// first so at most one warp has lanes of both windows.  Each (column, fiber) goes to one thread
-// or, for lane-pair tiles (pair = 1), to a lane pair (threads 2i and 2i + 1: the real and the
-// imaginary part).  Idle lanes mirror the last active entry.  Writes out[nthreads]; no
-// allocation.
+// first so at most one warp has lanes of both windows.  Each (column, fiber) goes to one thread,
+// to a lane pair for lane-pair tiles (pair = 1: threads 2i and 2i + 1, the real and the
+// imaginary part) or to a lane quad (pair = 2: threads 4i..4i + 3, a pair per entry).  Idle
+// lanes mirror the last active entry.  Writes out[nthreads]; no allocation.
 void build_lanemap(int L, int q, int ncol, int ncol0, int nthreads, int pair, int* out) {
     const int F = ipow_i(L, q) / L;
     int key[MAX_TILE_THREADS], val[MAX_TILE_THREADS];
@@ -156,7 +156,7 @@ void build_lanemap(int L, int q, int ncol, int ncol0, int nthreads, int pair, in
                 val[pos] = (c << 16) | f;
             }
     }
-    const int sh = pair ? 1 : 0;
+    const int sh = pair;
     for (int t = 0; t < nthreads; ++t) out[t] = (t >> sh) < n ? val[t >> sh] : ~val[n - 1];
 }
 
@@ -185,21 +185,26 @@ void build_lanemaps(int L, int q, int M, int E, int cpt, int nthreads, int pair,
     build_lanemap(L, q, last.ncol, last.ncol0, nthreads, pair, out + size_t(cpt) * nthreads);
 }
 
-// one thread, or a lane pair, per (column, fiber)
-int tile_threads(int cpt, int F, int pair) { return (((pair ? 2 : 1) * cpt * F + 31) / 32) * 32; }
-int max_tile_threads(int pair) { return pair ? MAX_PAIR_TILE_THREADS : MAX_TILE_THREADS; }
+// one thread, a lane pair or a lane quad (2^pair threads) per (column, fiber)
+int tile_threads(int cpt, int F, int pair) { return (((1 << pair) * cpt * F + 31) / 32) * 32; }
+int max_tile_threads(int pair) {
+    return pair == 2 ? MAX_QUAD_TILE_THREADS : pair ? MAX_PAIR_TILE_THREADS : MAX_TILE_THREADS;
+}
 
 // Is `cpt` columns per tile usable in the given kernel family?  Tiles must fit the family's
 // thread limit and the shared memory; a tile that covers two windows needs two warps (one per
 // window's coefficients), so a one-warp tile must divide the window's columns.
 bool tile_width_ok(int cpt, int E, int F, int q, int L, int N, int d, int solver, int pair) {
-    if (cpt < 1 || cpt > E || (pair ? 2 : 1) * cpt * F > max_tile_threads(pair)) return false;
+    if (cpt < 1 || cpt > E || (1 << pair) * cpt * F > max_tile_threads(pair)) return false;
     const int nthreads = tile_threads(cpt, F, pair);
     if (nthreads == 32 && E % cpt) return false;
     const size_t s1 = sweep_layout(q, L, N, cpt, nthreads, d, solver, true, pair).total;
     const size_t s0 = sweep_layout(q, L, N, cpt, nthreads, d, solver, false, pair).total;
     return std::max(s0, s1) <= 200 * 1024;
 }
+
+// Lane quads serve 2-level subsystems whose exchange-coupled pairs all have precomputed sources.
+bool quad_admitted(const ProbDev& pd) { return pd.L == 2 && pd.nex <= MAXEXF; }
 
 // Kernel family and columns per tile.  Makespan model, from FP64 throughput probes and sweep
 // timings on this GPU: a warp issues one FP64 instruction per 64 cycles on its SM sub-partition,
@@ -209,7 +214,10 @@ bool tile_width_ok(int cpt, int E, int F, int q, int L, int N, int d, int solver
 // w warps costs max(w c / 4, c0): c = c0 = 1 for that family; for lane pairs (half the FP64
 // instructions a thread, plus shuffles) c = 0.6 at full SM load and c0 = 0.7 alone (measured:
 // equal to the one-thread family on the 4-transmon tiles, 1.4x faster steps on small
-// problems).  Tiles that do not fit at once run in waves of the CTAs an SM holds (the kernels'
+// problems); for lane quads (2-level subsystems, a quarter of a fiber's work a thread)
+// c = 0.41 and c0 = 0.52 (measured on the paper's QFT cases: steps 1.33-1.38x faster than lane
+// pairs where the tiles are too few to fill the GPU; at full load a quad warp costs 0.41 of a
+// one-thread warp, from QFT-16 at 256 windows).  Tiles that do not fit at once run in waves of the CTAs an SM holds (the kernels'
 // occupancy at that width).  A tile over two windows pays a second gradient reduction and wider
 // class mixing in its warps: its cost is taken 1.18x (measured on the 4-transmon tiles: the
 // adjoint 9% slower, the forward 3% faster than 8-column one-window tiles, where the warp count
@@ -223,16 +231,20 @@ bool tile_width_ok(int cpt, int E, int F, int q, int L, int N, int d, int solver
 //      fewer threads meet at each barrier than in wider tiles, and the coefficient and gradient
 //      work of a tile is not serialised with the step as in one-warp tiles);
 //   4. the idle-lane fraction of a tile.
-// fixed_cpt > 0 restricts the width, layout (MSQOC_LAYOUT_*) the family.  cpt = -1: none fits.
+// fixed_cpt > 0 restricts the width, layout (MSQOC_LAYOUT_*) the family; quad_ok: the problem
+// admits lane quads.  cpt = -1: none fits.
+constexpr double QUAD_C = 0.41, QUAD_C0 = 0.52;
 TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int d, int solver, int sms, int fixed_cpt,
-                              int layout) {
+                              int layout, bool quad_ok) {
     TileChoice best{-1, 0};
     double best_a = 0.0, best_c = 0.0;
     int best_b = 0, best_w = 0;
-    for (int pair = 0; pair <= 1; ++pair) {
-        if ((layout == MSQOC_LAYOUT_FIBER && pair) || (layout == MSQOC_LAYOUT_PAIR && !pair)) continue;
-        const double c_load = pair ? 0.6 : 1.0, c_alone = pair ? 0.7 : 1.0;
-        const int hi = fixed_cpt > 0 ? fixed_cpt : std::min(E, max_tile_threads(pair) / ((pair ? 2 : 1) * F));
+    for (int pair = 0; pair <= 2; ++pair) {
+        if (layout != MSQOC_LAYOUT_AUTO && layout != MSQOC_LAYOUT_FIBER + pair) continue;
+        if (pair == 2 && !quad_ok) continue;
+        const double c_load = pair == 2 ? QUAD_C : pair ? 0.6 : 1.0;
+        const double c_alone = pair == 2 ? QUAD_C0 : pair ? 0.7 : 1.0;
+        const int hi = fixed_cpt > 0 ? fixed_cpt : std::min(E, max_tile_threads(pair) / ((1 << pair) * F));
         const int lo = fixed_cpt > 0 ? fixed_cpt : 1;
         for (int cpt = hi; cpt >= lo; --cpt) {
             if (!tile_width_ok(cpt, E, F, q, L, N, d, solver, pair)) continue;
@@ -259,7 +271,7 @@ TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int d, i
             const double ca = (cb ? 1.18 : 1.0) *
                               (double(waves - 1) * std::max(double(resident * warps) * c_load / 4.0, c_alone) +
                                std::max(double(last * warps) * c_load / 4.0, c_alone));
-            const double cc = 1.0 - double((pair ? 2 : 1) * cpt * F) / (32.0 * warps);
+            const double cc = 1.0 - double((1 << pair) * cpt * F) / (32.0 * warps);
             const bool at_floor = ca <= (cb ? 1.18 : 1.0) * double(waves) * c_alone + 1e-9;
             const int cw = !at_floor ? 0 : ((warps == 2 || warps == 3) ? 0 : (warps == 1 ? 1 : 2));
             const bool tie_a = ca < best_a + 1e-9, tie_b = cb == best_b, tie_w = cw == best_w;
@@ -356,15 +368,20 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
         pd.wsq[2 * l + 0] = std::sqrt(double(l + 1));
         pd.wsq[2 * l + 1] = std::sqrt(double(l));
     }
-    if (layout < MSQOC_LAYOUT_AUTO || layout > MSQOC_LAYOUT_PAIR)
+    if (layout < MSQOC_LAYOUT_AUTO || layout > MSQOC_LAYOUT_QUAD)
         return fail(MSQOC_ERR_INVALID_ARG, "layout %d is not an MSQOC_LAYOUT_* value", layout);
+    if (layout == MSQOC_LAYOUT_QUAD && !quad_admitted(pd))
+        return fail(MSQOC_ERR_INVALID_ARG, "lane quads need 2-level subsystems and at most %d exchange-coupled pairs",
+                    MAXEXF);
     if (col_block < 0) return fail(MSQOC_ERR_INVALID_ARG, "column block %d < 0", col_block);
-    const TileChoice tc = choose_tile_layout(pd.M, pd.E, pd.F, q, L, pd.N, pd.d, solver, sms, col_block, layout);
+    const TileChoice tc =
+        choose_tile_layout(pd.M, pd.E, pd.F, q, L, pd.N, pd.d, solver, sms, col_block, layout, quad_admitted(pd));
     if (tc.cpt < 0)
         return fail(MSQOC_ERR_INVALID_ARG,
                     "column block %d invalid for E=%d (needs 1 <= cb <= E, cb N/L <= %d threads with one thread "
-                    "per fiber or 2 cb N/L <= %d with lane pairs, cb | E for one-warp tiles, and the shared memory)",
-                    col_block, pd.E, MAX_TILE_THREADS, MAX_PAIR_TILE_THREADS);
+                    "per fiber, 2 cb N/L <= %d with lane pairs or 4 cb N/L <= %d with lane quads, cb | E for "
+                    "one-warp tiles, and the shared memory)",
+                    col_block, pd.E, MAX_TILE_THREADS, MAX_PAIR_TILE_THREADS, MAX_QUAD_TILE_THREADS);
     const int cpt = tc.cpt;
     pd.cb = cpt;
     pd.pair = tc.pair;
@@ -653,7 +670,7 @@ msqoc_status msqoc_query_layout(const msqoc_problem* p, int32_t* col_block, int3
     if (tiles) *tiles = p->pd.ntiles;
     if (threads) *threads = p->pd.nthreads;
     if (ckpt_interval) *ckpt_interval = p->ckpt_interval;
-    if (layout) *layout = p->pd.pair ? MSQOC_LAYOUT_PAIR : MSQOC_LAYOUT_FIBER;
+    if (layout) *layout = MSQOC_LAYOUT_FIBER + p->pd.pair;
     return MSQOC_OK;
 }
 
@@ -977,11 +994,13 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
     float best_ms = 0.f;
     int best = 0, nrec = 0;
     int best_layout = 0;
-    const int fam_lo = o.layout == MSQOC_LAYOUT_PAIR ? MSQOC_LAYOUT_PAIR : MSQOC_LAYOUT_FIBER;
-    const int fam_hi = o.layout == MSQOC_LAYOUT_FIBER ? MSQOC_LAYOUT_FIBER : MSQOC_LAYOUT_PAIR;
+    const int fam_lo = o.layout == MSQOC_LAYOUT_AUTO ? MSQOC_LAYOUT_FIBER : o.layout;
+    const int fam_hi = o.layout == MSQOC_LAYOUT_AUTO ? MSQOC_LAYOUT_QUAD : o.layout;
     for (int fam = fam_lo; fam <= fam_hi && st == MSQOC_OK; ++fam)
     for (int cb = std::min(pd.E, MAX_TILE_THREADS / pd.F); cb >= 1 && st == MSQOC_OK; --cb) {
-        if (choose_tile_layout(pd.M, pd.E, pd.F, pd.q, pd.L, pd.N, pd.d, solver, 1, cb, fam).cpt < 0) continue;
+        if (choose_tile_layout(pd.M, pd.E, pd.F, pd.q, pd.L, pd.N, pd.d, solver, 1, cb, fam, quad_admitted(pd)).cpt <
+            0)
+            continue;
         msqoc_options oc = o;
         oc.col_block = cb;
         oc.layout = fam;

@@ -12,6 +12,7 @@ constexpr int MAXNF = 64;     // carriers over all subsystems
 constexpr int MAXL = 4;       // levels per subsystem handled by the sweep kernels
 constexpr int MAX_TILE_THREADS = 256;       // threads of a one-thread-per-fiber tile (255 registers a thread)
 constexpr int MAX_PAIR_TILE_THREADS = 384;  // threads of a lane-pair tile (168 registers a thread)
+constexpr int MAX_QUAD_TILE_THREADS = 512;  // threads of a lane-quad tile (128 registers a thread)
 
 enum Solver { SOLVER_FP64 = 1, SOLVER_MIXED = 2 };
 
@@ -33,7 +34,9 @@ struct ProbDev {
     int q, L, N, E, F, ness, d1, M, nfsum, d;
     int cb;        // columns of a full tile
     int nthreads;  // threads per tile (multiple of 32)
-    int pair;      // 1: a lane pair per fiber (the real and the imaginary part), 0: one thread
+    int pair;      // kernel family: log2 of the threads per fiber (0: one thread, 1: a lane pair,
+                   // the real and the imaginary part; 2: a lane quad, a pair per entry of a
+                   // 2-level fiber)
     int ntiles;    // tiles of the problem's sweeps
     int solver;
     int kseg;      // steps per history segment (checkpoint interval; >= the longest window when
@@ -107,7 +110,7 @@ struct SweepArgs {
     int mode;             // SweepMode
     int seg;              // segment (SWEEP_RECOMPUTE, SWEEP_ADJOINT)
     int L, q, solver, nthreads;
-    int pair;             // kernel family: 1 = a lane pair per fiber, 0 = one thread per fiber
+    int pair;             // kernel family: log2 of the threads per fiber (0, 1 or 2)
     double2* out;         // SWEEP_ROLLOUT: [M-1][E][N] states at the window boundaries
 };
 

@@ -9,6 +9,12 @@
 // (the other component comes from the partner lane by a shuffle, or from shared memory).  The
 // cost is twice the threads and a lower register budget (384-thread tiles), so the one-thread
 // family stays the choice for problems that fill the GPU.
+//
+// The same kernel with SPLIT = 2 is the lane-quad family for 2-level subsystems: four threads
+// per fiber, a lane pair per entry of the fiber (lanes 4i + 2e and 4i + 2e + 1 own entry e).
+// Each thread then computes one component of one entry, half of a lane pair's work; the
+// entry the pair does not hold (the in-fiber ladder term) is read from the shared buffer like
+// any neighbour.  Tiles of up to 512 threads.
 #pragma once
 
 #include "msqoc_sweep_common.cuh"
@@ -92,58 +98,77 @@ __device__ __forceinline__ void apply_exchange_pair(const R* __restrict__ xb, co
 // the others from the shared buffer (entries interleaved re, im; both parts of the pair have
 // written theirs before the barrier).  xa: this part's components of the fiber (registers);
 // cf: this part's coefficient pairs of the step's slots, i(h/2)sqrt(.)d_k.
-template <int L, int Q, typename T2>
+//
+// SPLIT = 2 (lane quads, L = 2): the thread holds entry le of the fiber only (xa[0], w[0]); the
+// other entry of the in-fiber ladder term comes from the buffer, and exo[e] is the source of
+// exchange pair e for entry le (the problem has at most MAXEXF pairs: the host admits the
+// family only then).
+template <int L, int Q, typename T2, int SPLIT>
 __device__ __forceinline__ void apply_off_pair(const T2* __restrict__ buf, const T2* __restrict__ cf,
-                                          const Fiber<L, Q>& fb, const typename cx<T2>::T (&xa)[L],
-                                          typename cx<T2>::T (&w)[L], int p, const ProbDev& pd) {
+                                               const Fiber<L, Q>& fb, const typename cx<T2>::T (&xa)[L / SPLIT],
+                                               typename cx<T2>::T (&w)[L / SPLIT], int p, int le,
+                                               const int (&exo)[MAXEXF], const ProbDev& pd) {
     using R = typename cx<T2>::T;
+    constexpr int LS = L / SPLIT;
     const R* ba = reinterpret_cast<const R*>(buf) + p;        // component p of entry i: ba[2 i]
     const R* bb = reinterpret_cast<const R*>(buf) + (p ^ 1);  // component 1 - p
 #pragma unroll
-    for (int l = 0; l < L; ++l) w[l] = 0;
+    for (int l = 0; l < LS; ++l) w[l] = 0;
     constexpr int kl = Q - 1;
+    if constexpr (SPLIT == 1) {
 #pragma unroll
-    for (int l = 0; l < L; ++l) {
-        if (l < L - 1) w[l] = pmac(w[l], cf[(kl * L + l) * 2 + 0], xa[l + 1], bb[2 * (fb.xo + l + 1)]);
-        if (l > 0) w[l] = pmac(w[l], cf[(kl * L + l) * 2 + 1], xa[l - 1], bb[2 * (fb.xo + l - 1)]);
+        for (int l = 0; l < L; ++l) {
+            if (l < L - 1) w[l] = pmac(w[l], cf[(kl * L + l) * 2 + 0], xa[l + 1], bb[2 * (fb.xo + l + 1)]);
+            if (l > 0) w[l] = pmac(w[l], cf[(kl * L + l) * 2 + 1], xa[l - 1], bb[2 * (fb.xo + l - 1)]);
+        }
+    } else {
+        static_assert(SPLIT == 2 && L == 2, "lane quads are for 2-level subsystems");
+        // entry 0 takes entry 1 (slot (kl, 0, a_k)), entry 1 takes entry 0 (slot (kl, 1, a_k^+))
+        const int src = 2 * (fb.xo + 1 - le);
+        w[0] = pmac(w[0], cf[(kl * L + le) * 2 + le], ba[src], bb[src]);
     }
 #pragma unroll
     for (int k = 0; k < Fiber<L, Q>::NFIX; ++k) {
         const T2 c1 = cf[fb.sl1[k]];
-        const int o1 = 2 * fb.nb1[k];
+        const int o1 = 2 * (fb.nb1[k] + le);
 #pragma unroll
-        for (int l = 0; l < L; ++l) w[l] = pmac(w[l], c1, ba[o1 + 2 * l], bb[o1 + 2 * l]);
+        for (int l = 0; l < LS; ++l) w[l] = pmac(w[l], c1, ba[o1 + 2 * l], bb[o1 + 2 * l]);
         if (fb.two[k]) {
             const T2 c2 = cf[fb.sl2[k]];
-            const int o2 = 2 * fb.nb2[k];
+            const int o2 = 2 * (fb.nb2[k] + le);
 #pragma unroll
-            for (int l = 0; l < L; ++l) w[l] = pmac(w[l], c2, ba[o2 + 2 * l], bb[o2 + 2 * l]);
+            for (int l = 0; l < LS; ++l) w[l] = pmac(w[l], c2, ba[o2 + 2 * l], bb[o2 + 2 * l]);
         }
     }
     // exchange-coupled problems are 2-level qubit models (the only shapes compiled with it):
     // w += (i (h/2) J x_src)_p from the fiber's precomputed sources, or the general form
     if constexpr (L == 2 && Q >= 2) {
-        if (pd.nex > MAXEXF) {
-            apply_exchange_pair<L, Q, R>(bb, pd, fb.f, fb.xo, p, w);
+        if (SPLIT == 1 && pd.nex > MAXEXF) {
+            if constexpr (SPLIT == 1) apply_exchange_pair<L, Q, R>(bb, pd, fb.f, fb.xo, p, w);
         } else if (pd.nex) {
 #pragma unroll
             for (int e = 0; e < MAXEXF; ++e) {
                 if (e >= pd.nex) break;                        // warp-uniform
                 const R c = static_cast<R>(p ? pd.ex_c[e] : -pd.ex_c[e]);
+                if constexpr (SPLIT == 1) {
 #pragma unroll
-                for (int l = 0; l < L; ++l) w[l] += c * bb[2 * fb.exs[e][l]];   // zero entry where no term
+                    for (int l = 0; l < L; ++l) w[l] += c * bb[2 * fb.exs[e][l]];   // zero entry where no term
+                } else {
+                    w[0] += c * bb[2 * exo[e]];
+                }
             }
         }
     }
 }
 
-// this part's components of the fiber's entries into an interleaved (re, im) buffer
-template <int L, typename T2>
-__device__ __forceinline__ void store_part(T2* buf, int xo, int p, const typename cx<T2>::T (&v)[L]) {
+// this part's components of LS consecutive entries (from entry xo) into an interleaved (re, im)
+// buffer
+template <int LS, typename T2>
+__device__ __forceinline__ void store_part(T2* buf, int xo, int p, const typename cx<T2>::T (&v)[LS]) {
     using R = typename cx<T2>::T;
     R* b = reinterpret_cast<R*>(buf) + 2 * xo + p;
 #pragma unroll
-    for (int l = 0; l < L; ++l) b[2 * l] = v[l];
+    for (int l = 0; l < LS; ++l) b[2 * l] = v[l];
 }
 
 // ------------------------------------------------------------------ per-step coefficients
@@ -209,9 +234,12 @@ __device__ __forceinline__ double part_reduce_scatter(double (&acc)[VH], int lan
 // (the host only builds two-slot tiles with at least two warps).  Loops run to the longer of
 // the slots' ranges; a thread whose slot has no step at an iteration keeps its state.  Two
 // threads (a pair, parts 0 and 1) work on each (column, fiber).
-template <int L, int Q, int SOLVER, bool BWD, bool ROLLOUT = false>
-__global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const SweepArgs a) {
+template <int L, int Q, int SOLVER, bool BWD, bool ROLLOUT = false, int SPLIT = 1>
+__global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_TILE_THREADS, 1)
+    k_sweep_pair(const SweepArgs a) {
     static_assert(!(BWD && ROLLOUT), "the roll-out is a forward sweep");
+    static_assert(SPLIT == 1 || (SPLIT == 2 && L == 2), "lane quads are for 2-level subsystems");
+    constexpr int LS = L / SPLIT;          // entries of the fiber this thread holds
     constexpr int N = ipow_c(L, Q);
     constexpr int NSLOT = Q * L * 2;
     constexpr int S = BWD ? +1 : -1;       // sign of the preconditioned off-diagonal term
@@ -223,7 +251,7 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
     const ProbDev& pd = a.pds[tile.prob];
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const SweepSmem lay = sweep_layout(Q, L, N, a.cpt, blockDim.x, a.dmax, SOLVER, BWD, 1);
+    const SweepSmem lay = sweep_layout(Q, L, N, a.cpt, blockDim.x, a.dmax, SOLVER, BWD, SPLIT);
     double2* coef_d = reinterpret_cast<double2*>(smem + lay.coef_d);
     float2* coef_f = reinterpret_cast<float2*>(smem + lay.coef_f);
     int* params = reinterpret_cast<int*>(smem + lay.params);
@@ -244,6 +272,7 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
     const int warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
     const int part = tid & 1;              // component this thread computes (0: re, 1: im)
+    const int le = SPLIT > 1 ? ((tid >> 1) & (SPLIT - 1)) * LS : 0;   // first entry it holds
     const int E = pd.E;
     const int ncol = tile.ncol, ncol0 = tile.ncol0;
     const int nslot = ncol0 < ncol ? 2 : 1;
@@ -272,7 +301,7 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
         return BWD ? n0 + lo + cnt - 1 - jc : n0 + lo + jc;
     };
 
-    // ---- this thread's fiber (both threads of a pair read the same entry)
+    // ---- this thread's fiber (the threads of a pair, or quad, read the same entry)
     const int lm = a.lanemap[tile.map * static_cast<int>(blockDim.x) + tid];
     const bool act = lm >= 0;                       // idle pairs mirror an active one, store nothing
     const int lmv = act ? lm : ~lm;
@@ -288,6 +317,12 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
 
     Fiber<L, Q> fb;
     fb.init(c, f, pd, a.cpt * N);
+    // lane quads: the exchange sources of this thread's entry
+    int exo[MAXEXF] = {};
+    if constexpr (SPLIT > 1) {
+#pragma unroll
+        for (int e = 0; e < MAXEXF; ++e) exo[e] = le ? fb.exs[e][1] : fb.exs[e][0];
+    }
     // the apply buffers' zero entry (read by the exchange terms a fiber entry does not have; the
     // first barrier of the time loop orders these stores before any read)
     if (tid == 0) {
@@ -302,11 +337,11 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
 
     // preconditioner on the fiber (P forward, conj(P) adjoint) as this part's pairs, times the
     // sign S of the off-diagonal term: (S P w)_p = SP.x w_p + SP.y w_{1-p}
-    double2 Pp[L], SPp[L];
-    float2 SPf[L];
+    double2 Pp[LS], SPp[LS];
+    float2 SPf[LS];
 #pragma unroll
-    for (int l = 0; l < L; ++l) {
-        double2 pv = pd.P[f * L + l];
+    for (int l = 0; l < LS; ++l) {
+        double2 pv = pd.P[f * L + le + l];
         if (BWD) pv.y = -pv.y;
         Pp[l] = part_pair(pv, part);
         SPp[l] = make_double2(S * Pp[l].x, S * Pp[l].y);
@@ -318,10 +353,10 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
     //   forward, recompute    : the segment's checkpoint
     //   adjoint               : Lambda^m(t_m) for the window's last segment, else the state the
     //                           previous (later) segment left
-    double u[L];
+    double u[LS];
 #pragma unroll
-    for (int l = 0; l < L; ++l) {
-        const int i = f * L + l;
+    for (int l = 0; l < LS; ++l) {
+        const int i = f * L + le + l;
         if (my_cnt == 0) {
             u[l] = 0.0;
         } else if (BWD) {
@@ -336,9 +371,9 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
     }
     // this part's components of a [..][N] complex array at the fiber
     auto store_fiber = [&](double2* dst) {
-        double* d = reinterpret_cast<double*>(dst) + 2 * size_t(f) * L + part;
+        double* d = reinterpret_cast<double*>(dst) + 2 * (size_t(f) * L + le) + part;
 #pragma unroll
-        for (int l = 0; l < L; ++l) d[2 * l] = u[l];
+        for (int l = 0; l < LS; ++l) d[2 * l] = u[l];
     };
 
     // ---- history blocks: slot s of a tile covers a contiguous column range of its window
@@ -474,14 +509,14 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
         const int* prm1 = params + (par * 2 + 1) * 4;
 
         // right-hand side of the preconditioned step equation: b = P u (conj(P) for the adjoint)
-        double b[L];
+        double b[LS];
 #pragma unroll
-        for (int l = 0; l < L; ++l) {
+        for (int l = 0; l < LS; ++l) {
             const double uo = partner(u[l]);
             b[l] = fma(Pp[l].x, u[l], Pp[l].y * uo);
         }
 
-        double z[L];   // this part of the midpoint state being solved for (Ubar or Lbar)
+        double z[LS];   // this part of the midpoint state being solved for (Ubar or Lbar)
 
         // first barrier of the step: the coefficients are published; thread 0 stores the
         // previous iteration's midpoints (forward) or fetches the next iteration's (adjoint)
@@ -501,8 +536,8 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
             // Dc/Dn alternate on every write (persisting across steps): a buffer is never
             // rewritten before the sync that follows its last read.
 #pragma unroll
-            for (int l = 0; l < L; ++l) z[l] = b[l];
-            if (act) store_part<L, double2>(Dc, fb.xo, part, z);
+            for (int l = 0; l < LS; ++l) z[l] = b[l];
+            if (act) store_part<LS, double2>(Dc, fb.xo + le, part, z);
             tile_sync();
             first_sync_work();
             if (timed_out) break;
@@ -510,17 +545,17 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
             const int Kmax = nslot > 1 ? max(prm0[0], prm1[0]) : prm0[0];
             for (int it = 0; it < Kmax; ++it) {
                 if (it > 0) {
-                    if (act) store_part<L, double2>(Dc, fb.xo, part, z);
+                    if (act) store_part<LS, double2>(Dc, fb.xo + le, part, z);
                     tile_sync();
                 }
-                double w[L];
-                apply_off_pair<L, Q, double2>(Dc, cfd, fb, z, w, part, pd);
-                double wo[L];
+                double w[LS];
+                apply_off_pair<L, Q, double2, SPLIT>(Dc, cfd, fb, z, w, part, le, exo, pd);
+                double wo[LS];
 #pragma unroll
-                for (int l = 0; l < L; ++l) wo[l] = partner(w[l]);
+                for (int l = 0; l < LS; ++l) wo[l] = partner(w[l]);
                 if (it < Kown) {
 #pragma unroll
-                    for (int l = 0; l < L; ++l) z[l] = fma(SPp[l].x, w[l], fma(SPp[l].y, wo[l], b[l]));
+                    for (int l = 0; l < LS; ++l) z[l] = fma(SPp[l].x, w[l], fma(SPp[l].y, wo[l], b[l]));
                 }
                 double2* tmp = Dc;
                 Dc = Dn;
@@ -528,23 +563,23 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
             }
         } else {
             // ---- FP32 stage: d = Ubar - b from the preconditioned fixed point d = s P w(b + d)
-            float bf[L], df[L], y[L];
+            float bf[LS], df[LS], y[LS];
 #pragma unroll
-            for (int l = 0; l < L; ++l) {
+            for (int l = 0; l < LS; ++l) {
                 bf[l] = f32_of(b[l]);
                 y[l] = bf[l];
             }
             {
                 float2* Fb = fsel ? FB : FA;
                 fsel ^= 1;
-                if (act) store_part<L, float2>(Fb, fb.xo, part, y);
+                if (act) store_part<LS, float2>(Fb, fb.xo + le, part, y);
                 tile_sync();
                 first_sync_work();
                 if (timed_out) break;
-                float w[L];
-                apply_off_pair<L, Q, float2>(Fb, cff, fb, y, w, part, pd);
+                float w[LS];
+                apply_off_pair<L, Q, float2, SPLIT>(Fb, cff, fb, y, w, part, le, exo, pd);
 #pragma unroll
-                for (int l = 0; l < L; ++l) {
+                for (int l = 0; l < LS; ++l) {
                     const float wo = partner(w[l]);
                     df[l] = fmaf(SPf[l].x, w[l], SPf[l].y * wo);
                 }
@@ -555,40 +590,40 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
             const int Rmax = nslot > 1 ? max(prm0[2], prm1[2]) : prm0[2];
             for (int it = 1; it < j1max; ++it) {
 #pragma unroll
-                for (int l = 0; l < L; ++l) y[l] = bf[l] + df[l];
+                for (int l = 0; l < LS; ++l) y[l] = bf[l] + df[l];
                 float2* Fb = fsel ? FB : FA;
                 fsel ^= 1;
-                if (act) store_part<L, float2>(Fb, fb.xo, part, y);
+                if (act) store_part<LS, float2>(Fb, fb.xo + le, part, y);
                 tile_sync();
-                float w[L], wo[L];
-                apply_off_pair<L, Q, float2>(Fb, cff, fb, y, w, part, pd);
+                float w[LS], wo[LS];
+                apply_off_pair<L, Q, float2, SPLIT>(Fb, cff, fb, y, w, part, le, exo, pd);
 #pragma unroll
-                for (int l = 0; l < L; ++l) wo[l] = partner(w[l]);
+                for (int l = 0; l < LS; ++l) wo[l] = partner(w[l]);
                 if (it < j1) {
 #pragma unroll
-                    for (int l = 0; l < L; ++l) df[l] = fmaf(SPf[l].x, w[l], SPf[l].y * wo[l]);
+                    for (int l = 0; l < LS; ++l) df[l] = fmaf(SPf[l].x, w[l], SPf[l].y * wo[l]);
                 }
             }
             // ---- FP64 refinement: z = b + d, residual r = (b - z) + s P w(z), correction in FP32.
             // dacc accumulates z - b (= d, then d + e, ...); b - z = -dacc up to the rounding of z.
-            double dacc[L];
+            double dacc[LS];
 #pragma unroll
-            for (int l = 0; l < L; ++l) {
+            for (int l = 0; l < LS; ++l) {
                 dacc[l] = f64_of(df[l]);
                 z[l] = b[l] + dacc[l];
             }
             for (int pass = 0;; ++pass) {
-                if (act) store_part<L, double2>(D0, fb.xo, part, z);
+                if (act) store_part<LS, double2>(D0, fb.xo + le, part, z);
                 // forward: the staged midpoints of the previous step must have been read by their
                 // bulk store (issued at this step's first barrier) before this step's are staged;
                 // waiting here, ahead of a barrier every step has, makes the staging barrier-free
                 if (!BWD && want_hist && pass == 0 && tid == 0) bulk_wait_read_all();
                 tile_sync();
-                double w[L];
-                apply_off_pair<L, Q, double2>(D0, cfd, fb, z, w, part, pd);
-                float rf[L], e[L];
+                double w[LS];
+                apply_off_pair<L, Q, double2, SPLIT>(D0, cfd, fb, z, w, part, le, exo, pd);
+                float rf[LS], e[LS];
 #pragma unroll
-                for (int l = 0; l < L; ++l) {
+                for (int l = 0; l < LS; ++l) {
                     const double wo = partner(w[l]);
                     const double r = fma(SPp[l].x, w[l], fma(SPp[l].y, wo, -dacc[l]));
                     rf[l] = f32_of(r);
@@ -597,30 +632,30 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
                 for (int it = 0; it < j2max; ++it) {
                     float2* Fb = fsel ? FB : FA;
                     fsel ^= 1;
-                    if (act) store_part<L, float2>(Fb, fb.xo, part, e);
+                    if (act) store_part<LS, float2>(Fb, fb.xo + le, part, e);
                     tile_sync();
-                    float wf[L], wfo[L];
-                    apply_off_pair<L, Q, float2>(Fb, cff, fb, e, wf, part, pd);
+                    float wf[LS], wfo[LS];
+                    apply_off_pair<L, Q, float2, SPLIT>(Fb, cff, fb, e, wf, part, le, exo, pd);
 #pragma unroll
-                    for (int l = 0; l < L; ++l) wfo[l] = partner(wf[l]);
+                    for (int l = 0; l < LS; ++l) wfo[l] = partner(wf[l]);
                     if (it < j2) {
 #pragma unroll
-                        for (int l = 0; l < L; ++l) e[l] = fmaf(SPf[l].x, wf[l], fmaf(SPf[l].y, wfo[l], rf[l]));
+                        for (int l = 0; l < LS; ++l) e[l] = fmaf(SPf[l].x, wf[l], fmaf(SPf[l].y, wfo[l], rf[l]));
                     }
                 }
-                double ed[L];
+                double ed[LS];
 #pragma unroll
-                for (int l = 0; l < L; ++l) ed[l] = f64_of(e[l]);
+                for (int l = 0; l < LS; ++l) ed[l] = f64_of(e[l]);
                 if (pass < R) {
 #pragma unroll
-                    for (int l = 0; l < L; ++l) z[l] = z[l] + ed[l];
+                    for (int l = 0; l < LS; ++l) z[l] = z[l] + ed[l];
                 }
                 if (pass + 1 >= Rmax) break;
                 // another pass: dacc accumulates the correction; it rewrites D0, so every thread
                 // must be done reading it
                 if (pass + 1 < R) {
 #pragma unroll
-                    for (int l = 0; l < L; ++l) dacc[l] = dacc[l] + ed[l];
+                    for (int l = 0; l < LS; ++l) dacc[l] = dacc[l] + ed[l];
                 }
                 tile_sync();
             }
@@ -636,12 +671,12 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
                     if (tid == 0) bulk_wait_read_all();
                     tile_sync();
                 }
-                if (act && live) store_part<L, double2>(H, fb.xo, part, z);
+                if (act && live) store_part<LS, double2>(H, fb.xo + le, part, z);
                 fence_proxy_async_smem();
             }
             if (live) {
 #pragma unroll
-                for (int l = 0; l < L; ++l) u[l] = fma(2.0, z[l], -u[l]);
+                for (int l = 0; l < LS; ++l) u[l] = fma(2.0, z[l], -u[l]);
             }
             // roll-out: U(t_m) when the step ends on a window boundary t_m, i.e. when n + 1 =
             // floor(m N_T / M) for some 1 <= m < M; the only candidate is m = ceil((n+1) M / N_T)
@@ -656,9 +691,9 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
             double2* UB = par ? UB1 : UB0;
             // this part's products conj(Lbar) x Ubar: Re (part 0) = Lr Ur + Li Ui = za Ur + zb Ui,
             // Im (part 1) = Lr Ui - Li Ur = za Ur + zb Ui with (za, zb) = (-Li, Lr)
-            double za[L], zb[L];
+            double za[LS], zb[LS];
 #pragma unroll
-            for (int l = 0; l < L; ++l) {
+            for (int l = 0; l < LS; ++l) {
                 const double zo = partner(z[l]);
                 za[l] = part ? -z[l] : z[l];
                 zb[l] = zo;
@@ -670,7 +705,14 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
 #pragma unroll
             for (int v = 0; v < VH; ++v) acc[v] = 0.0;
             auto prod = [&](double s0, int l, double2 x) { return fma(za[l], x.x, fma(zb[l], x.y, s0)); };
-            {
+            if constexpr (SPLIT > 1) {
+                // last subsystem, lane quads (L = 2): entry 0 gives z (conj(Lbar_0) Ubar_1),
+                // entry 1 gives y (conj(Lbar_1) Ubar_0); every weight is 1
+                constexpr int kl = Q - 1;
+                const double pq = prod(0.0, 0, UB[fb.xo + 1 - le]);
+                acc[2 * kl + 0] = le ? 0.0 : pq;
+                acc[2 * kl + 1] = le ? pq : 0.0;
+            } else {
                 // last subsystem (stride 1) from the fiber itself
                 constexpr int kl = Q - 1;
                 double zq = 0.0, yq = 0.0;
@@ -698,17 +740,17 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
 #pragma unroll
             for (int k = 0; k < Fiber<L, Q>::NFIX; ++k) {
                 double p1 = 0.0;
-                const double2* q1 = UB + fb.nb1[k];
+                const double2* q1 = UB + fb.nb1[k] + le;
 #pragma unroll
-                for (int l = 0; l < L; ++l) p1 = prod(p1, l, q1[l]);
+                for (int l = 0; l < LS; ++l) p1 = prod(p1, l, q1[l]);
                 const double pv = fb.w1[k] * p1;
                 acc[2 * k + 0] = fb.plus1[k] ? pv : 0.0;
                 acc[2 * k + 1] = fb.plus1[k] ? 0.0 : pv;
                 if (fb.two[k]) {
                     double p2 = 0.0;
-                    const double2* q2 = UB + fb.nb2[k];
+                    const double2* q2 = UB + fb.nb2[k] + le;
 #pragma unroll
-                    for (int l = 0; l < L; ++l) p2 = prod(p2, l, q2[l]);
+                    for (int l = 0; l < LS; ++l) p2 = prod(p2, l, q2[l]);
                     acc[2 * k + 1] = fb.w2[k] * p2;
                 }
             }
@@ -748,7 +790,7 @@ __global__ void __launch_bounds__(MAX_PAIR_TILE_THREADS, 1) k_sweep_pair(const S
             // Lambda_n = 2 Lbar - Lambda_{n+1}
             if (live) {
 #pragma unroll
-                for (int l = 0; l < L; ++l) u[l] = fma(2.0, z[l], -u[l]);
+                for (int l = 0; l < LS; ++l) u[l] = fma(2.0, z[l], -u[l]);
             }
         }
 

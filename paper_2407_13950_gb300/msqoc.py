@@ -20,7 +20,7 @@ MSQOC_OK = 0
 STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OUT_OF_MEMORY", -3: "NOT_ADMITTED", -4: "CUDA_ERROR",
                 -5: "TIMEOUT", -6: "UNSUPPORTED", -7: "INTERNAL"}
 SOLVER_DEFAULT, SOLVER_FP64, SOLVER_MIXED = 0, 1, 2
-LAYOUT_AUTO, LAYOUT_FIBER, LAYOUT_PAIR = 0, 1, 2
+LAYOUT_AUTO, LAYOUT_FIBER, LAYOUT_PAIR, LAYOUT_QUAD = 0, 1, 2, 3
 
 EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_query_layout", "msqoc_eval_objective", "msqoc_eval_gradient",
             "msqoc_destroy_problem", "msqoc_last_error", "msqoc_version", "msqoc_kernel_times",

@@ -27,3 +27,10 @@ def test_autotune_returns_a_measured_admissible_width():
     assert_objective_close(got["P"], want["P"])
     assert_grad_close(got["grad_alpha"], want["grad_alpha"])
     assert_grad_close(got["grad_W"], want["grad_W"])
+
+
+def test_autotune_tries_lane_quads_on_two_levels():
+    spec = S.paper_qft_spec(2, M=4, nsteps=400)
+    best, layout, times = msqoc.autotune(spec, probe_steps=16)
+    assert {lay for lay, _ in times} == {msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_QUAD}
+    assert times[(layout, best)] == min(times.values())

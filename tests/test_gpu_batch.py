@@ -120,3 +120,29 @@ def test_subsets_on_two_streams_match_single_evaluations():
     finally:
         for p in probs:
             p.close()
+
+
+def test_batch_mixes_kernel_families():
+    """Problems of one shape built with different kernel families (one thread, a lane pair and
+    a lane quad per fiber) go to separate launch groups of one batch; each equals its single
+    evaluation."""
+    q8 = S.paper_qft_spec(3, M=4, nsteps=400)
+    items = [(q8, msqoc.LAYOUT_QUAD), (q8.replace(M=3), msqoc.LAYOUT_PAIR), (q8.replace(M=5), msqoc.LAYOUT_FIBER),
+             (S.paper_qft_spec(2, M=6, nsteps=300), msqoc.LAYOUT_QUAD), (S.transmon_spec(2, 20.0, 800, 4, 6), 0)]
+    probs = [msqoc.Problem(sp, layout=lay) for sp, lay in items]
+    try:
+        assert [p.layout for p in probs[:3]] == [msqoc.LAYOUT_QUAD, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_FIBER]
+        inputs = [(S.random_alpha(sp, 41, problem=i), S.random_W(sp, 41, problem=i)) for i, (sp, _) in enumerate(items)]
+        with msqoc.Batch(probs, gradient=True) as b:
+            for i, (a, W) in enumerate(inputs):
+                b.set_inputs(i, a, W)
+            b.eval_gradient()
+            got = [b.get_gradient(i) for i in range(len(items))]
+        for i, (sp, lay) in enumerate(items):
+            want, _ = single(sp, *inputs[i], layout=lay)
+            assert_objective_close(got[i]["P"], want["P"])
+            assert_grad_close(got[i]["grad_alpha"], want["grad_alpha"], what=f"grad_alpha[{i}]")
+            assert_grad_close(got[i]["grad_W"], want["grad_W"], what=f"grad_W[{i}]")
+    finally:
+        for p in probs:
+            p.close()

@@ -18,10 +18,18 @@ pytestmark = pytest.mark.gpu
 SOLVERS = {"mixed": msqoc.SOLVER_MIXED, "fp64": msqoc.SOLVER_FP64}
 
 
-def check(spec, seed, solver=msqoc.SOLVER_DEFAULT, ckpt_interval=0, col_block=0):
+def families(spec):
+    """The sweep kernel families a problem admits: lane quads need 2 levels and at most 6
+    exchange-coupled pairs."""
+    pairs = sum(1 for row in (spec.jx or []) for v in row if v != 0.0)
+    quad = (msqoc.LAYOUT_QUAD,) if spec.L == 2 and pairs <= 6 else ()
+    return (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR) + quad
+
+
+def check(spec, seed, solver=msqoc.SOLVER_DEFAULT, ckpt_interval=0, col_block=0, layouts=None):
     alpha, W = S.random_alpha(spec, seed), S.random_W(spec, seed)
     want = oracle.evaluate(spec, alpha, W, nthreads=os.cpu_count())
-    for layout in (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR):     # both sweep kernel families
+    for layout in layouts or families(spec):     # every sweep kernel family the problem admits
         with msqoc.Problem(spec, solver=solver, ckpt_interval=ckpt_interval, layout=layout,
                            col_block=col_block) as p:
             got = p.eval_gradient(alpha, W)
@@ -51,16 +59,47 @@ def test_qft16_short(solver):
 
 
 def test_qft16_tiles_over_two_windows():
-    """5-column tiles (E = 16): 40 threads (one thread per fiber) or 80 (lane pairs), tiles that
-    cover the end of one window and the start of the next, with exchange coupling."""
+    """5-column tiles (E = 16): 40 threads (one thread per fiber), 80 (lane pairs) or 160 (lane
+    quads), tiles that cover the end of one window and the start of the next, with exchange
+    coupling."""
     check(S.paper_qft_spec(4, M=5, nsteps=1001), 87, col_block=5)
+
+
+@pytest.mark.parametrize("cb", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_qft8_lane_quad_tile_widths(cb):
+    """Lane quads at every tile width of QFT-8 (16 threads a column): one-warp tiles (1, 2),
+    tiles over two windows (3, 5, 6, 7), a ragged last tile (M E = 56 is not a multiple of 3, 5,
+    6), ragged windows and checkpointed segments."""
+    spec = S.paper_qft_spec(3, M=7, nsteps=803)
+    check(spec, 88 + cb, col_block=cb, layouts=(msqoc.LAYOUT_QUAD,))
+    if cb in (3, 8):
+        check(spec, 88 + cb, col_block=cb, layouts=(msqoc.LAYOUT_QUAD,), ckpt_interval=9,
+              solver=msqoc.SOLVER_FP64)
+
+
+def test_lane_quads_rejected_where_not_admitted():
+    """Lane quads serve 2-level subsystems with at most 6 exchange-coupled pairs."""
+    three_levels = S.transmon_spec(2, 10.0, 100, 2, 5)
+    base = S.paper_qft_spec(4, M=2, nsteps=100)
+    q = 5
+    jx = [[(0.03 if l > k else 0.0) for l in range(q)] for k in range(q)]     # 10 pairs
+    omega = [list(base.omega[min(k, len(base.omega) - 1)]) for k in range(q)]
+    ten_pairs = base.replace(q=q, xi=[0.0] * q, xi_cross=[[0.0] * q for _ in range(q)], omega=omega,
+                             detune=[0.1 * k for k in range(q)], jx=jx)
+    for spec in (three_levels, ten_pairs):
+        with pytest.raises(msqoc.MsqocError) as err:
+            msqoc.Problem(spec, layout=msqoc.LAYOUT_QUAD)
+        assert err.value.status == -1
+        with msqoc.Problem(spec) as p:                      # the automatic choice avoids them
+            assert p.layout in (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR)
 
 
 @pytest.mark.parametrize("q", [4, 5])
 def test_all_to_all_exchange(q):
     """Every pair of qubits coupled, with distinct strengths: 4 qubits give 6 pairs (sources
     precomputed per fiber, pairs with the last subsystem and pairs between fixed subsystems at
-    every distance), 5 qubits give 10 (more than the per-fiber list holds: the general form)."""
+    every distance; all three kernel families), 5 qubits give 10 (more than the per-fiber list
+    holds: the general form, one thread or a lane pair per fiber)."""
     base = S.paper_qft_spec(min(q, 4), M=3, nsteps=300)
     jx = [[(2 * np.pi * 0.004 * (1 + 0.3 * k + 0.1 * l) if l > k else 0.0) for l in range(q)] for k in range(q)]
     omega = [list(base.omega[min(k, len(base.omega) - 1)]) for k in range(q)]
@@ -69,18 +108,16 @@ def test_all_to_all_exchange(q):
     check(spec, 85)
 
 
-def test_qft8_full_time_grid_pair_tiles():
-    """QFT-8 on the paper's full grid (19806 steps) at 32 windows, the lane-pair kernels."""
+def test_qft8_full_time_grid():
+    """QFT-8 on the paper's full grid (19806 steps) at 32 windows, every kernel family."""
     spec = S.paper_qft_spec(3, M=32)
-    with msqoc.Problem(spec) as p:
-        assert p.layout == msqoc.LAYOUT_PAIR
     check(spec, 86)
 
 
 @pytest.mark.parametrize("M", [64, 256])
 def test_qft16_full_size_sampled_windows(M):
-    """QFT-16 at the paper's full size (106072 steps) over 64 windows (lane-pair tiles) and 256
-    (the paper's largest run; one thread per fiber): the last two windows against the oracle (J,
+    """QFT-16 at the paper's full size (106072 steps) over 64 windows and 256 (the paper's
+    largest run), the library's choice of tiles: the last two windows against the oracle (J,
     pen_{M-1}, dP/dW^{M-1}), the gradients as a whole by central differences along seeded random
     directions."""
     spec = S.paper_qft_spec(4, M=M)

@@ -46,3 +46,16 @@ def test_rollout_estimate_is_the_formula_and_bounds_the_rollout_infidelity():
     J_ro = oracle.evaluate(spec.replace(M=1), alpha, np.zeros(0), grad=False)["P"]
     assert J_ro <= est * (1 + 1e-12)
     assert g["P"] == pytest.approx(obj["P"], rel=1e-12)
+
+
+@pytest.mark.parametrize("layout", [msqoc.LAYOUT_PAIR, msqoc.LAYOUT_QUAD])
+def test_rollout_two_level_exchange(layout):
+    """The roll-out of the paper's QFT-8 model (exchange coupling) with lane pairs and lane
+    quads, ragged windows and tiles over two windows."""
+    spec = S.paper_qft_spec(3, M=5, nsteps=601)
+    alpha = S.random_alpha(spec, 73)
+    want = oracle.rollout(spec, alpha)
+    with msqoc.Problem(spec, col_block=5, layout=layout) as p:     # 40 or 80 threads, E = 8
+        assert p.layout == layout
+        W = p.rollout(alpha)
+    np.testing.assert_allclose(W, want, rtol=0, atol=1e-12)
