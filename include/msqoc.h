@@ -250,6 +250,15 @@ msqoc_status msqoc_kernel_times(msqoc_problem* p, float* ms);
  * part of the paper's method. */
 msqoc_status msqoc_measure_fp64_peak(double* tflops);
 
+/* Self-test of the sweeps' failure path (not an operation of the paper): one thread waits on
+ * an mbarrier phase with the sweeps' bounded wait (a poll loop of at most `spins` try-waits,
+ * 1 <= spins <= 2^18, the limit the sweeps use), after completing the phase itself when
+ * arrive != 0 and otherwise on a phase that nothing completes.  Returns MSQOC_ERR_TIMEOUT when
+ * the wait gave up (the device status word was set), MSQOC_OK when the phase completed;
+ * *seconds_out (may be NULL) receives the launch's duration.  The device stays usable either
+ * way.  Synchronizes the device. */
+msqoc_status msqoc_selftest_bounded_wait(int64_t spins, int32_t arrive, double* seconds_out);
+
 /* ---------------------------------------------------------------------------------------
  * Batched evaluation (many problems per launch).
  *

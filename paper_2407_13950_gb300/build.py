@@ -51,7 +51,8 @@ def _units() -> List[tuple]:
              ("dispatch", os.path.join(CSRC, "dispatch.cu"), []),
              ("batch", os.path.join(CSRC, "msqoc_batch.cu"), []),
              ("peak", os.path.join(CSRC, "msqoc_peak.cu"), []),
-             ("lbfgs", os.path.join(CSRC, "msqoc_lbfgs.cu"), [])]
+             ("lbfgs", os.path.join(CSRC, "msqoc_lbfgs.cu"), []),
+             ("selftest", os.path.join(CSRC, "msqoc_selftest.cu"), [])]
     for L, q in SHAPES:
         units.append((f"sweep_L{L}_Q{q}", os.path.join(CSRC, "inst_sweep.cu"), [f"-DMSQOC_L={L}", f"-DMSQOC_Q={q}"]))
     return units

@@ -64,6 +64,9 @@ __device__ __forceinline__ void fence_mbar_init() {
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
@@ -87,10 +90,14 @@ __device__ __forceinline__ void bulk_wait_read_all() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-// bounded wait on an mbarrier phase; returns false if it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// polls of a bounded mbarrier wait before it gives up: a poll of a phase that does not complete
+// suspends ~3.8 us on this GPU (measured by msqoc_selftest_bounded_wait), so a stuck wait ends
+// after about a second
+constexpr int64_t MBAR_WAIT_SPINS = int64_t(1) << 18;
+// bounded wait on an mbarrier phase; returns false if it gave up after max_spins polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int64_t max_spins = MBAR_WAIT_SPINS) {
     const uint32_t a = smem_u32(bar);
-    for (int it = 0; it < (1 << 22); ++it) {
+    for (int64_t it = 0; it < max_spins; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"

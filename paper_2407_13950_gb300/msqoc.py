@@ -28,7 +28,7 @@ EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_query_layout", "msqoc_
             "msqoc_batch_eval_objective", "msqoc_batch_eval_gradient", "msqoc_batch_destroy", "msqoc_set_inputs",
             "msqoc_get_objective", "msqoc_get_gradient", "msqoc_batch_eval_subset", "msqoc_autotune",
             "msqoc_rollout", "msqoc_rollout_estimate", "msqoc_eval_regularization", "msqoc_lbfgs_direction",
-            "msqoc_lbfgs_trial", "msqoc_lbfgs_update"]
+            "msqoc_lbfgs_trial", "msqoc_lbfgs_update", "msqoc_selftest_bounded_wait"]
 BATCH_GRADIENT, BATCH_GRAPH = 1, 2
 KERNEL_NAMES = ["controls", "forward", "terminal", "adjoint", "finalize"]
 
@@ -84,6 +84,7 @@ def load(build_if_missing: bool = True):
             "msqoc_version": (i32, []),
             "msqoc_kernel_times": (i32, [vp, vp]),
             "msqoc_measure_fp64_peak": (i32, [vp]),
+            "msqoc_selftest_bounded_wait": (i32, [ctypes.c_int64, i32, vp]),
             "msqoc_eval_objective_noalloc": (i32, [vp, vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, i32,
                                                    vp, vp, vp, vp, vp, vp]),
             "msqoc_batch_create": (i32, [vp, i32, i32, vp]),
@@ -295,6 +296,14 @@ def measure_fp64_peak() -> float:
     """FP64 TFLOP/s of the current device (FMA microbenchmark in the library)."""
     t = ctypes.c_double()
     _check(load().msqoc_measure_fp64_peak(ctypes.byref(t)))
+    return t.value
+
+
+def selftest_bounded_wait(spins: int, arrive: bool = False) -> float:
+    """The sweeps' bounded mbarrier wait on a phase that completes (arrive) or never does: raises
+    MsqocError with status TIMEOUT (-5) when the wait gave up; returns the launch's seconds."""
+    t = ctypes.c_double()
+    _check(load().msqoc_selftest_bounded_wait(int(spins), 1 if arrive else 0, ctypes.byref(t)))
     return t.value
 
 

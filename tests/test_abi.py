@@ -92,3 +92,9 @@ def test_binding_rejects_wrong_dtypes():
         msqoc._ptr(np.zeros(3, dtype=np.float32))
     with pytest.raises(TypeError):
         msqoc._ptr(np.zeros((3, 3))[:, 0])
+
+
+def test_bounded_wait_selftest_rejects_spin_counts_outside_its_range():
+    lib = msqoc.load()
+    for spins in (0, -3, (1 << 18) + 1):
+        assert lib.msqoc_selftest_bounded_wait(spins, 0, None) == -1     # no device work
