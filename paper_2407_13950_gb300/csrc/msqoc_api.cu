@@ -193,13 +193,14 @@ int max_tile_threads(int pair) {
 
 // Is `cpt` columns per tile usable in the given kernel family?  Tiles must fit the family's
 // thread limit and the shared memory; a tile that covers two windows needs two warps (one per
-// window's coefficients), so a one-warp tile must divide the window's columns.
-bool tile_width_ok(int cpt, int E, int F, int q, int L, int N, int d, int solver, int pair) {
+// window's coefficients), so a one-warp tile must divide the window's columns.  g: doubles of
+// the adjoint's shared alpha-gradient per window slot.
+bool tile_width_ok(int cpt, int E, int F, int q, int L, int N, int g, int solver, int pair) {
     if (cpt < 1 || cpt > E || (1 << pair) * cpt * F > max_tile_threads(pair)) return false;
     const int nthreads = tile_threads(cpt, F, pair);
     if (nthreads == 32 && E % cpt) return false;
-    const size_t s1 = sweep_layout(q, L, N, cpt, nthreads, d, solver, true, pair).total;
-    const size_t s0 = sweep_layout(q, L, N, cpt, nthreads, d, solver, false, pair).total;
+    const size_t s1 = sweep_layout(q, L, N, cpt, nthreads, g, solver, true, pair).total;
+    const size_t s0 = sweep_layout(q, L, N, cpt, nthreads, g, solver, false, pair).total;
     return std::max(s0, s1) <= 200 * 1024;
 }
 
@@ -215,9 +216,10 @@ bool quad_admitted(const ProbDev& pd) { return pd.L == 2 && pd.nex <= MAXEXF; }
 // instructions a thread, plus shuffles) c = 0.6 at full SM load and c0 = 0.7 alone (measured:
 // equal to the one-thread family on the 4-transmon tiles, 1.4x faster steps on small
 // problems); for lane quads (2-level subsystems, a quarter of a fiber's work a thread)
-// c = 0.41 and c0 = 0.52 (measured on the paper's QFT cases: steps 1.33-1.38x faster than lane
-// pairs where the tiles are too few to fill the GPU; at full load a quad warp costs 0.41 of a
-// one-thread warp, from QFT-16 at 256 windows).  Tiles that do not fit at once run in waves of the CTAs an SM holds (the kernels'
+// c = 0.38 and c0 = 0.52 (measured on the paper's QFT cases: steps 1.33-1.38x faster than lane
+// pairs where the tiles are too few to fill the GPU; under load, from QFT-16 at 64 windows,
+// seven one-warp quad tiles per SM take 0.73 of the time of one-thread tiles at the floor).
+// Tiles that do not fit at once run in waves of the CTAs an SM holds (the kernels'
 // occupancy at that width).  A tile over two windows pays a second gradient reduction and wider
 // class mixing in its warps: its cost is taken 1.18x (measured on the 4-transmon tiles: the
 // adjoint 9% slower, the forward 3% faster than 8-column one-window tiles, where the warp count
@@ -233,8 +235,8 @@ bool quad_admitted(const ProbDev& pd) { return pd.L == 2 && pd.nex <= MAXEXF; }
 //   4. the idle-lane fraction of a tile.
 // fixed_cpt > 0 restricts the width, layout (MSQOC_LAYOUT_*) the family; quad_ok: the problem
 // admits lane quads.  cpt = -1: none fits.
-constexpr double QUAD_C = 0.41, QUAD_C0 = 0.52;
-TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int d, int solver, int sms, int fixed_cpt,
+constexpr double QUAD_C = 0.38, QUAD_C0 = 0.52;
+TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int g, int solver, int sms, int fixed_cpt,
                               int layout, bool quad_ok) {
     TileChoice best{-1, 0};
     double best_a = 0.0, best_c = 0.0;
@@ -247,13 +249,13 @@ TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int d, i
         const int hi = fixed_cpt > 0 ? fixed_cpt : std::min(E, max_tile_threads(pair) / ((1 << pair) * F));
         const int lo = fixed_cpt > 0 ? fixed_cpt : 1;
         for (int cpt = hi; cpt >= lo; --cpt) {
-            if (!tile_width_ok(cpt, E, F, q, L, N, d, solver, pair)) continue;
+            if (!tile_width_ok(cpt, E, F, q, L, N, g, solver, pair)) continue;
             const long tiles = (long(M) * E + cpt - 1) / cpt;
             const int threads = tile_threads(cpt, F, pair);
             const int warps = threads / 32;
             SweepArgs a{};
             a.cpt = cpt;
-            a.dmax = d;
+            a.gmax = g;
             a.L = L;
             a.q = q;
             a.solver = solver;
@@ -368,6 +370,18 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
         pd.wsq[2 * l + 0] = std::sqrt(double(l + 1));
         pd.wsq[2 * l + 1] = std::sqrt(double(l));
     }
+    // the tiles' shared alpha-gradient: the splines active in one window (the most over the
+    // windows, from each window's first active spline), plus a margin of two
+    int span = 3;
+    for (int m = 1; m <= pd.M; ++m) {
+        const int64_t n0 = (int64_t(m - 1) * nsteps) / pd.M, n1 = (int64_t(m) * nsteps) / pd.M;
+        if (n1 <= n0) continue;
+        const int s_first = spline_index((double(n0) + 0.5) * pd.h, pd.dtau, pd.d1);
+        const int s_last = spline_index((double(n1 - 1) + 0.5) * pd.h, pd.dtau, pd.d1);
+        span = std::max(span, s_last - s_first + 3);
+    }
+    pd.gspan = std::min(pd.d1, span + 2);
+    pd.glocal = 2 * nfsum * pd.gspan;
     if (layout < MSQOC_LAYOUT_AUTO || layout > MSQOC_LAYOUT_QUAD)
         return fail(MSQOC_ERR_INVALID_ARG, "layout %d is not an MSQOC_LAYOUT_* value", layout);
     if (layout == MSQOC_LAYOUT_QUAD && !quad_admitted(pd))
@@ -375,7 +389,7 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
                     MAXEXF);
     if (col_block < 0) return fail(MSQOC_ERR_INVALID_ARG, "column block %d < 0", col_block);
     const TileChoice tc =
-        choose_tile_layout(pd.M, pd.E, pd.F, q, L, pd.N, pd.d, solver, sms, col_block, layout, quad_admitted(pd));
+        choose_tile_layout(pd.M, pd.E, pd.F, q, L, pd.N, pd.glocal, solver, sms, col_block, layout, quad_admitted(pd));
     if (tc.cpt < 0)
         return fail(MSQOC_ERR_INVALID_ARG,
                     "column block %d invalid for E=%d (needs 1 <= cb <= E, cb N/L <= %d threads with one thread "
@@ -409,7 +423,7 @@ SweepArgs sweep_args(const ProbDev& pd, const ProbDev* pds_dev, const Tile* tile
     a.tiles = tiles;
     a.lanemap = lanemap;
     a.cpt = pd.cb;
-    a.dmax = pd.d;
+    a.gmax = pd.glocal;
     a.mode = mode;
     a.seg = seg;
     a.L = pd.L;
@@ -781,6 +795,8 @@ msqoc_status status_error(int st) {
     if (st & ST_TIMEOUT) return fail(MSQOC_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", st);
     if (st & ST_SOLVER_RANGE)
         return fail(MSQOC_ERR_UNSUPPORTED, "time step too large for the step solver (h*|H_c|/2 >= 0.5)");
+    if (st & ST_GRAD_RANGE)
+        return fail(MSQOC_ERR_INTERNAL, "a gradient spline index fell outside its tile's window range (status %d)", st);
     return fail(MSQOC_ERR_INTERNAL, "device status %d", st);
 }
 
@@ -998,7 +1014,7 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
     const int fam_hi = o.layout == MSQOC_LAYOUT_AUTO ? MSQOC_LAYOUT_QUAD : o.layout;
     for (int fam = fam_lo; fam <= fam_hi && st == MSQOC_OK; ++fam)
     for (int cb = std::min(pd.E, MAX_TILE_THREADS / pd.F); cb >= 1 && st == MSQOC_OK; --cb) {
-        if (choose_tile_layout(pd.M, pd.E, pd.F, pd.q, pd.L, pd.N, pd.d, solver, 1, cb, fam, quad_admitted(pd)).cpt <
+        if (choose_tile_layout(pd.M, pd.E, pd.F, pd.q, pd.L, pd.N, pd.glocal, solver, 1, cb, fam, quad_admitted(pd)).cpt <
             0)
             continue;
         msqoc_options oc = o;

@@ -67,8 +67,7 @@ struct SplineAt {
 
 __device__ __forceinline__ SplineAt spline_at(const ProbDev& pd, double t) {
     const double tau = t / pd.dtau;
-    int s0 = static_cast<int>(floor(tau));
-    s0 = s0 < 0 ? 0 : (s0 > pd.d1 - 3 ? pd.d1 - 3 : s0);
+    const int s0 = spline_index(t, pd.dtau, pd.d1);
     const double x = tau - s0;
     return SplineAt{s0, 0.5 * (1.0 - x) * (1.0 - x), 0.75 - (x - 0.5) * (x - 0.5), 0.5 * x * x};
 }

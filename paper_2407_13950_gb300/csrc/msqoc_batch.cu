@@ -199,12 +199,12 @@ msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t fla
         }
     for (auto& g : b->groups) {
         if (st) break;
-        int nthreads = 32, cpt = 1, dmax = 1;
+        int nthreads = 32, cpt = 1, gmax = 1;
         for (int i : g.members) {
             const ProbDev& pd = b->probs[i]->pd;
             nthreads = std::max(nthreads, pd.nthreads);
             cpt = std::max(cpt, pd.cb);
-            dmax = std::max(dmax, pd.d);
+            gmax = std::max(gmax, pd.glocal);
             g.nseg_max = std::max(g.nseg_max, pd.nseg);
         }
         std::vector<ProbDev> pds;
@@ -254,7 +254,7 @@ msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t fla
         const ProbDev& p0 = b->probs[g.members[0]]->pd;
         g.args = sweep_args(p0, g.pds, g.tiles, g.lanemap, SWEEP_OBJECTIVE, 0);
         g.args.cpt = cpt;
-        g.args.dmax = dmax;
+        g.args.gmax = gmax;
         g.args.nthreads = nthreads;
         SweepArgs adj = g.args;
         adj.mode = SWEEP_ADJOINT;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cstdint>
 
 namespace msqoc {
@@ -17,7 +18,15 @@ constexpr int MAX_QUAD_TILE_THREADS = 512;  // threads of a lane-quad tile (128 
 enum Solver { SOLVER_FP64 = 1, SOLVER_MIXED = 2 };
 
 // device status word bits
-enum Status { ST_OK = 0, ST_TIMEOUT = 1, ST_BAD_LAUNCH = 2, ST_SOLVER_RANGE = 4 };
+enum Status { ST_OK = 0, ST_TIMEOUT = 1, ST_BAD_LAUNCH = 2, ST_SOLVER_RANGE = 4, ST_GRAD_RANGE = 8 };
+
+// Index of the first of the three quadratic B-splines (spacing dtau, d1 of them) active at time
+// t, clamped to the grid.  The controls kernel, the sweeps and the host's sizing of the shared
+// gradient all take it from here.
+__host__ __device__ inline int spline_index(double t, double dtau, int d1) {
+    const int s0 = static_cast<int>(floor(t / dtau));
+    return s0 < 0 ? 0 : (s0 > d1 - 3 ? d1 - 3 : s0);
+}
 
 // Per-step table: first active spline index, the step solver's iteration counts packed as
 // j1 | j2 << 8 | passes << 16 | out-of-range << 24, and the three spline weights.
@@ -38,6 +47,9 @@ struct ProbDev {
                    // the real and the imaginary part; 2: a lane quad, a pair per entry of a
                    // 2-level fiber)
     int ntiles;    // tiles of the problem's sweeps
+    int gspan;     // splines per carrier in a tile's shared alpha-gradient: every spline active in
+                   // one window (from the window's first active spline), with a margin
+    int glocal;    // doubles of that gradient per window slot: nfsum gspan 2
     int solver;
     int kseg;      // steps per history segment (checkpoint interval; >= the longest window when
                    // every midpoint state is kept)
@@ -106,7 +118,7 @@ struct SweepArgs {
     const Tile* tiles;    // [tiles] one per CTA
     const int* lanemap;   // [maps][threads]: (column << 16 | fiber), ~value for idle lanes
     int cpt;              // columns of the widest tile (shared-memory sizing)
-    int dmax;             // largest d over the problems
+    int gmax;             // largest shared alpha-gradient per window slot (doubles) over the problems
     int mode;             // SweepMode
     int seg;              // segment (SWEEP_RECOMPUTE, SWEEP_ADJOINT)
     int L, q, solver, nthreads;

@@ -208,7 +208,7 @@ struct SweepSmem {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cpt, int nthreads, int dmax, int solver,
+__host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cpt, int nthreads, int gmax, int solver,
                                                   bool bwd, int pair) {
     SweepSmem s{};
     const int nslot = q * L * 2;
@@ -226,7 +226,7 @@ __host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cpt, 
     s.mbar = o;   o = align16(o + 2 * 8);
     s.red = o;    o = align16(o + (bwd ? size_t(2) * 2 * nwarps * V * 8 : 0));   // [parity][slot][warp][V]
     s.zy = o;     o = align16(o + (bwd ? size_t(2) * 2 * 4 * q * 8 : 0));        // [parity][slot][4q]
-    s.galpha = o; o = align16(o + (bwd ? size_t(2) * dmax * 8 : 0));             // [slot][d]
+    s.galpha = o; o = align16(o + (bwd ? size_t(2) * gmax * 8 : 0));             // [slot][nfsum][gspan][2]
     s.D0 = o;     o = align16(o + buf_d);
     s.D1 = o;     o = align16(o + (solver == SOLVER_FP64 ? buf_d : 0));
     s.FA = o;     o = align16(o + (solver == SOLVER_MIXED ? buf_f : 0));
@@ -251,6 +251,29 @@ __device__ __forceinline__ int tile_sync_or(int p) {
     return __syncthreads_or(p);
 }
 
+
+// first spline active at the midpoint of global step n (the controls kernel's spline table
+// holds the same index for every step)
+__device__ __forceinline__ int spline_first(const ProbDev& pd, int64_t n) {
+    return spline_index((double(n) + 0.5) * pd.h, pd.dtau, pd.d1);
+}
+
+// The tile's alpha-gradient partial gp[d] ([carrier][spline][re, im]) from the window-local
+// sums of its slots (slot s holds splines [slo_s, slo_s + gspan) of every carrier at
+// galpha + s gmax; slo_1 < 0: one slot), stored (first launch of the adjoint) or added.  Kept
+// out of line: it runs once per launch, and inlined into the lane-pair adjoint of some shapes
+// it crashed the assembler.
+static __device__ __noinline__ void store_grad_partial(double* gp, const double* galpha, const ProbDev& pd, int gmax,
+                                                int slo_0, int slo_1, bool first) {
+    for (int jx = threadIdx.x; jx < pd.d; jx += blockDim.x) {
+        const int kf = jx / (2 * pd.d1), sx = (jx >> 1) - kf * pd.d1;
+        const int l0 = sx - slo_0, l1 = sx - slo_1;
+        double v = 0.0;
+        if (l0 >= 0 && l0 < pd.gspan) v += galpha[(kf * pd.gspan + l0) * 2 + (jx & 1)];
+        if (slo_1 >= 0 && l1 >= 0 && l1 < pd.gspan) v += galpha[gmax + (kf * pd.gspan + l1) * 2 + (jx & 1)];
+        gp[jx] = first ? v : gp[jx] + v;
+    }
+}
 
 // first global step of window m (1-based); window m owns [win_start(m), win_start(m + 1))
 __device__ __forceinline__ int64_t win_start(const ProbDev& pd, int m) {

@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
     const ProbDev& pd = a.pds[tile.prob];
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const SweepSmem lay = sweep_layout(Q, L, N, a.cpt, blockDim.x, a.dmax, SOLVER, BWD, SPLIT);
+    const SweepSmem lay = sweep_layout(Q, L, N, a.cpt, blockDim.x, a.gmax, SOLVER, BWD, SPLIT);
     double2* coef_d = reinterpret_cast<double2*>(smem + lay.coef_d);
     float2* coef_f = reinterpret_cast<float2*>(smem + lay.coef_f);
     int* params = reinterpret_cast<int*>(smem + lay.params);
@@ -290,6 +290,17 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
     const int cnt_0 = idle_launch ? 0 : max(0, (segmented ? min(wns_0, lo_0 + pd.kseg) : wns_0) - lo_0);
     const int cnt_1 = nslot > 1 && !idle_launch ? max(0, (segmented ? min(wns_1, lo_1 + pd.kseg) : wns_1) - lo_1) : 0;
     const int nit = max(cnt_0, cnt_1);
+    // first spline active in each slot's window: the origin of the slot's window-local
+    // alpha-gradient (adjoint)
+    const int slo_0 = BWD ? spline_first(pd, wn0_0) : 0;
+    const int slo_1 = BWD && nslot > 1 ? spline_first(pd, wn0_1) : 0;
+    // every step's splines fit the slot's window-local range (the index grows with the step, so
+    // a window's last step bounds them all; the host sizes the range with a margin): checked
+    // once per launch, a failure reported in the status word and the gradient left unfolded
+    const bool grad_fits =
+        !BWD || (spline_first(pd, wn0_0 + wns_0 - 1) - slo_0 + 2 < pd.gspan &&
+                 (nslot < 2 || spline_first(pd, wn0_1 + wns_1 - 1) - slo_1 + 2 < pd.gspan));
+    if (!grad_fits && threadIdx.x == 0) atomicOr(pd.status, ST_GRAD_RANGE);
     // global step of slot s at iteration jj, clamped into the slot's range (a slot without steps
     // in this launch maps to its window's first step, which exists)
     auto step_of = [&](int s, int jj) -> int64_t {
@@ -401,7 +412,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
     };
 
     if (BWD) {
-        for (int j = tid; j < 2 * a.dmax; j += blockDim.x) galpha[j] = 0.0;
+        for (int j = tid; j < 2 * a.gmax; j += blockDim.x) galpha[j] = 0.0;
         if (tid == 0) {
             mbar_init(&mbar[0], 1);
             mbar_init(&mbar[1], 1);
@@ -448,8 +459,9 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
             zy[(pp * 2 + s) * 4 * Q + lane] = sum;
         }
         __syncwarp();
-        const int s0 = sp.s;
-        double* ga = galpha + size_t(s) * a.dmax;
+        if (!grad_fits) return;
+        const int s0 = sp.s - (s ? slo_1 : slo_0);   // first active spline, window-local
+        double* ga = galpha + size_t(s) * a.gmax;
         for (int i = lane; i < nscat; i += 32) {
             int kf = f_kf, jw = f_jw, k = f_k;   // this lane's first entry, precomputed
             if (i != lane) {
@@ -464,7 +476,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
             const double2 ph = (prefetched && i == lane) ? ph_lane : pd.phase[size_t(np) * pd.nfsum + kf];
             const double wgt = -2.0 * pd.h * (jw == 0 ? sp.w0 : (jw == 1 ? sp.w1 : sp.w2));
             const double A = zk.y + yk.y, B = zk.x - yk.x;
-            const int idx = (kf * pd.d1 + s0 + jw) * 2;
+            const int idx = (kf * pd.gspan + s0 + jw) * 2;
             ga[idx + 0] += wgt * fma(ph.x, A, ph.y * B);
             ga[idx + 1] += wgt * fma(ph.x, B, -ph.y * A);
         }
@@ -823,10 +835,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
             // adjoint launch is the last segment's)
             double* gp = pd.gpart + size_t(tile.tloc) * pd.d;
             const bool first_launch = a.seg == pd.nseg - 1;
-            for (int jx = tid; jx < pd.d; jx += blockDim.x) {
-                const double v = galpha[jx] + galpha[a.dmax + jx];
-                gp[jx] = first_launch ? v : gp[jx] + v;
-            }
+            store_grad_partial(gp, galpha, pd, a.gmax, slo_0, nslot > 1 ? slo_1 : -1, first_launch);
             // Lambda at the segment start: Lambda^m(t_{m-1}) for the window's first segment
             if (act && my_cnt > 0) store_fiber((my_lo == 0 ? pd.Lam0 : pd.Lstate) + wcol);
         }

@@ -76,6 +76,18 @@ def test_parity_column_blocks_4q(layout, cb):
     check(spec, alpha, W, msqoc.SOLVER_MIXED, col_block=cb, layouts=(LAYOUTS[layout],))
 
 
+@pytest.mark.parametrize("nsteps,M,d1", [(24, 24, 20), (60, 30, 10), (300, 5, 3), (301, 3, 41)])
+def test_parity_window_local_gradient_ranges(nsteps, M, d1):
+    """The adjoint keeps each window's alpha-gradient over the splines active in that window
+    only: one step per window (24 windows, 20 splines), windows shorter than a spline interval
+    (30 windows, 10 splines), the smallest basis (3 splines, all active everywhere) and long
+    ragged windows over many splines; also with tiles over two windows (cb = 5, E = 8)."""
+    spec = S.transmon_spec(3, 12.0, nsteps, M, d1)
+    alpha, W = S.random_alpha(spec, 9), S.random_W(spec, 9)
+    check(spec, alpha, W, msqoc.SOLVER_MIXED)
+    check(spec, alpha, W, msqoc.SOLVER_FP64, col_block=5)
+
+
 @pytest.mark.parametrize("solver", list(SOLVERS))
 @pytest.mark.parametrize("cb", [5, 7])
 def test_parity_tiles_over_ragged_windows_3q(cb, solver):
