@@ -328,6 +328,11 @@ def run_batched(args):
              torch.zeros(max(p.nW, 2), device=dev, dtype=torch.float64)) for p in probs]
     stream = torch.cuda.current_stream(dev)
     batch = msqoc.Batch(probs, gradient=True, graph=True)
+    fam = {1: "fiber", 2: "pair", 3: "quad"}
+    tile_mix = {}
+    for sp, p in zip(specs, probs):       # how many problems run each (shape, family, width)
+        key = f"{sp.q}q {fam[p.layout]} x{p.col_block} ({p.threads} threads)"
+        tile_mix[key] = tile_mix.get(key, 0) + 1
 
     def batched_step():
         for i, (a, W) in enumerate(dev_in):
@@ -411,6 +416,7 @@ def run_batched(args):
         "e2e": {"value": nprob / (e2e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clocks,
+        "tiles": tile_mix,
     }
     batch.close()
     for p in probs:

@@ -1,10 +1,12 @@
 // Batched evaluation: many problems per sweep launch, optionally replayed as a CUDA graph.
 //
-// Problems of one shape (levels, subsystems) and solver form a group; a group's sweep launch
-// takes the concatenation of its problems' tile lists (each tile names its problem), so
-// problems of different durations and window counts share every wave of the GPU instead of
-// each filling a fraction of it.  The per-problem steps (controls, terminal conditions, final
-// reductions) stay per problem.  With MSQOC_BATCH_GRAPH the whole sequence is captured once
+// Problems of one shape (levels, subsystems), solver, kernel family and tile size (threads)
+// form a group; a group's sweep launch takes the concatenation of its problems' tile lists (each
+// tile names its problem), so problems of different durations and window counts share every
+// wave of the GPU instead of each filling a fraction of it, and no tile runs with more threads
+// than its own problem's.  The groups' launches of one sweep run concurrently, each on a stream
+// of its own forked from the caller's stream and joined back.  The per-problem steps (controls,
+// terminal conditions, final reductions) stay per problem.  With MSQOC_BATCH_GRAPH the whole sequence is captured once
 // into a CUDA graph and replayed; every buffer it touches belongs to the problems and stays
 // where it is, so replays only need the problems' inputs staged with msqoc_set_inputs.
 #include <algorithm>
@@ -18,6 +20,7 @@ using namespace msqoc;
 struct msqoc_batch {
     struct Group {
         int L = 0, q = 0, solver = 0, pair = 0;   // shape, solver and kernel family of the group
+        int nthreads = 0;                          // threads of its tiles
         std::vector<int> members;     // indices into probs
         SweepArgs args{};             // pds / tiles / lanemap / geometry of the group's launches
         int ntiles = 0;
@@ -38,6 +41,11 @@ struct msqoc_batch {
     cudaStream_t cap = nullptr;                   // capture stream (graph mode)
     cudaGraphExec_t exec[2] = {nullptr, nullptr};  // [objective, gradient]
     cudaEvent_t slot_done[MSQOC_BATCH_SLOTS] = {};  // the slot's staging copies have been read
+    // per stream set (one per subset slot, the last for whole-batch evaluations): the groups'
+    // streams, the fork event on the caller's stream and each group's join event
+    std::vector<cudaStream_t> gstream[MSQOC_BATCH_SLOTS + 1];
+    std::vector<cudaEvent_t> gjoin[MSQOC_BATCH_SLOTS + 1];
+    cudaEvent_t gfork[MSQOC_BATCH_SLOTS + 1] = {};
 };
 
 namespace {
@@ -54,25 +62,59 @@ void free_batch(msqoc_batch* b) {
     }
     for (auto& e : b->slot_done)
         if (e) cudaEventDestroy(e);
+    for (int k = 0; k <= MSQOC_BATCH_SLOTS; ++k) {
+        for (cudaStream_t gs : b->gstream[k])
+            if (gs) cudaStreamDestroy(gs);
+        for (cudaEvent_t e : b->gjoin[k])
+            if (e) cudaEventDestroy(e);
+        if (b->gfork[k]) cudaEventDestroy(b->gfork[k]);
+    }
     for (auto& e : b->exec)
         if (e) cudaGraphExecDestroy(e);
     if (b->cap) cudaStreamDestroy(b->cap);
 }
 
+// One sweep of every group with tiles, each group's launches issued by launch(gi, stream): on
+// the caller's stream s when at most one group has tiles, else concurrently on the groups'
+// streams of stream set `set`, forked from s and joined back into it (both also under graph
+// capture, where the fork and join become the graph's branches).
+template <typename F>
+msqoc_status for_groups(msqoc_batch* b, const int* ntiles, int set, cudaStream_t s, F&& launch) {
+    const int ng = static_cast<int>(b->groups.size());
+    int active = 0;
+    for (int gi = 0; gi < ng; ++gi) active += ntiles[gi] > 0;
+    if (active <= 1 || b->gstream[set].empty()) {
+        for (int gi = 0; gi < ng; ++gi)
+            if (ntiles[gi] > 0) CUDA_TRY(launch(gi, s));
+        return MSQOC_OK;
+    }
+    CUDA_TRY(cudaEventRecord(b->gfork[set], s));
+    for (int gi = 0; gi < ng; ++gi) {
+        if (ntiles[gi] <= 0) continue;
+        cudaStream_t gs = b->gstream[set][gi];
+        CUDA_TRY(cudaStreamWaitEvent(gs, b->gfork[set], 0));
+        CUDA_TRY(launch(gi, gs));
+        CUDA_TRY(cudaEventRecord(b->gjoin[set][gi], gs));
+        CUDA_TRY(cudaStreamWaitEvent(s, b->gjoin[set][gi], 0));
+    }
+    return MSQOC_OK;
+}
+
 // The launch sequence of one batched evaluation of the problems `sel` (all when sel is empty);
-// tiles[g] / ntiles[g] are the tiles of group g to launch.
+// tiles[g] / ntiles[g] are the tiles of group g to launch; set: the stream set of the groups.
 msqoc_status enqueue(msqoc_batch* b, const std::vector<msqoc_problem*>& sel, Tile* const* tiles, const int* ntiles,
-                     bool grad, cudaStream_t s) {
+                     bool grad, int set, cudaStream_t s) {
     msqoc_status st;
     for (msqoc_problem* p : sel)
         if ((st = launch_controls(p, s))) return st;
-    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    st = for_groups(b, ntiles, set, s, [&](int gi, cudaStream_t gs) {
         SweepArgs a = b->groups[gi].args;
         a.tiles = tiles[gi];
         a.mode = grad ? SWEEP_HISTORY : SWEEP_OBJECTIVE;
         a.seg = 0;
-        CUDA_TRY(launch_sweep(a, ntiles[gi], s));
-    }
+        return launch_sweep(a, ntiles[gi], gs);
+    });
+    if (st) return st;
     for (msqoc_problem* p : sel)
         if ((st = launch_terminal(p, grad, s))) return st;
     if (!grad) {
@@ -82,7 +124,7 @@ msqoc_status enqueue(msqoc_batch* b, const std::vector<msqoc_problem*>& sel, Til
         }
         return MSQOC_OK;
     }
-    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    st = for_groups(b, ntiles, set, s, [&](int gi, cudaStream_t gs) {
         const auto& g = b->groups[gi];
         for (int seg = g.nseg_max - 1; seg >= 0; --seg) {
             SweepArgs a = g.args;
@@ -90,12 +132,16 @@ msqoc_status enqueue(msqoc_batch* b, const std::vector<msqoc_problem*>& sel, Til
             a.seg = seg;
             if (g.nseg_max > 1) {
                 a.mode = SWEEP_RECOMPUTE;
-                CUDA_TRY(launch_sweep(a, ntiles[gi], s));
+                const cudaError_t e = launch_sweep(a, ntiles[gi], gs);
+                if (e != cudaSuccess) return e;
             }
             a.mode = SWEEP_ADJOINT;
-            CUDA_TRY(launch_sweep(a, ntiles[gi], s));
+            const cudaError_t e = launch_sweep(a, ntiles[gi], gs);
+            if (e != cudaSuccess) return e;
         }
-    }
+        return cudaSuccess;
+    });
+    if (st) return st;
     for (msqoc_problem* p : sel) {
         const OutLayout ol = out_layout(p->pd.M, p->pd.d, p->nW);
         double* o = p->out_dev;
@@ -111,7 +157,7 @@ msqoc_status enqueue_all(msqoc_batch* b, bool grad, cudaStream_t s) {
         tiles.push_back(g.tiles);
         ntiles.push_back(g.ntiles);
     }
-    return enqueue(b, b->probs, tiles.data(), ntiles.data(), grad, s);
+    return enqueue(b, b->probs, tiles.data(), ntiles.data(), grad, MSQOC_BATCH_SLOTS, s);
 }
 
 msqoc_status eval(msqoc_batch* b, bool grad, cudaStream_t s) {
@@ -174,11 +220,12 @@ msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t fla
         for (msqoc_problem* p : b->probs)
             if (!st) st = ensure_gradient_buffers(p, nullptr);
     if (!st && cudaDeviceSynchronize() != cudaSuccess) st = fail(MSQOC_ERR_CUDA, "synchronize failed");
-    // groups by (levels, subsystems, solver)
+    // groups by (levels, subsystems, solver, kernel family, tile threads)
     for (int i = 0; i < n && !st; ++i) {
         const ProbDev& pd = b->probs[i]->pd;
         auto it = std::find_if(b->groups.begin(), b->groups.end(), [&](const msqoc_batch::Group& g) {
-            return g.L == pd.L && g.q == pd.q && g.solver == pd.solver && g.pair == pd.pair;
+            return g.L == pd.L && g.q == pd.q && g.solver == pd.solver && g.pair == pd.pair &&
+                   g.nthreads == pd.nthreads;
         });
         if (it == b->groups.end()) {
             b->groups.emplace_back();
@@ -187,6 +234,7 @@ msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t fla
             it->q = pd.q;
             it->solver = pd.solver;
             it->pair = pd.pair;
+            it->nthreads = pd.nthreads;
         }
         it->members.push_back(i);
     }
@@ -272,6 +320,18 @@ msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t fla
     for (int k = 0; k < MSQOC_BATCH_SLOTS && !st; ++k)
         if (cudaEventCreateWithFlags(&b->slot_done[k], cudaEventDisableTiming) != cudaSuccess)
             st = fail(MSQOC_ERR_CUDA, "event creation failed");
+    // the groups' streams and events (several groups only)
+    const size_t ng = b->groups.size();
+    for (int k = 0; k <= MSQOC_BATCH_SLOTS && !st && ng > 1; ++k) {
+        b->gstream[k].assign(ng, nullptr);
+        b->gjoin[k].assign(ng, nullptr);
+        cudaError_t e = cudaEventCreateWithFlags(&b->gfork[k], cudaEventDisableTiming);
+        for (size_t gi = 0; gi < ng && e == cudaSuccess; ++gi) {
+            e = cudaStreamCreateWithFlags(&b->gstream[k][gi], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->gjoin[k][gi], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) st = fail(MSQOC_ERR_CUDA, "group streams: %s", cudaGetErrorString(e));
+    }
     if (st) return st;
     *out = b;
     owner.b = nullptr;
@@ -317,7 +377,7 @@ msqoc_status batch_eval_subset(msqoc_batch* b, const int32_t* members, int32_t n
         ntiles[gi] = cnt;
     }
     CUDA_TRY(cudaEventRecord(b->slot_done[slot], s));
-    return enqueue(b, sel, tiles.data(), ntiles.data(), gradient != 0, s);
+    return enqueue(b, sel, tiles.data(), ntiles.data(), gradient != 0, slot, s);
 }
 
 }  // namespace
