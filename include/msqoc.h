@@ -100,7 +100,7 @@ typedef struct msqoc_options {
     int32_t solver;        /* MSQOC_SOLVER_* */
     int32_t col_block;     /* columns per sweep tile (1 <= col_block <= E; col_block N/L <= 256
                               threads with one thread per fiber, 2 col_block N/L <= 384 with
-                              lane pairs, 4 col_block N/L <= 512 with lane quads; tiles run
+                              lane pairs, 4 col_block N/L <= 384 with lane quads; tiles run
                               along the window-major column list and may cover two windows; a
                               one-warp tile must divide E); 0 = automatic */
     int32_t ckpt_interval; /* K: forward states kept for the adjoint sweep.  1 = every midpoint

@@ -13,7 +13,7 @@ constexpr int MAXNF = 64;     // carriers over all subsystems
 constexpr int MAXL = 4;       // levels per subsystem handled by the sweep kernels
 constexpr int MAX_TILE_THREADS = 256;       // threads of a one-thread-per-fiber tile (255 registers a thread)
 constexpr int MAX_PAIR_TILE_THREADS = 384;  // threads of a lane-pair tile (168 registers a thread)
-constexpr int MAX_QUAD_TILE_THREADS = 512;  // threads of a lane-quad tile (128 registers a thread)
+constexpr int MAX_QUAD_TILE_THREADS = 384;  // threads of a lane-quad tile (168 registers a thread)
 
 enum Solver { SOLVER_FP64 = 1, SOLVER_MIXED = 2 };
 

@@ -14,7 +14,8 @@
 // per fiber, a lane pair per entry of the fiber (lanes 4i + 2e and 4i + 2e + 1 own entry e).
 // Each thread then computes one component of one entry, half of a lane pair's work; the
 // entry the pair does not hold (the in-fiber ladder term) is read from the shared buffer like
-// any neighbour.  Tiles of up to 512 threads.
+// any neighbour.  Tiles of up to 384 threads, like lane pairs (at 512 threads the 128-register
+// budget cost the adjoint 2-4%).
 #pragma once
 
 #include "msqoc_sweep_common.cuh"
