@@ -142,21 +142,20 @@ __device__ __forceinline__ void apply_off_pair(const T2* __restrict__ buf, const
         }
     }
     // exchange-coupled problems are 2-level qubit models (the only shapes compiled with it):
-    // w += (i (h/2) J x_src)_p from the fiber's precomputed sources, or the general form
+    // w += (i (h/2) J x_src)_p from the fiber's precomputed sources (a zero entry where a pair
+    // gives an entry no term), or, lane pairs only, the general form beyond MAXEXF pairs
     if constexpr (L == 2 && Q >= 2) {
-        if (SPLIT == 1 && pd.nex > MAXEXF) {
+        bool general = false;
+        if constexpr (SPLIT == 1) general = pd.nex > MAXEXF;
+        if (general) {
             if constexpr (SPLIT == 1) apply_exchange_pair<L, Q, R>(bb, pd, fb.f, fb.xo, p, w);
         } else if (pd.nex) {
 #pragma unroll
             for (int e = 0; e < MAXEXF; ++e) {
                 if (e >= pd.nex) break;                        // warp-uniform
                 const R c = static_cast<R>(p ? pd.ex_c[e] : -pd.ex_c[e]);
-                if constexpr (SPLIT == 1) {
 #pragma unroll
-                    for (int l = 0; l < L; ++l) w[l] += c * bb[2 * fb.exs[e][l]];   // zero entry where no term
-                } else {
-                    w[0] += c * bb[2 * exo[e]];
-                }
+                for (int l = 0; l < LS; ++l) w[l] += c * bb[2 * (SPLIT == 1 ? fb.exs[e][l] : exo[e])];
             }
         }
     }
