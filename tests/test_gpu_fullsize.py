@@ -63,3 +63,29 @@ def test_fullsize_5q_sampled_windows_and_directional_derivatives():
     tol_w = 1e-6 * abs(gw_v) + 16 * np.finfo(float).eps * abs(got["P"]) / eps_w
     assert abs(fd_a - ga_v) <= tol_a, (fd_a, ga_v)
     assert abs(fd_w - gw_v) <= tol_w, (fd_w, gw_v)
+
+
+@pytest.mark.parametrize("K", [64, 512])
+def test_fullsize_4q_checkpoint_intervals_at_128_windows(K):
+    """The 4-transmon workload at 128 windows (781-782 steps each) with checkpoint interval K
+    (64: 13 segments per window; 512: a long and a short segment): every output equals the
+    K = 1 evaluation (the recomputed segments repeat the same arithmetic), and the last two
+    windows match the oracle (J, pen_127, dP/dW^127)."""
+    spec = S.config_4q(M=128)
+    alpha, W = S.random_alpha(spec, 4), S.random_W(spec, 4)
+    M = spec.M
+    with msqoc.Problem(spec, ckpt_interval=1) as p1:
+        ref = p1.eval_gradient(alpha, W)
+    with msqoc.Problem(spec, ckpt_interval=K) as pk:
+        assert pk.ckpt_interval == K
+        got = pk.eval_gradient(alpha, W)
+        obj = pk.eval_objective(alpha, W)
+    assert_objective_close(got["P"], ref["P"])
+    assert_grad_close(got["grad_alpha"], ref["grad_alpha"], what=f"grad_alpha (K={K} vs 1)")
+    assert_grad_close(got["grad_W"], ref["grad_W"], what=f"grad_W (K={K} vs 1)")
+    want = oracle.evaluate(spec, alpha, W, windows=(M - 1, M), nthreads=os.cpu_count())
+    assert_objective_close(obj["J"], want["J"])
+    np.testing.assert_allclose(obj["pen"][M - 2], want["pen"][M - 2], rtol=1e-12, atol=0)
+    ne2 = 2 * spec.N * spec.E
+    sl = slice((M - 2) * ne2, (M - 1) * ne2)
+    assert_grad_close(got["grad_W"][sl], want["grad_W"][sl], what="grad_W^{M-1}")
