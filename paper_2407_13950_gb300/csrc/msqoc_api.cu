@@ -646,6 +646,12 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
         A(cudaMemset(p->W_dev, 0, std::max<size_t>(p->nW, 2) * sizeof(double)), "W init");
         A(cudaMemset(p->status, 0, sizeof(int)), "status init");
         A(cudaMemcpy(p->pds, &pd, sizeof(ProbDev), cudaMemcpyHostToDevice), "problem record copy");
+        // the carrier phase table: a constant of the time grid, filled once
+        if (st == MSQOC_OK) {
+            k_phases<<<phase_blocks(pd), 256>>>(pd);
+            A(cudaGetLastError(), "phase table");
+            A(cudaDeviceSynchronize(), "phase table");
+        }
     }
     if (st != MSQOC_OK) return st;
     p->bytes = sizeof(double2) * (N + p->ne * (1 + 3 * M) + size_t(nsteps) * (q + nfsum)) +
@@ -738,6 +744,11 @@ msqoc_status sweep(msqoc_problem* p, int mode, int seg, cudaStream_t s) {
     const SweepArgs a = sweep_args(p->pd, p->pds, p->tiles, p->lanemap, mode, seg);
     CUDA_TRY(launch_sweep(a, p->pd.ntiles, s));
     return MSQOC_OK;
+}
+
+// blocks of 256 threads for the phase table (grid-stride loop)
+int phase_blocks(const ProbDev& pd) {
+    return static_cast<int>(std::min<int64_t>((pd.nsteps * pd.nfsum + 255) / 256, 4096));
 }
 
 msqoc_status launch_controls(msqoc_problem* p, cudaStream_t s) {
@@ -1240,6 +1251,8 @@ extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H,
     {
         const int threads = 256;
         const int blocks = static_cast<int>(std::min<int64_t>((pd.nsteps + threads - 1) / threads, 4096));
+        k_phases<<<phase_blocks(pd), threads, 0, s>>>(pd);
+        CUDA_TRY(cudaGetLastError());
         k_controls<<<blocks, threads, 0, s>>>(pd);
         CUDA_TRY(cudaGetLastError());
     }

@@ -74,8 +74,9 @@ __device__ __forceinline__ SplineAt spline_at(const ProbDev& pd, double t) {
 
 // Controls at every step midpoint t_{n+1/2} = (n + 1/2) h (Eq. dj-ctrl with the quadratic
 // B-spline envelope of Sec. 2): d_k(t) = sum_f e^{i Omega_kf t} sum_s (a1 + i a2)_kfs B_s(t),
-// and the step solver's iteration counts (step_counts).  Also stores the spline weights and
-// the carrier phases for the gradient quadrature of the adjoint sweep.
+// and the step solver's iteration counts (step_counts).  Also stores the spline weights for the
+// gradient quadrature of the adjoint sweep.  The carrier phases come from the problem's phase
+// table (k_phases).
 __global__ void k_controls(const ProbDev pd) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; n < pd.nsteps; n += stride) {
@@ -85,9 +86,8 @@ __global__ void k_controls(const ProbDev pd) {
         for (int k = 0; k < pd.q; ++k) {
             double2 dk = make_double2(0.0, 0.0);
             for (int fi = pd.cof[k]; fi < pd.cof[k + 1]; ++fi) {
-                double sn, cs;
-                sincos(pd.omega[fi] * t, &sn, &cs);
-                pd.phase[size_t(n) * pd.nfsum + fi] = make_double2(cs, sn);
+                const double2 ph = pd.phase[size_t(n) * pd.nfsum + fi];
+                const double cs = ph.x, sn = ph.y;
                 const double* a = pd.alpha + (size_t(fi) * pd.d1 + sp.s0) * 2;
                 const double er = a[0] * sp.w0 + a[2] * sp.w1 + a[4] * sp.w2;
                 const double ei = a[1] * sp.w0 + a[3] * sp.w1 + a[5] * sp.w2;
@@ -99,6 +99,23 @@ __global__ void k_controls(const ProbDev pd) {
         }
         const float rho = float(0.5 * pd.h * pd.lam * mag + pd.rho_ex) * 1.0001f;
         pd.spl[n] = Spline4{sp.s0, step_counts(pd.solver, rho), sp.w0, sp.w1, sp.w2};
+    }
+}
+
+// The carrier phases e^{i Omega_f t} at every step midpoint t_{n+1/2} = (n + 1/2) h: they
+// depend on the time grid and the carriers only, so the table is filled once per problem
+// (per call for the allocation-free objective) and read by the controls, the adjoint's gradient
+// quadrature and the regularization.
+__global__ void k_phases(const ProbDev pd) {
+    const int64_t total = pd.nsteps * pd.nfsum;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const int64_t n = i / pd.nfsum;
+        const int fi = static_cast<int>(i - n * pd.nfsum);
+        const double t = (double(n) + 0.5) * pd.h;
+        double sn, cs;
+        sincos(pd.omega[fi] * t, &sn, &cs);
+        pd.phase[i] = make_double2(cs, sn);
     }
 }
 
@@ -240,8 +257,8 @@ __global__ void __launch_bounds__(REG_THREADS) k_regularization(const ProbDev pd
             if (j < 0 || j > 2 || (fi < pd.cof[k] && j != 0)) continue;
             double2 dk = make_double2(0.0, 0.0), ph = make_double2(0.0, 0.0);
             for (int g = pd.cof[k]; g < pd.cof[k + 1]; ++g) {
-                double sn, cs;
-                sincos(pd.omega[g] * t, &sn, &cs);
+                const double2 pg = pd.phase[size_t(n) * pd.nfsum + g];   // the problem's phase table
+                const double cs = pg.x, sn = pg.y;
                 const double* a = alpha + (size_t(g) * pd.d1 + sp.s0) * 2;
                 const double er = a[0] * sp.w0 + a[2] * sp.w1 + a[4] * sp.w2;
                 const double ei = a[1] * sp.w0 + a[3] * sp.w1 + a[5] * sp.w2;

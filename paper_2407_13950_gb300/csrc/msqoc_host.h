@@ -101,6 +101,7 @@ OutLayout out_layout(int M, int d, size_t nW);
 // steps of an evaluation of one problem (stream-ordered)
 msqoc_status stage_inputs(msqoc_problem* p, const double* alpha, const double* W, cudaStream_t s);
 msqoc_status ensure_gradient_buffers(msqoc_problem* p, cudaStream_t s);
+int phase_blocks(const ProbDev& pd);   // blocks of 256 threads for k_phases
 msqoc_status launch_controls(msqoc_problem* p, cudaStream_t s);
 msqoc_status launch_terminal(msqoc_problem* p, bool want_lambda, cudaStream_t s);
 // P, J (may be NULL), pen (may be NULL) of the last forward sweep into device arrays
