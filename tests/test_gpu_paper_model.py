@@ -77,6 +77,15 @@ def test_qft8_lane_quad_tile_widths(cb):
               solver=msqoc.SOLVER_FP64)
 
 
+@pytest.mark.parametrize("q", [1, 2, 5, 6])
+def test_two_level_shapes_every_family(q):
+    """2-level subsystems at the edges of the compiled shapes: one qubit (one fiber a column, no
+    neighbour subsystems), two, and five and six qubits (32 and 64 fibers a column, quads of up to
+    256 threads a column); anharmonic transmon-style drift, cross-Kerr, no exchange."""
+    spec = S.transmon_spec(q, 6.0, 240, 3, 5, L=2, ness=2)
+    check(spec, 95 + q)
+
+
 def test_lane_quads_rejected_where_not_admitted():
     """Lane quads serve 2-level subsystems with at most 6 exchange-coupled pairs."""
     three_levels = S.transmon_spec(2, 10.0, 100, 2, 5)
