@@ -222,8 +222,8 @@ bool quad_admitted(const ProbDev& pd) { return pd.L == 2 && pd.nex <= MAXEXF; }
 // Tiles that do not fit at once run in waves of the CTAs an SM holds (the kernels'
 // occupancy at that width).  A tile over two windows pays a second gradient reduction and wider
 // class mixing in its warps: its cost is taken 1.18x (measured on the 4-transmon tiles: the
-// adjoint 9% slower, the forward 3% faster than 8-column one-window tiles, where the warp count
-// alone predicts both 14% faster).  Candidates are ranked by
+// adjoint 8% slower, the forward 3% faster than 8-column one-window tiles, where the warp count
+// alone predicts both 14% faster; at 6-7 warps per SM those steps are latency-bound).  Candidates are ranked by
 //   1. the makespan: an SM's ceil(tiles / SMs) tiles in waves of `resident`, summed over the
 //      waves;
 //   2. tiles that stay inside one window;

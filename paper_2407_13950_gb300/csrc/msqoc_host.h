@@ -82,7 +82,7 @@ msqoc_status guarded(F&& f) noexcept {
 
 // tile layout (see msqoc_api.cu)
 void build_lanemap(int L, int q, int ncol, int ncol0, int nthreads, int pair, int* out);
-// kernel family (pair: 1 = a lane pair per fiber) and columns per tile of a problem
+// kernel family (pair: log2 of the threads per fiber, 0, 1 or 2) and columns per tile of a problem
 struct TileChoice {
     int cpt, pair;
 };

@@ -1,7 +1,8 @@
-// Pieces shared by the two sweep kernel families (msqoc_sweep.cuh: one thread per fiber;
-// msqoc_sweep_pair.cuh: a lane pair per fiber): precision conversions, 1D bulk async copies
-// and bounded mbarrier waits, the per-thread neighbour lists, the shared-memory layout and
-// the tile barrier.
+// Pieces shared by the sweep kernel families (msqoc_sweep.cuh: one thread per fiber;
+// msqoc_sweep_pair.cuh: a lane pair, or for 2-level subsystems a lane quad, per fiber):
+// precision conversions, 1D bulk async copies and bounded mbarrier waits, the per-thread
+// neighbour lists, the shared-memory layout, the tile barrier, the spline origin of a window
+// and the write-out of a tile's gradient partial.
 #pragma once
 
 #include <cstdint>
