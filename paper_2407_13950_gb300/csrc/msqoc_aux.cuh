@@ -238,6 +238,9 @@ constexpr int REG_THREADS = 256;
 //   dR/d alpha2_kfs = gamma_tik alpha2_kfs - 2 gamma_energy (h/T) sum_n B Im(conj(d_k) e^{i Omega_kf t}),
 // and the block's share of the energy, (h/T) sum |d_k|^2 over the steps whose first active
 // spline is s (each step is counted by exactly one block per k).  Every sum has a fixed order.
+// A pass over the steps evaluates d_k once per step and accumulates the energy and up to
+// REG_CHUNK carriers' sums (the paper's subsystems have 2-3 carriers: one pass).
+constexpr int REG_CHUNK = 4;
 __global__ void __launch_bounds__(REG_THREADS) k_regularization(const ProbDev pd, const double* alpha,
                                                                  double gamma_tik, double gamma_energy,
                                                                  double* grad, double* epart) {
@@ -248,15 +251,22 @@ __global__ void __launch_bounds__(REG_THREADS) k_regularization(const ProbDev pd
     const double r = pd.dtau / pd.h;
     const int64_t lo = max(int64_t(0), int64_t(floor((s - 2) * r - 0.5)) - 2);
     const int64_t hi = min(pd.nsteps, int64_t(ceil((s + 1) * r)) + 2);
-    for (int fi = pd.cof[k] - 1; fi < pd.cof[k + 1]; ++fi) {   // fi = cof[k] - 1: the energy
-        double acc_re = 0.0, acc_im = 0.0;
+    const int f0 = pd.cof[k], nfk = pd.cof[k + 1] - f0;
+    const double wt = pd.h / pd.T;   // midpoint weight of the time average
+    for (int c0 = 0; c0 < nfk; c0 += REG_CHUNK) {   // carriers f0 + c0 .. f0 + c0 + REG_CHUNK - 1
+        double are[REG_CHUNK], aim[REG_CHUNK], en = 0.0;
+#pragma unroll
+        for (int c = 0; c < REG_CHUNK; ++c) are[c] = aim[c] = 0.0;
         for (int64_t n = lo + threadIdx.x; n < hi; n += REG_THREADS) {
             const double t = (double(n) + 0.5) * pd.h;
             const SplineAt sp = spline_at(pd, t);
             const int j = s - sp.s0;
-            if (j < 0 || j > 2 || (fi < pd.cof[k] && j != 0)) continue;
-            double2 dk = make_double2(0.0, 0.0), ph = make_double2(0.0, 0.0);
-            for (int g = pd.cof[k]; g < pd.cof[k + 1]; ++g) {
+            if (j < 0 || j > 2) continue;
+            double2 dk = make_double2(0.0, 0.0);
+            double2 ph[REG_CHUNK];
+#pragma unroll
+            for (int c = 0; c < REG_CHUNK; ++c) ph[c] = make_double2(0.0, 0.0);
+            for (int g = f0; g < f0 + nfk; ++g) {
                 const double2 pg = pd.phase[size_t(n) * pd.nfsum + g];   // the problem's phase table
                 const double cs = pg.x, sn = pg.y;
                 const double* a = alpha + (size_t(g) * pd.d1 + sp.s0) * 2;
@@ -264,25 +274,29 @@ __global__ void __launch_bounds__(REG_THREADS) k_regularization(const ProbDev pd
                 const double ei = a[1] * sp.w0 + a[3] * sp.w1 + a[5] * sp.w2;
                 dk.x += cs * er - sn * ei;
                 dk.y += cs * ei + sn * er;
-                if (g == fi) ph = make_double2(cs, sn);
+#pragma unroll
+                for (int c = 0; c < REG_CHUNK; ++c)
+                    if (g == f0 + c0 + c) ph[c] = pg;
             }
-            if (fi < pd.cof[k]) {
-                acc_re += dk.x * dk.x + dk.y * dk.y;
-            } else {
-                const double B = j == 0 ? sp.w0 : (j == 1 ? sp.w1 : sp.w2);
-                // conj(d_k) e^{i Omega t}
-                acc_re += B * (dk.x * ph.x + dk.y * ph.y);
-                acc_im += B * (dk.x * ph.y - dk.y * ph.x);
+            if (c0 == 0 && j == 0) en += dk.x * dk.x + dk.y * dk.y;
+            const double B = j == 0 ? sp.w0 : (j == 1 ? sp.w1 : sp.w2);
+#pragma unroll
+            for (int c = 0; c < REG_CHUNK; ++c) {   // conj(d_k) e^{i Omega t}
+                are[c] += B * (dk.x * ph[c].x + dk.y * ph[c].y);
+                aim[c] += B * (dk.x * ph[c].y - dk.y * ph[c].x);
             }
         }
-        const double sre = block_sum<REG_THREADS>(acc_re, sh);
-        const double sim = block_sum<REG_THREADS>(acc_im, sh);
-        if (threadIdx.x == 0) {
-            const double wt = pd.h / pd.T;   // midpoint weight of the time average
-            if (fi < pd.cof[k]) {
-                epart[blockIdx.x] = wt * sre;
-            } else {
-                const size_t i = (size_t(fi) * pd.d1 + s) * 2;
+        if (c0 == 0) {
+            const double se = block_sum<REG_THREADS>(en, sh);
+            if (threadIdx.x == 0) epart[blockIdx.x] = wt * se;
+        }
+#pragma unroll
+        for (int c = 0; c < REG_CHUNK; ++c) {
+            if (c0 + c >= nfk) break;                  // block-uniform
+            const double sre = block_sum<REG_THREADS>(are[c], sh);
+            const double sim = block_sum<REG_THREADS>(aim[c], sh);
+            if (threadIdx.x == 0) {
+                const size_t i = (size_t(f0 + c0 + c) * pd.d1 + s) * 2;
                 grad[i] = gamma_tik * alpha[i] + 2.0 * gamma_energy * wt * sre;
                 grad[i + 1] = gamma_tik * alpha[i + 1] - 2.0 * gamma_energy * wt * sim;
             }
