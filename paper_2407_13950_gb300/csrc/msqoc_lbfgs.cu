@@ -12,19 +12,27 @@ namespace {
 
 constexpr int LB_THREADS = 1024;
 
-// sum of v over the block in a fixed order (every thread gets the result)
+// sum of v over the block in a fixed order (every thread gets the result): an xor butterfly in
+// each warp (lanes i and i ^ o add the same two values, so every lane ends with the same sum),
+// then the same over the warps' sums.  sh: at least 33 doubles.
 __device__ double lb_block_sum(double v, double* sh) {
-    const int t = threadIdx.x;
-    sh[t] = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w] = v;
     __syncthreads();
-    for (int o = LB_THREADS / 2; o > 0; o >>= 1) {
-        if (t < o) sh[t] += sh[t + o];
-        __syncthreads();
+    if (w == 0) {
+        double r = sh[lane];   // LB_THREADS / 32 = 32 warps
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if (lane == 0) sh[32] = r;
     }
-    const double r = sh[0];
     __syncthreads();
+    const double r = sh[32];
+    __syncthreads();   // sh is reused by the next sum
     return r;
 }
+static_assert(LB_THREADS == 1024, "lb_block_sum reduces 32 warps");
 
 // x_i at a bound with the gradient pushing it outward (held fixed for the iteration)
 __device__ __forceinline__ bool lb_active(int64_t i, int64_t nb, const double* x, const double* g,
@@ -52,9 +60,11 @@ __global__ void __launch_bounds__(LB_THREADS) k_lbfgs_direction(int64_t n, int64
         const double* Sj = S + size_t(s) * n;
         const double* Yj = Y + size_t(s) * n;
         double acc = 0.0;
+#pragma unroll 4
         for (int64_t i = t; i < n; i += LB_THREADS) acc += Sj[i] * d[i];
         const double a = rho[s] * lb_block_sum(acc, sh);
         if (t == 0) alpha_s[j] = a;
+#pragma unroll 4
         for (int64_t i = t; i < n; i += LB_THREADS) d[i] -= a * Yj[i];
         __syncthreads();
     }
@@ -64,6 +74,7 @@ __global__ void __launch_bounds__(LB_THREADS) k_lbfgs_direction(int64_t n, int64
         gamma = (1.0 / rho[s]) / yy[s];   // <s, y> / <y, y> of the newest pair
     } else {
         double acc = 0.0;
+#pragma unroll 4
         for (int64_t i = t; i < n; i += LB_THREADS) acc += d[i] * d[i];
         gamma = 1.0 / fmax(sqrt(lb_block_sum(acc, sh)), 1e-300);   // first step: unit length
     }
@@ -74,8 +85,10 @@ __global__ void __launch_bounds__(LB_THREADS) k_lbfgs_direction(int64_t n, int64
         const double* Sj = S + size_t(s) * n;
         const double* Yj = Y + size_t(s) * n;
         double acc = 0.0;
+#pragma unroll 4
         for (int64_t i = t; i < n; i += LB_THREADS) acc += Yj[i] * d[i];
         const double c = alpha_s[j] - rho[s] * lb_block_sum(acc, sh);
+#pragma unroll 4
         for (int64_t i = t; i < n; i += LB_THREADS) d[i] += c * Sj[i];
         __syncthreads();
     }
