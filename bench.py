@@ -325,7 +325,7 @@ def run_batched(args):
     specs = S.mixed_batch_specs(seed=1, n_per_shape=args.batch_per_shape,
                                 shapes=[S.config_2q(), S.config_3q(), S.config_4q()])
     nprob = len(specs)
-    probs = [msqoc.Problem(sp) for sp in specs]
+    probs = [msqoc.Problem(sp, layout=LAYOUTS[args.layout]) for sp in specs]
     host_in = [(S.random_alpha(sp, 1, problem=i), S.random_W(sp, 1, problem=i)) for i, sp in enumerate(specs)]
     dev_in = [(torch.tensor(a, device=dev, dtype=torch.float64), torch.tensor(W, device=dev, dtype=torch.float64))
               for a, W in host_in]
