@@ -232,8 +232,9 @@ __device__ __forceinline__ double part_reduce_scatter(double (&acc)[VH], int lan
 // One CTA per tile.  A tile covers one or two windows ("slots"); each slot has its own step
 // range, per-step coefficients, iteration counts and gradient fold, computed by warp `slot`
 // (the host only builds two-slot tiles with at least two warps).  Loops run to the longer of
-// the slots' ranges; a thread whose slot has no step at an iteration keeps its state.  Two
-// threads (a pair, parts 0 and 1) work on each (column, fiber).
+// the slots' ranges; a thread whose slot has no step at an iteration keeps its state.  A lane
+// pair (parts 0 and 1) works on each (column, fiber) for SPLIT = 1, on each of its entries for
+// SPLIT = 2 (lane quads).
 template <int L, int Q, int SOLVER, bool BWD, bool ROLLOUT = false, int SPLIT = 1>
 __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_TILE_THREADS, 1)
     k_sweep_pair(const SweepArgs a) {
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
 
     // ---- this thread's fiber (the threads of a pair, or quad, read the same entry)
     const int lm = a.lanemap[tile.map * static_cast<int>(blockDim.x) + tid];
-    const bool act = lm >= 0;                       // idle pairs mirror an active one, store nothing
+    const bool act = lm >= 0;                       // idle lanes mirror an active unit, store nothing
     const int lmv = act ? lm : ~lm;
     const int c = lmv >> 16;                        // tile column
     const int f = lmv & 0xffff;                     // fiber
