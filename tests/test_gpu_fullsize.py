@@ -16,19 +16,55 @@ from gpu_helpers import assert_grad_close, assert_objective_close
 pytestmark = pytest.mark.gpu
 
 
+_ORACLE = {}
+
+
+def oracle_4q(M):
+    """The oracle's full evaluation of the 4-transmon workload (seed 1), computed once per M."""
+    if M not in _ORACLE:
+        spec = S.config_4q(M=M)
+        alpha, W = S.random_alpha(spec, 1), S.random_W(spec, 1)
+        _ORACLE[M] = (spec, alpha, W, oracle.evaluate(spec, alpha, W, nthreads=os.cpu_count()))
+    return _ORACLE[M]
+
+
 @pytest.mark.parametrize("M", [64, 256])
 def test_fullsize_4q(M):
-    spec = S.config_4q(M=M)
-    alpha, W = S.random_alpha(spec, 1), S.random_W(spec, 1)
+    spec, alpha, W, want = oracle_4q(M)
     with msqoc.Problem(spec) as p:
         got = p.eval_gradient(alpha, W)
         obj = p.eval_objective(alpha, W)
-    want = oracle.evaluate(spec, alpha, W, nthreads=os.cpu_count())
     assert_objective_close(got["P"], want["P"])
     assert_objective_close(obj["J"], want["J"])
     np.testing.assert_allclose(obj["pen"], want["pen"], rtol=1e-12, atol=0)
     assert_grad_close(got["grad_alpha"], want["grad_alpha"], what="grad_alpha")
     assert_grad_close(got["grad_W"], want["grad_W"], what="grad_W")
+
+
+def test_fullsize_4q_fp64_solver():
+    """The pure-FP64 fixed-point step solver on the full 4-transmon workload at 64 windows,
+    against the complete oracle."""
+    spec, alpha, W, want = oracle_4q(64)
+    with msqoc.Problem(spec, solver=msqoc.SOLVER_FP64) as p:
+        got = p.eval_gradient(alpha, W)
+    assert_objective_close(got["P"], want["P"])
+    assert_grad_close(got["grad_alpha"], want["grad_alpha"], what="grad_alpha")
+    assert_grad_close(got["grad_W"], want["grad_W"], what="grad_W")
+
+
+def test_fullsize_5q_every_midpoint_kept_equals_checkpointed():
+    """The 5-transmon workload with every midpoint state kept (K = 1: an 18.7 GB history) and
+    with checkpoint interval 64: the same arithmetic, so the same outputs."""
+    spec = S.config_5q()
+    alpha, W = S.random_alpha(spec, 3), S.random_W(spec, 3)
+    with msqoc.Problem(spec, ckpt_interval=1) as p1:
+        assert p1.ckpt_interval == 1
+        g1 = p1.eval_gradient(alpha, W)
+    with msqoc.Problem(spec, ckpt_interval=64) as p64:
+        g64 = p64.eval_gradient(alpha, W)
+    assert_objective_close(g1["P"], g64["P"])
+    assert_grad_close(g1["grad_alpha"], g64["grad_alpha"], what="grad_alpha (K=1 vs 64)")
+    assert_grad_close(g1["grad_W"], g64["grad_W"], what="grad_W (K=1 vs 64)")
 
 
 def test_fullsize_5q_sampled_windows_and_directional_derivatives():
