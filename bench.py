@@ -3,7 +3,7 @@
 
 Workload: 4 transmons x 3 levels (N=81 rows, E=16 essential columns), all-pair cross-Kerr,
 2 carriers per transmon with 40 B-spline coefficients each (d=640), QFT_16 target,
-T=600 ns, 100000 implicit-midpoint steps, M windows (default 64), seeded synthetic controls
+T=600 ns, 100000 implicit-midpoint steps, M windows (default 256), seeded synthetic controls
 and non-unitary window states.  A step of this benchmark is one full evaluation
 (controls, forward sweep of every window, terminal conditions, adjoint sweep with the fused
 gradient, reductions).  The midpoint-state history (2 GB) is far larger than L2, so no L2
@@ -99,29 +99,31 @@ class ClockSampler:
 
 SWEEP_SOURCES = ["msqoc_sweep.cuh", "msqoc_sweep_pair.cuh", "msqoc_sweep_common.cuh", "inst_sweep.cu",
                  "msqoc_internal.h"]
-PROFILE = os.path.join(ROOT, "profiles", "k_sweep_4q_small_full.md")
+PROFILES = os.path.join(ROOT, "profiles")
 LAYOUTS = {"auto": 0, "fiber": 1, "pair": 2, "quad": 3}
 
 
-def sweep_traffic(kernel: str):
-    """DRAM bytes per launch of a sweep kernel from the committed ncu summary, or None when the
-    kernel sources changed since that capture (their digest differs)."""
+def sweep_traffic(kernel: str, windows: int, col_block: int, layout: int):
+    """DRAM bytes per launch of a sweep kernel from the committed ncu summary of the same tiles
+    (a `capture_config:` line naming windows, columns per tile and kernel family), or None when
+    there is none or the kernel sources changed since that capture (their digest differs)."""
+    import glob
     import hashlib
     import re
-    try:
-        text = open(PROFILE).read()
-    except OSError:
-        return None
     h = hashlib.sha256()
     for fn in SWEEP_SOURCES:
         h.update(fn.encode())
         with open(os.path.join(ROOT, "paper_2407_13950_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
-    m = re.search(r"sources_sha256: ([0-9a-f]+)", text)
-    t = re.search(rf"{kernel}=([0-9.e+]+)", text)
-    if not m or not t or m.group(1) != h.hexdigest()[:16]:
-        return None
-    return float(t.group(1))
+    digest = h.hexdigest()[:16]
+    want = f"capture_config: windows={windows} col_block={col_block} layout={layout}"
+    for path in sorted(glob.glob(os.path.join(PROFILES, "k_sweep_4q_*small_full.md"))):
+        text = open(path).read()
+        m = re.search(r"sources_sha256: ([0-9a-f]+)", text)
+        t = re.search(rf"{kernel}=([0-9.e+]+)", text)
+        if want in text and m and t and m.group(1) == digest:
+            return float(t.group(1)), os.path.relpath(path, ROOT)
+    return None, None
 
 
 def max_over_ranks(value: float, dist, device) -> float:
@@ -225,7 +227,8 @@ def run_ours(args, spec):
     tuned = tune_ms = None
     if args.col_block < 0:
         tuned, layout, tune_ms = msqoc.autotune(spec, alpha=alpha, probe_steps=64, solver=solver, layout=layout)
-        tune_ms = {f"{'pair' if lay == 2 else 'fiber'}-{cb}": v for (lay, cb), v in tune_ms.items()}
+        fam = {1: "fiber", 2: "pair", 3: "quad"}
+        tune_ms = {f"{fam[lay]}-{cb}": v for (lay, cb), v in tune_ms.items()}
     col_block = tuned if args.col_block < 0 else args.col_block
     prob = msqoc.Problem(spec, solver=solver, col_block=col_block, profile=True, layout=layout)
     peak_tflops = msqoc.measure_fp64_peak()
@@ -273,6 +276,8 @@ def run_ours(args, spec):
 
     fl = flops_model(spec)
     dom = max(("forward", "adjoint"), key=lambda k: kt[k])
+    traffic, traffic_src = (sweep_traffic(dom, spec.M, prob.col_block, prob.layout) if spec.nsteps == 100000
+                            else (None, None))
     dom_ms = kt[dom] / args.steps
     achieved = fl[dom] / (dom_ms * 1e-3) / 1e12
     launches_per_eval = 6 if spec.M > 1 else 5
@@ -282,16 +287,18 @@ def run_ours(args, spec):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": spec.name, "N": spec.N, "E": spec.E, "nsteps": spec.nsteps, "windows": spec.M,
                    "T_ns": spec.T, "d": spec.d, "solver": args.solver,
-                   "col_block": col_block if col_block > 0 else f"model ({prob.col_block})",
+                   "col_block": (f"autotuned ({prob.col_block})" if tuned else
+                                 col_block if col_block > 0 else f"model ({prob.col_block})"),
                    "layout": {1: "one thread per fiber", 2: "lane pair per fiber", 3: "lane quad per fiber"}[prob.layout],
                    **({"autotune": {"best": tuned, "ms_per_probe_eval": tune_ms}} if tuned else {}),
                    "l2": "inputs larger than L2 (2 GB midpoint history per evaluation)",
                    "parallelism": f"independent problem per GPU x{world}"},
         "roofline": {"bound": "alu", "kernel": f"k_sweep ({dom})", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                     "traffic": sweep_traffic(dom) if spec.nsteps == 100000 and spec.M == 64 else None,
-                     "traffic_note": "DRAM bytes per launch from profiles/k_sweep_4q_small_full.md (6400-step capture "
-                                     "x 15.625); null when the sweep sources changed since",
+                     "traffic": traffic,
+                     "traffic_note": (f"DRAM bytes per launch from {traffic_src} (6400-step capture of the same "
+                                      "tiles x 15.625)" if traffic else
+                                      "null: no ncu summary of these tiles for the current sweep sources"),
                      "peak_source": "measured FP64 FMA microbenchmark (msqoc_measure_fp64_peak), same run",
                      "algorithmic_flops_per_launch": fl[dom], "avg_launch_ms": dom_ms},
         "kernel_ms": {k: v / args.steps for k, v in kt.items()},
@@ -638,10 +645,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--windows", type=int, default=64)
+    ap.add_argument("--windows", type=int, default=256,
+                    help="4q workload: windows M (64, 128 or 256 in the workload's configuration)")
     ap.add_argument("--solver", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--col-block", type=int, default=0,
-                    help="columns per sweep tile: 0 = the library's model, -1 = measured by the autotuner")
+    ap.add_argument("--col-block", type=int, default=-1,
+                    help="columns per sweep tile: -1 = measured by the library's autotuner (default), "
+                         "0 = the library's model")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--layout", choices=list(LAYOUTS), default="auto",
                     help="sweep kernel family: one thread, a lane pair or (2-level subsystems) a lane quad per fiber "

@@ -28,11 +28,16 @@ static auto kernel_of() {
         return k_sweep<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT>;
 }
 
+// Dynamic shared memory above 48 KB needs the kernel's opt-in attribute; the limit counts the
+// kernels' static shared memory too (a flag, and the alignment of the dynamic block), so the
+// opt-in is set from this margin below 48 KB on.
+constexpr size_t SMEM_OPT_IN = 48 * 1024 - 1024;
+
 template <int SOLVER, bool BWD, bool ROLLOUT, int FAM>
 static cudaError_t launch_one(const SweepArgs& a, int ntiles, cudaStream_t s) {
     auto kern = kernel_of<SOLVER, BWD, ROLLOUT, FAM>();
     const size_t smem = sweep_smem_bytes(a);
-    if (smem > 48 * 1024) {
+    if (smem > SMEM_OPT_IN) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
@@ -45,7 +50,7 @@ template <int SOLVER, bool BWD, int FAM>
 static int occupancy_one(const SweepArgs& a) {
     auto kern = kernel_of<SOLVER, BWD, false, FAM>();
     const size_t smem = sweep_smem_bytes(a);
-    if (smem > 48 * 1024 &&
+    if (smem > SMEM_OPT_IN &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
         return 0;
     int n = 0;

@@ -28,10 +28,12 @@ def oracle_4q(M):
     return _ORACLE[M]
 
 
-@pytest.mark.parametrize("M", [64, 256])
-def test_fullsize_4q(M):
+@pytest.mark.parametrize("M,cb", [(64, 0), (256, 0), (256, 9)])
+def test_fullsize_4q(M, cb):
+    """The library's tiles, and at 256 windows also 9-column tiles over two windows (456 tiles:
+    three waves of 152), the autotuner's choice there."""
     spec, alpha, W, want = oracle_4q(M)
-    with msqoc.Problem(spec) as p:
+    with msqoc.Problem(spec, col_block=cb) as p:
         got = p.eval_gradient(alpha, W)
         obj = p.eval_objective(alpha, W)
     assert_objective_close(got["P"], want["P"])

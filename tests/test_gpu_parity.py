@@ -65,12 +65,12 @@ def test_parity_small(case, solver):
     check(spec, alpha, W, SOLVERS[solver])
 
 
-@pytest.mark.parametrize("layout,cb", [("fiber", cb) for cb in (1, 2, 3, 4, 5, 7, 8)] +
+@pytest.mark.parametrize("layout,cb", [("fiber", cb) for cb in (1, 2, 3, 4, 5, 7, 8, 9)] +
                          [("pair", cb) for cb in (1, 2, 3, 4, 5, 6, 7)])
 def test_parity_column_blocks_4q(layout, cb):
     """Tiles of cb columns run along the window-major column list; widths that do not divide
-    E = 16 give tiles covering two windows (3, 5, 6 and 7 here).  8 columns (224 threads) is the
-    widest one-thread-per-fiber tile, 7 (384 threads) the widest lane-pair tile."""
+    E = 16 give tiles covering two windows (3, 5, 6, 7 and 9 here).  9 columns (243 threads) is
+    the widest one-thread-per-fiber tile, 7 (384 threads) the widest lane-pair tile."""
     spec = S.transmon_spec(4, 1.2, 200, 3, 4)
     alpha, W = S.random_alpha(spec, 7), S.random_W(spec, 7)
     check(spec, alpha, W, msqoc.SOLVER_MIXED, col_block=cb, layouts=(LAYOUTS[layout],))
