@@ -169,7 +169,13 @@ class _Description:
 
 
 class Problem:
-    """One multiple-shooting problem living on the current CUDA device."""
+    """One multiple-shooting problem living on the current CUDA device.
+
+    solver: SOLVER_MIXED (default: FP64 residual, FP32 corrections) or SOLVER_FP64; col_block:
+    columns per sweep tile (0: the library's model); ckpt_interval: K (0: automatic); layout:
+    LAYOUT_FIBER, LAYOUT_PAIR or LAYOUT_QUAD (2-level subsystems) to force a sweep kernel family
+    (LAYOUT_AUTO: the model's choice).  After creation .col_block, .tiles, .threads,
+    .ckpt_interval and .layout report what the library chose."""
 
     def __init__(self, spec, target: Optional[np.ndarray] = None, solver: int = SOLVER_DEFAULT,
                  col_block: int = 0, ckpt_interval: int = 0, profile: bool = False, layout: int = 0):
