@@ -335,8 +335,10 @@ msqoc_status msqoc_batch_destroy(msqoc_batch* b);
  * MSQOC_ERR_INVALID_ARG before any device work, whatever kind of pointers it passes.  The
  * 4-transmon workload (N = 81, E = 16, 2 carriers each, 100000 steps, M <= 256) fits.
  * Synchronization: the call is synchronous; it returns once the results are in the outputs.
- * Set-up: the first call on a device looks up the device address of the scratch array on
- * that device (with the device current); make that first call before any stream capture.
+ * Set-up: every call looks up the device address of the scratch array on the current device
+ * (cudaGetSymbolAddress, a host-side query; nothing is cached, so a context that was reset
+ * and recreated is served at the array's new address).  Make the first call on a device
+ * before any stream capture, since it may load the library's module on that device.
  * Sharing: every call on a device uses the same scratch array, which keeps the previous
  * call's contents (what must start at zero is cleared by each call).  Calls that overlap on
  * the GPU (from several host threads or streams at once) race on it and corrupt each

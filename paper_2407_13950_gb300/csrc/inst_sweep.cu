@@ -28,16 +28,29 @@ static auto kernel_of() {
         return k_sweep<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT>;
 }
 
-// Dynamic shared memory above 48 KB needs the kernel's opt-in attribute; the limit counts the
-// kernels' static shared memory too (a flag, and the alignment of the dynamic block), so the
-// opt-in is set from this margin below 48 KB on.
-constexpr size_t SMEM_OPT_IN = 48 * 1024 - 1024;
+// Dynamic shared memory above 48 KB needs the kernel's opt-in attribute, and the 48 KB limit
+// counts the kernel's static shared memory too.  The static size of each instantiation is read
+// once from the runtime (cudaFuncGetAttributes); the opt-in is set when static + dynamic bytes
+// exceed 48 KB.
+constexpr size_t SMEM_DEFAULT_LIMIT = 48 * 1024;
+
+// one static per kernel instantiation (the template parameters name the kernel)
+template <int SOLVER, bool BWD, bool ROLLOUT, int FAM>
+static bool needs_opt_in(size_t smem) {
+    static const size_t static_bytes = [] {
+        cudaFuncAttributes fa{};
+        // an unreadable attribute counts as the largest static size, so the opt-in is taken
+        return cudaFuncGetAttributes(&fa, kernel_of<SOLVER, BWD, ROLLOUT, FAM>()) == cudaSuccess ? fa.sharedSizeBytes
+                                                                                                 : SMEM_DEFAULT_LIMIT;
+    }();
+    return smem + static_bytes > SMEM_DEFAULT_LIMIT;
+}
 
 template <int SOLVER, bool BWD, bool ROLLOUT, int FAM>
 static cudaError_t launch_one(const SweepArgs& a, int ntiles, cudaStream_t s) {
     auto kern = kernel_of<SOLVER, BWD, ROLLOUT, FAM>();
     const size_t smem = sweep_smem_bytes(a);
-    if (smem > SMEM_OPT_IN) {
+    if (needs_opt_in<SOLVER, BWD, ROLLOUT, FAM>(smem)) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
@@ -50,7 +63,7 @@ template <int SOLVER, bool BWD, int FAM>
 static int occupancy_one(const SweepArgs& a) {
     auto kern = kernel_of<SOLVER, BWD, false, FAM>();
     const size_t smem = sweep_smem_bytes(a);
-    if (smem > SMEM_OPT_IN &&
+    if (needs_opt_in<SOLVER, BWD, false, FAM>(smem) &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
         return 0;
     int n = 0;

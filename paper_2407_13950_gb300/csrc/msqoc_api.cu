@@ -4,7 +4,6 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1101,28 +1100,19 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[MSQOC_NOALLOC_S
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-unsigned char* g_noalloc_base[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up on the first call
-// for that device (with that device current) and cached.
+// Device address of the scratch array on the current device.  It is looked up on every call,
+// with the calling device current: a cached address would go stale when the context is torn
+// down and recreated (cudaDeviceReset), since the module and its static storage are then
+// loaded again, possibly elsewhere.  The lookup is a host-side table query.
 msqoc_status noalloc_scratch(unsigned char** base) {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices)
-        return fail(MSQOC_ERR_UNSUPPORTED, "device %d is beyond the %d devices this entry point serves", dev,
-                    kMaxDevices);
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_base[dev]) {
-        void* ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr)
-            return fail(MSQOC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch on device %d failed: %s", dev,
-                        cudaGetErrorString(e));
-        g_noalloc_base[dev] = static_cast<unsigned char*>(ptr);
-    }
-    *base = g_noalloc_base[dev];
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+        return fail(MSQOC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch on device %d failed: %s", dev,
+                    cudaGetErrorString(e));
+    *base = static_cast<unsigned char*>(ptr);
     return MSQOC_OK;
 }
 
@@ -1139,11 +1129,12 @@ struct Carve {
 
 }  // namespace
 
-extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H, const msqoc_controls* C,
-                                                     const double* target, double T, int64_t nsteps,
-                                                     int32_t nwindows, double mu, int32_t solver,
-                                                     const double* alpha, const double* W, double* P_out,
-                                                     double* J_out, double* pen_out, void* stream) {
+namespace {
+
+msqoc_status eval_objective_noalloc(const msqoc_hamiltonian* H, const msqoc_controls* C, const double* target,
+                                   double T, int64_t nsteps, int32_t nwindows, double mu, int32_t solver,
+                                   const double* alpha, const double* W, double* P_out, double* J_out,
+                                   double* pen_out, void* stream) {
     if (!alpha || !P_out) return fail(MSQOC_ERR_INVALID_ARG, "alpha or P_out is NULL");
     msqoc_status st = check_description(H, C, T, nsteps, nwindows);
     if (st != MSQOC_OK) return st;
@@ -1237,7 +1228,10 @@ extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H,
             for (long t = 0; t < n; ++t) chunk[t] = tile_at(t0 + t, pd.M, pd.E, pd.cb, 0);
             CUDA_TRY(cudaMemcpyAsync(tiles_d + t0, chunk, n * sizeof(Tile), cudaMemcpyHostToDevice, s));
         }
-        int map[MAX_PAIR_TILE_THREADS > MAX_TILE_THREADS ? MAX_PAIR_TILE_THREADS : MAX_TILE_THREADS];
+        constexpr int kMapMax = std::max({MAX_TILE_THREADS, MAX_PAIR_TILE_THREADS, MAX_QUAD_TILE_THREADS});
+        int map[kMapMax];
+        if (pd.nthreads > kMapMax)
+            return fail(MSQOC_ERR_INVALID_ARG, "tile of %d threads exceeds the %d-entry lane map", pd.nthreads, kMapMax);
         const Tile last = tile_at(pd.ntiles - 1, pd.M, pd.E, pd.cb, 0);
         for (int k = 0; k <= pd.cb; ++k) {
             build_lanemap(pd.L, pd.q, k < pd.cb ? pd.cb : last.ncol, k < pd.cb ? k + 1 : last.ncol0, pd.nthreads,
@@ -1271,4 +1265,17 @@ extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H,
     CUDA_TRY(cudaStreamSynchronize(s));
     if (status_word) return status_error(status_word);
     return MSQOC_OK;
+}
+
+}  // namespace
+
+extern "C" msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H, const msqoc_controls* C,
+                                                     const double* target, double T, int64_t nsteps,
+                                                     int32_t nwindows, double mu, int32_t solver,
+                                                     const double* alpha, const double* W, double* P_out,
+                                                     double* J_out, double* pen_out, void* stream) {
+    return guarded([&] {
+        return eval_objective_noalloc(H, C, target, T, nsteps, nwindows, mu, solver, alpha, W, P_out, J_out, pen_out,
+                                      stream);
+    });
 }

@@ -88,3 +88,22 @@ def test_noalloc_rejects_a_problem_beyond_the_scratch_limit():
     spec2 = S.config_2q()
     a2, W2 = S.random_alpha(spec2, 5), S.random_W(spec2, 5)
     assert_same_objective(msqoc.eval_objective_noalloc(spec2, a2, W2), regular_objective(spec2, a2, W2), spec2.M)
+
+
+def test_noalloc_calls_leave_device_free_memory_unchanged():
+    # what the entry point is for: calls take no device memory.  One warm call per size first:
+    # the CUDA runtime loads each kernel's code onto the device at its first launch, which is
+    # device memory the driver takes once, not an allocation of the call
+    import torch
+    cases = [S.config_2q(), S.config_3q(), S.transmon_spec(3, 30.0, 2000, 7, 8), S.config_4q(M=64)]
+    inputs = [(sp, S.random_alpha(sp, 3), S.random_W(sp, 3)) for sp in cases]
+    warm = [msqoc.eval_objective_noalloc(sp, a, W) for sp, a, W in inputs]
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    results = [msqoc.eval_objective_noalloc(sp, a, W) for sp, a, W in inputs for _ in range(2)]
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before, (free_before, free_after)
+    # every call on the same inputs gives the same numbers
+    for k, w in enumerate(warm):
+        assert results[2 * k]["P"] == w["P"] and results[2 * k + 1]["P"] == w["P"]
