@@ -9,8 +9,18 @@ and non-unitary window states.  A step of this benchmark is one full evaluation
 gradient, reductions).  The midpoint-state history (2 GB) is far larger than L2, so no L2
 flush is needed between steps.
 
+The default line also carries, measured in the same process:
+  config3      the 4-transmon workload at every window count (64, 128, 256) and checkpoint
+               interval (1, 64, 512), tiles from the library's model;
+  solver_fp64  the benchmark workload with the all-FP64 step solver;
+  batched      96 mixed problems (32 x 2q + 32 x 3q + 32 x 4q) in one graph-replayed batch
+               against the same problems one after another;
+  serving      a Poisson request stream over 64 sessions (2q/3q/4q/5q) served with continuous
+               batching (arrival-order and throughput policies) against one request at a time.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--windows M]
                   [--solver mixed|fp64] [--col-block CB] [--nsteps NT] [--no-cpu-baseline]
+                  [--no-extras]
 
 Prints one JSON line.  Under torchrun (N > 1) every rank evaluates its own independent
 problem (weak scaling, no collective on the data path); rank 0 prints.
@@ -148,24 +158,28 @@ def dist_info():
     return rank, world, local
 
 
-def cpu_baseline(spec, alpha, W, budget_s: float = 20.0):
-    """The oracle, as it stands, on this host's cores, on a bounded sample of the workload:
-    the first `ncores` windows (forward + adjoint), scaled to a full evaluation by the number of
-    window rounds the full problem needs on the same cores."""
+def workload_config(spec) -> dict:
+    """The workload as both arms name it (implementation choices are reported separately)."""
+    return {"workload": spec.name, "N": spec.N, "E": spec.E, "nsteps": spec.nsteps, "windows": spec.M,
+            "T_ns": spec.T, "d": spec.d, "l2": "inputs larger than L2 (2 GB midpoint history per evaluation)"}
+
+
+def cpu_baseline(spec, alpha, W):
+    """The oracle, as it stands, on this host's cores: one whole evaluation (objective and
+    gradient of every window; windows in parallel on all cores)."""
     import oracle
     cores = os.cpu_count() or 1
-    nwin = min(spec.M, cores)
     t0 = time.perf_counter()
-    oracle.evaluate(spec, alpha, W, windows=(1, nwin), nthreads=cores)
+    oracle.evaluate(spec, alpha, W, nthreads=cores)
     dt = time.perf_counter() - t0
-    rounds = math.ceil(spec.M / cores)
-    per_eval = dt * rounds * (nwin / min(nwin, cores))
-    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"windows 1-{nwin} of {spec.M} (forward+adjoint, {spec.nsteps // spec.M} steps each) "
-                      f"on {cores} threads in {dt:.2f} s, scaled x{rounds} window rounds"}
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one whole evaluation ({spec.M} windows, forward+adjoint, {spec.nsteps} steps) on "
+                      f"{cores} threads in {dt:.2f} s"}
 
 
 def run_reference(args, spec):
+    """The oracle as the reference arm: each step one whole evaluation of the same workload on
+    every host core."""
     rank, world, _ = dist_info()
     if rank != 0:
         return
@@ -173,27 +187,101 @@ def run_reference(args, spec):
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    nwin = min(spec.M, cores)
-    rounds = math.ceil(spec.M / cores)
     times = []
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.evaluate(spec, alpha, W, windows=(1, nwin), nthreads=cores)
+        oracle.evaluate(spec, alpha, W, nthreads=cores)
         dt = time.perf_counter() - t0
         if it >= args.warmup:
-            times.append(dt * rounds)
+            times.append(dt)
     per_eval = float(np.mean(times))
     value = 1.0 / per_eval
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": spec.name, "N": spec.N, "E": spec.E, "nsteps": spec.nsteps, "windows": spec.M,
-                       "T_ns": spec.T, "d": spec.d},
+            "config": {**workload_config(spec), "parallelism": f"independent problem per GPU x{world}"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step: windows 1-{nwin} of {spec.M} (forward+adjoint) on {cores} threads, "
-                                       f"scaled x{rounds} window rounds"},
+                             "sample": f"each step one whole evaluation ({spec.M} windows, forward+adjoint) on "
+                                       f"{cores} threads; {args.steps} timed steps after {args.warmup} warm-up"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def time_evaluations(prob, a_d, W_d, outs, stream, steps: int, warmup: int, kernel_times: bool = True):
+    """ms per objective+gradient evaluation (CUDA events around `steps` back-to-back evaluations
+    after `warmup`), and the library's per-kernel event times averaged over `steps` more."""
+    import torch
+    P_d, ga_d, gW_d = outs
+    for _ in range(warmup):
+        prob.eval_gradient_into(a_d, W_d, P_d, ga_d, gW_d, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        prob.eval_gradient_into(a_d, W_d, P_d, ga_d, gW_d, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    kt = None
+    if kernel_times:
+        from paper_2407_13950_gb300 import msqoc
+        kt = {k: 0.0 for k in msqoc.KERNEL_NAMES}
+        for _ in range(steps):
+            prob.eval_gradient_into(a_d, W_d, P_d, ga_d, gW_d, stream=stream)
+            t = prob.kernel_times()
+            for k in kt:
+                kt[k] += t[k] / steps
+    return ms, kt
+
+
+FAMILY = {1: "one thread per fiber", 2: "lane pair per fiber", 3: "lane quad per fiber"}
+
+
+def config3_section(dev, stream, peak, steps: int = 5, warmup: int = 2) -> dict:
+    """The 4-transmon workload at every window count and checkpoint interval of its
+    configuration, with the library's own tile choice (no autotuning)."""
+    import torch
+    from paper_2407_13950_gb300 import msqoc
+    out = {}
+    for M in (64, 128, 256):
+        spec = S.config_4q(M=M)
+        alpha, W = S.random_alpha(spec, 1), S.random_W(spec, 1)
+        a_d = torch.tensor(alpha, device=dev, dtype=torch.float64)
+        W_d = torch.tensor(W, device=dev, dtype=torch.float64)
+        outs = (torch.zeros(1, device=dev, dtype=torch.float64), torch.zeros(spec.d, device=dev, dtype=torch.float64),
+                torch.zeros(spec.nW, device=dev, dtype=torch.float64))
+        fl = flops_model(spec)
+        for K in (1, 64, 512):
+            with msqoc.Problem(spec, ckpt_interval=K, profile=True) as p:
+                ms, kt = time_evaluations(p, a_d, W_d, outs, stream, steps, warmup)
+                out[f"M{M}_K{K}"] = {
+                    "evals_per_s": 1e3 / ms, "ms_per_eval": ms, "kernel_ms": kt,
+                    "adjoint_frac_of_fp64_peak": fl["adjoint"] / (kt["adjoint"] * 1e-3) / 1e12 / peak,
+                    "whole_eval_frac_of_fp64_peak": fl["total"] / (ms * 1e-3) / 1e12 / peak,
+                    "tiles": f"{FAMILY[p.layout]} x {p.col_block} columns ({p.tiles} CTAs)",
+                    "ckpt_interval": p.ckpt_interval, "device_bytes": p.device_bytes}
+        del a_d, W_d, outs
+        torch.cuda.empty_cache()
+    return out
+
+
+def solver_fp64_section(spec, dev, stream, peak, steps: int = 5, warmup: int = 2) -> dict:
+    """The benchmark workload with the all-FP64 fixed-point step solver."""
+    import torch
+    from paper_2407_13950_gb300 import msqoc
+    alpha, W = S.random_alpha(spec, 1), S.random_W(spec, 1)
+    a_d = torch.tensor(alpha, device=dev, dtype=torch.float64)
+    W_d = torch.tensor(W, device=dev, dtype=torch.float64)
+    outs = (torch.zeros(1, device=dev, dtype=torch.float64), torch.zeros(spec.d, device=dev, dtype=torch.float64),
+            torch.zeros(spec.nW, device=dev, dtype=torch.float64))
+    fl = flops_model(spec)
+    with msqoc.Problem(spec, solver=msqoc.SOLVER_FP64, profile=True) as p:
+        ms, kt = time_evaluations(p, a_d, W_d, outs, stream, steps, warmup)
+        achieved = fl["adjoint"] / (kt["adjoint"] * 1e-3) / 1e12
+        return {"value": 1e3 / ms, "unit": UNIT, "ms_per_eval": ms, "kernel_ms": kt,
+                "tiles": f"{FAMILY[p.layout]} x {p.col_block} columns ({p.tiles} CTAs)",
+                "roofline": {"kernel": "k_sweep (adjoint)", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak}}
 
 
 def run_ours(args, spec):
@@ -285,19 +373,18 @@ def run_ours(args, spec):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": spec.name, "N": spec.N, "E": spec.E, "nsteps": spec.nsteps, "windows": spec.M,
-                   "T_ns": spec.T, "d": spec.d, "solver": args.solver,
-                   "col_block": (f"autotuned ({prob.col_block})" if tuned else
-                                 col_block if col_block > 0 else f"model ({prob.col_block})"),
-                   "layout": {1: "one thread per fiber", 2: "lane pair per fiber", 3: "lane quad per fiber"}[prob.layout],
-                   **({"autotune": {"best": tuned, "ms_per_probe_eval": tune_ms}} if tuned else {}),
-                   "l2": "inputs larger than L2 (2 GB midpoint history per evaluation)",
-                   "parallelism": f"independent problem per GPU x{world}"},
+        "config": {**workload_config(spec), "parallelism": f"independent problem per GPU x{world}"},
+        "implementation": {
+            "solver": args.solver,
+            "col_block": (f"autotuned ({prob.col_block})" if tuned else
+                          col_block if col_block > 0 else f"model ({prob.col_block})"),
+            "layout": FAMILY[prob.layout], "ctas": prob.tiles, "threads_per_cta": prob.threads,
+            **({"autotune": {"best": tuned, "ms_per_probe_eval": tune_ms}} if tuned else {})},
         "roofline": {"bound": "alu", "kernel": f"k_sweep ({dom})", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": traffic,
-                     "traffic_note": (f"DRAM bytes per launch from {traffic_src} (6400-step capture of the same "
-                                      "tiles x 15.625)" if traffic else
+                     "traffic_note": (f"DRAM bytes per launch from {traffic_src} (capture of the same tiles on a "
+                                      "shorter grid, scaled by the steps)" if traffic else
                                       "null: no ncu summary of these tiles for the current sweep sources"),
                      "peak_source": "measured FP64 FMA microbenchmark (msqoc_measure_fp64_peak), same run",
                      "algorithmic_flops_per_launch": fl[dom], "avg_launch_ms": dom_ms},
@@ -309,26 +396,34 @@ def run_ours(args, spec):
         "gpu_launches": launches_per_eval * args.steps,
         "clocks": clocks,
     }
+    prob.close()
+    del a_d, W_d, P_d, ga_d, gW_d
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_extras and spec.nsteps == 100000:
+        # the other settings of the workload and the systems patterns, same process and box
+        t_extra = time.perf_counter()
+        line["config3"] = config3_section(dev, stream, peak_tflops)
+        line["solver_fp64"] = solver_fp64_section(spec, dev, stream, peak_tflops)
+        line["batched"] = batched_section(args, dev, stream, peak_tflops, steps=3, warmup=1)
+        torch.cuda.empty_cache()
+        line["serving"] = serving_section(args, peak_tflops, seconds=args.extra_serve_seconds)
+        line["extras_seconds"] = time.perf_counter() - t_extra
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, alpha, W)
-    prob.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def run_batched(args):
-    """Config of the batched launch: 32 x 2 transmons + 32 x 3 + 32 x 4 (durations uniform in
+def batched_section(args, dev, stream, peak, steps: int, warmup: int) -> dict:
+    """The batched workload: 32 x 2 transmons + 32 x 3 + 32 x 4 (durations uniform in
     [0.5 T, 1.5 T] at the base step size, windows drawn from {8, 32, 64, 128}), one
     objective+gradient evaluation of all 96 per step, as one batch replayed from a CUDA graph,
     against the same problems evaluated one after another (one problem per launch sequence)."""
     import torch
     from paper_2407_13950_gb300 import msqoc
 
-    rank, world, local = dist_info()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     specs = S.mixed_batch_specs(seed=1, n_per_shape=args.batch_per_shape,
                                 shapes=[S.config_2q(), S.config_3q(), S.config_4q()])
     nprob = len(specs)
@@ -338,7 +433,6 @@ def run_batched(args):
               for a, W in host_in]
     outs = [(torch.zeros(1, device=dev, dtype=torch.float64), torch.zeros(p.d, device=dev, dtype=torch.float64),
              torch.zeros(max(p.nW, 2), device=dev, dtype=torch.float64)) for p in probs]
-    stream = torch.cuda.current_stream(dev)
     batch = msqoc.Batch(probs, gradient=True, graph=True)
     fam = {1: "fiber", 2: "pair", 3: "quad"}
     tile_mix = {}
@@ -359,25 +453,25 @@ def run_batched(args):
             if ev is not None:
                 ev[i].record(stream)
 
-    def timed(fn, steps):
+    def timed(fn, n):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(steps):
+        for _ in range(n):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
+        return e0.elapsed_time(e1) / n
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batched_step()
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    ms_b = timed(batched_step, args.steps)
+    ms_b = timed(batched_step, steps)
     clocks = sampler.stop()
-    for _ in range(max(1, args.warmup // 2)):
+    for _ in range(warmup):
         plain_step()
-    ms_p = timed(plain_step, args.steps)
+    ms_p = timed(plain_step, steps)
     # completion times when all requests are submitted together: the batch finishes them all at
     # once; one after another, request i waits for the ones before it
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(nprob)]
@@ -404,37 +498,56 @@ def run_batched(args):
 
     e2e_step()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         e2e_step()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
     h2d = sum(8 * (sp.d + (sp.nW if sp.M > 1 else 0)) for sp in specs)
     d2h = sum(8 * (1 + sp.d + (sp.nW if sp.M > 1 else 0)) for sp in specs)
     fl = sum(flops_model(sp)["total"] for sp in specs)
-    peak = msqoc.measure_fp64_peak()
-    line = {
-        "metric": "mixed-batch objective+gradient evals/s", "value": nprob / (ms_b * 1e-3), "unit": "evals/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"batched-{nprob}: {args.batch_per_shape}x2q + {args.batch_per_shape}x3q + "
-                               f"{args.batch_per_shape}x4q, durations U[0.5T,1.5T], windows in {{8,32,64,128}}",
-                   "launch": "one CUDA graph per step (shared sweep launches per shape)",
-                   "l2": "inputs larger than L2 (midpoint histories of GBs per step)"},
+    out = {
+        "workload": f"{nprob} problems: {args.batch_per_shape}x2q + {args.batch_per_shape}x3q + "
+                    f"{args.batch_per_shape}x4q, durations U[0.5T,1.5T], windows in {{8,32,64,128}}",
+        "launch": "one CUDA graph per step (shared sweep launches per shape and tile width)",
+        "value": nprob / (ms_b * 1e-3), "unit": "evals/s", "ms_per_step": ms_b, "steps": steps, "warmup": warmup,
+        "algorithmic_tflops": fl / (ms_b * 1e-3) / 1e12, "frac_of_fp64_peak": fl / (ms_b * 1e-3) / 1e12 / peak,
         "plain": {"value": nprob / (ms_p * 1e-3), "unit": "evals/s", "ms_per_step": ms_p,
+                  "algorithmic_tflops": fl / (ms_p * 1e-3) / 1e12,
                   "launch": "one problem after another, each its own launch sequence"},
         "speedup_vs_plain": ms_p / ms_b,
         "latency_ms": {"batched": {"p50": ms_b, "p99": ms_b},
                        "plain": {"p50": float(np.percentile(done_p, 50)), "p99": float(np.percentile(done_p, 99))},
-                       "note": "all requests submitted at once; completion time of each"},
-        "whole_step": {"algorithmic_tflops": fl / (ms_b * 1e-3) / 1e12,
-                       "frac_of_fp64_peak": fl / (ms_b * 1e-3) / 1e12 / peak, "peak_tflops": peak},
-        "e2e": {"value": nprob / (e2e_ms * 1e-3), "unit": "evals/s", "buffers": "pinned host", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                       "note": "all 96 requests submitted at once; completion time of each (the batch "
+                               "completes them together)"},
+        "e2e": {"value": nprob / (e2e_ms * 1e-3), "unit": "evals/s", "buffers": "pinned host",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks,
         "tiles": tile_mix,
     }
     batch.close()
     for p in probs:
         p.close()
+    del dev_in, outs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args):
+    import torch
+    from paper_2407_13950_gb300 import msqoc
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sec = batched_section(args, dev, stream, msqoc.measure_fp64_peak(), steps=args.steps, warmup=args.warmup)
+    line = {
+        "metric": "mixed-batch objective+gradient evals/s", "value": sec["value"], "unit": "evals/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batched-" + sec["workload"], "launch": sec["launch"],
+                   "l2": "inputs larger than L2 (midpoint histories of GBs per step)"},
+        **{k: v for k, v in sec.items() if k not in ("value", "unit", "ms_per_step", "workload", "launch")},
+    }
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -571,19 +684,32 @@ def run_optimize(args):
         print(json.dumps(line), flush=True)
 
 
-def run_serving(args):
-    """Serving loop: sessions of 2/3/4/5 transmons (the 5-transmon ones with forced
-    checkpointing), a Poisson stream of objective/gradient requests over them, served with
-    continuous batching and, on the same request stream, one request at a time."""
-    import torch
-    from paper_2407_13950_gb300 import msqoc, serving
+def serving_summary(done, specs, seconds: float, peak: float) -> dict:
+    """Completions, algorithmic FP64 throughput and latencies of one serving run, overall and
+    by shape (requests of unequal cost are compared by their algorithmic flops)."""
+    from paper_2407_13950_gb300 import serving
+    fl = sum(serving.eval_flops(specs[r.session], r.gradient) for r in done)
+    shapes = sorted({sp.q for sp in specs})
+    by = {f"{q}q": [r for r in done if specs[r.session].q == q] for q in shapes}
+    return {"evals_per_s": len(done) / seconds, "completed": len(done),
+            "completed_by_shape": {k: len(v) for k, v in by.items()},
+            "algorithmic_tflops": fl / seconds / 1e12, "frac_of_fp64_peak": fl / seconds / 1e12 / peak,
+            "latency_ms": serving.latency_summary(done),
+            "latency_by_shape_ms": {k: serving.latency_summary(v) for k, v in by.items() if v}}
 
-    rank, world, local = dist_info()
-    torch.cuda.set_device(local)
+
+def serving_section(args, peak, seconds: float) -> dict:
+    """The serving workload: 16 sessions each of 2, 3, 4 and 5 transmons (the 5-transmon ones
+    with checkpoint interval 64), a Poisson stream of `args.rate` requests/s (half gradients)
+    for `seconds`, served with continuous batching under the arrival-order policy and the
+    throughput policy, and one request at a time, on the same request stream."""
+    import torch
+    from paper_2407_13950_gb300 import serving
+
     per = args.sessions_per_shape
     shapes = [(S.config_2q(), 0), (S.config_3q(), 0), (S.config_4q(), 0), (S.config_5q(), 64)]
     free, _ = torch.cuda.mem_get_info()
-    srv = serving.Server(device_budget_bytes=int(0.85 * free))
+    srv = serving.Server(device_budget_bytes=int(0.85 * free), lookahead=args.lookahead)
     specs, refused = [], 0
     for k in range(per):
         for base, K in shapes:
@@ -592,49 +718,61 @@ def run_serving(args):
                 specs.append(base)
             except serving.NotAdmitted:
                 refused += 1
-    # warm-up: one gradient request per session (kernel set-up, first-touch of the histories)
-    warm = [serving.Request(session=i, gradient=True, alpha=S.random_alpha(sp, 7, problem=i),
-                            W=S.random_W(sp, 7, problem=i) if sp.M > 1 else None) for i, sp in enumerate(specs)]
+    # warm-up: an objective and a gradient request of one session per shape (kernel set-up)
+    first = {}
+    for i, sp in enumerate(specs):
+        first.setdefault(sp.q, i)
+    warm = [serving.Request(session=i, gradient=g, alpha=S.random_alpha(specs[i], 7, problem=i),
+                            W=S.random_W(specs[i], 7, problem=i) if specs[i].M > 1 else None)
+            for i in first.values() for g in (False, True)]
     srv.run(warm)
-    reqs = serving.poisson_requests(specs, rate=args.rate, duration=args.serve_seconds, seed=1)
-    sampler = ClockSampler(local)
+    out = {"workload": f"{len(specs)} sessions ({per} each of 2q, 3q, 4q, 5q; 5q with checkpoint interval 64), "
+                       f"Poisson {args.rate:.0f} requests/s for {seconds:.0f} s per run, half gradients",
+           "admitted": len(specs), "refused": refused, "budget_bytes": srv.budget, "used_bytes": srv.used,
+           "lookahead": srv.lookahead,
+           "latency_note": "from_ready: from the head of an idle session's queue (the previous request of "
+                           "the session done) to the result; service: dispatch to result; from_arrival "
+                           "includes the queue at the session (the offered load exceeds capacity)"}
+    sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    done = srv.run(reqs, duration=args.serve_seconds)
-    clocks = sampler.stop()
-    reqs_p = serving.poisson_requests(specs, rate=args.rate, duration=args.serve_seconds, seed=1)
-    done_p = srv.run_plain(reqs_p, duration=args.serve_seconds)
+    for policy in ("fifo", "throughput"):
+        srv.policy = policy
+        srv.dispatch_flops = 2e12 if policy == "fifo" else 2e11
+        reqs = serving.poisson_requests(specs, rate=args.rate, duration=seconds, seed=1)
+        done = srv.run(reqs, duration=seconds)
+        out["served_" + policy] = serving_summary(done, specs, seconds, peak)
+    reqs = serving.poisson_requests(specs, rate=args.rate, duration=seconds, seed=1)
+    done = srv.run_plain(reqs, duration=seconds)
+    out["plain"] = serving_summary(done, specs, seconds, peak)
+    out["clocks"] = sampler.stop()
+    srv.close()
+    fifo, plain = out["served_fifo"], out["plain"]
+    out["fifo_vs_plain"] = {
+        "completed_ratio_by_shape": {k: fifo["completed_by_shape"].get(k, 0) / max(v, 1)
+                                     for k, v in plain["completed_by_shape"].items()},
+        "tflops_ratio": fifo["algorithmic_tflops"] / max(plain["algorithmic_tflops"], 1e-30),
+        "p99_from_ready_ms_by_shape": {k: [fifo["latency_by_shape_ms"].get(k, {}).get("from_ready", {}).get("p99"),
+                                           v["from_ready"]["p99"]]
+                                       for k, v in plain["latency_by_shape_ms"].items()}}
+    torch.cuda.empty_cache()
+    return out
 
-    def by_shape(dn):
-        c = {}
-        for r in dn:
-            q = specs[r.session].q
-            c[f"{q}q"] = c.get(f"{q}q", 0) + 1
-        return c
 
-    def lat_by_shape(dn):
-        out = {}
-        for q in sorted({sp.q for sp in specs}):
-            sub = [r for r in dn if specs[r.session].q == q]
-            if sub:
-                out[f"{q}q"] = serving.latency_summary(sub)["from_ready"]
-        return out
+def run_serving(args):
+    import torch
+    from paper_2407_13950_gb300 import msqoc
 
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    sec = serving_section(args, msqoc.measure_fp64_peak(), seconds=args.serve_seconds)
+    fifo = sec["served_fifo"]
     line = {
-        "metric": "served objective/gradient evals/s", "value": len(done) / args.serve_seconds, "unit": "evals/s",
+        "metric": "served objective/gradient evals/s", "value": fifo["evals_per_s"], "unit": "evals/s",
         "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": args.serve_seconds * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"serving: {len(specs)} sessions ({per} each of 2q, 3q, 4q, 5q; 5q with checkpoint "
-                               f"interval 64), Poisson {args.rate:.0f} requests/s for {args.serve_seconds:.0f} s, "
-                               f"half gradients", "admitted": len(specs), "refused": refused,
-                   "budget_bytes": srv.budget, "used_bytes": srv.used},
-        "offered": len(reqs), "completed": len(done), "completed_by_shape": by_shape(done),
-        "latency_ms": serving.latency_summary(done), "latency_from_ready_by_shape_ms": lat_by_shape(done),
-        "plain": {"value": len(done_p) / args.serve_seconds, "unit": "evals/s", "completed": len(done_p),
-                  "completed_by_shape": by_shape(done_p), "latency_ms": serving.latency_summary(done_p),
-                  "latency_from_ready_by_shape_ms": lat_by_shape(done_p)},
-        "clocks": clocks,
+        "config": {"workload": "serving: " + sec["workload"]},
+        **{k: v for k, v in sec.items() if k != "workload"},
     }
-    srv.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -652,6 +790,12 @@ def main():
                     help="columns per sweep tile: -1 = measured by the library's autotuner (default), "
                          "0 = the library's model")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="4q workload: leave out the config3, solver_fp64, batched and serving sub-objects")
+    ap.add_argument("--extra-serve-seconds", type=float, default=10.0,
+                    help="4q workload: seconds of each serving run inside the default line")
+    ap.add_argument("--lookahead", type=int, default=64,
+                    help="serving: requests the arrival-order policy may run ahead of the oldest one")
     ap.add_argument("--layout", choices=list(LAYOUTS), default="auto",
                     help="sweep kernel family: one thread, a lane pair or (2-level subsystems) a lane quad per fiber "
                          "(auto: the library's model)")

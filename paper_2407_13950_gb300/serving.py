@@ -9,13 +9,24 @@ needs) fits the server's budget; a session that does not fit raises ``NotAdmitte
 Scheduling (host side, this module): requests join their session's queue on arrival; a session
 has at most one request on the GPU (an optimiser needs the previous result before its next
 step), so the head of every idle session's queue is *ready*.  Whenever one of the
-``MSQOC_BATCH_SLOTS`` dispatch slots is free, the scheduler takes the (shape, kind) class of the
-oldest ready request and dispatches every ready request of that class as one subset of the
-server's batch (``msqoc_batch_eval_subset``): their sweeps share launches.  Each class has at
-most one dispatch in flight and each slot its own CUDA stream, with smaller shapes on
-higher-priority streams, so requests that arrive while others run are admitted as slots free
-up and their kernels overlap on the device.  All arithmetic runs in the library's kernels;
-this module only moves pointers, streams and events.
+``MSQOC_BATCH_SLOTS`` dispatch slots is free, the scheduler picks a (shape, kind) class and
+dispatches ready requests of that class as one subset of the server's batch
+(``msqoc_batch_eval_subset``): their sweeps share launches.  Each class has at most one
+dispatch in flight and each slot its own CUDA streams, so requests that arrive while others run
+are admitted as slots free up and their kernels overlap on the device.  Two policies:
+
+* ``fifo`` (default): only the first ``lookahead`` requests not yet dispatched, in arrival
+  order, are eligible; the class of the oldest eligible ready request goes first, with every
+  eligible ready request of that class, and the class holding the oldest undispatched request
+  runs on a high-priority stream.  Every shape therefore advances in arrival order, as it would
+  on a one-request-at-a-time server, while the look-ahead fills the GPU with the requests just
+  behind the oldest one.
+* ``throughput``: any ready request is eligible; cheap classes and classes that waited longer
+  than ``age_limit`` run on high-priority streams.  It completes the most evaluations but
+  serves the expensive shapes later than arrival order.
+
+All arithmetic runs in the library's kernels; this module only moves pointers, streams and
+events.
 """
 from __future__ import annotations
 
@@ -47,6 +58,8 @@ class Request:
     dispatched: float = math.nan
     done: float = math.nan
     result: Optional[dict] = None
+    slot: int = -1                # dispatch slot (served) or -1 (one at a time)
+    events: Optional[tuple] = None   # (start, end) CUDA events of its dispatch, when recorded
 
 
 def eval_flops(spec, gradient: bool) -> float:
@@ -59,24 +72,51 @@ def eval_flops(spec, gradient: bool) -> float:
     return float(fwd + (spec.E * spec.nsteps * (f_step + 8 * nnz) if gradient else 0))
 
 
+class _Dispatched:
+    """Fenwick tree over request indices marking the dispatched ones: how many requests before
+    index i are still undispatched, in O(log n)."""
+
+    def __init__(self, n: int):
+        self.t = [0] * (n + 1)
+
+    def mark(self, i: int):
+        i += 1
+        while i < len(self.t):
+            self.t[i] += 1
+            i += i & -i
+
+    def before(self, i: int) -> int:
+        c = 0
+        while i > 0:
+            c += self.t[i]
+            i -= i & -i
+        return c
+
+
 class Server:
     """Sessions and the continuous-batching loop.
 
-    Dispatch policy: a dispatch takes the ready requests of one (shape, kind) class, oldest
-    first, up to `dispatch_flops` of estimated work (at least one request), so that one
-    dispatch of a large shape holds the GPU for a bounded time.  Classes whose requests cost
-    less than `cheap_flops` each run on high-priority streams (their CTAs are scheduled ahead
-    of the large shapes' pending ones); a class whose oldest ready request has waited longer
-    than `age_limit` seconds is promoted to a high-priority stream too, so large shapes are not
-    starved under a stream of small requests."""
+    policy "fifo": a ready request is eligible while fewer than `lookahead` undispatched
+    requests arrived before it; a dispatch takes every eligible ready request of the class of
+    the oldest one (up to `dispatch_flops` of estimated work, at least one request); the
+    dispatch holding the oldest undispatched request runs on a high-priority stream.
+    policy "throughput": every ready request is eligible; a dispatch takes the ready requests of
+    the oldest one's class up to `dispatch_flops`; classes whose requests cost less than
+    `cheap_flops` each, or whose oldest ready request has waited longer than `age_limit`
+    seconds, run on high-priority streams."""
 
-    def __init__(self, device_budget_bytes: int, dispatch_flops: float = 2e11, cheap_flops: float = 1e10,
-                 age_limit: float = 1.0):
+    def __init__(self, device_budget_bytes: int, policy: str = "fifo", lookahead: int = 64,
+                 dispatch_flops: Optional[float] = None, cheap_flops: float = 1e10, age_limit: float = 1.0):
+        if policy not in ("fifo", "throughput"):
+            raise ValueError(f"unknown policy {policy!r}")
         self.budget = int(device_budget_bytes)
         self.used = 0
         self.sessions: List[msqoc.Problem] = []
         self.batch: Optional[msqoc.Batch] = None
-        self.dispatch_flops = dispatch_flops
+        self.policy = policy
+        self.lookahead = int(lookahead)
+        self.dispatch_flops = dispatch_flops if dispatch_flops is not None else (
+            2e12 if policy == "fifo" else 2e11)
         self.cheap_flops = cheap_flops
         self.age_limit = age_limit
 
@@ -109,24 +149,38 @@ class Server:
         return (sp.L, sp.q)
 
     # ------------------------------------------------------------------ serving
-    def run(self, requests: Sequence[Request], duration: Optional[float] = None) -> List[Request]:
+    def run(self, requests: Sequence[Request], duration: Optional[float] = None,
+            record_events: bool = False) -> List[Request]:
         """Serve `requests` (sorted by arrival time, seconds from now).  Stops when all are done,
         or at `duration` seconds (requests then still queued or in flight are not completed).
-        Returns the completed requests with their results and timestamps."""
+        Returns the completed requests with their results and timestamps.  With
+        `record_events`, each request's `events` holds CUDA timing events recorded on its
+        dispatch's stream before its inputs are staged and after its launches, and
+        `self.base_event` one recorded before the loop (device-side start and end offsets of
+        every dispatch: `base_event.elapsed_time(ev)`)."""
         import torch
         if self.batch is None:
             self.batch = msqoc.Batch(self.sessions, gradient=True)
         b = self.batch
+        fifo = self.policy == "fifo"
         # per slot a normal and a high-priority stream (a lower number is a higher priority;
         # CUDA clamps values beyond the device's range)
         streams = [(torch.cuda.Stream(priority=0), torch.cuda.Stream(priority=-8)) for _ in range(SLOTS)]
         cost = [(eval_flops(p.spec, False), eval_flops(p.spec, True)) for p in self.sessions]
         queues: Dict[int, collections.deque] = {s: collections.deque() for s in range(len(self.sessions))}
+        index = {id(r): i for i, r in enumerate(requests)}
+        dispatched = _Dispatched(len(requests))
         busy = [False] * len(self.sessions)
         inflight = {}            # slot -> (event, class, [requests])
         busy_class = set()
         free_slots = list(range(SLOTS))
         done: List[Request] = []
+        self.base_event = None
+        if record_events:
+            self.base_event = torch.cuda.Event(enable_timing=True)
+            self.base_event.record(torch.cuda.current_stream())
+        oldest = 0               # index of the oldest undispatched request (fifo)
+        is_dispatched = [False] * len(requests)
         t0 = time.perf_counter()
         nxt = 0
         n = len(requests)
@@ -154,7 +208,7 @@ class Server:
                     busy_class.discard(cls)
                     free_slots.append(slot)
                     progressed = True
-            # dispatch: oldest ready request's class, all ready requests of that class
+            # dispatch: the oldest eligible ready request's class
             while free_slots:
                 ready = []
                 for s, q in queues.items():
@@ -163,11 +217,15 @@ class Server:
                         if math.isnan(r.ready):
                             r.ready = max(r.arrival, now)
                         ready.append(r)
+                if fifo:
+                    # eligible: fewer than `lookahead` undispatched requests arrived before it
+                    ready = [r for r in ready
+                             if index[id(r)] - dispatched.before(index[id(r)]) < self.lookahead]
                 ready = [r for r in ready if (self._shape(r.session), r.gradient) not in busy_class]
                 if not ready:
                     break
-                oldest = min(ready, key=lambda r: r.arrival)
-                cls = (self._shape(oldest.session), oldest.gradient)
+                first = min(ready, key=lambda r: r.arrival)
+                cls = (self._shape(first.session), first.gradient)
                 sel, work = [], 0.0
                 for r in sorted((r for r in ready if (self._shape(r.session), r.gradient) == cls),
                                 key=lambda r: r.arrival):
@@ -177,17 +235,33 @@ class Server:
                     sel.append(r)
                     work += c
                 slot = free_slots.pop()
-                cheap = cost[oldest.session][1 if oldest.gradient else 0] < self.cheap_flops
-                aged = now - oldest.ready > self.age_limit
-                stream = streams[slot][1 if (cheap or aged) else 0]
+                if fifo:
+                    while oldest < n and is_dispatched[oldest]:
+                        oldest += 1
+                    high = any(index[id(r)] == oldest for r in sel)
+                else:
+                    cheap = cost[first.session][1 if first.gradient else 0] < self.cheap_flops
+                    high = cheap or now - first.ready > self.age_limit
+                stream = streams[slot][1 if high else 0]
+                ev0 = None
+                if record_events:
+                    ev0 = torch.cuda.Event(enable_timing=True)
+                    ev0.record(stream)
                 for r in sel:
                     queues[r.session].popleft()
                     busy[r.session] = True
                     r.dispatched = now
+                    r.slot = slot
+                    i = index[id(r)]
+                    is_dispatched[i] = True
+                    dispatched.mark(i)
                     b.set_inputs(r.session, r.alpha, r.W, stream=stream)
                 b.eval_subset([r.session for r in sel], gradient=cls[1], slot=slot, stream=stream)
-                ev = torch.cuda.Event()
+                ev = torch.cuda.Event(enable_timing=record_events)
                 ev.record(stream)
+                if record_events:
+                    for r in sel:
+                        r.events = (ev0, ev)
                 inflight[slot] = (ev, cls, sel)
                 busy_class.add(cls)
                 progressed = True
@@ -198,9 +272,11 @@ class Server:
 
     def run_plain(self, requests: Sequence[Request], duration: Optional[float] = None) -> List[Request]:
         """The same requests one at a time in arrival order, each its own synchronous
-        evaluation (one problem per launch sequence, nothing overlapped)."""
+        evaluation (one problem per launch sequence, nothing overlapped).  A request is ready,
+        as in `run`, once it has arrived and its session's previous request is done."""
         t0 = time.perf_counter()
         done: List[Request] = []
+        last_done: Dict[int, float] = {}
         for r in requests:
             now = time.perf_counter() - t0
             if duration is not None and now >= duration:
@@ -208,10 +284,12 @@ class Server:
             if r.arrival > now:
                 time.sleep(r.arrival - now)
                 now = time.perf_counter() - t0
-            r.ready = r.dispatched = now
+            r.ready = max(r.arrival, last_done.get(r.session, 0.0))
+            r.dispatched = now
             p = self.sessions[r.session]
             r.result = p.eval_gradient(r.alpha, r.W) if r.gradient else p.eval_objective(r.alpha, r.W)
             r.done = time.perf_counter() - t0
+            last_done[r.session] = r.done
             done.append(r)
         return done
 
@@ -251,10 +329,13 @@ def poisson_requests(sessions: Sequence, rate: float, duration: float, seed: int
 
 
 def latency_summary(done: Sequence[Request]) -> dict:
-    """p50/p99 (ms) from arrival and from readiness (head of an idle session's queue)."""
+    """p50/p99 (ms) from arrival, from readiness (head of an idle session's queue) and of the
+    service alone (dispatch to completion)."""
     if not done:
         return {}
-    arr = np.array([r.done - r.arrival for r in done]) * 1e3
-    rdy = np.array([r.done - r.ready for r in done]) * 1e3
-    return {"from_arrival": {"p50": float(np.percentile(arr, 50)), "p99": float(np.percentile(arr, 99))},
-            "from_ready": {"p50": float(np.percentile(rdy, 50)), "p99": float(np.percentile(rdy, 99))}}
+    out = {}
+    for key, t in (("from_arrival", lambda r: r.arrival), ("from_ready", lambda r: r.ready),
+                   ("service", lambda r: r.dispatched)):
+        x = np.array([r.done - t(r) for r in done]) * 1e3
+        out[key] = {"p50": float(np.percentile(x, 50)), "p99": float(np.percentile(x, 99))}
+    return out

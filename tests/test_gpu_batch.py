@@ -146,3 +146,34 @@ def test_batch_mixes_kernel_families():
     finally:
         for p in probs:
             p.close()
+
+
+def test_batched_workload_at_full_size_matches_alone_and_the_oracle():
+    # the batched workload as benchmarked: 32 x 2q + 32 x 3q + 32 x 4q, durations uniform in
+    # [0.5 T, 1.5 T], windows in {8, 32, 64, 128}, one graph-replayed batch
+    specs = S.mixed_batch_specs(seed=1, n_per_shape=32, shapes=[S.config_2q(), S.config_3q(), S.config_4q()])
+    inputs = [(S.random_alpha(sp, 1, problem=i), S.random_W(sp, 1, problem=i)) for i, sp in enumerate(specs)]
+    probs = [msqoc.Problem(sp) for sp in specs]
+    try:
+        with msqoc.Batch(probs, gradient=True, graph=True) as b:
+            for i, (a, W) in enumerate(inputs):
+                b.set_inputs(i, a, W)
+            b.eval_gradient()
+            got = [b.get_gradient(i) for i in range(len(specs))]
+        for i, p in enumerate(probs):
+            want = p.eval_gradient(*inputs[i])
+            assert_objective_close(got[i]["P"], want["P"])
+            assert_grad_close(got[i]["grad_alpha"], want["grad_alpha"], what=f"grad_alpha[{i}]")
+            assert_grad_close(got[i]["grad_W"], want["grad_W"], what=f"grad_W[{i}]")
+    finally:
+        for p in probs:
+            p.close()
+    # a member of each shape against the oracle (the one the oracle finishes first)
+    ncores = oracle.default_threads()
+    for q in (2, 3, 4):
+        i = min((k for k, sp in enumerate(specs) if sp.q == q),
+                key=lambda k: specs[k].nsteps / min(specs[k].M, ncores))
+        want = oracle.evaluate(specs[i], *inputs[i])
+        assert_objective_close(got[i]["P"], want["P"])
+        assert_grad_close(got[i]["grad_alpha"], want["grad_alpha"], what=f"oracle grad_alpha[{i}]")
+        assert_grad_close(got[i]["grad_W"], want["grad_W"], what=f"oracle grad_W[{i}]")
