@@ -737,7 +737,6 @@ def serving_section(args, peak, seconds: float) -> dict:
     sampler.start()
     for policy in ("fifo", "throughput"):
         srv.policy = policy
-        srv.dispatch_flops = 2e12 if policy == "fifo" else 2e11
         reqs = serving.poisson_requests(specs, rate=args.rate, duration=seconds, seed=1)
         done = srv.run(reqs, duration=seconds)
         out["served_" + policy] = serving_summary(done, specs, seconds, peak)
@@ -794,7 +793,7 @@ def main():
                     help="4q workload: leave out the config3, solver_fp64, batched and serving sub-objects")
     ap.add_argument("--extra-serve-seconds", type=float, default=10.0,
                     help="4q workload: seconds of each serving run inside the default line")
-    ap.add_argument("--lookahead", type=int, default=64,
+    ap.add_argument("--lookahead", type=int, default=16,
                     help="serving: requests the arrival-order policy may run ahead of the oldest one")
     ap.add_argument("--layout", choices=list(LAYOUTS), default="auto",
                     help="sweep kernel family: one thread, a lane pair or (2-level subsystems) a lane quad per fiber "

@@ -111,8 +111,32 @@ typedef struct msqoc_options {
                               64) */
     int32_t profile;       /* 1 = record CUDA events around every kernel (msqoc_kernel_times) */
     int32_t layout;        /* MSQOC_LAYOUT_*: threads per (column, fiber) of the sweep tiles */
-    int32_t reserved[3];
+    int32_t window_first;  /* a window range [window_first, window_last] (1-based) of the
+                              M-window problem: the problem is then one shard of it (below);
+                              0 and 0 = every window */
+    int32_t window_last;
+    int32_t reserved;
 } msqoc_options;
+
+/* Shards (window ranges).  Sec. 3 makes the windows independent given the window states: the
+ * objective is a sum of window terms, window m reads W^{m-1} (its initial state) and W^m (the
+ * target of its penalty), and dP/dW^m = mu (W^m - U^m(t_m)) - 2 Lambda^{m+1}(t_m) joins window
+ * m's end state to window m+1's adjoint at its start (Eq. dP-dW; Sec. 4 splits the windows over
+ * processes the same way).  A problem created with window_first = a, window_last = b runs only
+ * windows a..b on the global time grid of the M-window problem (window m owns the steps
+ * floor((m-1) N_T / M) .. floor(m N_T / M) - 1) and exchanges nothing itself:
+ *   W (input)  : the window states it reads, W^k for k = max(a-1, 1) .. min(b, M-1), in the
+ *                layout of W (nW = 2 N E times their count; W^0, the identity embedding, and
+ *                the nonexistent W^M are never passed);
+ *   P_out      : the sum of its windows' terms (pen_m for m < M, J for m = M);
+ *   J_out      : J when b = M, else 0;  pen_out: pen_m for m = a .. min(b, M-1);
+ *   grad_alpha : the sum of its windows' contributions (Eq. grad-int over windows a..b);
+ *   grad_W     : for the same k as W, the terms of dP/dW^k it owns: mu (W^k - U^k(t_k)) when
+ *                k >= a and -2 Lambda^{k+1}(t_k) when k + 1 <= b.
+ * Summing P, grad_alpha and the overlapping grad_W blocks of shards that partition 1..M gives
+ * the whole problem's values: two consecutive shards overlap in one window state, to which the
+ * earlier shard contributes its penalty term and the later one -2 Lambda of its first window.
+ * Roll-outs, roll-out estimates and batches take whole problems only (MSQOC_ERR_UNSUPPORTED). */
 
 /* Sweep kernel families.  FIBER: one thread per fiber (the L entries of a column along the last
  * subsystem), the choice for problems whose tiles fill the GPU.  PAIR: a lane pair per fiber,
@@ -148,9 +172,9 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
                                   int32_t nwindows, double mu, const msqoc_options* opt,
                                   msqoc_problem** out);
 
-/* Sizes: d (control parameters), nW (doubles of the W vector, 2 N E (M-1)) and the bytes of
- * device memory the problem holds once a gradient has been evaluated.  Any pointer may be
- * NULL. */
+/* Sizes: d (control parameters), nW (doubles of the W vector, 2 N E (M-1); for a shard the
+ * window states it reads) and the bytes of device memory the problem holds once a gradient has
+ * been evaluated.  Any pointer may be NULL. */
 msqoc_status msqoc_query(const msqoc_problem* p, int64_t* d, int64_t* nW, size_t* device_bytes);
 
 /* Sweep layout of a problem: columns per tile, tiles (CTAs) per sweep launch, threads per
@@ -160,13 +184,15 @@ msqoc_status msqoc_query_layout(const msqoc_problem* p, int32_t* col_block, int3
                                 int32_t* threads, int32_t* ckpt_interval, int32_t* layout);
 
 /* Objective only (forward sweep of every window, Eq. penalty-fcn).  P_out: 1 double;
- * J_out (1 double) and pen_out (M-1 doubles) may be NULL. */
+ * J_out (1 double) and pen_out (M-1 doubles; for a shard, one per penalty it owns) may be
+ * NULL. */
 msqoc_status msqoc_eval_objective(msqoc_problem* p, const double* alpha, const double* W,
                                   double* P_out, double* J_out, double* pen_out, void* stream);
 
 /* Objective and gradient (forward sweep, terminal conditions Eq. terminal, discrete adjoint
  * sweep with the fused Eq. grad-int quadrature, Eq. dP-dW).  grad_alpha: d doubles;
- * grad_W: 2 N E (M-1) doubles (may be NULL when M = 1).  P_out may be NULL. */
+ * grad_W: nW doubles, 2 N E (M-1) for a whole problem (may be NULL when nW = 0).  P_out may be
+ * NULL. */
 msqoc_status msqoc_eval_gradient(msqoc_problem* p, const double* alpha, const double* W,
                                  double* P_out, double* grad_alpha, double* grad_W, void* stream);
 

@@ -219,10 +219,12 @@ bool quad_admitted(const ProbDev& pd) { return pd.L == 2 && pd.nex <= MAXEXF; }
 // pairs where the tiles are too few to fill the GPU; under load, from QFT-16 at 64 windows,
 // seven one-warp quad tiles per SM take 0.73 of the time of one-thread tiles at the floor).
 // Tiles that do not fit at once run in waves of the CTAs an SM holds (the kernels'
-// occupancy at that width).  A tile over two windows pays a second gradient reduction and wider
-// class mixing in its warps: its cost is taken 1.18x (measured on the 4-transmon tiles: the
-// adjoint 8% slower, the forward 3% faster than 8-column one-window tiles, where the warp count
-// alone predicts both 14% faster; at 6-7 warps per SM those steps are latency-bound).  Candidates are ranked by
+// occupancy at that width).  A tile over two windows pays a second coefficient set, gradient
+// reduction and fold each step and wider class mixing in its warps: about one more warp's work
+// per step, so its cost is taken (w + 1) / w times that of w warps (measured on the 4-transmon
+// tiles: 6-warp two-window tiles as slow as 7-warp one-window ones, at 64 windows; 8-warp
+// two-window tiles in three waves 7% faster than 7-warp one-window tiles in four, at 256
+// windows, where (w + 1) / w predicts 4%).  Candidates are ranked by
 //   1. the makespan: an SM's ceil(tiles / SMs) tiles in waves of `resident`, summed over the
 //      waves;
 //   2. tiles that stay inside one window;
@@ -269,11 +271,11 @@ TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int g, i
             const long waves = (per_sm + resident - 1) / resident;
             const long last = per_sm - (waves - 1) * resident;
             const int cb = (E % cpt) ? 1 : 0;
-            const double ca = (cb ? 1.18 : 1.0) *
-                              (double(waves - 1) * std::max(double(resident * warps) * c_load / 4.0, c_alone) +
-                               std::max(double(last * warps) * c_load / 4.0, c_alone));
+            const double two = cb ? double(warps + 1) / double(warps) : 1.0;
+            const double ca = two * (double(waves - 1) * std::max(double(resident * warps) * c_load / 4.0, c_alone) +
+                                     std::max(double(last * warps) * c_load / 4.0, c_alone));
             const double cc = 1.0 - double((1 << pair) * cpt * F) / (32.0 * warps);
-            const bool at_floor = ca <= (cb ? 1.18 : 1.0) * double(waves) * c_alone + 1e-9;
+            const bool at_floor = ca <= two * double(waves) * c_alone + 1e-9;
             const int cw = !at_floor ? 0 : ((warps == 2 || warps == 3) ? 0 : (warps == 1 ? 1 : 2));
             const bool tie_a = ca < best_a + 1e-9, tie_b = cb == best_b, tie_w = cw == best_w;
             const bool better = best.cpt < 0 || ca < best_a - 1e-9 ||
@@ -322,7 +324,8 @@ msqoc_status check_description(const msqoc_hamiltonian* H, const msqoc_controls*
 // Shape, time grid, model scalars and tile geometry of a validated description (every field
 // of pd except the device pointers and the history segmentation).  col_block 0 = automatic.
 msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps,
-                           int32_t nwindows, double mu, int solver, int col_block, int layout, int sms, ProbDev& pd) {
+                           int32_t nwindows, double mu, int solver, int col_block, int layout, int sms, ProbDev& pd,
+                           int wfirst = 0, int wlast = 0) {
     const int q = H->nqubits, L = H->nlevels, ness = H->ness;
     int nfsum = 0;
     for (int k = 0; k < q; ++k) nfsum += C->ncarriers[k];
@@ -333,7 +336,10 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
     pd.E = ipow_i(ness, q);
     pd.F = pd.N / L;
     pd.d1 = C->nsplines;
-    pd.M = nwindows;
+    // windows: every one, or the shard wfirst..wlast (validated by the caller)
+    pd.M_glob = nwindows;
+    pd.m_off = wfirst > 0 ? wfirst - 1 : 0;
+    pd.M = wfirst > 0 ? wlast - wfirst + 1 : nwindows;
     pd.nfsum = nfsum;
     pd.d = 2 * pd.d1 * nfsum;
     pd.nsteps = nsteps;
@@ -372,8 +378,8 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
     // the tiles' shared alpha-gradient: the splines active in one window (the most over the
     // windows, from each window's first active spline), plus a margin of two
     int span = 3;
-    for (int m = 1; m <= pd.M; ++m) {
-        const int64_t n0 = (int64_t(m - 1) * nsteps) / pd.M, n1 = (int64_t(m) * nsteps) / pd.M;
+    for (int m = pd.m_off + 1; m <= pd.m_off + pd.M; ++m) {
+        const int64_t n0 = (int64_t(m - 1) * nsteps) / pd.M_glob, n1 = (int64_t(m) * nsteps) / pd.M_glob;
         if (n1 <= n0) continue;
         const int s_first = spline_index((double(n0) + 0.5) * pd.h, pd.dtau, pd.d1);
         const int s_last = spline_index((double(n1 - 1) + 0.5) * pd.h, pd.dtau, pd.d1);
@@ -409,7 +415,7 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
 
 // history segmentation for a checkpoint interval K (1 = keep every midpoint state)
 void set_segments(ProbDev& pd, int K) {
-    const int64_t max_ns = (pd.nsteps + pd.M - 1) / pd.M;
+    const int64_t max_ns = (pd.nsteps + pd.M_glob - 1) / pd.M_glob;
     pd.kseg = (K <= 1 || K >= max_ns) ? static_cast<int>(max_ns) : K;
     pd.nseg = static_cast<int>((max_ns + pd.kseg - 1) / pd.kseg);
 }
@@ -433,14 +439,23 @@ SweepArgs sweep_args(const ProbDev& pd, const ProbDev* pds_dev, const Tile* tile
     return a;
 }
 
-OutLayout out_layout(int M, int d, size_t nW) {
+OutLayout out_layout(int npen, int d, size_t nW) {
     OutLayout o;
     o.pen = 2;
-    o.ga = (o.pen + size_t(M - 1) + 1) & ~size_t(1);
+    o.ga = (o.pen + size_t(npen) + 1) & ~size_t(1);
     o.gw = (o.ga + size_t(d) + 1) & ~size_t(1);
     o.total = o.gw + nW + 2;
     return o;
 }
+
+int w_blocks(const ProbDev& pd) {
+    const int kfirst = std::max(pd.m_off, 1), klast = std::min(pd.m_off + pd.M, pd.M_glob - 1);
+    return std::max(0, klast - kfirst + 1);
+}
+
+int pen_count(const ProbDev& pd) { return pd.M - (pd.m_off + pd.M == pd.M_glob ? 1 : 0); }
+
+bool is_shard(const ProbDev& pd) { return pd.M != pd.M_glob; }
 
 }  // namespace msqoc
 
@@ -534,6 +549,10 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
     const int solver = o.solver == MSQOC_SOLVER_FP64 ? SOLVER_FP64 : SOLVER_MIXED;
     if (o.ckpt_interval < 0) return fail(MSQOC_ERR_INVALID_ARG, "checkpoint interval %d < 0", o.ckpt_interval);
     if (o.profile != 0 && o.profile != 1) return fail(MSQOC_ERR_INVALID_ARG, "profile must be 0 or 1");
+    if ((o.window_first == 0) != (o.window_last == 0) ||
+        (o.window_first != 0 && (o.window_first < 1 || o.window_first > o.window_last || o.window_last > nwindows)))
+        return fail(MSQOC_ERR_INVALID_ARG, "window range %d..%d is not within 1..%d (0 and 0 = every window)",
+                    o.window_first, o.window_last, nwindows);
 
     ProblemOwner owner{new (std::nothrow) msqoc_problem()};
     msqoc_problem* p = owner.p;
@@ -543,7 +562,8 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     if (sms <= 0) sms = 1;
-    st0 = shape_problem(H, C, T, nsteps, nwindows, mu, solver, o.col_block, o.layout, sms, pd);
+    st0 = shape_problem(H, C, T, nsteps, nwindows, mu, solver, o.col_block, o.layout, sms, pd, o.window_first,
+                        o.window_last);
     if (st0 != MSQOC_OK) return st0;
     const int q = pd.q, L = pd.L, nfsum = pd.nfsum;
     // checkpoint interval: 0 = automatic (every midpoint state unless that history would take
@@ -561,7 +581,9 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
     // ---- host-side model tables and tile layout
     const int N = pd.N, E = pd.E;
     p->ne = size_t(N) * E;
-    p->nW = 2 * p->ne * size_t(pd.M - 1);
+    p->nWs = w_blocks(pd);
+    p->npen = pen_count(pd);
+    p->nW = 2 * p->ne * size_t(p->nWs);
     std::vector<double2> P(N);
     for (int i = 0; i < N; ++i) P[i] = precond_entry(pd.h, drift_entry(H, q, L, i));
     std::vector<int> emb(E);
@@ -611,7 +633,7 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
     A(dalloc(&p->term, M), "terms");
     A(dalloc(&p->gpart, size_t(pd.ntiles) * pd.d), "gradient partials");
     A(dalloc(&p->status, 1), "status");
-    A(dalloc(&p->out_dev, out_layout(pd.M, pd.d, p->nW).total), "outputs");
+    A(dalloc(&p->out_dev, out_layout(p->npen, pd.d, p->nW).total), "outputs");
     A(dalloc(&p->reg_dev, reg_doubles(pd)), "regularization scratch");
     A(cudaMallocHost(reinterpret_cast<void**>(&p->status_host), sizeof(int)), "pinned status");
     p->profile = o.profile == 1;
@@ -623,7 +645,8 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
         pd.emb = p->emb;
         pd.V = p->V;
         pd.alpha = p->alpha_dev;
-        pd.W = reinterpret_cast<const double2*>(p->W_dev);
+        // a shard past the first window reads its first window's initial state at index -1
+        pd.W = reinterpret_cast<const double2*>(p->W_dev) + (pd.m_off >= 1 ? p->ne : 0);
         pd.ctrl = p->ctrl;
         pd.spl = p->spl;
         pd.phase = p->phase;
@@ -654,7 +677,7 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
     }
     if (st != MSQOC_OK) return st;
     p->bytes = sizeof(double2) * (N + p->ne * (1 + 3 * M) + size_t(nsteps) * (q + nfsum)) +
-               sizeof(Spline4) * size_t(nsteps) + sizeof(double) * (pd.d + p->nW + M + size_t(pd.ntiles) * pd.d + out_layout(pd.M, pd.d, p->nW).total +
+               sizeof(Spline4) * size_t(nsteps) + sizeof(double) * (pd.d + p->nW + M + size_t(pd.ntiles) * pd.d + out_layout(p->npen, pd.d, p->nW).total +
                                 reg_doubles(pd)) +
                sizeof(int) * (E + 1 + maps.size() + maps_ro.size()) + sizeof(Tile) * (tiles.size() + tiles_ro.size()) +
                sizeof(ProbDev);
@@ -708,9 +731,9 @@ namespace msqoc {
 // copy the evaluation's inputs into the problem's input buffers (stream-ordered)
 msqoc_status stage_inputs(msqoc_problem* p, const double* alpha, const double* W, cudaStream_t s) {
     if (!alpha) return fail(MSQOC_ERR_INVALID_ARG, "alpha is NULL");
-    if (p->pd.M > 1 && !W) return fail(MSQOC_ERR_INVALID_ARG, "W is NULL but M > 1");
+    if (p->nW > 0 && !W) return fail(MSQOC_ERR_INVALID_ARG, "W is NULL but the problem reads window states");
     CUDA_TRY(cudaMemcpyAsync(p->alpha_dev, alpha, p->pd.d * sizeof(double), cudaMemcpyDefault, s));
-    if (p->pd.M > 1) CUDA_TRY(cudaMemcpyAsync(p->W_dev, W, p->nW * sizeof(double), cudaMemcpyDefault, s));
+    if (p->nW > 0) CUDA_TRY(cudaMemcpyAsync(p->W_dev, W, p->nW * sizeof(double), cudaMemcpyDefault, s));
     return MSQOC_OK;
 }
 
@@ -769,7 +792,7 @@ msqoc_status launch_terminal(msqoc_problem* p, bool want_lambda, cudaStream_t s)
 
 msqoc_status launch_objective_outputs(msqoc_problem* p, double* P, double* J, double* pen, cudaStream_t s) {
     Mark mk(p, MSQOC_KERNEL_FINALIZE, s);
-    k_finalize_scalars<<<1, 32, 0, s>>>(p->pd, P, J, p->pd.M > 1 ? pen : nullptr, nullptr);
+    k_finalize_scalars<<<1, 32, 0, s>>>(p->pd, P, J, p->npen > 0 ? pen : nullptr, nullptr);
     CUDA_TRY(cudaGetLastError());
     return MSQOC_OK;
 }
@@ -779,10 +802,10 @@ msqoc_status launch_gradient_outputs(msqoc_problem* p, double* P, double* ga, do
     Mark mk(p, MSQOC_KERNEL_FINALIZE, s);
     k_finalize_scalars<<<std::max(1, (pd.d + 255) / 256), 256, 0, s>>>(pd, P, nullptr, nullptr, ga);
     CUDA_TRY(cudaGetLastError());
-    if (pd.M > 1) {
-        const size_t total = p->ne * (pd.M - 1);
+    if (p->nWs > 0) {
+        const size_t total = p->ne * size_t(p->nWs);
         const int blocks = static_cast<int>(std::min<size_t>((total + 255) / 256, 8192));
-        k_grad_W<<<blocks, 256, 0, s>>>(pd, reinterpret_cast<double2*>(gw));
+        k_grad_W<<<blocks, 256, 0, s>>>(pd, reinterpret_cast<double2*>(gw), p->nWs);
         CUDA_TRY(cudaGetLastError());
     }
     return MSQOC_OK;
@@ -844,8 +867,8 @@ msqoc_status msqoc_eval_objective(msqoc_problem* p, const double* alpha, const d
     if (all_dev) return MSQOC_OK;
     if (!dP) CUDA_TRY(cudaMemcpyAsync(P_out, o, sizeof(double), cudaMemcpyDeviceToHost, s));
     if (J_out && !dJ) CUDA_TRY(cudaMemcpyAsync(J_out, o + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
-    if (pen_out && !dpen && pd.M > 1)
-        CUDA_TRY(cudaMemcpyAsync(pen_out, o + 2, (pd.M - 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (pen_out && !dpen && p->npen > 0)
+        CUDA_TRY(cudaMemcpyAsync(pen_out, o + 2, p->npen * sizeof(double), cudaMemcpyDeviceToHost, s));
     return check_status_sync(p, s);
 }
 
@@ -853,7 +876,7 @@ msqoc_status msqoc_eval_gradient(msqoc_problem* p, const double* alpha, const do
                                  double* grad_alpha, double* grad_W, void* stream) {
     if (!p) return fail(MSQOC_ERR_INVALID_ARG, "problem is NULL");
     if (!grad_alpha) return fail(MSQOC_ERR_INVALID_ARG, "grad_alpha is NULL");
-    if (p->pd.M > 1 && !grad_W) return fail(MSQOC_ERR_INVALID_ARG, "grad_W is NULL but M > 1");
+    if (p->nW > 0 && !grad_W) return fail(MSQOC_ERR_INVALID_ARG, "grad_W is NULL but the problem reads window states");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     msqoc_status st = ensure_gradient_buffers(p, s);
     if (st) return st;
@@ -876,13 +899,13 @@ msqoc_status msqoc_eval_gradient(msqoc_problem* p, const double* alpha, const do
         }
     }
     const bool dP = !P_out || is_device_ptr(P_out), dga = is_device_ptr(grad_alpha),
-               dgw = pd.M == 1 || is_device_ptr(grad_W);
+               dgw = p->nW == 0 || is_device_ptr(grad_W);
     double* o = p->out_dev;
-    const OutLayout ol = out_layout(pd.M, pd.d, p->nW);
-    if (pd.M > 1 && dgw && reinterpret_cast<uintptr_t>(grad_W) % 16)
+    const OutLayout ol = out_layout(p->npen, pd.d, p->nW);
+    if (p->nW > 0 && dgw && reinterpret_cast<uintptr_t>(grad_W) % 16)
         return fail(MSQOC_ERR_INVALID_ARG, "device grad_W must be 16-byte aligned");
     double* ga_dst = dga ? grad_alpha : o + ol.ga;
-    double* gw_dst = pd.M == 1 ? nullptr : (dgw ? grad_W : o + ol.gw);
+    double* gw_dst = p->nW == 0 ? nullptr : (dgw ? grad_W : o + ol.gw);
     st = launch_gradient_outputs(p, P_out ? (dP ? P_out : o) : nullptr, ga_dst, gw_dst, s);
     if (st) return st;
     if (dP && dga && dgw) return MSQOC_OK;
@@ -894,6 +917,7 @@ msqoc_status msqoc_eval_gradient(msqoc_problem* p, const double* alpha, const do
 
 msqoc_status msqoc_rollout(msqoc_problem* p, const double* alpha, double* W_out, void* stream) {
     if (!p) return fail(MSQOC_ERR_INVALID_ARG, "problem is NULL");
+    if (is_shard(p->pd)) return fail(MSQOC_ERR_UNSUPPORTED, "the roll-out takes a whole problem, not a window range");
     if (p->pd.M > 1 && !W_out) return fail(MSQOC_ERR_INVALID_ARG, "W_out is NULL but M > 1");
     if (!alpha) return fail(MSQOC_ERR_INVALID_ARG, "alpha is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -901,7 +925,7 @@ msqoc_status msqoc_rollout(msqoc_problem* p, const double* alpha, double* W_out,
     CUDA_TRY(cudaMemcpyAsync(p->alpha_dev, alpha, p->pd.d * sizeof(double), cudaMemcpyDefault, s));
     msqoc_status st;
     const bool dev = is_device_ptr(W_out) && reinterpret_cast<uintptr_t>(W_out) % 16 == 0;
-    double* dst = dev ? W_out : p->out_dev + out_layout(p->pd.M, p->pd.d, p->nW).gw;
+    double* dst = dev ? W_out : p->out_dev + out_layout(p->npen, p->pd.d, p->nW).gw;
     for (bool& r : p->ran) r = false;
     if ((st = launch_controls(p, s))) return st;
     SweepArgs a = sweep_args(p->pd, p->pds, p->tiles_ro, p->lanemap_ro, SWEEP_ROLLOUT, 0);
@@ -917,10 +941,12 @@ msqoc_status msqoc_rollout(msqoc_problem* p, const double* alpha, double* W_out,
 
 msqoc_status msqoc_rollout_estimate(msqoc_problem* p, double* est_out, void* stream) {
     if (!p || !est_out) return fail(MSQOC_ERR_INVALID_ARG, "problem or est_out is NULL");
+    if (is_shard(p->pd))
+        return fail(MSQOC_ERR_UNSUPPORTED, "the roll-out estimate takes a whole problem, not a window range");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool dev = is_device_ptr(est_out);
     // a spare slot at the end of the output staging (the other slots hold the last results)
-    double* dst = dev ? est_out : p->out_dev + out_layout(p->pd.M, p->pd.d, p->nW).total - 1;
+    double* dst = dev ? est_out : p->out_dev + out_layout(p->npen, p->pd.d, p->nW).total - 1;
     k_rollout_estimate<<<1, 32, 0, s>>>(p->pd, dst);
     CUDA_TRY(cudaGetLastError());
     if (dev) return MSQOC_OK;
@@ -985,6 +1011,7 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
     msqoc_options o{};
     if (opt) o = *opt;
     o.profile = 0;
+    o.window_first = o.window_last = 0;   // the probes are whole problems
     const int solver = o.solver == MSQOC_SOLVER_FP64 ? SOLVER_FP64 : SOLVER_MIXED;
     // the probe: same shape, step size and window count, probe_steps steps per window
     const int64_t psteps = std::min<int64_t>(nsteps, int64_t(nwindows) * probe_steps);

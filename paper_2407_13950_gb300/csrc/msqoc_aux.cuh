@@ -139,13 +139,14 @@ constexpr int TERM_THREADS = 256;
 // Terminal conditions per window (Eq. terminal) and the window's objective term:
 //   m < M: pen_m = mu/2 ||U^m - W^m||^2,  Lambda^m(t_m) = mu/2 (W^m - U^m)
 //   m = M: gamma = <V, U^M>, J = ||U^M||^2/E - |gamma|^2/E^2, Lambda^M(t_M) = (gamma V - E U^M)/E^2
+// (m and M global: a shard's last window is the problem's last only when it ends the grid)
 __global__ void __launch_bounds__(TERM_THREADS) k_terminal(const ProbDev pd, const int want_lambda) {
     __shared__ double sh[TERM_THREADS];
     const int m = blockIdx.x + 1;
     const size_t ne = size_t(pd.N) * pd.E;
     const double2* U = pd.Uend + size_t(m - 1) * ne;
     double2* Lt = pd.Lterm + size_t(m - 1) * ne;
-    if (m < pd.M) {
+    if (m + pd.m_off < pd.M_glob) {
         const double2* Wm = pd.W + size_t(m - 1) * ne;
         double s = 0.0;
         for (size_t e = threadIdx.x; e < ne; e += TERM_THREADS) {
@@ -182,16 +183,18 @@ __global__ void __launch_bounds__(TERM_THREADS) k_terminal(const ProbDev pd, con
 }
 
 // P = J + sum_m pen_m (window order), J and pen outputs, and the alpha-gradient as the sum of
-// the per-tile partials in tile order.
+// the per-tile partials in tile order.  A shard sums its own windows' terms; J is 0 unless its
+// last window is the problem's last.
 __global__ void k_finalize_scalars(const ProbDev pd, double* P_out, double* J_out, double* pen_out,
                                    double* galpha_out) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const bool has_last = pd.m_off + pd.M == pd.M_glob;
         double P = 0.0;
         for (int m = 1; m <= pd.M; ++m) P += pd.term[m - 1];
         if (P_out) *P_out = P;
-        if (J_out) *J_out = pd.term[pd.M - 1];
+        if (J_out) *J_out = has_last ? pd.term[pd.M - 1] : 0.0;
         if (pen_out)
-            for (int m = 1; m < pd.M; ++m) pen_out[m - 1] = pd.term[m - 1];
+            for (int m = 1; m <= pd.M - (has_last ? 1 : 0); ++m) pen_out[m - 1] = pd.term[m - 1];
     }
     if (galpha_out) {
         for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < pd.d; l += gridDim.x * blockDim.x) {
@@ -215,15 +218,25 @@ __global__ void k_rollout_estimate(const ProbDev pd, double* est) {
     }
 }
 
-// dP/dW^m = mu (W^m - U^m(t_m)) - 2 Lambda^{m+1}(t_m) = 2 (Lambda^m(t_m) - Lambda^{m+1}(t_m))
-// (Eq. dP-dW with the factor of Appendix B, Eq. dT-dW-j), m = 1..M-1.
-__global__ void k_grad_W(const ProbDev pd, double2* gW) {
+// dP/dW^k = mu (W^k - U^k(t_k)) - 2 Lambda^{k+1}(t_k) = 2 (Lambda^k(t_k) - Lambda^{k+1}(t_k))
+// (Eq. dP-dW with the factor of Appendix B, Eq. dT-dW-j), k = 1..M-1.  A shard (global windows
+// m_off + 1 .. m_off + M) writes, for the window states it reads (k = max(m_off, 1) ..
+// min(m_off + M, M_glob - 1)), the terms it owns: 2 Lambda^k(t_k) if window k is its own,
+// -2 Lambda^{k+1}(t_k) if window k + 1 is.
+__global__ void k_grad_W(const ProbDev pd, double2* gW, int nblocks) {
     const size_t ne = size_t(pd.N) * pd.E;
-    const size_t total = ne * (pd.M - 1);
+    const size_t total = ne * size_t(nblocks);
+    const int kfirst = pd.m_off > 1 ? pd.m_off : 1;
     for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += size_t(gridDim.x) * blockDim.x) {
-        const double2 lt = pd.Lterm[e];
-        const double2 l0 = pd.Lam0[e + ne];
-        gW[e] = make_double2(2.0 * (lt.x - l0.x), 2.0 * (lt.y - l0.y));
+        const int k = kfirst + static_cast<int>(e / ne);
+        const size_t i = e % ne;
+        const int jk = k - pd.m_off;                  // local index of window k (own if >= 1)
+        const bool own_k = jk >= 1, own_next = jk + 1 <= pd.M;
+        const double2 lt = own_k ? pd.Lterm[size_t(jk - 1) * ne + i] : make_double2(0.0, 0.0);
+        const double2 l0 = own_next ? pd.Lam0[size_t(jk) * ne + i] : make_double2(0.0, 0.0);
+        gW[e] = own_k && own_next ? make_double2(2.0 * (lt.x - l0.x), 2.0 * (lt.y - l0.y))
+                                  : (own_k ? make_double2(2.0 * lt.x, 2.0 * lt.y)
+                                           : make_double2(-2.0 * l0.x, -2.0 * l0.y));
     }
 }
 

@@ -143,7 +143,7 @@ msqoc_status enqueue(msqoc_batch* b, const std::vector<msqoc_problem*>& sel, Til
     });
     if (st) return st;
     for (msqoc_problem* p : sel) {
-        const OutLayout ol = out_layout(p->pd.M, p->pd.d, p->nW);
+        const OutLayout ol = out_layout(p->npen, p->pd.d, p->nW);
         double* o = p->out_dev;
         if ((st = launch_gradient_outputs(p, o, o + ol.ga, p->pd.M > 1 ? o + ol.gw : nullptr, s))) return st;
     }
@@ -205,6 +205,8 @@ msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t fla
     for (int i = 0; i < n; ++i) {
         if (!problems[i]) return fail(MSQOC_ERR_INVALID_ARG, "problem %d is NULL", i);
         if (problems[i]->device != dev) return fail(MSQOC_ERR_INVALID_ARG, "problem %d lives on another device", i);
+        if (is_shard(problems[i]->pd))
+            return fail(MSQOC_ERR_UNSUPPORTED, "problem %d is a window range; batches take whole problems", i);
         for (int j = 0; j < i; ++j)
             if (problems[j] == problems[i]) return fail(MSQOC_ERR_INVALID_ARG, "problem %d appears twice", i);
     }
@@ -434,7 +436,7 @@ msqoc_status msqoc_get_gradient(msqoc_problem* p, double* P_out, double* grad_al
     if (p->pd.M > 1 && !grad_W) return fail(MSQOC_ERR_INVALID_ARG, "grad_W is NULL but M > 1");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double* o = p->out_dev;
-    const OutLayout ol = out_layout(p->pd.M, p->pd.d, p->nW);
+    const OutLayout ol = out_layout(p->npen, p->pd.d, p->nW);
     if (P_out) CUDA_TRY(cudaMemcpyAsync(P_out, o, sizeof(double), cudaMemcpyDefault, s));
     CUDA_TRY(cudaMemcpyAsync(grad_alpha, o + ol.ga, p->pd.d * sizeof(double), cudaMemcpyDefault, s));
     if (p->pd.M > 1) CUDA_TRY(cudaMemcpyAsync(grad_W, o + ol.gw, p->nW * sizeof(double), cudaMemcpyDefault, s));

@@ -15,6 +15,8 @@ struct msqoc_problem {
     int device = 0;
     int ckpt_interval = 1;   // K (1 = every midpoint state kept)
     size_t nW = 0;           // doubles in W
+    int nWs = 0;             // window states in W (M - 1, or those a shard reads)
+    int npen = 0;            // penalty terms (M - 1, or those a shard owns)
     size_t ne = 0;           // N*E
     // owned device buffers
     msqoc::ProbDev* pds = nullptr;   // device copy of pd (read by the sweeps)
@@ -91,12 +93,18 @@ long tile_count(int M, int E, int cpt);
 SweepArgs sweep_args(const ProbDev& pd, const ProbDev* pds_dev, const Tile* tiles, const int* lanemap, int mode,
                      int seg);
 
-// Output staging layout in out_dev (doubles): P, J, pen[M-1], grad_alpha[d], grad_W[nW].
+// Output staging layout in out_dev (doubles): P, J, pen[npen], grad_alpha[d], grad_W[nW].
 // grad_alpha and grad_W start at even offsets: grad_W is written as double2 (16-byte aligned).
 struct OutLayout {
     size_t pen, ga, gw, total;
 };
-OutLayout out_layout(int M, int d, size_t nW);
+OutLayout out_layout(int npen, int d, size_t nW);
+// window states a problem reads (W blocks) and penalty terms it owns: M - 1 each for a whole
+// problem; for a shard, W^k for k = max(m_off, 1) .. min(m_off + M, M_glob - 1) and pen_m for
+// its windows m < M_glob
+int w_blocks(const ProbDev& pd);
+int pen_count(const ProbDev& pd);
+bool is_shard(const ProbDev& pd);
 
 // steps of an evaluation of one problem (stream-ordered)
 msqoc_status stage_inputs(msqoc_problem* p, const double* alpha, const double* W, cudaStream_t s);
@@ -106,7 +114,8 @@ msqoc_status launch_controls(msqoc_problem* p, cudaStream_t s);
 msqoc_status launch_terminal(msqoc_problem* p, bool want_lambda, cudaStream_t s);
 // P, J (may be NULL), pen (may be NULL) of the last forward sweep into device arrays
 msqoc_status launch_objective_outputs(msqoc_problem* p, double* P, double* J, double* pen, cudaStream_t s);
-// P (may be NULL), dP/dalpha, dP/dW (NULL when M = 1) of the last adjoint sweep into device arrays
+// P (may be NULL), dP/dalpha, dP/dW (NULL when there is no window state) of the last adjoint
+// sweep into device arrays
 msqoc_status launch_gradient_outputs(msqoc_problem* p, double* P, double* ga, double* gw, cudaStream_t s);
 msqoc_status status_error(int st);
 msqoc_status check_status_sync(msqoc_problem* p, cudaStream_t s);

@@ -41,6 +41,9 @@ struct __align__(16) Spline4 {
 struct ProbDev {
     // shape
     int q, L, N, E, F, ness, d1, M, nfsum, d;
+    int m_off;     // global index of the first window minus one (0 unless the problem is a shard)
+    int M_glob;    // windows of the whole problem (M for a whole problem; windows are local
+                   // 1..M, global m_off + 1 .. m_off + M, on the whole problem's time grid)
     int cb;        // columns of a full tile
     int nthreads;  // threads per tile (multiple of 32)
     int pair;      // kernel family: log2 of the threads per fiber (0: one thread, 1: a lane pair,
@@ -74,7 +77,9 @@ struct ProbDev {
     const double2* V;            // [E][N] target
     // inputs of this evaluation (device memory)
     const double* alpha;         // [d]
-    const double2* W;            // [M-1][E][N]
+    const double2* W;            // [M-1][E][N]; W + (m - 2) E N is the initial state of local
+                                 // window m (a shard that starts past the first window reads its
+                                 // first window's initial state at index -1)
     // scratch
     double2* ctrl;               // [nsteps][q] d_k(t_{n+1/2})
     Spline4* spl;                // [nsteps] (first spline index, solver counts, w0, w1, w2)

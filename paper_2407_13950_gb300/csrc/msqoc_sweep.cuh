@@ -22,7 +22,9 @@
 //     the FP64 residual r = P rhs - z + s P (iX_C) z of z = P rhs + d is formed once with an
 //     FP64 apply, and the FP32 correction e (I + ...)e = r is added in FP64.  Conversions
 //     between f64 and f32 are done with integer bit operations because the hardware
-//     conversions issue on the (slow) FP64 pipe.
+//     conversions issue on the (slow) FP64 pipe; they carry a per-column binary scale taken
+//     from the launch's initial state (the step preserves column norms), so the FP32 stage
+//     works relative to the column norm whatever the state's magnitude.
 // The adjoint sweep fuses the gradient quadrature of Eq. grad-int at the midpoints:
 //   z_k = <Lbar, a_k Ubar>_F, y_k = <Lbar, a_k^+ Ubar>_F (summed over the tile's columns),
 //   dP/dalpha1_kfs += -2h B_s Im(e^{i W t} z_k + e^{-i W t} y_k),
@@ -383,7 +385,8 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
     }
 
     // ---- initial state
-    //   forward, whole window : U^m(t_{m-1}) = W^{m-1} (identity embedding for m = 1)
+    //   forward, whole window : U^m(t_{m-1}) = W^{m-1} (identity embedding for the first window
+    //                           of the whole problem)
     //   forward, recompute    : the segment's checkpoint
     //   adjoint               : Lambda^m(t_m) for the window's last segment, else the state the
     //                           previous (later) segment left
@@ -397,11 +400,25 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
             u[l] = (my_lo + my_cnt == my_ns) ? pd.Lterm[wcol + i] : pd.Lstate[wcol + i];
         } else if (a.mode == SWEEP_RECOMPUTE) {
             u[l] = pd.ckpt[((size_t(m - 1) * pd.nseg + a.seg) * E + col) * N + i];
-        } else if (m == 1) {
+        } else if (m + pd.m_off == 1) {
             u[l] = make_double2(pd.emb[col] == i ? 1.0 : 0.0, 0.0);
         } else {
             u[l] = pd.W[(size_t(m - 2) * E + col) * N + i];
         }
+    }
+
+    // ---- the mixed solver's per-column scale, from the launch's initial state (column_shift)
+    int sh = 0;
+    if constexpr (SOLVER == SOLVER_MIXED) {
+        __shared__ int colexp_s[MAX_TILE_COLS];
+        for (int j = tid; j < MAX_TILE_COLS; j += blockDim.x) colexp_s[j] = 0;
+        tile_sync();
+        int ce = 0;
+#pragma unroll
+        for (int l = 0; l < L; ++l) ce = max(ce, max(exp_field(u[l].x), exp_field(u[l].y)));
+        if (act && ce > 0 && c < MAX_TILE_COLS) atomicMax(&colexp_s[c], ce);
+        tile_sync();
+        sh = column_shift(colexp_s[c < MAX_TILE_COLS ? c : 0]);
     }
 
     // ---- history blocks: slot s of a tile covers a contiguous column range of its window
@@ -595,7 +612,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
             float2 bf[L], df[L], y[L];
 #pragma unroll
             for (int l = 0; l < L; ++l) {
-                bf[l] = f32_of(b[l]);
+                bf[l] = f32_of_scaled(b[l], sh);
                 y[l] = bf[l];
             }
             {
@@ -639,7 +656,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
             double2 dacc[L];
 #pragma unroll
             for (int l = 0; l < L; ++l) {
-                dacc[l] = f64_of(df[l]);
+                dacc[l] = f64_of_scaled(df[l], sh);
                 z[l] = make_double2(b[l].x + dacc[l].x, b[l].y + dacc[l].y);
             }
             for (int pass = 0;; ++pass) {
@@ -658,7 +675,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
                     const double2 r = resid_from<S>(dacc[l], Pd[l], w[l]);
-                    rf[l] = f32_of(r);
+                    rf[l] = f32_of_scaled(r, sh);
                     e[l] = rf[l];
                 }
                 for (int it = 0; it < j2max; ++it) {
@@ -678,7 +695,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
                 }
                 double2 ed[L];
 #pragma unroll
-                for (int l = 0; l < L; ++l) ed[l] = f64_of(e[l]);
+                for (int l = 0; l < L; ++l) ed[l] = f64_of_scaled(e[l], sh);
                 if (pass < R) {
 #pragma unroll
                     for (int l = 0; l < L; ++l) z[l] = make_double2(z[l].x + ed[l].x, z[l].y + ed[l].y);

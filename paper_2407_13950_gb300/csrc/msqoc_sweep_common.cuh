@@ -43,6 +43,61 @@ __device__ __forceinline__ double f64_of(float f) {
 __device__ __forceinline__ float2 f32_of(double2 v) { return make_float2(f32_of(v.x), f32_of(v.y)); }
 __device__ __forceinline__ double2 f64_of(float2 v) { return make_double2(f64_of(v.x), f64_of(v.y)); }
 
+// The same conversions of a state entry with a per-column binary scale: f32_of_scaled(x, sh) is
+// x 2^-sh rounded to f32 as above, f64_of_scaled(f, sh) is f 2^sh exactly.  The scale is an
+// exponent offset applied to the bit fields (no FP64 instruction); |sh| <= SCALE_SHIFT_MAX keeps
+// zero at zero.  Magnitudes of 2^128 and more after scaling become infinities (a visible failure
+// instead of a wrapped exponent); below 2^-126 they become signed zero.
+constexpr int SCALE_SHIFT_MAX = 896;
+__device__ __forceinline__ float f32_of_scaled(double x, int sh) {
+    unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned int sgn = static_cast<unsigned int>(bits >> 32) & 0x80000000u;
+    const long long ahi = static_cast<long long>(static_cast<unsigned int>(bits >> 32) & 0x7fffffffu) -
+                          static_cast<long long>(sh) * (1 << 20);
+    bits -= static_cast<unsigned long long>(static_cast<long long>(sh)) << 52;
+    bits += (1ull << 28);
+    const unsigned int hi = static_cast<unsigned int>(bits >> 32);
+    const unsigned int lo = static_cast<unsigned int>(bits);
+    const unsigned int t = __funnelshift_l(lo, hi, 3);
+    unsigned int fb = ((t ^ 0x40000000u) & 0x7fffffffu) | sgn;
+    fb = (ahi < 0x38100000ll) ? sgn : fb;
+    fb = (ahi >= 0x47f00000ll) ? (sgn | 0x7f800000u) : fb;
+    return __uint_as_float(fb);
+}
+__device__ __forceinline__ double f64_of_scaled(float f, int sh) {
+    const unsigned int fb = __float_as_uint(f);
+    const unsigned int s = fb & 0x80000000u;
+    const unsigned int a = fb & 0x7fffffffu;
+    unsigned int hi = s | ((a >> 3) + 0x38000000u + (static_cast<unsigned int>(sh) << 20));
+    unsigned int lo = a << 29;
+    hi = (a < 0x00800000u) ? s : hi;
+    lo = (a < 0x00800000u) ? 0u : lo;
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+__device__ __forceinline__ float2 f32_of_scaled(double2 v, int sh) {
+    return make_float2(f32_of_scaled(v.x, sh), f32_of_scaled(v.y, sh));
+}
+__device__ __forceinline__ double2 f64_of_scaled(float2 v, int sh) {
+    return make_double2(f64_of_scaled(v.x, sh), f64_of_scaled(v.y, sh));
+}
+// biased exponent field of a double (0 for zero and subnormals)
+__device__ __forceinline__ int exp_field(double x) {
+    return static_cast<int>(static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7ff;
+}
+// Scale of a column of the mixed-precision solver: the step preserves every column's 2-norm (the
+// Cayley map of a Hermitian H is unitary, forward and adjoint), so the largest entry exponent
+// ce of the column's state at the start of a launch bounds every entry of every later step by
+// 2^(ce - 1022) sqrt(N) < 2^(ce - 1018) (N <= 256).  Entries scaled by 2^-sh with
+// sh = ce - 1018 stay below 1, and the FP32 stage's range limits apply relative to the column
+// norm instead of to absolute magnitudes.
+__device__ __forceinline__ int column_shift(int ce) {
+    if (ce == 0) return 0;   // an all-zero column
+    const int sh = ce - 1018;
+    return sh > SCALE_SHIFT_MAX ? SCALE_SHIFT_MAX : (sh < -SCALE_SHIFT_MAX ? -SCALE_SHIFT_MAX : sh);
+}
+// tile columns at most (E = 2^q for 2-level shapes, q <= MAXQ)
+constexpr int MAX_TILE_COLS = 1 << MAXQ;
+
 template <typename T2> struct cx;
 template <> struct cx<double2> { using T = double; };
 template <> struct cx<float2> { using T = float; };
@@ -276,9 +331,10 @@ static __device__ __noinline__ void store_grad_partial(double* gp, const double*
     }
 }
 
-// first global step of window m (1-based); window m owns [win_start(m), win_start(m + 1))
+// first global step of local window m (1-based); window m owns [win_start(m), win_start(m + 1))
+// of the whole problem's grid
 __device__ __forceinline__ int64_t win_start(const ProbDev& pd, int m) {
-    return (static_cast<int64_t>(m - 1) * pd.nsteps) / pd.M;
+    return (static_cast<int64_t>(pd.m_off + m - 1) * pd.nsteps) / pd.M_glob;
 }
 
 }  // namespace msqoc

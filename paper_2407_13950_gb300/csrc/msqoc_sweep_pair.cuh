@@ -361,7 +361,8 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
     }
 
     // ---- initial state (this part's component)
-    //   forward, whole window : U^m(t_{m-1}) = W^{m-1} (identity embedding for m = 1)
+    //   forward, whole window : U^m(t_{m-1}) = W^{m-1} (identity embedding for the first window
+    //                           of the whole problem)
     //   forward, recompute    : the segment's checkpoint
     //   adjoint               : Lambda^m(t_m) for the window's last segment, else the state the
     //                           previous (later) segment left
@@ -375,11 +376,24 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
             u[l] = comp((my_lo + my_cnt == my_ns) ? pd.Lterm[wcol + i] : pd.Lstate[wcol + i], part);
         } else if (a.mode == SWEEP_RECOMPUTE) {
             u[l] = comp(pd.ckpt[((size_t(m - 1) * pd.nseg + a.seg) * E + col) * N + i], part);
-        } else if (m == 1) {
+        } else if (m + pd.m_off == 1) {
             u[l] = (part == 0 && pd.emb[col] == i) ? 1.0 : 0.0;
         } else {
             u[l] = comp(pd.W[(size_t(m - 2) * E + col) * N + i], part);
         }
+    }
+    // ---- the mixed solver's per-column scale, from the launch's initial state (column_shift)
+    int sh = 0;
+    if constexpr (SOLVER == SOLVER_MIXED) {
+        __shared__ int colexp_s[MAX_TILE_COLS];
+        for (int j = tid; j < MAX_TILE_COLS; j += blockDim.x) colexp_s[j] = 0;
+        tile_sync();
+        int ce = 0;
+#pragma unroll
+        for (int l = 0; l < LS; ++l) ce = max(ce, exp_field(u[l]));
+        if (act && ce > 0 && c < MAX_TILE_COLS) atomicMax(&colexp_s[c], ce);
+        tile_sync();
+        sh = column_shift(colexp_s[c < MAX_TILE_COLS ? c : 0]);
     }
     // this part's components of a [..][N] complex array at the fiber
     auto store_fiber = [&](double2* dst) {
@@ -579,7 +593,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
             float bf[LS], df[LS], y[LS];
 #pragma unroll
             for (int l = 0; l < LS; ++l) {
-                bf[l] = f32_of(b[l]);
+                bf[l] = f32_of_scaled(b[l], sh);
                 y[l] = bf[l];
             }
             {
@@ -622,7 +636,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
             double dacc[LS];
 #pragma unroll
             for (int l = 0; l < LS; ++l) {
-                dacc[l] = f64_of(df[l]);
+                dacc[l] = f64_of_scaled(df[l], sh);
                 z[l] = b[l] + dacc[l];
             }
             for (int pass = 0;; ++pass) {
@@ -639,7 +653,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
                 for (int l = 0; l < LS; ++l) {
                     const double wo = partner(w[l]);
                     const double r = fma(SPp[l].x, w[l], fma(SPp[l].y, wo, -dacc[l]));
-                    rf[l] = f32_of(r);
+                    rf[l] = f32_of_scaled(r, sh);
                     e[l] = rf[l];
                 }
                 for (int it = 0; it < j2max; ++it) {
@@ -658,7 +672,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
                 }
                 double ed[LS];
 #pragma unroll
-                for (int l = 0; l < LS; ++l) ed[l] = f64_of(e[l]);
+                for (int l = 0; l < LS; ++l) ed[l] = f64_of_scaled(e[l], sh);
                 if (pass < R) {
 #pragma unroll
                     for (int l = 0; l < LS; ++l) z[l] = z[l] + ed[l];

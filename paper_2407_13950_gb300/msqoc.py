@@ -51,7 +51,8 @@ class Controls(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int32), ("col_block", ctypes.c_int32), ("ckpt_interval", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("layout", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("profile", ctypes.c_int32), ("layout", ctypes.c_int32), ("window_first", ctypes.c_int32),
+                ("window_last", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -174,15 +175,21 @@ class Problem:
     solver: SOLVER_MIXED (default: FP64 residual, FP32 corrections) or SOLVER_FP64; col_block:
     columns per sweep tile (0: the library's model); ckpt_interval: K (0: automatic); layout:
     LAYOUT_FIBER, LAYOUT_PAIR or LAYOUT_QUAD (2-level subsystems) to force a sweep kernel family
-    (LAYOUT_AUTO: the model's choice).  After creation .col_block, .tiles, .threads,
-    .ckpt_interval and .layout report what the library chose."""
+    (LAYOUT_AUTO: the model's choice); windows: (first, last), 1-based, to create the shard of
+    windows first..last of the spec's M-window problem (its W input and grad_W output are the
+    window states W^max(first-1,1) .. W^min(last,M-1); see `shard_w_range`).  After creation
+    .col_block, .tiles, .threads, .ckpt_interval and .layout report what the library chose, .nW
+    the doubles of W and .npen the penalty terms the problem owns."""
 
     def __init__(self, spec, target: Optional[np.ndarray] = None, solver: int = SOLVER_DEFAULT,
-                 col_block: int = 0, ckpt_interval: int = 0, profile: bool = False, layout: int = 0):
+                 col_block: int = 0, ckpt_interval: int = 0, profile: bool = False, layout: int = 0,
+                 windows: Optional[tuple] = None):
         lib = load()
         self.spec = spec
         self._desc = _Description(spec, target)
-        O = Options(solver, col_block, ckpt_interval, 1 if profile else 0, layout)
+        first, last = windows if windows is not None else (0, 0)
+        self.windows = (first, last) if windows is not None else (1, spec.M)
+        O = Options(solver, col_block, ckpt_interval, 1 if profile else 0, layout, int(first), int(last))
         h = ctypes.c_void_p()
         _check(lib.msqoc_create_problem(ctypes.byref(self._desc.H), ctypes.byref(self._desc.C), self._desc.target_ptr,
                                         float(spec.T), int(spec.nsteps), int(spec.M), float(spec.mu),
@@ -197,6 +204,8 @@ class Problem:
         d, nW, nbytes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
         _check(lib.msqoc_query(h, ctypes.byref(d), ctypes.byref(nW), ctypes.byref(nbytes)))
         self.d, self.nW, self.device_bytes = d.value, nW.value, nbytes.value
+        a, b = self.windows
+        self.npen = (b - a + 1) - (1 if b == spec.M else 0)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -223,22 +232,20 @@ class Problem:
 
     # ---- host-array convenience API (numpy in, numpy out; synchronous)
     def eval_objective(self, alpha, W=None, stream=None) -> dict:
-        M = self.spec.M
         P, J = np.zeros(1), np.zeros(1)
-        pen = np.zeros(max(M - 1, 1))
-        w = W if M > 1 else None
+        pen = np.zeros(max(self.npen, 1))
+        w = W if self.nW > 0 else None
         _check(load().msqoc_eval_objective(self.handle, _ptr(alpha), _ptr(w), _ptr(P), _ptr(J),
-                                           _ptr(pen) if M > 1 else None, _stream_handle(stream)))
-        return {"P": float(P[0]), "J": float(J[0]), "pen": pen[:M - 1].copy()}
+                                           _ptr(pen) if self.npen > 0 else None, _stream_handle(stream)))
+        return {"P": float(P[0]), "J": float(J[0]), "pen": pen[:self.npen].copy()}
 
     def eval_gradient(self, alpha, W=None, stream=None) -> dict:
-        M = self.spec.M
         P = np.zeros(1)
         ga = np.zeros(self.d)
         gW = np.zeros(max(self.nW, 1))
-        w = W if M > 1 else None
+        w = W if self.nW > 0 else None
         _check(load().msqoc_eval_gradient(self.handle, _ptr(alpha), _ptr(w), _ptr(P), _ptr(ga),
-                                          _ptr(gW) if M > 1 else None, _stream_handle(stream)))
+                                          _ptr(gW) if self.nW > 0 else None, _stream_handle(stream)))
         return {"P": float(P[0]), "grad_alpha": ga, "grad_W": gW[:self.nW].copy()}
 
     def rollout(self, alpha, stream=None) -> np.ndarray:
@@ -275,6 +282,12 @@ class Problem:
     def eval_objective_into(self, alpha, W, P_out, J_out=None, pen_out=None, stream=None):
         _check(load().msqoc_eval_objective(self.handle, _ptr(alpha), _ptr(W), _ptr(P_out), _ptr(J_out),
                                            _ptr(pen_out), _stream_handle(stream)))
+
+
+def shard_w_range(M: int, first: int, last: int):
+    """Window states W^k (k, 1-based) a shard of windows first..last of an M-window problem
+    reads, and whose dP/dW terms it returns: (k_first, k_last), empty when k_last < k_first."""
+    return max(first - 1, 1), min(last, M - 1)
 
 
 # C-ABI-named functions

@@ -15,12 +15,14 @@ dispatches ready requests of that class as one subset of the server's batch
 dispatch in flight and each slot its own CUDA streams, so requests that arrive while others run
 are admitted as slots free up and their kernels overlap on the device.  Two policies:
 
-* ``fifo`` (default): only the first ``lookahead`` requests not yet dispatched, in arrival
-  order, are eligible; the class of the oldest eligible ready request goes first, with every
-  eligible ready request of that class, and the class holding the oldest undispatched request
-  runs on a high-priority stream.  Every shape therefore advances in arrival order, as it would
-  on a one-request-at-a-time server, while the look-ahead fills the GPU with the requests just
-  behind the oldest one.
+* ``fifo`` (default): requests advance in arrival order.  A ready request is eligible while
+  fewer than ``lookahead`` requests that arrived before it are unfinished; the class of the
+  oldest eligible ready request is dispatched with every eligible ready request of that class.
+  The dispatch holding the oldest unfinished request runs on the highest-priority stream, the
+  other eligible dispatches on a middle one.  Requests of cheap classes (each below
+  ``cheap_flops``) may also run ahead of the window, on at most ``background_slots`` slots and
+  the lowest-priority stream, so they fill what the large shapes leave idle without holding
+  them back.
 * ``throughput``: any ready request is eligible; cheap classes and classes that waited longer
   than ``age_limit`` run on high-priority streams.  It completes the most evaluations but
   serves the expensive shapes later than arrival order.
@@ -73,8 +75,8 @@ def eval_flops(spec, gradient: bool) -> float:
 
 
 class _Dispatched:
-    """Fenwick tree over request indices marking the dispatched ones: how many requests before
-    index i are still undispatched, in O(log n)."""
+    """Fenwick tree over request indices marking requests (the finished ones): how many marked
+    requests precede index i, in O(log n)."""
 
     def __init__(self, n: int):
         self.t = [0] * (n + 1)
@@ -96,17 +98,20 @@ class _Dispatched:
 class Server:
     """Sessions and the continuous-batching loop.
 
-    policy "fifo": a ready request is eligible while fewer than `lookahead` undispatched
-    requests arrived before it; a dispatch takes every eligible ready request of the class of
-    the oldest one (up to `dispatch_flops` of estimated work, at least one request); the
-    dispatch holding the oldest undispatched request runs on a high-priority stream.
+    policy "fifo": a ready request is eligible while fewer than `lookahead` requests that
+    arrived before it are unfinished; a dispatch takes every eligible ready request of the class
+    of the oldest one (up to `dispatch_flops` of estimated work, at least one request); the
+    dispatch holding the oldest unfinished request runs on the highest-priority stream.  Ready
+    requests of classes costing less than `cheap_flops` each may run ahead of the window on at
+    most `background_slots` slots, at the lowest priority.
     policy "throughput": every ready request is eligible; a dispatch takes the ready requests of
     the oldest one's class up to `dispatch_flops`; classes whose requests cost less than
     `cheap_flops` each, or whose oldest ready request has waited longer than `age_limit`
     seconds, run on high-priority streams."""
 
-    def __init__(self, device_budget_bytes: int, policy: str = "fifo", lookahead: int = 64,
-                 dispatch_flops: Optional[float] = None, cheap_flops: float = 1e10, age_limit: float = 1.0):
+    def __init__(self, device_budget_bytes: int, policy: str = "fifo", lookahead: int = 16,
+                 dispatch_flops: float = 2.1e11, cheap_flops: float = 1e9, background_slots: int = 2,
+                 age_limit: float = 1.0):
         if policy not in ("fifo", "throughput"):
             raise ValueError(f"unknown policy {policy!r}")
         self.budget = int(device_budget_bytes)
@@ -115,9 +120,9 @@ class Server:
         self.batch: Optional[msqoc.Batch] = None
         self.policy = policy
         self.lookahead = int(lookahead)
-        self.dispatch_flops = dispatch_flops if dispatch_flops is not None else (
-            2e12 if policy == "fifo" else 2e11)
+        self.dispatch_flops = dispatch_flops
         self.cheap_flops = cheap_flops
+        self.background_slots = int(background_slots)
         self.age_limit = age_limit
 
     # ------------------------------------------------------------------ sessions
@@ -163,27 +168,32 @@ class Server:
             self.batch = msqoc.Batch(self.sessions, gradient=True)
         b = self.batch
         fifo = self.policy == "fifo"
-        # per slot a normal and a high-priority stream (a lower number is a higher priority;
-        # CUDA clamps values beyond the device's range)
-        streams = [(torch.cuda.Stream(priority=0), torch.cuda.Stream(priority=-8)) for _ in range(SLOTS)]
+        # per slot a lowest-, a middle- and a highest-priority stream (a lower number is a higher
+        # priority; CUDA clamps values beyond the device's range)
+        lo_pri, hi_pri = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") \
+            else (0, -5)
+        mid_pri = (lo_pri + hi_pri) // 2 if hi_pri < lo_pri else lo_pri
+        streams = [(torch.cuda.Stream(priority=lo_pri), torch.cuda.Stream(priority=mid_pri),
+                    torch.cuda.Stream(priority=hi_pri)) for _ in range(SLOTS)]
         cost = [(eval_flops(p.spec, False), eval_flops(p.spec, True)) for p in self.sessions]
         queues: Dict[int, collections.deque] = {s: collections.deque() for s in range(len(self.sessions))}
+        n = len(requests)
         index = {id(r): i for i, r in enumerate(requests)}
-        dispatched = _Dispatched(len(requests))
+        finished = _Dispatched(n)          # marks finished requests
+        is_done = [False] * n
+        oldest = 0                         # index of the oldest unfinished request
         busy = [False] * len(self.sessions)
-        inflight = {}            # slot -> (event, class, [requests])
+        inflight = {}            # slot -> (event, class, [requests], background)
         busy_class = set()
         free_slots = list(range(SLOTS))
+        n_background = 0
         done: List[Request] = []
         self.base_event = None
         if record_events:
             self.base_event = torch.cuda.Event(enable_timing=True)
             self.base_event.record(torch.cuda.current_stream())
-        oldest = 0               # index of the oldest undispatched request (fifo)
-        is_dispatched = [False] * len(requests)
         t0 = time.perf_counter()
         nxt = 0
-        n = len(requests)
         while len(done) < n:
             now = time.perf_counter() - t0
             if duration is not None and now >= duration:
@@ -196,19 +206,25 @@ class Server:
                 progressed = True
             # completions
             for slot in list(inflight):
-                ev, cls, reqs = inflight[slot]
+                ev, cls, reqs, bg = inflight[slot]
                 if ev.query():
                     tdone = time.perf_counter() - t0
                     for r in reqs:
                         r.result = b.get_gradient(r.session) if r.gradient else b.get_objective(r.session)
                         r.done = tdone
                         busy[r.session] = False
+                        i = index[id(r)]
+                        is_done[i] = True
+                        finished.mark(i)
                     done.extend(reqs)
                     del inflight[slot]
                     busy_class.discard(cls)
                     free_slots.append(slot)
+                    n_background -= 1 if bg else 0
                     progressed = True
-            # dispatch: the oldest eligible ready request's class
+            while oldest < n and is_done[oldest]:
+                oldest += 1
+            # dispatch
             while free_slots:
                 ready = []
                 for s, q in queues.items():
@@ -216,18 +232,26 @@ class Server:
                         r = q[0]
                         if math.isnan(r.ready):
                             r.ready = max(r.arrival, now)
-                        ready.append(r)
-                if fifo:
-                    # eligible: fewer than `lookahead` undispatched requests arrived before it
-                    ready = [r for r in ready
-                             if index[id(r)] - dispatched.before(index[id(r)]) < self.lookahead]
-                ready = [r for r in ready if (self._shape(r.session), r.gradient) not in busy_class]
+                        if (self._shape(r.session), r.gradient) not in busy_class:
+                            ready.append(r)
                 if not ready:
                     break
-                first = min(ready, key=lambda r: r.arrival)
+                background = False
+                if fifo:
+                    # eligible: fewer than `lookahead` unfinished requests arrived before it
+                    elig = [r for r in ready if index[id(r)] - finished.before(index[id(r)]) < self.lookahead]
+                    if not elig and n_background < self.background_slots:
+                        elig = [r for r in ready if cost[r.session][1 if r.gradient else 0] < self.cheap_flops]
+                        background = True
+                    if not elig:
+                        break
+                    pool = elig
+                else:
+                    pool = ready
+                first = min(pool, key=lambda r: r.arrival)
                 cls = (self._shape(first.session), first.gradient)
                 sel, work = [], 0.0
-                for r in sorted((r for r in ready if (self._shape(r.session), r.gradient) == cls),
+                for r in sorted((r for r in pool if (self._shape(r.session), r.gradient) == cls),
                                 key=lambda r: r.arrival):
                     c = cost[r.session][1 if r.gradient else 0]
                     if sel and work + c > self.dispatch_flops:
@@ -236,13 +260,11 @@ class Server:
                     work += c
                 slot = free_slots.pop()
                 if fifo:
-                    while oldest < n and is_dispatched[oldest]:
-                        oldest += 1
-                    high = any(index[id(r)] == oldest for r in sel)
+                    pri = 0 if background else (2 if any(index[id(r)] == oldest for r in sel) else 1)
                 else:
                     cheap = cost[first.session][1 if first.gradient else 0] < self.cheap_flops
-                    high = cheap or now - first.ready > self.age_limit
-                stream = streams[slot][1 if high else 0]
+                    pri = 2 if (cheap or now - first.ready > self.age_limit) else 0
+                stream = streams[slot][pri]
                 ev0 = None
                 if record_events:
                     ev0 = torch.cuda.Event(enable_timing=True)
@@ -252,9 +274,6 @@ class Server:
                     busy[r.session] = True
                     r.dispatched = now
                     r.slot = slot
-                    i = index[id(r)]
-                    is_dispatched[i] = True
-                    dispatched.mark(i)
                     b.set_inputs(r.session, r.alpha, r.W, stream=stream)
                 b.eval_subset([r.session for r in sel], gradient=cls[1], slot=slot, stream=stream)
                 ev = torch.cuda.Event(enable_timing=record_events)
@@ -262,7 +281,8 @@ class Server:
                 if record_events:
                     for r in sel:
                         r.events = (ev0, ev)
-                inflight[slot] = (ev, cls, sel)
+                inflight[slot] = (ev, cls, sel, background)
+                n_background += 1 if background else 0
                 busy_class.add(cls)
                 progressed = True
             if not progressed:
@@ -273,7 +293,8 @@ class Server:
     def run_plain(self, requests: Sequence[Request], duration: Optional[float] = None) -> List[Request]:
         """The same requests one at a time in arrival order, each its own synchronous
         evaluation (one problem per launch sequence, nothing overlapped).  A request is ready,
-        as in `run`, once it has arrived and its session's previous request is done."""
+        as in `run`, once it has arrived and its session's previous request is done; as in
+        `run`, a request that finishes after `duration` is not counted."""
         t0 = time.perf_counter()
         done: List[Request] = []
         last_done: Dict[int, float] = {}
@@ -290,6 +311,8 @@ class Server:
             r.result = p.eval_gradient(r.alpha, r.W) if r.gradient else p.eval_objective(r.alpha, r.W)
             r.done = time.perf_counter() - t0
             last_done[r.session] = r.done
+            if duration is not None and r.done > duration:
+                break            # finished after the end of the run: not counted, as in `run`
             done.append(r)
         return done
 

@@ -34,3 +34,13 @@ def test_autotune_tries_lane_quads_on_two_levels():
     best, layout, times = msqoc.autotune(spec, probe_steps=16)
     assert {lay for lay, _ in times} == {msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_QUAD}
     assert times[(layout, best)] == min(times.values())
+
+
+def test_tile_model_picks_the_measured_fastest_tiles_of_the_benchmark_workload():
+    # 4 transmons at 256 windows: 9-column tiles (456 CTAs, three full waves of 152, each tile over
+    # two windows) measured fastest by the autotuner (5.5 ms per probe evaluation against 5.9 for
+    # 8-column tiles in four waves); at 64 windows 8-column one-window tiles (128 CTAs)
+    with msqoc.Problem(S.config_4q(M=256)) as p:
+        assert (p.layout, p.col_block, p.tiles) == (msqoc.LAYOUT_FIBER, 9, 456)
+    with msqoc.Problem(S.config_4q(M=64)) as p:
+        assert (p.layout, p.col_block) == (msqoc.LAYOUT_FIBER, 8)
