@@ -259,6 +259,7 @@ def config3_section(dev, stream, peak, steps: int = 5, warmup: int = 2) -> dict:
                     "adjoint_frac_of_fp64_peak": fl["adjoint"] / (kt["adjoint"] * 1e-3) / 1e12 / peak,
                     "whole_eval_frac_of_fp64_peak": fl["total"] / (ms * 1e-3) / 1e12 / peak,
                     "tiles": f"{FAMILY[p.layout]} x {p.col_block} columns ({p.tiles} CTAs)",
+                    "steps_per_sync": p.steps_per_sync,
                     "ckpt_interval": p.ckpt_interval, "device_bytes": p.device_bytes}
         del a_d, W_d, outs
         torch.cuda.empty_cache()
@@ -313,12 +314,14 @@ def run_ours(args, spec):
     # autotuner (-1)
     layout = LAYOUTS[args.layout]
     tuned = tune_ms = None
+    sps = args.steps_per_sync
     if args.col_block < 0:
-        tuned, layout, tune_ms = msqoc.autotune(spec, alpha=alpha, probe_steps=64, solver=solver, layout=layout)
+        tuned, layout, sps, tune_ms = msqoc.autotune(spec, alpha=alpha, probe_steps=64, solver=solver, layout=layout,
+                                                     steps_per_sync=args.steps_per_sync)
         fam = {1: "fiber", 2: "pair", 3: "quad"}
-        tune_ms = {f"{fam[lay]}-{cb}": v for (lay, cb), v in tune_ms.items()}
+        tune_ms = {f"{fam[lay]}-{cb}-s{dp}": v for (lay, cb, dp), v in tune_ms.items()}
     col_block = tuned if args.col_block < 0 else args.col_block
-    prob = msqoc.Problem(spec, solver=solver, col_block=col_block, profile=True, layout=layout)
+    prob = msqoc.Problem(spec, solver=solver, col_block=col_block, profile=True, layout=layout, steps_per_sync=sps)
     peak_tflops = msqoc.measure_fp64_peak()
 
     for _ in range(args.warmup):
@@ -379,6 +382,7 @@ def run_ours(args, spec):
             "col_block": (f"autotuned ({prob.col_block})" if tuned else
                           col_block if col_block > 0 else f"model ({prob.col_block})"),
             "layout": FAMILY[prob.layout], "ctas": prob.tiles, "threads_per_cta": prob.threads,
+            "steps_per_sync": prob.steps_per_sync,
             **({"autotune": {"best": tuned, "ms_per_probe_eval": tune_ms}} if tuned else {})},
         "roofline": {"bound": "alu", "kernel": f"k_sweep ({dom})", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,
@@ -789,6 +793,9 @@ def main():
                     help="columns per sweep tile: -1 = measured by the library's autotuner (default), "
                          "0 = the library's model")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--steps-per-sync", type=int, default=0,
+                    help="time steps per history synchronisation of a sweep tile (0: measured by the autotuner "
+                         "with --col-block -1, else one)")
     ap.add_argument("--no-extras", action="store_true",
                     help="4q workload: leave out the config3, solver_fp64, batched and serving sub-objects")
     ap.add_argument("--extra-serve-seconds", type=float, default=10.0,

@@ -115,7 +115,12 @@ typedef struct msqoc_options {
                               M-window problem: the problem is then one shard of it (below);
                               0 and 0 = every window */
     int32_t window_last;
-    int32_t reserved;
+    int32_t steps_per_sync; /* time steps per synchronisation of a sweep tile with the midpoint
+                              history in device memory: the forward stages this many steps'
+                              states in shared memory and stores them with one wait, the adjoint
+                              fetches this many steps per mbarrier phase (one group ahead).
+                              1..8; 0 = 1.  Larger groups take more shared memory; a group that
+                              does not fit is MSQOC_ERR_INVALID_ARG */
 } msqoc_options;
 
 /* Shards (window ranges).  Sec. 3 makes the windows independent given the window states: the
@@ -178,10 +183,12 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
 msqoc_status msqoc_query(const msqoc_problem* p, int64_t* d, int64_t* nW, size_t* device_bytes);
 
 /* Sweep layout of a problem: columns per tile, tiles (CTAs) per sweep launch, threads per
- * tile, the checkpoint interval K and the kernel family (MSQOC_LAYOUT_FIBER, MSQOC_LAYOUT_PAIR
- * or MSQOC_LAYOUT_QUAD) in use (after automatic choices).  Any pointer may be NULL. */
+ * tile, the checkpoint interval K, the kernel family (MSQOC_LAYOUT_FIBER, MSQOC_LAYOUT_PAIR
+ * or MSQOC_LAYOUT_QUAD) and the steps per history synchronisation in use (after automatic
+ * choices).  Any pointer may be NULL. */
 msqoc_status msqoc_query_layout(const msqoc_problem* p, int32_t* col_block, int32_t* tiles,
-                                int32_t* threads, int32_t* ckpt_interval, int32_t* layout);
+                                int32_t* threads, int32_t* ckpt_interval, int32_t* layout,
+                                int32_t* steps_per_sync);
 
 /* Objective only (forward sweep of every window, Eq. penalty-fcn).  P_out: 1 double;
  * J_out (1 double) and pen_out (M-1 doubles; for a shard, one per penalty it owns) may be
@@ -378,23 +385,27 @@ msqoc_status msqoc_eval_objective_noalloc(const msqoc_hamiltonian* H, const msqo
                                           const double* alpha, const double* W, double* P_out,
                                           double* J_out, double* pen_out, void* stream);
 
-/* Sweep kernel family and tile width by measurement (not an operation of the paper): for every
- * admissible (family, columns per tile) pair, a problem of the same description, step size and
- * window count but only probe_steps steps per window is created with it and its objective +
- * gradient is timed (one warm-up, two timed evaluations, CUDA events on the default stream).
- * *col_block and *layout (may be NULL) receive the fastest pair (use them as
- * msqoc_options.col_block and .layout); widths[i], layouts[i], ms[i] (i < *n_out <= max_out;
- * may be NULL) the pairs tried and their milliseconds per evaluation.  alpha: d control
- * coefficients (host) of a typical iterate (the iteration counts of the step solver depend on
- * the control amplitude); NULL = alternating +-2 pi 0.002 rad/ns.  opt: solver, checkpoint
- * interval and layout as for msqoc_create_problem (layout AUTO tries every family the problem
- * admits; col_block is ignored).  Allocates and frees temporary problems; synchronizes the
- * device. */
+/* Sweep kernel family, tile width and steps per history synchronisation by measurement (not
+ * an operation of the paper): for every admissible (family, columns per tile) pair, a problem
+ * of the same description, step size and window count but only probe_steps steps per window
+ * is created with it and its objective + gradient is timed (one warm-up, two timed
+ * evaluations, CUDA events on the default stream); then the fastest pair is timed with 2, 4
+ * and 8 steps per synchronisation (those whose history groups fit the shared memory), unless
+ * opt->steps_per_sync fixes it.  *col_block, *layout and *steps_per_sync (the last two may be
+ * NULL) receive the fastest (use them as msqoc_options.col_block, .layout, .steps_per_sync);
+ * widths[i], layouts[i], depths[i], ms[i] (i < *n_out <= max_out; may be NULL) the candidates
+ * tried and their milliseconds per evaluation.  alpha: d control coefficients (host) of a
+ * typical iterate (the iteration counts of the step solver depend on the control amplitude);
+ * NULL = alternating +-2 pi 0.002 rad/ns.  opt: solver, checkpoint interval, layout and steps
+ * per synchronisation as for msqoc_create_problem (layout AUTO tries every family the problem
+ * admits; col_block and the window range are ignored).  Allocates and frees temporary
+ * problems; synchronizes the device. */
 msqoc_status msqoc_autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, double T,
                             int64_t nsteps, int32_t nwindows, double mu, const msqoc_options* opt,
                             const double* alpha, int32_t probe_steps, int32_t* col_block,
-                            int32_t* layout, int32_t* widths, int32_t* layouts, float* ms,
-                            int32_t max_out, int32_t* n_out);
+                            int32_t* layout, int32_t* steps_per_sync, int32_t* widths,
+                            int32_t* layouts, int32_t* depths, float* ms, int32_t max_out,
+                            int32_t* n_out);
 
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t msqoc_version(void);

@@ -16,7 +16,8 @@ MSQOC_DECL(3, 1) MSQOC_DECL(3, 2) MSQOC_DECL(3, 3) MSQOC_DECL(3, 4) MSQOC_DECL(3
 
 size_t sweep_smem_bytes(const SweepArgs& a) {
     const int N = ipow_c(a.L, a.q);
-    return sweep_layout(a.q, a.L, N, a.cpt, a.nthreads, a.gmax, a.solver, a.mode == SWEEP_ADJOINT, a.pair).total;
+    return sweep_layout(a.q, a.L, N, a.cpt, a.nthreads, a.gmax, a.solver, a.mode == SWEEP_ADJOINT, a.pair,
+                        a.hdepth).total;
 }
 
 cudaError_t launch_sweep(const SweepArgs& a, int ntiles, cudaStream_t s) {

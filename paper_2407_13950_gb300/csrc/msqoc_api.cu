@@ -1,5 +1,6 @@
 // Host side of libmsqoc: problem packing, tile layout, device memory, launches and the C ABI.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -410,7 +411,18 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
     const int64_t max_ns = (nsteps + nwindows - 1) / nwindows;
     pd.kseg = static_cast<int>(max_ns);
     pd.nseg = 1;
+    pd.hdepth = 1;
     return MSQOC_OK;
+}
+
+// the sweeps' shared memory fits with history groups of `depth` steps
+bool history_depth_ok(const ProbDev& pd, int depth) {
+    if (depth < 1 || depth > MAX_HDEPTH) return false;
+    for (int bwd = 0; bwd < 2; ++bwd)
+        if (sweep_layout(pd.q, pd.L, pd.N, pd.cb, pd.nthreads, pd.glocal, pd.solver, bwd != 0, pd.pair, depth).total >
+            200 * 1024)
+            return false;
+    return true;
 }
 
 // history segmentation for a checkpoint interval K (1 = keep every midpoint state)
@@ -436,6 +448,7 @@ SweepArgs sweep_args(const ProbDev& pd, const ProbDev* pds_dev, const Tile* tile
     a.solver = pd.solver;
     a.nthreads = pd.nthreads;
     a.pair = pd.pair;
+    a.hdepth = pd.hdepth;
     return a;
 }
 
@@ -549,6 +562,8 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
     const int solver = o.solver == MSQOC_SOLVER_FP64 ? SOLVER_FP64 : SOLVER_MIXED;
     if (o.ckpt_interval < 0) return fail(MSQOC_ERR_INVALID_ARG, "checkpoint interval %d < 0", o.ckpt_interval);
     if (o.profile != 0 && o.profile != 1) return fail(MSQOC_ERR_INVALID_ARG, "profile must be 0 or 1");
+    if (o.steps_per_sync < 0 || o.steps_per_sync > MAX_HDEPTH)
+        return fail(MSQOC_ERR_INVALID_ARG, "steps_per_sync %d is not within 0..%d", o.steps_per_sync, MAX_HDEPTH);
     if ((o.window_first == 0) != (o.window_last == 0) ||
         (o.window_first != 0 && (o.window_first < 1 || o.window_first > o.window_last || o.window_last > nwindows)))
         return fail(MSQOC_ERR_INVALID_ARG, "window range %d..%d is not within 1..%d (0 and 0 = every window)",
@@ -577,6 +592,11 @@ msqoc_status create_problem(const msqoc_hamiltonian* H, const msqoc_controls* C,
     }
     p->ckpt_interval = K;
     set_segments(pd, K);
+    // steps per history synchronisation: 0 = one (every step)
+    pd.hdepth = o.steps_per_sync > 0 ? o.steps_per_sync : 1;
+    if (!history_depth_ok(pd, pd.hdepth))
+        return fail(MSQOC_ERR_INVALID_ARG, "history groups of %d steps do not fit the tile's shared memory",
+                    pd.hdepth);
 
     // ---- host-side model tables and tile layout
     const int N = pd.N, E = pd.E;
@@ -706,8 +726,9 @@ msqoc_status msqoc_query(const msqoc_problem* p, int64_t* d, int64_t* nW, size_t
 }
 
 msqoc_status msqoc_query_layout(const msqoc_problem* p, int32_t* col_block, int32_t* tiles, int32_t* threads,
-                                int32_t* ckpt_interval, int32_t* layout) {
+                                int32_t* ckpt_interval, int32_t* layout, int32_t* steps_per_sync) {
     if (!p) return fail(MSQOC_ERR_INVALID_ARG, "problem is NULL");
+    if (steps_per_sync) *steps_per_sync = p->pd.hdepth;
     if (col_block) *col_block = p->pd.cb;
     if (tiles) *tiles = p->pd.ntiles;
     if (threads) *threads = p->pd.nthreads;
@@ -999,11 +1020,12 @@ namespace {
 
 msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps, int32_t nwindows,
                       double mu, const msqoc_options* opt, const double* alpha, int32_t probe_steps,
-                      int32_t* col_block, int32_t* layout, int32_t* widths, int32_t* layouts, float* ms,
-                      int32_t max_out, int32_t* n_out) {
+                      int32_t* col_block, int32_t* layout, int32_t* steps_per_sync, int32_t* widths, int32_t* layouts,
+                      int32_t* depths, float* ms, int32_t max_out, int32_t* n_out) {
     if (!col_block) return fail(MSQOC_ERR_INVALID_ARG, "col_block is NULL");
     *col_block = 0;
     if (layout) *layout = 0;
+    if (steps_per_sync) *steps_per_sync = 0;
     if (n_out) *n_out = 0;
     msqoc_status st = check_description(H, C, T, nsteps, nwindows);
     if (st != MSQOC_OK) return st;
@@ -1046,19 +1068,27 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
     double* o_gW = o_ga + ((pd.d + 1) & ~1);
     float best_ms = 0.f;
     int best = 0, nrec = 0;
-    int best_layout = 0;
+    int best_layout = 0, best_depth = 1;
     const int fam_lo = o.layout == MSQOC_LAYOUT_AUTO ? MSQOC_LAYOUT_FIBER : o.layout;
     const int fam_hi = o.layout == MSQOC_LAYOUT_AUTO ? MSQOC_LAYOUT_QUAD : o.layout;
-    for (int fam = fam_lo; fam <= fam_hi && st == MSQOC_OK; ++fam)
-    for (int cb = std::min(pd.E, MAX_TILE_THREADS / pd.F); cb >= 1 && st == MSQOC_OK; --cb) {
-        if (choose_tile_layout(pd.M, pd.E, pd.F, pd.q, pd.L, pd.N, pd.glocal, solver, 1, cb, fam, quad_admitted(pd)).cpt <
-            0)
-            continue;
+    // candidates: every (family, width) with one step per history synchronisation, then the
+    // best pair with 2, 4 and 8 steps per synchronisation
+    std::vector<std::array<int, 3>> cands;
+    for (int fam = fam_lo; fam <= fam_hi; ++fam)
+        for (int cb = std::min(pd.E, MAX_TILE_THREADS / pd.F); cb >= 1; --cb)
+            if (choose_tile_layout(pd.M, pd.E, pd.F, pd.q, pd.L, pd.N, pd.glocal, solver, 1, cb, fam,
+                                   quad_admitted(pd)).cpt >= 0)
+                cands.push_back({fam, cb, o.steps_per_sync > 0 ? o.steps_per_sync : 1});
+    const size_t n_first = cands.size();
+    for (size_t ci = 0; ci < cands.size() && st == MSQOC_OK; ++ci) {
+        const int fam = cands[ci][0], cb = cands[ci][1], dp = cands[ci][2];
         msqoc_options oc = o;
         oc.col_block = cb;
         oc.layout = fam;
+        oc.steps_per_sync = dp;
         msqoc_problem* p = nullptr;
         msqoc_status cs = msqoc_create_problem(H, C, nullptr, pT, psteps, nwindows, mu, &oc, &p);
+        if (cs == MSQOC_ERR_INVALID_ARG && ci >= n_first) continue;   // that depth does not fit
         if (cs != MSQOC_OK) {
             st = cs;
             break;
@@ -1085,13 +1115,18 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
             widths[nrec] = cb;
             ms[nrec] = t;
             if (layouts) layouts[nrec] = fam;
+            if (depths) depths[nrec] = dp;
         }
         ++nrec;
         if (best == 0 || t < best_ms) {
             best = cb;
             best_layout = fam;
+            best_depth = dp;
             best_ms = t;
         }
+        // the depth candidates are appended once the (family, width) sweep is done
+        if (ci + 1 == n_first && best > 0 && o.steps_per_sync == 0)
+            for (int dp2 : {2, 4, 8}) cands.push_back({best_layout, best, dp2});
     }
     cudaFree(dbuf);
     cudaFree(d_out);
@@ -1101,6 +1136,7 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
     if (best == 0) return fail(MSQOC_ERR_UNSUPPORTED, "no admissible tile width");
     *col_block = best;
     if (layout) *layout = best_layout;
+    if (steps_per_sync) *steps_per_sync = best_depth;
     if (n_out) *n_out = std::min(nrec, max_out);
     return MSQOC_OK;
 }
@@ -1109,11 +1145,12 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
 
 extern "C" msqoc_status msqoc_autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, double T, int64_t nsteps,
                                        int32_t nwindows, double mu, const msqoc_options* opt, const double* alpha,
-                                       int32_t probe_steps, int32_t* col_block, int32_t* layout, int32_t* widths,
-                                       int32_t* layouts, float* ms, int32_t max_out, int32_t* n_out) {
+                                       int32_t probe_steps, int32_t* col_block, int32_t* layout,
+                                       int32_t* steps_per_sync, int32_t* widths, int32_t* layouts, int32_t* depths,
+                                       float* ms, int32_t max_out, int32_t* n_out) {
     return guarded([&] {
-        return autotune(H, C, T, nsteps, nwindows, mu, opt, alpha, probe_steps, col_block, layout, widths, layouts, ms,
-                        max_out, n_out);
+        return autotune(H, C, T, nsteps, nwindows, mu, opt, alpha, probe_steps, col_block, layout, steps_per_sync,
+                        widths, layouts, depths, ms, max_out, n_out);
     });
 }
 

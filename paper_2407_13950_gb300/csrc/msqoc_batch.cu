@@ -303,6 +303,8 @@ msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t fla
         }
         const ProbDev& p0 = b->probs[g.members[0]]->pd;
         g.args = sweep_args(p0, g.pds, g.tiles, g.lanemap, SWEEP_OBJECTIVE, 0);
+        // one history depth for the launch: the smallest of the members' (it always fits)
+        for (int mi : g.members) g.args.hdepth = std::min(g.args.hdepth, b->probs[mi]->pd.hdepth);
         g.args.cpt = cpt;
         g.args.gmax = gmax;
         g.args.nthreads = nthreads;

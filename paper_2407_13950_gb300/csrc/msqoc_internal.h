@@ -14,6 +14,7 @@ constexpr int MAXL = 4;       // levels per subsystem handled by the sweep kerne
 constexpr int MAX_TILE_THREADS = 256;       // threads of a one-thread-per-fiber tile (255 registers a thread)
 constexpr int MAX_PAIR_TILE_THREADS = 384;  // threads of a lane-pair tile (168 registers a thread)
 constexpr int MAX_QUAD_TILE_THREADS = 384;  // threads of a lane-quad tile (168 registers a thread)
+constexpr int MAX_HDEPTH = 8;               // steps per history group at most
 
 enum Solver { SOLVER_FP64 = 1, SOLVER_MIXED = 2 };
 
@@ -57,6 +58,8 @@ struct ProbDev {
     int kseg;      // steps per history segment (checkpoint interval; >= the longest window when
                    // every midpoint state is kept)
     int nseg;      // segments per window: ceil(longest window / kseg)
+    int hdepth;    // steps per history synchronisation: midpoint states staged and stored (forward)
+                   // or fetched (adjoint) in groups of hdepth steps, one wait per group
     int64_t nsteps;
     double T, h, mu, dtau;
     double lam;    // ||a + a^+|| on L levels (bound of the ladder-term norm per unit |d|)
@@ -128,6 +131,7 @@ struct SweepArgs {
     int seg;              // segment (SWEEP_RECOMPUTE, SWEEP_ADJOINT)
     int L, q, solver, nthreads;
     int pair;             // kernel family: log2 of the threads per fiber (0, 1 or 2)
+    int hdepth;           // steps per history group (ProbDev::hdepth), >= 1
     double2* out;         // SWEEP_ROLLOUT: [M-1][E][N] states at the window boundaries
 };
 

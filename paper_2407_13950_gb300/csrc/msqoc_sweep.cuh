@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
     const ProbDev& pd = a.pds[tile.prob];
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const SweepSmem lay = sweep_layout(Q, L, N, a.cpt, blockDim.x, a.gmax, SOLVER, BWD, 0);
+    const SweepSmem lay = sweep_layout(Q, L, N, a.cpt, blockDim.x, a.gmax, SOLVER, BWD, 0, a.hdepth);
     double2* coef_d = reinterpret_cast<double2*>(smem + lay.coef_d);
     float2* coef_f = reinterpret_cast<float2*>(smem + lay.coef_f);
     int* params = reinterpret_cast<int*>(smem + lay.params);
@@ -432,17 +432,32 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
         const int jr = static_cast<int>(step_of(s, jj) - n0) - lo;   // step within the segment
         return pd.hist + ((size_t(tile.m0 + s - 1) * pd.kseg + jr) * E + (s ? 0 : tile.c0)) * N;
     };
-    // forward (thread 0): store the staged midpoints of iteration jj of every slot that had a step
-    auto publish = [&](int jj) {
-        if (jj < cnt_0) bulk_s2g(hist_ptr(0, jj), H, bytes_0);
-        if (jj < cnt_1) bulk_s2g(hist_ptr(1, jj), H + size_t(ncol0) * N, bytes_1);
+    // Steps per history synchronisation: the midpoint states move in groups of hd iterations
+    // (iterations g hd .. g hd + hd - 1), one block of the tile's cpt N states per iteration.  The
+    // forward stages a group in H and stores it with one wait per group; the adjoint fetches
+    // group g into UB0 / UB1 (g even / odd) on mbar[g & 1], one group ahead.
+    const int hd = a.hdepth;
+    const size_t hstride = size_t(a.cpt) * N;
+    // forward (thread 0): store the staged group starting at iteration g0 (every slot with a step)
+    auto publish_group = [&](int g0) {
+        const int g1 = min(g0 + hd, nit);
+        for (int j = g0; j < g1; ++j) {
+            const double2* src = H + size_t(j - g0) * hstride;
+            if (j < cnt_0) bulk_s2g(hist_ptr(0, j), src, bytes_0);
+            if (j < cnt_1) bulk_s2g(hist_ptr(1, j), src + size_t(ncol0) * N, bytes_1);
+        }
     };
-    // adjoint (thread 0): fetch the midpoints of iteration jj into dst, completing on bar
-    auto fetch = [&](double2* dst, int jj, uint64_t* bar) {
-        const uint32_t b0 = jj < cnt_0 ? bytes_0 : 0u, b1 = jj < cnt_1 ? bytes_1 : 0u;
-        mbar_expect_tx(bar, b0 + b1);
-        if (b0) bulk_g2s(dst, hist_ptr(0, jj), b0, bar);
-        if (b1) bulk_g2s(dst + size_t(ncol0) * N, hist_ptr(1, jj), b1, bar);
+    // adjoint (thread 0): fetch the group starting at iteration g0 into dst, completing on bar
+    auto fetch_group = [&](double2* dst, int g0, uint64_t* bar) {
+        const int g1 = min(g0 + hd, nit);
+        uint32_t total = 0;
+        for (int j = g0; j < g1; ++j) total += (j < cnt_0 ? bytes_0 : 0u) + (j < cnt_1 ? bytes_1 : 0u);
+        mbar_expect_tx(bar, total);
+        for (int j = g0; j < g1; ++j) {
+            double2* d = dst + size_t(j - g0) * hstride;
+            if (j < cnt_0) bulk_g2s(d, hist_ptr(0, j), bytes_0, bar);
+            if (j < cnt_1) bulk_g2s(d + size_t(ncol0) * N, hist_ptr(1, j), bytes_1, bar);
+        }
     };
 
     if (BWD) {
@@ -453,7 +468,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
             fence_mbar_init();
         }
         tile_sync();
-        if (tid == 0 && nit > 0) fetch(UB0, 0, &mbar[0]);
+        if (tid == 0 && nit > 0) fetch_group(UB0, 0, &mbar[0]);
     }
 
     // warp s < nslot computes slot s's coefficients and folds its gradient; it keeps d_k and
@@ -565,13 +580,13 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
         // previous iteration's midpoints (forward) or fetches the next iteration's (adjoint)
         auto first_sync_work = [&]() {
             if (BWD && *tflag) timed_out = true;   // uniform: read after a barrier
-            if (!BWD && want_hist && tid == 0 && jj > 0) {
+            if (!BWD && want_hist && tid == 0 && jj > 0 && jj % hd == 0) {
                 fence_proxy_async_smem();
-                publish(jj - 1);
+                publish_group(jj - hd);
             }
-            if (BWD && tid == 0 && jj + 1 < nit) {
-                const int nx = (jj + 1) & 1;
-                fetch(nx ? UB1 : UB0, jj + 1, &mbar[nx]);
+            if (BWD && tid == 0 && jj % hd == 0 && jj + hd < nit) {
+                const int gn = jj / hd + 1;
+                fetch_group((gn & 1) ? UB1 : UB0, jj + hd, &mbar[gn & 1]);
             }
         };
 
@@ -667,7 +682,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
                 // forward: the staged midpoints of the previous step must have been read by their
                 // bulk store (issued at this step's first barrier) before this step's are staged;
                 // waiting here, ahead of a barrier every step has, makes the staging barrier-free
-                if (!BWD && want_hist && pass == 0 && tid == 0) bulk_wait_read_all();
+                if (!BWD && want_hist && pass == 0 && tid == 0 && jj % hd == 0) bulk_wait_read_all();
                 tile_sync();
                 double2 w[L];
                 apply_off<L, Q, double2>(D0, cfd, fb, z, w, pd);
@@ -718,12 +733,14 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
             if (want_hist) {
                 if constexpr (SOLVER == SOLVER_FP64) {
                     // (the FP64 solver's step may have no barrier after the first one)
-                    if (tid == 0) bulk_wait_read_all();
-                    tile_sync();
+                    if (jj % hd == 0) {
+                        if (tid == 0) bulk_wait_read_all();
+                        tile_sync();
+                    }
                 }
                 if (act && live) {
 #pragma unroll
-                    for (int l = 0; l < L; ++l) H[fb.xo + l] = z[l];
+                    for (int l = 0; l < L; ++l) H[size_t(jj % hd) * hstride + fb.xo + l] = z[l];
                 }
                 fence_proxy_async_smem();
             }
@@ -744,10 +761,11 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
             }
         } else {
             // ---- gradient quadrature on the midpoints (fused): needs Ubar_n of the tile
-            double2* UB = par ? UB1 : UB0;
+            const int hg = jj / hd;   // history group of this iteration
+            double2* UB = ((hg & 1) ? UB1 : UB0) + size_t(jj - hg * hd) * hstride;
             // a wait that gives up raises the tile's flag, read after the next barrier (the
             // products below then use whatever landed; the evaluation reports the timeout)
-            if (!mbar_wait(&mbar[par], (jj >> 1) & 1)) *tflag = 1;
+            if (jj == hg * hd && !mbar_wait(&mbar[hg & 1], (hg >> 1) & 1)) *tflag = 1;
             double acc[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = 0.0;
@@ -858,7 +876,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
         if constexpr (!BWD) {
             if (want_hist && tid == 0 && nit > 0) {
                 fence_proxy_async_smem();
-                publish(nit - 1);
+                publish_group(((nit - 1) / hd) * hd);
                 bulk_wait_all();
             }
             if (a.mode != SWEEP_RECOMPUTE && !rollout && act && my_cnt > 0) {

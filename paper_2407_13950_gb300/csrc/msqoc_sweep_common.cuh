@@ -265,7 +265,7 @@ struct SweepSmem {
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 __host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cpt, int nthreads, int gmax, int solver,
-                                                  bool bwd, int pair) {
+                                                  bool bwd, int pair, int hdepth = 1) {
     SweepSmem s{};
     const int nslot = q * L * 2;
     const int nwarps = nthreads / 32;
@@ -287,9 +287,11 @@ __host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cpt, 
     s.D1 = o;     o = align16(o + (solver == SOLVER_FP64 ? buf_d : 0));
     s.FA = o;     o = align16(o + (solver == SOLVER_MIXED ? buf_f : 0));
     s.FB = o;     o = align16(o + (solver == SOLVER_MIXED ? buf_f : 0));
-    s.H = o;      o = align16(o + (bwd ? 0 : buf_d));
-    s.UB0 = o;    o = align16(o + (bwd ? buf_d : 0));
-    s.UB1 = o;    o = align16(o + (bwd ? buf_d : 0));
+    // history staging: hdepth blocks of cpt N states (forward H; adjoint UB0 / UB1, one group each)
+    const size_t hist_b = size_t(hdepth) * cpt * N * 16;
+    s.H = o;      o = align16(o + (bwd ? 0 : hist_b));
+    s.UB0 = o;    o = align16(o + (bwd ? hist_b : 0));
+    s.UB1 = o;    o = align16(o + (bwd ? hist_b : 0));
     s.total = o;
     return s;
 }

@@ -52,7 +52,7 @@ class Controls(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int32), ("col_block", ctypes.c_int32), ("ckpt_interval", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("layout", ctypes.c_int32), ("window_first", ctypes.c_int32),
-                ("window_last", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("window_last", ctypes.c_int32), ("steps_per_sync", ctypes.c_int32)]
 
 
 _lib = None
@@ -77,7 +77,7 @@ def load(build_if_missing: bool = True):
         sigs = {
             "msqoc_create_problem": (i32, [vp, vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, vp, vp]),
             "msqoc_query": (i32, [vp, vp, vp, vp]),
-            "msqoc_query_layout": (i32, [vp, vp, vp, vp, vp, vp]),
+            "msqoc_query_layout": (i32, [vp, vp, vp, vp, vp, vp, vp]),
             "msqoc_eval_objective": (i32, [vp, vp, vp, vp, vp, vp, vp]),
             "msqoc_eval_gradient": (i32, [vp, vp, vp, vp, vp, vp, vp]),
             "msqoc_destroy_problem": (i32, [vp]),
@@ -103,7 +103,7 @@ def load(build_if_missing: bool = True):
             "msqoc_lbfgs_trial": (i32, [i64, i64, vp, vp, ctypes.c_double, vp, vp, vp, vp, vp]),
             "msqoc_lbfgs_update": (i32, [i64, vp, vp, vp, vp, vp, vp, vp, vp]),
             "msqoc_autotune": (i32, [vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, vp, vp, i32, vp, vp, vp, vp,
-                                     vp, i32, vp]),
+                                     vp, vp, vp, i32, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -175,32 +175,34 @@ class Problem:
     solver: SOLVER_MIXED (default: FP64 residual, FP32 corrections) or SOLVER_FP64; col_block:
     columns per sweep tile (0: the library's model); ckpt_interval: K (0: automatic); layout:
     LAYOUT_FIBER, LAYOUT_PAIR or LAYOUT_QUAD (2-level subsystems) to force a sweep kernel family
-    (LAYOUT_AUTO: the model's choice); windows: (first, last), 1-based, to create the shard of
+    (LAYOUT_AUTO: the model's choice); steps_per_sync: time steps per synchronisation of a tile
+    with the midpoint history (0: one); windows: (first, last), 1-based, to create the shard of
     windows first..last of the spec's M-window problem (its W input and grad_W output are the
     window states W^max(first-1,1) .. W^min(last,M-1); see `shard_w_range`).  After creation
-    .col_block, .tiles, .threads, .ckpt_interval and .layout report what the library chose, .nW
-    the doubles of W and .npen the penalty terms the problem owns."""
+    .col_block, .tiles, .threads, .ckpt_interval, .layout and .steps_per_sync report what the
+    library chose, .nW the doubles of W and .npen the penalty terms the problem owns."""
 
     def __init__(self, spec, target: Optional[np.ndarray] = None, solver: int = SOLVER_DEFAULT,
                  col_block: int = 0, ckpt_interval: int = 0, profile: bool = False, layout: int = 0,
-                 windows: Optional[tuple] = None):
+                 windows: Optional[tuple] = None, steps_per_sync: int = 0):
         lib = load()
         self.spec = spec
         self._desc = _Description(spec, target)
         first, last = windows if windows is not None else (0, 0)
         self.windows = (first, last) if windows is not None else (1, spec.M)
-        O = Options(solver, col_block, ckpt_interval, 1 if profile else 0, layout, int(first), int(last))
+        O = Options(solver, col_block, ckpt_interval, 1 if profile else 0, layout, int(first), int(last),
+                    int(steps_per_sync))
         h = ctypes.c_void_p()
         _check(lib.msqoc_create_problem(ctypes.byref(self._desc.H), ctypes.byref(self._desc.C), self._desc.target_ptr,
                                         float(spec.T), int(spec.nsteps), int(spec.M), float(spec.mu),
                                         ctypes.byref(O), ctypes.byref(h)))
         self.handle = h
         cb, nt, th, K = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        lay = ctypes.c_int32()
+        lay, sps = ctypes.c_int32(), ctypes.c_int32()
         _check(lib.msqoc_query_layout(h, ctypes.byref(cb), ctypes.byref(nt), ctypes.byref(th), ctypes.byref(K),
-                                      ctypes.byref(lay)))
+                                      ctypes.byref(lay), ctypes.byref(sps)))
         self.col_block, self.tiles, self.threads, self.ckpt_interval = cb.value, nt.value, th.value, K.value
-        self.layout = lay.value
+        self.layout, self.steps_per_sync = lay.value, sps.value
         d, nW, nbytes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
         _check(lib.msqoc_query(h, ctypes.byref(d), ctypes.byref(nW), ctypes.byref(nbytes)))
         self.d, self.nW, self.device_bytes = d.value, nW.value, nbytes.value
@@ -437,20 +439,23 @@ def lbfgs_update(n, x, x_new, g, g_new, s_out, y_out, sy_yy_out, stream=None):
 
 
 def autotune(spec, alpha=None, probe_steps: int = 64, solver: int = SOLVER_DEFAULT, ckpt_interval: int = 0,
-             layout: int = LAYOUT_AUTO):
-    """Kernel family and columns per sweep tile by measurement (msqoc_autotune): returns
-    (best width, best layout, {(layout, width): ms per probe evaluation})."""
+             layout: int = LAYOUT_AUTO, steps_per_sync: int = 0):
+    """Kernel family, columns per sweep tile and steps per history synchronisation by measurement
+    (msqoc_autotune): returns (best width, best layout, best steps per sync,
+    {(layout, width, steps per sync): ms per probe evaluation})."""
     lib = load()
     desc = _Description(spec)
-    O = Options(solver, 0, ckpt_interval, 0, layout)
+    O = Options(solver, 0, ckpt_interval, 0, layout, 0, 0, steps_per_sync)
     a = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float64)
-    best, best_layout = ctypes.c_int32(), ctypes.c_int32()
+    best, best_layout, best_sps = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     widths = (ctypes.c_int32 * 128)()
     layouts = (ctypes.c_int32 * 128)()
+    depths = (ctypes.c_int32 * 128)()
     ms = (ctypes.c_float * 128)()
     n = ctypes.c_int32()
     _check(lib.msqoc_autotune(ctypes.byref(desc.H), ctypes.byref(desc.C), float(spec.T), int(spec.nsteps),
                               int(spec.M), float(spec.mu), ctypes.byref(O), None if a is None else a.ctypes.data,
-                              int(probe_steps), ctypes.byref(best), ctypes.byref(best_layout), widths, layouts, ms, 128,
-                              ctypes.byref(n)))
-    return best.value, best_layout.value, {(int(layouts[i]), int(widths[i])): float(ms[i]) for i in range(n.value)}
+                              int(probe_steps), ctypes.byref(best), ctypes.byref(best_layout), ctypes.byref(best_sps),
+                              widths, layouts, depths, ms, 128, ctypes.byref(n)))
+    return best.value, best_layout.value, best_sps.value, {
+        (int(layouts[i]), int(widths[i]), int(depths[i])): float(ms[i]) for i in range(n.value)}

@@ -14,14 +14,18 @@ pytestmark = pytest.mark.gpu
 def test_autotune_returns_a_measured_admissible_width():
     spec = S.transmon_spec(3, 30.0, 2001, 7, 8)
     alpha, W = S.random_alpha(spec, 61), S.random_W(spec, 61)
-    best, layout, times = msqoc.autotune(spec, alpha=alpha, probe_steps=16)
-    assert (layout, best) in times and len(times) >= 6
-    assert {lay for lay, _ in times} == {msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR}   # both families tried
+    best, layout, sps, times = msqoc.autotune(spec, alpha=alpha, probe_steps=16)
+    assert (layout, best, sps) in times and len(times) >= 6
+    assert {lay for lay, _, _ in times} == {msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR}   # both families tried
+    assert {dp for _, _, dp in times} >= {1, 2, 4}      # steps per synchronisation tried
     assert all(t > 0 for t in times.values())
-    assert times[(layout, best)] == min(times.values())
-    _, lay1, times1 = msqoc.autotune(spec, alpha=alpha, probe_steps=16, layout=msqoc.LAYOUT_FIBER)
-    assert lay1 == msqoc.LAYOUT_FIBER and {lay for lay, _ in times1} == {msqoc.LAYOUT_FIBER}
-    with msqoc.Problem(spec, col_block=best, layout=layout) as p:
+    assert times[(layout, best, sps)] == min(times.values())
+    _, lay1, sps1, times1 = msqoc.autotune(spec, alpha=alpha, probe_steps=16, layout=msqoc.LAYOUT_FIBER,
+                                           steps_per_sync=2)
+    assert lay1 == msqoc.LAYOUT_FIBER and {lay for lay, _, _ in times1} == {msqoc.LAYOUT_FIBER}
+    assert sps1 == 2 and {dp for _, _, dp in times1} == {2}
+    with msqoc.Problem(spec, col_block=best, layout=layout, steps_per_sync=sps) as p:
+        assert p.steps_per_sync == sps
         got = p.eval_gradient(alpha, W)
     want = oracle.evaluate(spec, alpha, W)
     assert_objective_close(got["P"], want["P"])
@@ -31,9 +35,9 @@ def test_autotune_returns_a_measured_admissible_width():
 
 def test_autotune_tries_lane_quads_on_two_levels():
     spec = S.paper_qft_spec(2, M=4, nsteps=400)
-    best, layout, times = msqoc.autotune(spec, probe_steps=16)
-    assert {lay for lay, _ in times} == {msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_QUAD}
-    assert times[(layout, best)] == min(times.values())
+    best, layout, sps, times = msqoc.autotune(spec, probe_steps=16)
+    assert {lay for lay, _, _ in times} == {msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_QUAD}
+    assert times[(layout, best, sps)] == min(times.values())
 
 
 def test_tile_model_picks_the_measured_fastest_tiles_of_the_benchmark_workload():
