@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
     }
 
     // ---- the mixed solver's per-column scale, from the launch's initial state (column_shift)
-    int sh = 0;
+    int sh = 0;   // the column's scale exponent (ColScale cs below)
     if constexpr (SOLVER == SOLVER_MIXED) {
         __shared__ int colexp_s[MAX_TILE_COLS];
         for (int j = tid; j < MAX_TILE_COLS; j += blockDim.x) colexp_s[j] = 0;
@@ -420,6 +420,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
         tile_sync();
         sh = column_shift(colexp_s[c < MAX_TILE_COLS ? c : 0]);
     }
+    const ColScale cs = col_scale(sh);
 
     // ---- history blocks: slot s of a tile covers a contiguous column range of its window
     const bool want_hist = !BWD && ((a.mode == SWEEP_HISTORY && pd.nseg == 1) || a.mode == SWEEP_RECOMPUTE);
@@ -538,6 +539,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
     double2* Dn = D1;
     if (nit > 0) load_ctrl(0);
 
+    int hpos = 0, hgrp = 0;   // iteration jj = hgrp hd + hpos (history group and position)
     for (int jj = 0; jj < nit; ++jj) {
         const int par = jj & 1;
         const bool live = jj < my_cnt;
@@ -580,12 +582,12 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
         // previous iteration's midpoints (forward) or fetches the next iteration's (adjoint)
         auto first_sync_work = [&]() {
             if (BWD && *tflag) timed_out = true;   // uniform: read after a barrier
-            if (!BWD && want_hist && tid == 0 && jj > 0 && jj % hd == 0) {
+            if (!BWD && want_hist && tid == 0 && jj > 0 && hpos == 0) {
                 fence_proxy_async_smem();
                 publish_group(jj - hd);
             }
-            if (BWD && tid == 0 && jj % hd == 0 && jj + hd < nit) {
-                const int gn = jj / hd + 1;
+            if (BWD && tid == 0 && hpos == 0 && jj + hd < nit) {
+                const int gn = hgrp + 1;
                 fetch_group((gn & 1) ? UB1 : UB0, jj + hd, &mbar[gn & 1]);
             }
         };
@@ -627,7 +629,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
             float2 bf[L], df[L], y[L];
 #pragma unroll
             for (int l = 0; l < L; ++l) {
-                bf[l] = f32_of_scaled(b[l], sh);
+                bf[l] = f32_of_scaled(b[l], cs);
                 y[l] = bf[l];
             }
             {
@@ -671,7 +673,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
             double2 dacc[L];
 #pragma unroll
             for (int l = 0; l < L; ++l) {
-                dacc[l] = f64_of_scaled(df[l], sh);
+                dacc[l] = f64_of_scaled(df[l], cs);
                 z[l] = make_double2(b[l].x + dacc[l].x, b[l].y + dacc[l].y);
             }
             for (int pass = 0;; ++pass) {
@@ -682,7 +684,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
                 // forward: the staged midpoints of the previous step must have been read by their
                 // bulk store (issued at this step's first barrier) before this step's are staged;
                 // waiting here, ahead of a barrier every step has, makes the staging barrier-free
-                if (!BWD && want_hist && pass == 0 && tid == 0 && jj % hd == 0) bulk_wait_read_all();
+                if (!BWD && want_hist && pass == 0 && tid == 0 && hpos == 0) bulk_wait_read_all();
                 tile_sync();
                 double2 w[L];
                 apply_off<L, Q, double2>(D0, cfd, fb, z, w, pd);
@@ -690,7 +692,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
                     const double2 r = resid_from<S>(dacc[l], Pd[l], w[l]);
-                    rf[l] = f32_of_scaled(r, sh);
+                    rf[l] = f32_of_scaled(r, cs);
                     e[l] = rf[l];
                 }
                 for (int it = 0; it < j2max; ++it) {
@@ -710,7 +712,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
                 }
                 double2 ed[L];
 #pragma unroll
-                for (int l = 0; l < L; ++l) ed[l] = f64_of_scaled(e[l], sh);
+                for (int l = 0; l < L; ++l) ed[l] = f64_of_scaled(e[l], cs);
                 if (pass < R) {
 #pragma unroll
                     for (int l = 0; l < L; ++l) z[l] = make_double2(z[l].x + ed[l].x, z[l].y + ed[l].y);
@@ -733,14 +735,14 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
             if (want_hist) {
                 if constexpr (SOLVER == SOLVER_FP64) {
                     // (the FP64 solver's step may have no barrier after the first one)
-                    if (jj % hd == 0) {
+                    if (hpos == 0) {
                         if (tid == 0) bulk_wait_read_all();
                         tile_sync();
                     }
                 }
                 if (act && live) {
 #pragma unroll
-                    for (int l = 0; l < L; ++l) H[size_t(jj % hd) * hstride + fb.xo + l] = z[l];
+                    for (int l = 0; l < L; ++l) H[size_t(hpos) * hstride + fb.xo + l] = z[l];
                 }
                 fence_proxy_async_smem();
             }
@@ -761,11 +763,10 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
             }
         } else {
             // ---- gradient quadrature on the midpoints (fused): needs Ubar_n of the tile
-            const int hg = jj / hd;   // history group of this iteration
-            double2* UB = ((hg & 1) ? UB1 : UB0) + size_t(jj - hg * hd) * hstride;
+            double2* UB = ((hgrp & 1) ? UB1 : UB0) + size_t(hpos) * hstride;
             // a wait that gives up raises the tile's flag, read after the next barrier (the
             // products below then use whatever landed; the evaluation reports the timeout)
-            if (jj == hg * hd && !mbar_wait(&mbar[hg & 1], (hg >> 1) & 1)) *tflag = 1;
+            if (hpos == 0 && !mbar_wait(&mbar[hgrp & 1], (hgrp >> 1) & 1)) *tflag = 1;
             double acc[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = 0.0;
@@ -866,6 +867,10 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a
         // (the barrier that published red[par ^ 1] was this iteration's first one)
         if (BWD && jj > 0 && coef_warp && jj - 1 < (cslot ? cnt_1 : cnt_0))
             fold(cslot, par ^ 1, step_of(cslot, jj - 1), sp_prev, ph_prev, true);
+        if (++hpos == hd) {
+            hpos = 0;
+            ++hgrp;
+        }
     }
 
     if (!timed_out) {

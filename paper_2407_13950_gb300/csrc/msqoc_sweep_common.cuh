@@ -43,42 +43,50 @@ __device__ __forceinline__ double f64_of(float f) {
 __device__ __forceinline__ float2 f32_of(double2 v) { return make_float2(f32_of(v.x), f32_of(v.y)); }
 __device__ __forceinline__ double2 f64_of(float2 v) { return make_double2(f64_of(v.x), f64_of(v.y)); }
 
-// The same conversions of a state entry with a per-column binary scale: f32_of_scaled(x, sh) is
-// x 2^-sh rounded to f32 as above, f64_of_scaled(f, sh) is f 2^sh exactly.  The scale is an
-// exponent offset applied to the bit fields (no FP64 instruction); |sh| <= SCALE_SHIFT_MAX keeps
-// zero at zero.  Magnitudes of 2^128 and more after scaling become infinities (a visible failure
-// instead of a wrapped exponent); below 2^-126 they become signed zero.
+// The same conversions of a state entry with a per-column binary scale 2^-sh (|sh| <=
+// SCALE_SHIFT_MAX): f32_of_scaled gives x 2^-sh rounded to f32 as above, f64_of_scaled gives
+// f 2^sh exactly.  The scale is an offset of the exponent field, applied to the high word (no
+// FP64 instruction); the per-column constants are formed once per launch (ColScale).  Scaled
+// magnitudes below 2^-126 become signed zero.  The column scale bounds every scaled entry, the
+// corrections and residuals included, below 1, so no overflow handling is needed.
 constexpr int SCALE_SHIFT_MAX = 896;
-__device__ __forceinline__ float f32_of_scaled(double x, int sh) {
-    unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
-    const unsigned int sgn = static_cast<unsigned int>(bits >> 32) & 0x80000000u;
-    const long long ahi = static_cast<long long>(static_cast<unsigned int>(bits >> 32) & 0x7fffffffu) -
-                          static_cast<long long>(sh) * (1 << 20);
-    bits -= static_cast<unsigned long long>(static_cast<long long>(sh)) << 52;
-    bits += (1ull << 28);
-    const unsigned int hi = static_cast<unsigned int>(bits >> 32);
-    const unsigned int lo = static_cast<unsigned int>(bits);
-    const unsigned int t = __funnelshift_l(lo, hi, 3);
-    unsigned int fb = ((t ^ 0x40000000u) & 0x7fffffffu) | sgn;
-    fb = (ahi < 0x38100000ll) ? sgn : fb;
-    fb = (ahi >= 0x47f00000ll) ? (sgn | 0x7f800000u) : fb;
-    return __uint_as_float(fb);
+struct ColScale {
+    unsigned int sub;    // sh 2^20 (mod 2^32): subtracted from the high word
+    int flush;           // |high word| below this flushes: 0x38100000 + sh 2^20
+    unsigned int bias;   // f32 -> f64 exponent bias with the scale: 0x38000000 + sh 2^20
+};
+__device__ __forceinline__ ColScale col_scale(int sh) {
+    const unsigned int s20 = static_cast<unsigned int>(sh) * (1u << 20);
+    return ColScale{s20, 0x38100000 + sh * (1 << 20), 0x38000000u + s20};
 }
-__device__ __forceinline__ double f64_of_scaled(float f, int sh) {
+__device__ __forceinline__ float f32_of_scaled(double x, const ColScale& cs) {
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned int hi0 = static_cast<unsigned int>(bits >> 32);
+    const unsigned int sgn = hi0 & 0x80000000u;
+    const int ahi = static_cast<int>(hi0 & 0x7fffffffu);
+    const unsigned long long adj = (static_cast<unsigned long long>(hi0 - cs.sub) << 32 |
+                                    static_cast<unsigned int>(bits)) + (1ull << 28);
+    const unsigned int hi = static_cast<unsigned int>(adj >> 32);
+    const unsigned int lo = static_cast<unsigned int>(adj);
+    const unsigned int t = __funnelshift_l(lo, hi, 3);
+    const unsigned int fb = ((t ^ 0x40000000u) & 0x7fffffffu) | sgn;
+    return __uint_as_float(ahi < cs.flush ? sgn : fb);
+}
+__device__ __forceinline__ double f64_of_scaled(float f, const ColScale& cs) {
     const unsigned int fb = __float_as_uint(f);
     const unsigned int s = fb & 0x80000000u;
     const unsigned int a = fb & 0x7fffffffu;
-    unsigned int hi = s | ((a >> 3) + 0x38000000u + (static_cast<unsigned int>(sh) << 20));
+    unsigned int hi = s | ((a >> 3) + cs.bias);
     unsigned int lo = a << 29;
     hi = (a < 0x00800000u) ? s : hi;
     lo = (a < 0x00800000u) ? 0u : lo;
     return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
 }
-__device__ __forceinline__ float2 f32_of_scaled(double2 v, int sh) {
-    return make_float2(f32_of_scaled(v.x, sh), f32_of_scaled(v.y, sh));
+__device__ __forceinline__ float2 f32_of_scaled(double2 v, const ColScale& cs) {
+    return make_float2(f32_of_scaled(v.x, cs), f32_of_scaled(v.y, cs));
 }
-__device__ __forceinline__ double2 f64_of_scaled(float2 v, int sh) {
-    return make_double2(f64_of_scaled(v.x, sh), f64_of_scaled(v.y, sh));
+__device__ __forceinline__ double2 f64_of_scaled(float2 v, const ColScale& cs) {
+    return make_double2(f64_of_scaled(v.x, cs), f64_of_scaled(v.y, cs));
 }
 // biased exponent field of a double (0 for zero and subnormals)
 __device__ __forceinline__ int exp_field(double x) {
@@ -89,7 +97,7 @@ __device__ __forceinline__ int exp_field(double x) {
 // ce of the column's state at the start of a launch bounds every entry of every later step by
 // 2^(ce - 1022) sqrt(N) < 2^(ce - 1018) (N <= 256).  Entries scaled by 2^-sh with
 // sh = ce - 1018 stay below 1, and the FP32 stage's range limits apply relative to the column
-// norm instead of to absolute magnitudes.
+// norm instead of to absolute magnitudes (the flush below 2^-126 of the column's scale).
 __device__ __forceinline__ int column_shift(int ce) {
     if (ce == 0) return 0;   // an all-zero column
     const int sh = ce - 1018;

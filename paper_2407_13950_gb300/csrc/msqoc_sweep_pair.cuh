@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
         }
     }
     // ---- the mixed solver's per-column scale, from the launch's initial state (column_shift)
-    int sh = 0;
+    int sh = 0;   // the column's scale exponent (ColScale cs below)
     if constexpr (SOLVER == SOLVER_MIXED) {
         __shared__ int colexp_s[MAX_TILE_COLS];
         for (int j = tid; j < MAX_TILE_COLS; j += blockDim.x) colexp_s[j] = 0;
@@ -395,6 +395,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
         tile_sync();
         sh = column_shift(colexp_s[c < MAX_TILE_COLS ? c : 0]);
     }
+    const ColScale cs = col_scale(sh);
     // this part's components of a [..][N] complex array at the fiber
     auto store_fiber = [&](double2* dst) {
         double* d = reinterpret_cast<double*>(dst) + 2 * (size_t(f) * L + le) + part;
@@ -522,6 +523,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
     double2* Dn = D1;
     if (nit > 0) load_ctrl(0);
 
+    int hpos = 0, hgrp = 0;   // iteration jj = hgrp hd + hpos (history group and position)
     for (int jj = 0; jj < nit; ++jj) {
         const int par = jj & 1;
         const bool live = jj < my_cnt;
@@ -564,12 +566,12 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
         // previous iteration's midpoints (forward) or fetches the next iteration's (adjoint)
         auto first_sync_work = [&]() {
             if (BWD && *tflag) timed_out = true;   // uniform: read after a barrier
-            if (!BWD && want_hist && tid == 0 && jj > 0 && jj % hd == 0) {
+            if (!BWD && want_hist && tid == 0 && jj > 0 && hpos == 0) {
                 fence_proxy_async_smem();
                 publish_group(jj - hd);
             }
-            if (BWD && tid == 0 && jj % hd == 0 && jj + hd < nit) {
-                const int gn = jj / hd + 1;
+            if (BWD && tid == 0 && hpos == 0 && jj + hd < nit) {
+                const int gn = hgrp + 1;
                 fetch_group((gn & 1) ? UB1 : UB0, jj + hd, &mbar[gn & 1]);
             }
         };
@@ -608,7 +610,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
             float bf[LS], df[LS], y[LS];
 #pragma unroll
             for (int l = 0; l < LS; ++l) {
-                bf[l] = f32_of_scaled(b[l], sh);
+                bf[l] = f32_of_scaled(b[l], cs);
                 y[l] = bf[l];
             }
             {
@@ -651,7 +653,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
             double dacc[LS];
 #pragma unroll
             for (int l = 0; l < LS; ++l) {
-                dacc[l] = f64_of_scaled(df[l], sh);
+                dacc[l] = f64_of_scaled(df[l], cs);
                 z[l] = b[l] + dacc[l];
             }
             for (int pass = 0;; ++pass) {
@@ -659,7 +661,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
                 // forward: the staged midpoints of the previous step must have been read by their
                 // bulk store (issued at this step's first barrier) before this step's are staged;
                 // waiting here, ahead of a barrier every step has, makes the staging barrier-free
-                if (!BWD && want_hist && pass == 0 && tid == 0 && jj % hd == 0) bulk_wait_read_all();
+                if (!BWD && want_hist && pass == 0 && tid == 0 && hpos == 0) bulk_wait_read_all();
                 tile_sync();
                 double w[LS];
                 apply_off_pair<L, Q, double2, SPLIT>(D0, cfd, fb, z, w, part, le, exo, pd);
@@ -668,7 +670,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
                 for (int l = 0; l < LS; ++l) {
                     const double wo = partner(w[l]);
                     const double r = fma(SPp[l].x, w[l], fma(SPp[l].y, wo, -dacc[l]));
-                    rf[l] = f32_of_scaled(r, sh);
+                    rf[l] = f32_of_scaled(r, cs);
                     e[l] = rf[l];
                 }
                 for (int it = 0; it < j2max; ++it) {
@@ -687,7 +689,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
                 }
                 double ed[LS];
 #pragma unroll
-                for (int l = 0; l < LS; ++l) ed[l] = f64_of_scaled(e[l], sh);
+                for (int l = 0; l < LS; ++l) ed[l] = f64_of_scaled(e[l], cs);
                 if (pass < R) {
 #pragma unroll
                     for (int l = 0; l < LS; ++l) z[l] = z[l] + ed[l];
@@ -710,12 +712,12 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
             if (want_hist) {
                 if constexpr (SOLVER == SOLVER_FP64) {
                     // (the FP64 solver's step may have no barrier after the first one)
-                    if (jj % hd == 0) {
+                    if (hpos == 0) {
                         if (tid == 0) bulk_wait_read_all();
                         tile_sync();
                     }
                 }
-                if (act && live) store_part<LS, double2>(H + size_t(jj % hd) * hstride, fb.xo + le, part, z);
+                if (act && live) store_part<LS, double2>(H + size_t(hpos) * hstride, fb.xo + le, part, z);
                 fence_proxy_async_smem();
             }
             if (live) {
@@ -732,8 +734,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
             }
         } else {
             // ---- gradient quadrature on the midpoints (fused): needs Ubar_n of the tile
-            const int hg = jj / hd;   // history group of this iteration
-            double2* UB = ((hg & 1) ? UB1 : UB0) + size_t(jj - hg * hd) * hstride;
+            double2* UB = ((hgrp & 1) ? UB1 : UB0) + size_t(hpos) * hstride;
             // this part's products conj(Lbar) x Ubar: Re (part 0) = Lr Ur + Li Ui = za Ur + zb Ui,
             // Im (part 1) = Lr Ui - Li Ur = za Ur + zb Ui with (za, zb) = (-Li, Lr)
             double za[LS], zb[LS];
@@ -745,7 +746,7 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
             }
             // a wait that gives up raises the tile's flag, read after the next barrier (the
             // products below then use whatever landed; the evaluation reports the timeout)
-            if (jj == hg * hd && !mbar_wait(&mbar[hg & 1], (hg >> 1) & 1)) *tflag = 1;
+            if (hpos == 0 && !mbar_wait(&mbar[hgrp & 1], (hgrp >> 1) & 1)) *tflag = 1;
             double acc[VH];   // index 2k: z_k, 2k + 1: y_k (this part's component)
 #pragma unroll
             for (int v = 0; v < VH; ++v) acc[v] = 0.0;
@@ -843,6 +844,10 @@ __global__ void __launch_bounds__(SPLIT > 1 ? MAX_QUAD_TILE_THREADS : MAX_PAIR_T
         // (the barrier that published red[par ^ 1] was this iteration's first one)
         if (BWD && jj > 0 && coef_warp && jj - 1 < (cslot ? cnt_1 : cnt_0))
             fold(cslot, par ^ 1, step_of(cslot, jj - 1), sp_prev, ph_prev, true);
+        if (++hpos == hd) {
+            hpos = 0;
+            ++hgrp;
+        }
     }
 
     if (!timed_out) {

@@ -26,7 +26,7 @@ def run(spec, alpha, W, **kw):
 def test_every_depth_matches_one_step_groups_bitwise(layout, solver):
     spec = S.transmon_spec(3, 30.0, 2001, 7, 8)         # ragged windows of 285-286 steps
     alpha, W = S.random_alpha(spec, 71), S.random_W(spec, 71)
-    cb = 3                                               # 3 does not divide 8: tiles over two windows
+    cb = 5                                               # 5 does not divide 8: tiles over two windows
     ref, d1 = run(spec, alpha, W, layout=layout, solver=solver, col_block=cb, steps_per_sync=1)
     assert d1 == 1
     for depth in (2, 3, 4, 8):
