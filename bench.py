@@ -110,7 +110,7 @@ class ClockSampler:
 SWEEP_SOURCES = ["msqoc_sweep.cuh", "msqoc_sweep_pair.cuh", "msqoc_sweep_common.cuh", "inst_sweep.cu",
                  "msqoc_internal.h"]
 PROFILES = os.path.join(ROOT, "profiles")
-LAYOUTS = {"auto": 0, "fiber": 1, "pair": 2, "quad": 3}
+LAYOUTS = {"auto": 0, "fiber": 1, "pair": 2, "quad": 3, "lean": 4}
 
 
 def sweep_traffic(kernel: str, windows: int, col_block: int, layout: int):
@@ -234,7 +234,8 @@ def time_evaluations(prob, a_d, W_d, outs, stream, steps: int, warmup: int, kern
     return ms, kt
 
 
-FAMILY = {1: "one thread per fiber", 2: "lane pair per fiber", 3: "lane quad per fiber"}
+FAMILY = {1: "one thread per fiber", 2: "lane pair per fiber", 3: "lane quad per fiber",
+          4: "one thread per fiber, 168 registers"}
 
 
 def config3_section(dev, stream, peak, steps: int = 5, warmup: int = 2) -> dict:
@@ -318,7 +319,7 @@ def run_ours(args, spec):
     if args.col_block < 0:
         tuned, layout, sps, tune_ms = msqoc.autotune(spec, alpha=alpha, probe_steps=64, solver=solver, layout=layout,
                                                      steps_per_sync=args.steps_per_sync)
-        fam = {1: "fiber", 2: "pair", 3: "quad"}
+        fam = {1: "fiber", 2: "pair", 3: "quad", 4: "lean"}
         tune_ms = {f"{fam[lay]}-{cb}-s{dp}": v for (lay, cb, dp), v in tune_ms.items()}
     col_block = tuned if args.col_block < 0 else args.col_block
     prob = msqoc.Problem(spec, solver=solver, col_block=col_block, profile=True, layout=layout, steps_per_sync=sps)
@@ -438,7 +439,7 @@ def batched_section(args, dev, stream, peak, steps: int, warmup: int) -> dict:
     outs = [(torch.zeros(1, device=dev, dtype=torch.float64), torch.zeros(p.d, device=dev, dtype=torch.float64),
              torch.zeros(max(p.nW, 2), device=dev, dtype=torch.float64)) for p in probs]
     batch = msqoc.Batch(probs, gradient=True, graph=True)
-    fam = {1: "fiber", 2: "pair", 3: "quad"}
+    fam = {1: "fiber", 2: "pair", 3: "quad", 4: "lean"}
     tile_mix = {}
     for sp, p in zip(specs, probs):       # how many problems run each (shape, family, width)
         key = f"{sp.q}q {fam[p.layout]} x{p.col_block} ({p.threads} threads)"
@@ -556,6 +557,48 @@ def run_batched(args):
         print(json.dumps(line), flush=True)
 
 
+def run_sharded(args, spec):
+    """One problem's windows spread over the ranks (shard.ShardedProblem): every rank evaluates
+    its contiguous window range on its GPU, hands -2 Lambda across its boundary and joins one
+    all-reduce of d + 1 doubles (NCCL).  Strong scaling: the value is evaluations per second of
+    the one problem.  Host arrays in, host arrays out (the optimiser's replicated W)."""
+    import torch
+    from paper_2407_13950_gb300 import msqoc, shard
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    else:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29533")
+        dist.init_process_group("gloo", rank=0, world_size=1)
+    alpha, W = S.random_alpha(spec, 1), S.random_W(spec, 1)
+    sp = shard.ShardedProblem(spec, dist)
+    for _ in range(args.warmup):
+        sp.eval_gradient(alpha, W)
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sp.eval_gradient(alpha, W)
+    torch.cuda.synchronize()
+    dt = max_over_ranks((time.perf_counter() - t0) / args.steps, dist if world > 1 else None,
+                        torch.device("cuda", local))
+    line = {"metric": METRIC + " (one problem, windows over ranks)", "value": 1.0 / dt, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**workload_config(spec), "parallelism": f"windows of one problem over {world} ranks",
+                       "windows_per_rank": [b - a + 1 for a, b in sp.ranges]},
+            "e2e": {"value": 1.0 / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * (spec.d + (sp.hi - sp.lo)),
+                    "d2h_bytes_per_step": 8 * (1 + spec.d + (sp.hi - sp.lo))}}
+    sp.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def run_paper(args):
     """The paper's own test cases (Table 1-2: QFT-4/8/16 on 2/3/4 qubits with exchange coupling,
     full time grids): objective+gradient evaluations per second for each window count, and the
@@ -572,7 +615,7 @@ def run_paper(args):
     cases = ((2, (1, 16)), (3, (1, 128)), (4, (1, 256)))
     if args.qft:
         cases = tuple(c for c in cases if 2 ** c[0] == args.qft)
-    fam_names = {1: "fiber", 2: "pair", 3: "quad"}
+    fam_names = {1: "fiber", 2: "pair", 3: "quad", 4: "lean"}
     for q, Ms in cases:
         row, tiles = {}, {}
         for M in Ms:
@@ -809,10 +852,11 @@ def main():
                     help="optimize workload: window count of the multiple-shooting run (0 = the paper's best)")
     ap.add_argument("--nsteps", type=int, default=0,
                     help="shorter time grid with the same step size (small profiling case); 0 = 100000 steps")
-    ap.add_argument("--workload", choices=["4q", "batched", "serving", "paper", "optimize"], default="4q",
+    ap.add_argument("--workload", choices=["4q", "batched", "serving", "paper", "optimize", "sharded"], default="4q",
                     help="4q: the benchmark workload (one 4-transmon problem); batched: 96 mixed problems; "
                          "serving: continuous batching of a Poisson request stream; paper: the paper's QFT cases; "
-                         "optimize: time to solution of the paper's QFT-4 optimisation")
+                         "optimize: time to solution of the paper's QFT-4 optimisation; sharded: the 4q problem's "
+                         "windows over the ranks (strong scaling)")
     ap.add_argument("--batch-per-shape", type=int, default=32)
     ap.add_argument("--sessions-per-shape", type=int, default=16)
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: offered requests per second")
@@ -848,6 +892,12 @@ def main():
     if args.nsteps:
         spec = spec.replace(nsteps=args.nsteps, T=spec.T * args.nsteps / spec.nsteps,
                             name=f"{spec.name}-{args.nsteps}steps")
+    if args.workload == "sharded":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the sharded workload has no CPU reference run"}))
+            return
+        run_sharded(args, spec)
+        return
     if args.impl == "reference":
         run_reference(args, spec)
     else:

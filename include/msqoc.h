@@ -99,7 +99,7 @@ typedef struct msqoc_controls {
 typedef struct msqoc_options {
     int32_t solver;        /* MSQOC_SOLVER_* */
     int32_t col_block;     /* columns per sweep tile (1 <= col_block <= E; col_block N/L <= 256
-                              threads with one thread per fiber, 2 col_block N/L <= 384 with
+                              threads with one thread per fiber (384 with FIBER_LEAN), 2 col_block N/L <= 384 with
                               lane pairs, 4 col_block N/L <= 384 with lane quads; tiles run
                               along the window-major column list and may cover two windows; a
                               one-warp tile must divide E); 0 = automatic */
@@ -149,12 +149,17 @@ typedef struct msqoc_options {
  * the FP64 instructions per thread, so steps run faster when the tiles are too few to fill the
  * GPU (small problems, the paper's QFT cases).  QUAD: 2-level subsystems only (and at most 6
  * exchange-coupled pairs): a lane pair per entry of the fiber, four threads per fiber, a
- * quarter of its work per thread.  AUTO: chosen with the column block by the library's
- * makespan model.  A family the problem does not admit is rejected (MSQOC_ERR_INVALID_ARG). */
+ * quarter of its work per thread.  FIBER_LEAN: one thread per fiber like FIBER, compiled for
+ * 168 registers a thread instead of 255: tiles of up to 384 threads, and two 6-warp tiles fit
+ * on an SM, 12 warps whose stalls it hides better (the choice for the large 4-transmon
+ * workloads); FIBER keeps the registers for problems whose tiles are few.  AUTO: chosen with
+ * the column block by the library's makespan model.  A family the problem does not admit is
+ * rejected (MSQOC_ERR_INVALID_ARG). */
 #define MSQOC_LAYOUT_AUTO 0
 #define MSQOC_LAYOUT_FIBER 1
 #define MSQOC_LAYOUT_PAIR 2
 #define MSQOC_LAYOUT_QUAD 3
+#define MSQOC_LAYOUT_FIBER_LEAN 4
 
 /* Kernels of one evaluation, in launch order, as indexed by msqoc_kernel_times. */
 #define MSQOC_KERNEL_CONTROLS 0  /* control evaluation at the step midpoints */
@@ -183,8 +188,8 @@ msqoc_status msqoc_create_problem(const msqoc_hamiltonian* H, const msqoc_contro
 msqoc_status msqoc_query(const msqoc_problem* p, int64_t* d, int64_t* nW, size_t* device_bytes);
 
 /* Sweep layout of a problem: columns per tile, tiles (CTAs) per sweep launch, threads per
- * tile, the checkpoint interval K, the kernel family (MSQOC_LAYOUT_FIBER, MSQOC_LAYOUT_PAIR
- * or MSQOC_LAYOUT_QUAD) and the steps per history synchronisation in use (after automatic
+ * tile, the checkpoint interval K, the kernel family (MSQOC_LAYOUT_FIBER, _PAIR, _QUAD or
+ * _FIBER_LEAN) and the steps per history synchronisation in use (after automatic
  * choices).  Any pointer may be NULL. */
 msqoc_status msqoc_query_layout(const msqoc_problem* p, int32_t* col_block, int32_t* tiles,
                                 int32_t* threads, int32_t* ckpt_interval, int32_t* layout,

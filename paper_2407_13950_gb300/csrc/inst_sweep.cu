@@ -17,10 +17,13 @@
 
 namespace msqoc {
 
-// FAM: log2 of the threads per fiber (0: k_sweep; 1, 2: k_sweep_pair with one or two entry groups)
+// FAM: log2 of the threads per fiber (0: k_sweep; 1, 2: k_sweep_pair with one or two entry groups),
+// or 3: k_sweep with the 168-register budget (one thread per fiber, up to 12 warps an SM)
 template <int SOLVER, bool BWD, bool ROLLOUT, int FAM>
 static auto kernel_of() {
-    if constexpr (FAM == 2)
+    if constexpr (FAM == 3)
+        return k_sweep<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT, MAX_LEAN_TILE_THREADS>;
+    else if constexpr (FAM == 2)
         return k_sweep_pair<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT, 2>;
     else if constexpr (FAM == 1)
         return k_sweep_pair<MSQOC_L, MSQOC_Q, SOLVER, BWD, ROLLOUT, 1>;
@@ -93,7 +96,7 @@ static int occupancy_family(const SweepArgs& a) {
 }
 
 cudaError_t MSQOC_CAT(launch_sweep, MSQOC_L, MSQOC_Q)(const SweepArgs& a, int ntiles, cudaStream_t s) {
-    if (a.pair == 0) return launch_family<0>(a, ntiles, s);
+    if (a.pair == 0) return a.lean ? launch_family<3>(a, ntiles, s) : launch_family<0>(a, ntiles, s);
     if (a.pair == 1) return launch_family<1>(a, ntiles, s);
 #if MSQOC_L == 2
     if (a.pair == 2) return launch_family<2>(a, ntiles, s);
@@ -102,7 +105,7 @@ cudaError_t MSQOC_CAT(launch_sweep, MSQOC_L, MSQOC_Q)(const SweepArgs& a, int nt
 }
 
 int MSQOC_CAT(sweep_occupancy, MSQOC_L, MSQOC_Q)(const SweepArgs& a) {
-    if (a.pair == 0) return occupancy_family<0>(a);
+    if (a.pair == 0) return a.lean ? occupancy_family<3>(a) : occupancy_family<0>(a);
     if (a.pair == 1) return occupancy_family<1>(a);
 #if MSQOC_L == 2
     if (a.pair == 2) return occupancy_family<2>(a);

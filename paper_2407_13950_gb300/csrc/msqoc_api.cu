@@ -187,16 +187,16 @@ void build_lanemaps(int L, int q, int M, int E, int cpt, int nthreads, int pair,
 
 // one thread, a lane pair or a lane quad (2^pair threads) per (column, fiber)
 int tile_threads(int cpt, int F, int pair) { return (((1 << pair) * cpt * F + 31) / 32) * 32; }
-int max_tile_threads(int pair) {
-    return pair == 2 ? MAX_QUAD_TILE_THREADS : pair ? MAX_PAIR_TILE_THREADS : MAX_TILE_THREADS;
+int max_tile_threads(int pair, int lean = 0) {
+    return pair == 2 ? MAX_QUAD_TILE_THREADS : pair ? MAX_PAIR_TILE_THREADS : lean ? MAX_LEAN_TILE_THREADS : MAX_TILE_THREADS;
 }
 
 // Is `cpt` columns per tile usable in the given kernel family?  Tiles must fit the family's
 // thread limit and the shared memory; a tile that covers two windows needs two warps (one per
 // window's coefficients), so a one-warp tile must divide the window's columns.  g: doubles of
 // the adjoint's shared alpha-gradient per window slot.
-bool tile_width_ok(int cpt, int E, int F, int q, int L, int N, int g, int solver, int pair) {
-    if (cpt < 1 || cpt > E || (1 << pair) * cpt * F > max_tile_threads(pair)) return false;
+bool tile_width_ok(int cpt, int E, int F, int q, int L, int N, int g, int solver, int pair, int lean = 0) {
+    if (cpt < 1 || cpt > E || (1 << pair) * cpt * F > max_tile_threads(pair, lean)) return false;
     const int nthreads = tile_threads(cpt, F, pair);
     if (nthreads == 32 && E % cpt) return false;
     const size_t s1 = sweep_layout(q, L, N, cpt, nthreads, g, solver, true, pair).total;
@@ -238,20 +238,27 @@ bool quad_admitted(const ProbDev& pd) { return pd.L == 2 && pd.nex <= MAXEXF; }
 // fixed_cpt > 0 restricts the width, layout (MSQOC_LAYOUT_*) the family; quad_ok: the problem
 // admits lane quads.  cpt = -1: none fits.
 constexpr double QUAD_C = 0.38, QUAD_C0 = 0.52;
+// the one-thread family with 168 registers a thread: an SM holds 12 warps (two 6-warp tiles, or
+// one of up to 12), whose stalls it hides better than the 8 warps of the 255-register build:
+// measured on the 4-transmon tiles, 7-column tiles two to an SM 7% faster at 256 windows and
+// 13% at 128 than the 255-register build's best tiles, so a warp of it counts 0.9
+constexpr double LEAN_C = 0.9;
 TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int g, int solver, int sms, int fixed_cpt,
                               int layout, bool quad_ok) {
-    TileChoice best{-1, 0};
+    TileChoice best{-1, 0, 0};
     double best_a = 0.0, best_c = 0.0;
     int best_b = 0, best_w = 0;
-    for (int pair = 0; pair <= 2; ++pair) {
-        if (layout != MSQOC_LAYOUT_AUTO && layout != MSQOC_LAYOUT_FIBER + pair) continue;
+    for (int fam = MSQOC_LAYOUT_FIBER; fam <= MSQOC_LAYOUT_FIBER_LEAN; ++fam) {
+        if (layout != MSQOC_LAYOUT_AUTO && layout != fam) continue;
+        const int pair = fam == MSQOC_LAYOUT_FIBER_LEAN ? 0 : fam - MSQOC_LAYOUT_FIBER;
+        const int lean = fam == MSQOC_LAYOUT_FIBER_LEAN ? 1 : 0;
         if (pair == 2 && !quad_ok) continue;
-        const double c_load = pair == 2 ? QUAD_C : pair ? 0.6 : 1.0;
+        const double c_load = pair == 2 ? QUAD_C : pair ? 0.6 : lean ? LEAN_C : 1.0;
         const double c_alone = pair == 2 ? QUAD_C0 : pair ? 0.7 : 1.0;
-        const int hi = fixed_cpt > 0 ? fixed_cpt : std::min(E, max_tile_threads(pair) / ((1 << pair) * F));
+        const int hi = fixed_cpt > 0 ? fixed_cpt : std::min(E, max_tile_threads(pair, lean) / ((1 << pair) * F));
         const int lo = fixed_cpt > 0 ? fixed_cpt : 1;
         for (int cpt = hi; cpt >= lo; --cpt) {
-            if (!tile_width_ok(cpt, E, F, q, L, N, g, solver, pair)) continue;
+            if (!tile_width_ok(cpt, E, F, q, L, N, g, solver, pair, lean)) continue;
             const long tiles = (long(M) * E + cpt - 1) / cpt;
             const int threads = tile_threads(cpt, F, pair);
             const int warps = threads / 32;
@@ -263,6 +270,8 @@ TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int g, i
             a.solver = solver;
             a.nthreads = threads;
             a.pair = pair;
+            a.lean = lean;
+            a.hdepth = 1;
             a.mode = SWEEP_HISTORY;
             const int r0 = sweep_ctas_per_sm(a);
             a.mode = SWEEP_ADJOINT;
@@ -282,7 +291,7 @@ TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int g, i
             const bool better = best.cpt < 0 || ca < best_a - 1e-9 ||
                                 (tie_a && (cb < best_b || (tie_b && (cw < best_w || (tie_w && cc < best_c - 1e-9)))));
             if (better) {
-                best = TileChoice{cpt, pair};
+                best = TileChoice{cpt, pair, lean};
                 best_a = ca;
                 best_b = cb;
                 best_w = cw;
@@ -388,7 +397,7 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
     }
     pd.gspan = std::min(pd.d1, span + 2);
     pd.glocal = 2 * nfsum * pd.gspan;
-    if (layout < MSQOC_LAYOUT_AUTO || layout > MSQOC_LAYOUT_QUAD)
+    if (layout < MSQOC_LAYOUT_AUTO || layout > MSQOC_LAYOUT_FIBER_LEAN)
         return fail(MSQOC_ERR_INVALID_ARG, "layout %d is not an MSQOC_LAYOUT_* value", layout);
     if (layout == MSQOC_LAYOUT_QUAD && !quad_admitted(pd))
         return fail(MSQOC_ERR_INVALID_ARG, "lane quads need 2-level subsystems and at most %d exchange-coupled pairs",
@@ -399,12 +408,14 @@ msqoc_status shape_problem(const msqoc_hamiltonian* H, const msqoc_controls* C, 
     if (tc.cpt < 0)
         return fail(MSQOC_ERR_INVALID_ARG,
                     "column block %d invalid for E=%d (needs 1 <= cb <= E, cb N/L <= %d threads with one thread "
-                    "per fiber, 2 cb N/L <= %d with lane pairs or 4 cb N/L <= %d with lane quads, cb | E for "
-                    "one-warp tiles, and the shared memory)",
-                    col_block, pd.E, MAX_TILE_THREADS, MAX_PAIR_TILE_THREADS, MAX_QUAD_TILE_THREADS);
+                    "per fiber (%d with the lean build), 2 cb N/L <= %d with lane pairs or 4 cb N/L <= %d with lane "
+                    "quads, cb | E for one-warp tiles, and the shared memory)",
+                    col_block, pd.E, MAX_TILE_THREADS, MAX_LEAN_TILE_THREADS, MAX_PAIR_TILE_THREADS,
+                    MAX_QUAD_TILE_THREADS);
     const int cpt = tc.cpt;
     pd.cb = cpt;
     pd.pair = tc.pair;
+    pd.lean = tc.lean;
     pd.nthreads = tile_threads(cpt, pd.F, tc.pair);
     pd.ntiles = static_cast<int>((long(pd.M) * pd.E + cpt - 1) / cpt);
     // whole windows in one history segment unless a checkpoint interval is set later
@@ -448,6 +459,7 @@ SweepArgs sweep_args(const ProbDev& pd, const ProbDev* pds_dev, const Tile* tile
     a.solver = pd.solver;
     a.nthreads = pd.nthreads;
     a.pair = pd.pair;
+    a.lean = pd.lean;
     a.hdepth = pd.hdepth;
     return a;
 }
@@ -733,7 +745,7 @@ msqoc_status msqoc_query_layout(const msqoc_problem* p, int32_t* col_block, int3
     if (tiles) *tiles = p->pd.ntiles;
     if (threads) *threads = p->pd.nthreads;
     if (ckpt_interval) *ckpt_interval = p->ckpt_interval;
-    if (layout) *layout = MSQOC_LAYOUT_FIBER + p->pd.pair;
+    if (layout) *layout = p->pd.lean ? MSQOC_LAYOUT_FIBER_LEAN : MSQOC_LAYOUT_FIBER + p->pd.pair;
     return MSQOC_OK;
 }
 
@@ -1070,12 +1082,12 @@ msqoc_status autotune(const msqoc_hamiltonian* H, const msqoc_controls* C, doubl
     int best = 0, nrec = 0;
     int best_layout = 0, best_depth = 1;
     const int fam_lo = o.layout == MSQOC_LAYOUT_AUTO ? MSQOC_LAYOUT_FIBER : o.layout;
-    const int fam_hi = o.layout == MSQOC_LAYOUT_AUTO ? MSQOC_LAYOUT_QUAD : o.layout;
+    const int fam_hi = o.layout == MSQOC_LAYOUT_AUTO ? MSQOC_LAYOUT_FIBER_LEAN : o.layout;
     // candidates: every (family, width) with one step per history synchronisation, then the
     // best pair with 2, 4 and 8 steps per synchronisation
     std::vector<std::array<int, 3>> cands;
     for (int fam = fam_lo; fam <= fam_hi; ++fam)
-        for (int cb = std::min(pd.E, MAX_TILE_THREADS / pd.F); cb >= 1; --cb)
+        for (int cb = std::min(pd.E, MAX_LEAN_TILE_THREADS / pd.F); cb >= 1; --cb)
             if (choose_tile_layout(pd.M, pd.E, pd.F, pd.q, pd.L, pd.N, pd.glocal, solver, 1, cb, fam,
                                    quad_admitted(pd)).cpt >= 0)
                 cands.push_back({fam, cb, o.steps_per_sync > 0 ? o.steps_per_sync : 1});

@@ -19,7 +19,7 @@ using namespace msqoc;
 
 struct msqoc_batch {
     struct Group {
-        int L = 0, q = 0, solver = 0, pair = 0;   // shape, solver and kernel family of the group
+        int L = 0, q = 0, solver = 0, pair = 0, lean = 0;   // shape, solver and kernel family of the group
         int nthreads = 0;                          // threads of its tiles
         std::vector<int> members;     // indices into probs
         SweepArgs args{};             // pds / tiles / lanemap / geometry of the group's launches
@@ -226,7 +226,7 @@ msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t fla
     for (int i = 0; i < n && !st; ++i) {
         const ProbDev& pd = b->probs[i]->pd;
         auto it = std::find_if(b->groups.begin(), b->groups.end(), [&](const msqoc_batch::Group& g) {
-            return g.L == pd.L && g.q == pd.q && g.solver == pd.solver && g.pair == pd.pair &&
+            return g.L == pd.L && g.q == pd.q && g.solver == pd.solver && g.pair == pd.pair && g.lean == pd.lean &&
                    g.nthreads == pd.nthreads;
         });
         if (it == b->groups.end()) {
@@ -236,6 +236,7 @@ msqoc_status batch_create(msqoc_problem* const* problems, int32_t n, int32_t fla
             it->q = pd.q;
             it->solver = pd.solver;
             it->pair = pd.pair;
+            it->lean = pd.lean;
             it->nthreads = pd.nthreads;
         }
         it->members.push_back(i);

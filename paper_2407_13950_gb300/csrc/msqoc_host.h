@@ -86,7 +86,7 @@ msqoc_status guarded(F&& f) noexcept {
 void build_lanemap(int L, int q, int ncol, int ncol0, int nthreads, int pair, int* out);
 // kernel family (pair: log2 of the threads per fiber, 0, 1 or 2) and columns per tile of a problem
 struct TileChoice {
-    int cpt, pair;
+    int cpt, pair, lean;
 };
 Tile tile_at(long t, int M, int E, int cpt, int prob);
 long tile_count(int M, int E, int cpt);

@@ -12,6 +12,8 @@ constexpr int MAXEX = 15;     // exchange-coupled pairs (q (q - 1) / 2)
 constexpr int MAXNF = 64;     // carriers over all subsystems
 constexpr int MAXL = 4;       // levels per subsystem handled by the sweep kernels
 constexpr int MAX_TILE_THREADS = 256;       // threads of a one-thread-per-fiber tile (255 registers a thread)
+constexpr int MAX_LEAN_TILE_THREADS = 384;  // the same family compiled for 168 registers a thread: tiles of
+                                            // up to 12 warps, or two 6-warp tiles on an SM
 constexpr int MAX_PAIR_TILE_THREADS = 384;  // threads of a lane-pair tile (168 registers a thread)
 constexpr int MAX_QUAD_TILE_THREADS = 384;  // threads of a lane-quad tile (168 registers a thread)
 constexpr int MAX_HDEPTH = 8;               // steps per history group at most
@@ -50,6 +52,7 @@ struct ProbDev {
     int pair;      // kernel family: log2 of the threads per fiber (0: one thread, 1: a lane pair,
                    // the real and the imaginary part; 2: a lane quad, a pair per entry of a
                    // 2-level fiber)
+    int lean;      // one thread per fiber compiled for 168 registers (more warps per SM), pair = 0
     int ntiles;    // tiles of the problem's sweeps
     int gspan;     // splines per carrier in a tile's shared alpha-gradient: every spline active in
                    // one window (from the window's first active spline), with a margin
@@ -131,6 +134,7 @@ struct SweepArgs {
     int seg;              // segment (SWEEP_RECOMPUTE, SWEEP_ADJOINT)
     int L, q, solver, nthreads;
     int pair;             // kernel family: log2 of the threads per fiber (0, 1 or 2)
+    int lean;             // pair = 0 with the 168-register build (ProbDev::lean)
     int hdepth;           // steps per history group (ProbDev::hdepth), >= 1
     double2* out;         // SWEEP_ROLLOUT: [M-1][E][N] states at the window boundaries
 };

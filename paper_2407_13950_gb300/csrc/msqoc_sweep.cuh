@@ -273,8 +273,10 @@ __device__ __forceinline__ double warp_reduce_scatter(double (&acc)[V], int lane
 // range, per-step coefficients, iteration counts and gradient fold, computed by warp `slot`
 // (the host only builds two-slot tiles with at least two warps).  Loops run to the longer of
 // the slots' ranges; a thread whose slot has no step at an iteration keeps its state.
-template <int L, int Q, int SOLVER, bool BWD, bool ROLLOUT = false>
-__global__ void __launch_bounds__(MAX_TILE_THREADS, 1) k_sweep(const SweepArgs a) {
+// MAXT: the largest tile the instantiation serves; it sets the register budget (255 registers a
+// thread for MAX_TILE_THREADS, 168 for MAX_LEAN_TILE_THREADS: 12 warps on an SM).
+template <int L, int Q, int SOLVER, bool BWD, bool ROLLOUT = false, int MAXT = MAX_TILE_THREADS>
+__global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
     static_assert(!(BWD && ROLLOUT), "the roll-out is a forward sweep");
     constexpr int N = ipow_c(L, Q);
     constexpr int NSLOT = Q * L * 2;

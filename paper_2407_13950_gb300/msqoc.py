@@ -20,7 +20,7 @@ MSQOC_OK = 0
 STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OUT_OF_MEMORY", -3: "NOT_ADMITTED", -4: "CUDA_ERROR",
                 -5: "TIMEOUT", -6: "UNSUPPORTED", -7: "INTERNAL"}
 SOLVER_DEFAULT, SOLVER_FP64, SOLVER_MIXED = 0, 1, 2
-LAYOUT_AUTO, LAYOUT_FIBER, LAYOUT_PAIR, LAYOUT_QUAD = 0, 1, 2, 3
+LAYOUT_AUTO, LAYOUT_FIBER, LAYOUT_PAIR, LAYOUT_QUAD, LAYOUT_FIBER_LEAN = 0, 1, 2, 3, 4
 
 EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_query_layout", "msqoc_eval_objective", "msqoc_eval_gradient",
             "msqoc_destroy_problem", "msqoc_last_error", "msqoc_version", "msqoc_kernel_times",
@@ -174,7 +174,8 @@ class Problem:
 
     solver: SOLVER_MIXED (default: FP64 residual, FP32 corrections) or SOLVER_FP64; col_block:
     columns per sweep tile (0: the library's model); ckpt_interval: K (0: automatic); layout:
-    LAYOUT_FIBER, LAYOUT_PAIR or LAYOUT_QUAD (2-level subsystems) to force a sweep kernel family
+    LAYOUT_FIBER, LAYOUT_PAIR, LAYOUT_QUAD (2-level subsystems) or LAYOUT_FIBER_LEAN (one thread
+    per fiber, 168 registers: 12 warps an SM) to force a sweep kernel family
     (LAYOUT_AUTO: the model's choice); steps_per_sync: time steps per synchronisation of a tile
     with the midpoint history (0: one); windows: (first, last), 1-based, to create the shard of
     windows first..last of the spec's M-window problem (its W input and grad_W output are the

@@ -16,7 +16,8 @@ def test_autotune_returns_a_measured_admissible_width():
     alpha, W = S.random_alpha(spec, 61), S.random_W(spec, 61)
     best, layout, sps, times = msqoc.autotune(spec, alpha=alpha, probe_steps=16)
     assert (layout, best, sps) in times and len(times) >= 6
-    assert {lay for lay, _, _ in times} == {msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR}   # both families tried
+    assert {lay for lay, _, _ in times} == {msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR,
+                                            msqoc.LAYOUT_FIBER_LEAN}        # every family tried
     assert {dp for _, _, dp in times} >= {1, 2, 4}      # steps per synchronisation tried
     assert all(t > 0 for t in times.values())
     assert times[(layout, best, sps)] == min(times.values())
@@ -36,15 +37,19 @@ def test_autotune_returns_a_measured_admissible_width():
 def test_autotune_tries_lane_quads_on_two_levels():
     spec = S.paper_qft_spec(2, M=4, nsteps=400)
     best, layout, sps, times = msqoc.autotune(spec, probe_steps=16)
-    assert {lay for lay, _, _ in times} == {msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_QUAD}
+    assert {lay for lay, _, _ in times} == {msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_QUAD,
+                                            msqoc.LAYOUT_FIBER_LEAN}
     assert times[(layout, best, sps)] == min(times.values())
 
 
 def test_tile_model_picks_the_measured_fastest_tiles_of_the_benchmark_workload():
-    # 4 transmons at 256 windows: 9-column tiles (456 CTAs, three full waves of 152, each tile over
-    # two windows) measured fastest by the autotuner (5.5 ms per probe evaluation against 5.9 for
-    # 8-column tiles in four waves); at 64 windows 8-column one-window tiles (128 CTAs)
+    # 4 transmons at 256 and 128 windows: 7-column tiles of the 168-register build, two to an SM
+    # (12 warps), measured fastest (32.2 and 31.2 evaluations/s against 29.9 and 27.7 with the
+    # 255-register build's best tiles); at 64 windows (1024 columns, too few tiles for two an
+    # SM) 8-column tiles of the 255-register build (128 CTAs)
     with msqoc.Problem(S.config_4q(M=256)) as p:
-        assert (p.layout, p.col_block, p.tiles) == (msqoc.LAYOUT_FIBER, 9, 456)
+        assert (p.layout, p.col_block, p.tiles) == (msqoc.LAYOUT_FIBER_LEAN, 7, 586)
+    with msqoc.Problem(S.config_4q(M=128)) as p:
+        assert (p.layout, p.col_block) == (msqoc.LAYOUT_FIBER_LEAN, 7)
     with msqoc.Problem(S.config_4q(M=64)) as p:
         assert (p.layout, p.col_block) == (msqoc.LAYOUT_FIBER, 8)

@@ -26,7 +26,7 @@ def test_checkpointed_gradient_matches_oracle_3q(K):
     spec = S.transmon_spec(3, 30.0, 2001, 7, 8)     # windows of 285 and 286 steps
     alpha, W = S.random_alpha(spec, 21), S.random_W(spec, 21)
     want = oracle.evaluate(spec, alpha, W)
-    for layout in (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR):
+    for layout in (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_FIBER_LEAN):
         got = evaluate(spec, alpha, W, K, col_block=5, layout=layout)
         assert_objective_close(got["P"], want["P"])
         assert_grad_close(got["grad_alpha"], want["grad_alpha"], what=f"grad_alpha (layout {layout})")

@@ -28,12 +28,14 @@ def oracle_4q(M):
     return _ORACLE[M]
 
 
-@pytest.mark.parametrize("M,cb", [(64, 0), (256, 0), (256, 9)])
-def test_fullsize_4q(M, cb):
-    """The library's tiles, and at 256 windows also 9-column tiles over two windows (456 tiles:
-    three waves of 152), the autotuner's choice there."""
+@pytest.mark.parametrize("M,cb,layout", [(64, 0, 0), (256, 0, 0), (256, 9, msqoc.LAYOUT_FIBER),
+                                         (256, 7, msqoc.LAYOUT_FIBER_LEAN), (256, 14, msqoc.LAYOUT_FIBER_LEAN)])
+def test_fullsize_4q(M, cb, layout):
+    """The library's tiles (at 256 windows 7-column tiles of the 168-register build, two to an
+    SM: 586 tiles over two windows), 9-column tiles of the 255-register build (456 tiles: three
+    waves of 152) and 14-column tiles (378 threads, 12 warps)."""
     spec, alpha, W, want = oracle_4q(M)
-    with msqoc.Problem(spec, col_block=cb) as p:
+    with msqoc.Problem(spec, col_block=cb, layout=layout) as p:
         got = p.eval_gradient(alpha, W)
         obj = p.eval_objective(alpha, W)
     assert_objective_close(got["P"], want["P"])

@@ -21,7 +21,7 @@ def run(spec, alpha, W, **kw):
         return p.eval_gradient(alpha, W), p.steps_per_sync
 
 
-@pytest.mark.parametrize("layout", [msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR])
+@pytest.mark.parametrize("layout", [msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_FIBER_LEAN])
 @pytest.mark.parametrize("solver", [msqoc.SOLVER_MIXED, msqoc.SOLVER_FP64])
 def test_every_depth_matches_one_step_groups_bitwise(layout, solver):
     spec = S.transmon_spec(3, 30.0, 2001, 7, 8)         # ragged windows of 285-286 steps

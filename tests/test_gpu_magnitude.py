@@ -40,7 +40,7 @@ def test_extreme_window_state_magnitudes_match_the_oracle(scale, solver):
     want = oracle.evaluate(spec, alpha, W)
     tail = oracle.evaluate(spec, alpha, W, windows=(2, spec.M))       # windows 2..M
     nb = 2 * spec.N * spec.E
-    for layout in (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR):
+    for layout in (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_FIBER_LEAN):
         with msqoc.Problem(spec, solver=solver, layout=layout) as p:
             got = p.eval_gradient(alpha, W)
             obj = p.eval_objective(alpha, W)

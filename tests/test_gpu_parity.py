@@ -20,8 +20,9 @@ pytestmark = pytest.mark.gpu
 SOLVERS = {"mixed": msqoc.SOLVER_MIXED, "fp64": msqoc.SOLVER_FP64}
 
 
-LAYOUTS = {"fiber": msqoc.LAYOUT_FIBER, "pair": msqoc.LAYOUT_PAIR}
-BOTH = (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR)
+LAYOUTS = {"fiber": msqoc.LAYOUT_FIBER, "pair": msqoc.LAYOUT_PAIR, "lean": msqoc.LAYOUT_FIBER_LEAN}
+# one thread per fiber (255 and 168 registers) and a lane pair per fiber
+BOTH = (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_FIBER_LEAN)
 
 
 def run_gpu(spec, alpha, W, solver, col_block=0, ckpt_interval=0, layout=msqoc.LAYOUT_AUTO):
@@ -32,8 +33,8 @@ def run_gpu(spec, alpha, W, solver, col_block=0, ckpt_interval=0, layout=msqoc.L
 
 
 def check(spec, alpha, W, solver, col_block=0, ckpt_interval=0, layouts=BOTH):
-    """Both sweep kernel families (one thread per fiber, a lane pair per fiber) against one
-    oracle evaluation."""
+    """The sweep kernel families (one thread per fiber in both register budgets, a lane pair per
+    fiber) against one oracle evaluation."""
     want = oracle.evaluate(spec, alpha, W)
     for layout in layouts:
         got, obj = run_gpu(spec, alpha, W, solver, col_block, ckpt_interval, layout)
@@ -66,11 +67,13 @@ def test_parity_small(case, solver):
 
 
 @pytest.mark.parametrize("layout,cb", [("fiber", cb) for cb in (1, 2, 3, 4, 5, 7, 8, 9)] +
-                         [("pair", cb) for cb in (1, 2, 3, 4, 5, 6, 7)])
+                         [("pair", cb) for cb in (1, 2, 3, 4, 5, 6, 7)] +
+                         [("lean", cb) for cb in (1, 6, 7, 9, 11, 13, 14)])
 def test_parity_column_blocks_4q(layout, cb):
     """Tiles of cb columns run along the window-major column list; widths that do not divide
-    E = 16 give tiles covering two windows (3, 5, 6, 7 and 9 here).  9 columns (243 threads) is
-    the widest one-thread-per-fiber tile, 7 (384 threads) the widest lane-pair tile."""
+    E = 16 give tiles covering two windows (3, 5, 6, 7, 9, 11, 13 and 14 here).  9 columns (243
+    threads) is the widest one-thread-per-fiber tile of the 255-register build, 14 (378 threads)
+    of the 168-register build, 7 (384 threads) the widest lane-pair tile."""
     spec = S.transmon_spec(4, 1.2, 200, 3, 4)
     alpha, W = S.random_alpha(spec, 7), S.random_W(spec, 7)
     check(spec, alpha, W, msqoc.SOLVER_MIXED, col_block=cb, layouts=(LAYOUTS[layout],))
@@ -108,14 +111,17 @@ def test_one_warp_tiles_must_not_cover_two_windows():
 
 def test_column_block_beyond_the_tile_limit_is_rejected():
     spec = S.transmon_spec(4, 0.6, 100, 2, 4)
-    for cb, layout in ((16, msqoc.LAYOUT_AUTO),     # 16 x 27 fibers > 256 threads, x 2 > 384
+    for cb, layout in ((16, msqoc.LAYOUT_AUTO),     # 16 x 27 fibers > 384 threads, x 2 > 384
                        (10, msqoc.LAYOUT_FIBER),    # 270 > 256
+                       (15, msqoc.LAYOUT_FIBER_LEAN),   # 405 > 384
                        (8, msqoc.LAYOUT_PAIR)):     # 432 > 384
         with pytest.raises(msqoc.MsqocError) as err:
             msqoc.Problem(spec, col_block=cb, layout=layout)
         assert err.value.status == -1
     with msqoc.Problem(spec, col_block=8) as p:    # automatic family: only one thread per fiber fits
-        assert p.layout == msqoc.LAYOUT_FIBER
+        assert p.layout in (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_FIBER_LEAN)
+    with msqoc.Problem(spec, col_block=12) as p:   # 324 threads: only the 168-register build
+        assert p.layout == msqoc.LAYOUT_FIBER_LEAN
     with pytest.raises(msqoc.MsqocError) as err:
         msqoc.Problem(spec, layout=3)
     assert err.value.status == -1

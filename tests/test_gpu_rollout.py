@@ -14,7 +14,7 @@ from gpu_helpers import assert_objective_close
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("layout", [msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR])
+@pytest.mark.parametrize("layout", [msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_FIBER_LEAN])
 @pytest.mark.parametrize("solver", [msqoc.SOLVER_MIXED, msqoc.SOLVER_FP64])
 def test_rollout_matches_oracle_and_zeroes_the_penalties(solver, layout):
     spec = S.transmon_spec(3, 30.0, 2001, 7, 8)            # ragged windows
