@@ -238,10 +238,12 @@ bool quad_admitted(const ProbDev& pd) { return pd.L == 2 && pd.nex <= MAXEXF; }
 // fixed_cpt > 0 restricts the width, layout (MSQOC_LAYOUT_*) the family; quad_ok: the problem
 // admits lane quads.  cpt = -1: none fits.
 constexpr double QUAD_C = 0.38, QUAD_C0 = 0.52;
-// the one-thread family with 168 registers a thread: an SM holds 12 warps (two 6-warp tiles, or
-// one of up to 12), whose stalls it hides better than the 8 warps of the 255-register build:
-// measured on the 4-transmon tiles, 7-column tiles two to an SM 7% faster at 256 windows and
-// 13% at 128 than the 255-register build's best tiles, so a warp of it counts 0.9
+// the one-thread family with 168 registers a thread: an SM holds 12 warps.  Two or more of its
+// tiles on an SM fall out of step (each has its own barriers), so one tile's FP32 sweeps and
+// barrier waits overlap another's FP64 work: measured on the 4-transmon tiles, 7-column tiles
+// two to an SM 7% faster at 256 windows and 13% at 128 than the 255-register build's best
+// tiles, while one 14-column tile of 12 warps per SM gains only what its warp count predicts;
+// a warp of two or more co-resident lean tiles counts 0.9
 constexpr double LEAN_C = 0.9;
 TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int g, int solver, int sms, int fixed_cpt,
                               int layout, bool quad_ok) {
@@ -253,7 +255,7 @@ TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int g, i
         const int pair = fam == MSQOC_LAYOUT_FIBER_LEAN ? 0 : fam - MSQOC_LAYOUT_FIBER;
         const int lean = fam == MSQOC_LAYOUT_FIBER_LEAN ? 1 : 0;
         if (pair == 2 && !quad_ok) continue;
-        const double c_load = pair == 2 ? QUAD_C : pair ? 0.6 : lean ? LEAN_C : 1.0;
+        const double c_load = pair == 2 ? QUAD_C : pair ? 0.6 : 1.0;
         const double c_alone = pair == 2 ? QUAD_C0 : pair ? 0.7 : 1.0;
         const int hi = fixed_cpt > 0 ? fixed_cpt : std::min(E, max_tile_threads(pair, lean) / ((1 << pair) * F));
         const int lo = fixed_cpt > 0 ? fixed_cpt : 1;
@@ -282,8 +284,13 @@ TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int g, i
             const long last = per_sm - (waves - 1) * resident;
             const int cb = (E % cpt) ? 1 : 0;
             const double two = cb ? double(warps + 1) / double(warps) : 1.0;
-            const double ca = two * (double(waves - 1) * std::max(double(resident * warps) * c_load / 4.0, c_alone) +
-                                     std::max(double(last * warps) * c_load / 4.0, c_alone));
+            // a wave of n tiles on an SM; the lean build's warps count LEAN_C when two or more
+            // of its tiles share the SM (independent tiles fall out of step)
+            auto wave = [&](long n) {
+                const double c = (lean && n >= 2) ? LEAN_C : c_load;
+                return std::max(double(n * warps) * c / 4.0, c_alone);
+            };
+            const double ca = two * (double(waves - 1) * wave(resident) + wave(last));
             const double cc = 1.0 - double((1 << pair) * cpt * F) / (32.0 * warps);
             const bool at_floor = ca <= two * double(waves) * c_alone + 1e-9;
             const int cw = !at_floor ? 0 : ((warps == 2 || warps == 3) ? 0 : (warps == 1 ? 1 : 2));
