@@ -137,7 +137,8 @@ int gray_rank(int g) {
 // lanes mirror the last active entry.  Writes out[nthreads]; no allocation.
 void build_lanemap(int L, int q, int ncol, int ncol0, int nthreads, int pair, int* out) {
     const int F = ipow_i(L, q) / L;
-    int key[MAX_TILE_THREADS], val[MAX_TILE_THREADS];
+    int key[MAX_ANY_TILE_THREADS], val[MAX_ANY_TILE_THREADS];
+    if (ncol * F > MAX_ANY_TILE_THREADS || nthreads > MAX_ANY_TILE_THREADS) return;   // rejected by tile_width_ok
     int n = 0;
     for (int part = 0; part < 2; ++part) {
         const int first = n;
@@ -243,7 +244,9 @@ constexpr double QUAD_C = 0.38, QUAD_C0 = 0.52;
 // barrier waits overlap another's FP64 work: measured on the 4-transmon tiles, 7-column tiles
 // two to an SM 7% faster at 256 windows and 13% at 128 than the 255-register build's best
 // tiles, while one 14-column tile of 12 warps per SM gains only what its warp count predicts;
-// a warp of two or more co-resident lean tiles counts 0.9
+// a warp of two or more co-resident lean tiles of four or more warps counts 0.9 (narrower tiles
+// pay their per-tile coefficient and gradient work once per warp or two, as one-warp tiles of
+// the 255-register build measured)
 constexpr double LEAN_C = 0.9;
 TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int g, int solver, int sms, int fixed_cpt,
                               int layout, bool quad_ok) {
@@ -287,7 +290,7 @@ TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int g, i
             // a wave of n tiles on an SM; the lean build's warps count LEAN_C when two or more
             // of its tiles share the SM (independent tiles fall out of step)
             auto wave = [&](long n) {
-                const double c = (lean && n >= 2) ? LEAN_C : c_load;
+                const double c = (lean && n >= 2 && warps >= 4) ? LEAN_C : c_load;
                 return std::max(double(n * warps) * c / 4.0, c_alone);
             };
             const double ca = two * (double(waves - 1) * wave(resident) + wave(last));
@@ -1311,7 +1314,7 @@ msqoc_status eval_objective_noalloc(const msqoc_hamiltonian* H, const msqoc_cont
             for (long t = 0; t < n; ++t) chunk[t] = tile_at(t0 + t, pd.M, pd.E, pd.cb, 0);
             CUDA_TRY(cudaMemcpyAsync(tiles_d + t0, chunk, n * sizeof(Tile), cudaMemcpyHostToDevice, s));
         }
-        constexpr int kMapMax = std::max({MAX_TILE_THREADS, MAX_PAIR_TILE_THREADS, MAX_QUAD_TILE_THREADS});
+        constexpr int kMapMax = MAX_ANY_TILE_THREADS;
         int map[kMapMax];
         if (pd.nthreads > kMapMax)
             return fail(MSQOC_ERR_INVALID_ARG, "tile of %d threads exceeds the %d-entry lane map", pd.nthreads, kMapMax);

@@ -17,6 +17,11 @@ constexpr int MAX_LEAN_TILE_THREADS = 384;  // the same family compiled for 168 
 constexpr int MAX_PAIR_TILE_THREADS = 384;  // threads of a lane-pair tile (168 registers a thread)
 constexpr int MAX_QUAD_TILE_THREADS = 384;  // threads of a lane-quad tile (168 registers a thread)
 constexpr int MAX_HDEPTH = 8;               // steps per history group at most
+// threads of any tile (host arrays of a tile's lane map are sized by it)
+constexpr int MAX_ANY_TILE_THREADS = 384;
+static_assert(MAX_TILE_THREADS <= MAX_ANY_TILE_THREADS && MAX_LEAN_TILE_THREADS <= MAX_ANY_TILE_THREADS &&
+                  MAX_PAIR_TILE_THREADS <= MAX_ANY_TILE_THREADS && MAX_QUAD_TILE_THREADS <= MAX_ANY_TILE_THREADS,
+              "a tile limit exceeds MAX_ANY_TILE_THREADS");
 
 enum Solver { SOLVER_FP64 = 1, SOLVER_MIXED = 2 };
 
