@@ -114,9 +114,10 @@ LAYOUTS = {"auto": 0, "fiber": 1, "pair": 2, "quad": 3, "lean": 4}
 
 
 def sweep_traffic(kernel: str, windows: int, col_block: int, layout: int):
-    """DRAM bytes per launch of a sweep kernel from the committed ncu summary of the same tiles
-    (a `capture_config:` line naming windows, columns per tile and kernel family), or None when
-    there is none or the kernel sources changed since that capture (their digest differs)."""
+    """DRAM bytes per launch of a sweep kernel from a committed ncu summary of the same tiles
+    (a `capture_config:` line naming windows, columns per tile and kernel family, and a
+    `traffic_per_launch_bytes:` line), or None when there is none or the kernel sources changed
+    since that capture (their digest differs)."""
     import glob
     import hashlib
     import re
@@ -127,7 +128,7 @@ def sweep_traffic(kernel: str, windows: int, col_block: int, layout: int):
             h.update(f.read())
     digest = h.hexdigest()[:16]
     want = f"capture_config: windows={windows} col_block={col_block} layout={layout}"
-    for path in sorted(glob.glob(os.path.join(PROFILES, "k_sweep_4q_*small_full.md"))):
+    for path in sorted(glob.glob(os.path.join(PROFILES, "k_sweep_4q_*.md"))):
         text = open(path).read()
         m = re.search(r"sources_sha256: ([0-9a-f]+)", text)
         t = re.search(rf"{kernel}=([0-9.e+]+)", text)
@@ -388,8 +389,8 @@ def run_ours(args, spec):
         "roofline": {"bound": "alu", "kernel": f"k_sweep ({dom})", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": traffic,
-                     "traffic_note": (f"DRAM bytes per launch from {traffic_src} (capture of the same tiles on a "
-                                      "shorter grid, scaled by the steps)" if traffic else
+                     "traffic_note": (f"DRAM bytes per launch from {traffic_src} (ncu capture of the same "
+                                      "tiles and sweep sources)" if traffic else
                                       "null: no ncu summary of these tiles for the current sweep sources"),
                      "peak_source": "measured FP64 FMA microbenchmark (msqoc_measure_fp64_peak), same run",
                      "algorithmic_flops_per_launch": fl[dom], "avg_launch_ms": dom_ms},

@@ -281,7 +281,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
     constexpr int N = ipow_c(L, Q);
     constexpr int NSLOT = Q * L * 2;
     constexpr int S = BWD ? +1 : -1;       // sign of the preconditioned off-diagonal term
-    constexpr int V = next_pow2_c(4 * Q);  // padded count of reduced gradient values
+    // reduced gradient values per subsystem: A_k = Im z_k + Im y_k and B_k = Re z_k - Re y_k, the
+    // only combinations of the products the quadrature needs (padded to a power of two)
+    constexpr int V = next_pow2_c(2 * Q);
     constexpr int NH = log2_c(V);          // halving levels of the warp reduce-scatter
 
     const Tile tile = a.tiles[blockIdx.x];
@@ -500,9 +502,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
 
     // fold slot s's reduced products of step np (parity pp of the reduction buffers) into the
     // slot's alpha-gradient: dP/dalpha1_kfs += -2h B_s Im(e^{iWt} z_k + e^{-iWt} y_k),
-    // dP/dalpha2_kfs += -2h B_s Re(e^{iWt} z_k - e^{-iWt} y_k)  (Eq. grad-int at the midpoint)
+    // dP/dalpha2_kfs += -2h B_s Re(e^{iWt} z_k - e^{-iWt} y_k)  (Eq. grad-int at the midpoint),
+    // i.e. with (A, B) = (Im z + Im y, Re z - Re y) and the phase p: -2h B_s (p.x A + p.y B) and
+    // -2h B_s (p.x B - p.y A)
     auto fold = [&](int s, int pp, int64_t np, const Spline4& sp, double2 ph_lane, bool prefetched) {
-        if (lane < 4 * Q) {
+        if (lane < 2 * Q) {
             double sum = 0.0;
             for (int w2 = 0; w2 < nwarps; ++w2) sum += red[((pp * 2 + s) * nwarps + w2) * V + lane];
             zy[(pp * 2 + s) * 4 * Q + lane] = sum;
@@ -519,12 +523,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 k = 0;
                 while (k + 1 < Q && pd.cof[k + 1] <= kf) ++k;
             }
-            const double* zyk = zy + (pp * 2 + s) * 4 * Q + 4 * k;
-            const double2 zk = make_double2(zyk[0], zyk[1]);
-            const double2 yk = make_double2(zyk[2], zyk[3]);
+            const double* zyk = zy + (pp * 2 + s) * 4 * Q + 2 * k;
             const double2 ph = (prefetched && i == lane) ? ph_lane : pd.phase[size_t(np) * pd.nfsum + kf];
             const double wgt = -2.0 * pd.h * (jw == 0 ? sp.w0 : (jw == 1 ? sp.w1 : sp.w2));
-            const double A = zk.y + yk.y, B = zk.x - yk.x;
+            const double A = zyk[0], B = zyk[1];
             const int idx = (kf * pd.gspan + s0 + jw) * 2;
             ga[idx + 0] += wgt * fma(ph.x, A, ph.y * B);
             ga[idx + 1] += wgt * fma(ph.x, B, -ph.y * A);
@@ -802,10 +804,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                         }
                     }
                 }
-                acc[4 * kl + 0] = zq.x;
-                acc[4 * kl + 1] = zq.y;
-                acc[4 * kl + 2] = yq.x;
-                acc[4 * kl + 3] = yq.y;
+                acc[2 * kl + 0] = zq.y + yq.y;
+                acc[2 * kl + 1] = zq.x - yq.x;
             }
 #pragma unroll
             for (int k = 0; k < Fiber<L, Q>::NFIX; ++k) {
@@ -813,19 +813,20 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 const double2* q1 = UB + fb.nb1[k];
 #pragma unroll
                 for (int l = 0; l < L; ++l) cjmac(p, z[l], q1[l]);
-                const double px = fb.w1[k] * p.x, py = fb.w1[k] * p.y;
-                acc[4 * k + 0] = fb.plus1[k] ? px : 0.0;
-                acc[4 * k + 1] = fb.plus1[k] ? py : 0.0;
-                acc[4 * k + 2] = fb.plus1[k] ? 0.0 : px;
-                acc[4 * k + 3] = fb.plus1[k] ? 0.0 : py;
+                // entry 1 is a z_k term (a_k) or, for a fiber at the top level, a y_k term
+                // (a_k^+); entry 2, where there is one, a y_k term: A = Im z + Im y, B = Re z - Re y
+                const double sw1 = fb.plus1[k] ? fb.w1[k] : -fb.w1[k];
+                double A = fb.w1[k] * p.y, B = sw1 * p.x;
                 if (fb.two[k]) {
                     double2 p2 = make_double2(0.0, 0.0);
                     const double2* q2 = UB + fb.nb2[k];
 #pragma unroll
                     for (int l = 0; l < L; ++l) cjmac(p2, z[l], q2[l]);
-                    acc[4 * k + 2] = fb.w2[k] * p2.x;
-                    acc[4 * k + 3] = fb.w2[k] * p2.y;
+                    A = fma(fb.w2[k], p2.y, A);
+                    B = fma(-fb.w2[k], p2.x, B);
                 }
+                acc[2 * k + 0] = A;
+                acc[2 * k + 1] = B;
             }
             if (!act || !live) {
 #pragma unroll
