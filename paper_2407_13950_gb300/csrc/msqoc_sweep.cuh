@@ -775,37 +775,49 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = 0.0;
             {
-                // last subsystem (stride 1) from the fiber itself
+                // last subsystem (stride 1) from the fiber itself, grouped by entry l of Lbar:
+                // A += Im(conj(Lbar_l) v+), B += Re(conj(Lbar_l) v-) with
+                // v+- = sqrt(l+1) Ubar_{l+1} +- sqrt(l) Ubar_{l-1} (the z and y terms of entry l)
                 constexpr int kl = Q - 1;
-                double2 zq = make_double2(0.0, 0.0), yq = make_double2(0.0, 0.0);
+                double A = 0.0, B = 0.0;
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
-                    // z: conj(Lbar_l) sqrt(l+1) Ubar_{l+1};  y: conj(Lbar_l) sqrt(l) Ubar_{l-1}
-                    if (l < L - 1) {
-                        const double wz = sqrt_small(l + 1);   // folded after unrolling
-                        if (wz == 1.0) {
-                            cjmac(zq, z[l], UB[fb.xo + l + 1]);
+                    constexpr double kOne = 1.0;
+                    const double wp = l < L - 1 ? sqrt_small(l + 1) : 0.0;   // folded after unrolling
+                    const double wm = l > 0 ? sqrt_small(l) : 0.0;
+                    const double2 zl = z[l];
+                    if (wp != 0.0 && wm != 0.0) {
+                        const double2 up = UB[fb.xo + l + 1], um = UB[fb.xo + l - 1];
+                        double2 vp, vm;
+                        if (wp == kOne) {
+                            vp = make_double2(up.x + wm * um.x, up.y + wm * um.y);
+                            vm = make_double2(up.x - wm * um.x, up.y - wm * um.y);
+                        } else if (wm == kOne) {
+                            vp = make_double2(fma(wp, up.x, um.x), fma(wp, up.y, um.y));
+                            vm = make_double2(fma(wp, up.x, -um.x), fma(wp, up.y, -um.y));
                         } else {
-                            double2 p = make_double2(0.0, 0.0);
-                            cjmac(p, z[l], UB[fb.xo + l + 1]);
-                            zq.x = fma(wz, p.x, zq.x);
-                            zq.y = fma(wz, p.y, zq.y);
+                            vp = make_double2(fma(wp, up.x, wm * um.x), fma(wp, up.y, wm * um.y));
+                            vm = make_double2(fma(wp, up.x, -wm * um.x), fma(wp, up.y, -wm * um.y));
                         }
-                    }
-                    if (l > 0) {
-                        const double wy = sqrt_small(l);
-                        if (wy == 1.0) {
-                            cjmac(yq, z[l], UB[fb.xo + l - 1]);
+                        A = fma(zl.x, vp.y, fma(-zl.y, vp.x, A));
+                        B = fma(zl.x, vm.x, fma(zl.y, vm.y, B));
+                    } else {
+                        // one term: plus (first entry) or minus (last), weight w
+                        const bool plus = wp != 0.0;
+                        const double w = plus ? wp : wm;
+                        const double2 u = UB[fb.xo + (plus ? l + 1 : l - 1)];
+                        if (w == kOne) {
+                            A = fma(zl.x, u.y, fma(-zl.y, u.x, A));
+                            B = plus ? fma(zl.x, u.x, fma(zl.y, u.y, B)) : fma(-zl.x, u.x, fma(-zl.y, u.y, B));
                         } else {
-                            double2 p = make_double2(0.0, 0.0);
-                            cjmac(p, z[l], UB[fb.xo + l - 1]);
-                            yq.x = fma(wy, p.x, yq.x);
-                            yq.y = fma(wy, p.y, yq.y);
+                            const double ti = fma(zl.x, u.y, -zl.y * u.x), tr = fma(zl.x, u.x, zl.y * u.y);
+                            A = fma(w, ti, A);
+                            B = fma(plus ? w : -w, tr, B);
                         }
                     }
                 }
-                acc[2 * kl + 0] = zq.y + yq.y;
-                acc[2 * kl + 1] = zq.x - yq.x;
+                acc[2 * kl + 0] = A;
+                acc[2 * kl + 1] = B;
             }
 #pragma unroll
             for (int k = 0; k < Fiber<L, Q>::NFIX; ++k) {
@@ -815,15 +827,23 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 for (int l = 0; l < L; ++l) cjmac(p, z[l], q1[l]);
                 // entry 1 is a z_k term (a_k) or, for a fiber at the top level, a y_k term
                 // (a_k^+); entry 2, where there is one, a y_k term: A = Im z + Im y, B = Re z - Re y
-                const double sw1 = fb.plus1[k] ? fb.w1[k] : -fb.w1[k];
-                double A = fb.w1[k] * p.y, B = sw1 * p.x;
-                if (fb.two[k]) {
+                double A, B;
+                if (fb.two[k]) {   // an interior level (warp-uniform: lanes are sorted by class)
                     double2 p2 = make_double2(0.0, 0.0);
                     const double2* q2 = UB + fb.nb2[k];
 #pragma unroll
                     for (int l = 0; l < L; ++l) cjmac(p2, z[l], q2[l]);
-                    A = fma(fb.w2[k], p2.y, A);
-                    B = fma(-fb.w2[k], p2.x, B);
+                    if constexpr (L == 3) {   // level 1 of 3: weights sqrt(2) (a_k) and 1 (a_k^+)
+                        A = fma(fb.w1[k], p.y, p2.y);
+                        B = fma(fb.w1[k], p.x, -p2.x);
+                    } else {
+                        A = fma(fb.w1[k], p.y, fb.w2[k] * p2.y);
+                        B = fma(fb.w1[k], p.x, -fb.w2[k] * p2.x);
+                    }
+                } else {
+                    const double sw1 = fb.plus1[k] ? fb.w1[k] : -fb.w1[k];
+                    A = fb.w1[k] * p.y;
+                    B = sw1 * p.x;
                 }
                 acc[2 * k + 0] = A;
                 acc[2 * k + 1] = B;
