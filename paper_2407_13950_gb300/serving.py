@@ -95,6 +95,30 @@ class _Dispatched:
         return c
 
 
+class _CudaDevice:
+    """The streams, events and synchronisation of the serving loop (torch.cuda)."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+
+    def priority_range(self):
+        S = self.torch.cuda.Stream
+        return S.priority_range() if hasattr(S, "priority_range") else (0, -5)
+
+    def stream(self, priority: int):
+        return self.torch.cuda.Stream(priority=priority)
+
+    def event(self, timing: bool):
+        return self.torch.cuda.Event(enable_timing=timing)
+
+    def current_stream(self):
+        return self.torch.cuda.current_stream()
+
+    def synchronize(self):
+        self.torch.cuda.synchronize()
+
+
 class Server:
     """Sessions and the continuous-batching loop.
 
@@ -155,26 +179,26 @@ class Server:
 
     # ------------------------------------------------------------------ serving
     def run(self, requests: Sequence[Request], duration: Optional[float] = None,
-            record_events: bool = False) -> List[Request]:
+            record_events: bool = False, device=None, trace: Optional[list] = None) -> List[Request]:
         """Serve `requests` (sorted by arrival time, seconds from now).  Stops when all are done,
         or at `duration` seconds (requests then still queued or in flight are not completed).
         Returns the completed requests with their results and timestamps.  With
         `record_events`, each request's `events` holds CUDA timing events recorded on its
         dispatch's stream before its inputs are staged and after its launches, and
         `self.base_event` one recorded before the loop (device-side start and end offsets of
-        every dispatch: `base_event.elapsed_time(ev)`)."""
-        import torch
+        every dispatch: `base_event.elapsed_time(ev)`).  `device` replaces torch.cuda's streams
+        and events (tests of the scheduling on CPU); `trace`, if a list, receives one tuple
+        (time, slot, priority level 0-2, background, [request indices], class) per dispatch."""
+        dv = device if device is not None else _CudaDevice()
         if self.batch is None:
             self.batch = msqoc.Batch(self.sessions, gradient=True)
         b = self.batch
         fifo = self.policy == "fifo"
         # per slot a lowest-, a middle- and a highest-priority stream (a lower number is a higher
         # priority; CUDA clamps values beyond the device's range)
-        lo_pri, hi_pri = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") \
-            else (0, -5)
+        lo_pri, hi_pri = dv.priority_range()
         mid_pri = (lo_pri + hi_pri) // 2 if hi_pri < lo_pri else lo_pri
-        streams = [(torch.cuda.Stream(priority=lo_pri), torch.cuda.Stream(priority=mid_pri),
-                    torch.cuda.Stream(priority=hi_pri)) for _ in range(SLOTS)]
+        streams = [(dv.stream(lo_pri), dv.stream(mid_pri), dv.stream(hi_pri)) for _ in range(SLOTS)]
         cost = [(eval_flops(p.spec, False), eval_flops(p.spec, True)) for p in self.sessions]
         queues: Dict[int, collections.deque] = {s: collections.deque() for s in range(len(self.sessions))}
         n = len(requests)
@@ -190,8 +214,8 @@ class Server:
         done: List[Request] = []
         self.base_event = None
         if record_events:
-            self.base_event = torch.cuda.Event(enable_timing=True)
-            self.base_event.record(torch.cuda.current_stream())
+            self.base_event = dv.event(True)
+            self.base_event.record(dv.current_stream())
         t0 = time.perf_counter()
         nxt = 0
         while len(done) < n:
@@ -224,6 +248,8 @@ class Server:
                     progressed = True
             while oldest < n and is_done[oldest]:
                 oldest += 1
+            if progressed:
+                now = time.perf_counter() - t0   # dispatches below come after these completions
             # dispatch
             while free_slots:
                 ready = []
@@ -267,7 +293,7 @@ class Server:
                 stream = streams[slot][pri]
                 ev0 = None
                 if record_events:
-                    ev0 = torch.cuda.Event(enable_timing=True)
+                    ev0 = dv.event(True)
                     ev0.record(stream)
                 for r in sel:
                     queues[r.session].popleft()
@@ -276,8 +302,10 @@ class Server:
                     r.slot = slot
                     b.set_inputs(r.session, r.alpha, r.W, stream=stream)
                 b.eval_subset([r.session for r in sel], gradient=cls[1], slot=slot, stream=stream)
-                ev = torch.cuda.Event(enable_timing=record_events)
+                ev = dv.event(record_events)
                 ev.record(stream)
+                if trace is not None:
+                    trace.append((now, slot, pri, background, [index[id(r)] for r in sel], cls))
                 if record_events:
                     for r in sel:
                         r.events = (ev0, ev)
@@ -287,7 +315,7 @@ class Server:
                 progressed = True
             if not progressed:
                 time.sleep(0.0002)
-        torch.cuda.synchronize()
+        dv.synchronize()
         return done
 
     def run_plain(self, requests: Sequence[Request], duration: Optional[float] = None) -> List[Request]:
