@@ -23,7 +23,7 @@ def families(spec):
     exchange-coupled pairs."""
     pairs = sum(1 for row in (spec.jx or []) for v in row if v != 0.0)
     quad = (msqoc.LAYOUT_QUAD,) if spec.L == 2 and pairs <= 6 else ()
-    return (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR) + quad
+    return (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_FIBER_LEAN) + quad
 
 
 def check(spec, seed, solver=msqoc.SOLVER_DEFAULT, ckpt_interval=0, col_block=0, layouts=None):
@@ -100,7 +100,7 @@ def test_lane_quads_rejected_where_not_admitted():
             msqoc.Problem(spec, layout=msqoc.LAYOUT_QUAD)
         assert err.value.status == -1
         with msqoc.Problem(spec) as p:                      # the automatic choice avoids them
-            assert p.layout in (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR)
+            assert p.layout in (msqoc.LAYOUT_FIBER, msqoc.LAYOUT_PAIR, msqoc.LAYOUT_FIBER_LEAN)
 
 
 @pytest.mark.parametrize("q", [4, 5])
