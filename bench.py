@@ -780,7 +780,9 @@ def serving_section(args, peak, seconds: float) -> dict:
            "lookahead": srv.lookahead,
            "latency_note": "from_ready: from the head of an idle session's queue (the previous request of "
                            "the session done) to the result; service: dispatch to result; from_arrival "
-                           "includes the queue at the session (the offered load exceeds capacity)"}
+                           "includes the queue at the session (the offered load exceeds capacity); "
+                           "below_capacity: a stream the GPU keeps up with, every request served, latencies "
+                           "from arrival"}
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     for policy in ("fifo", "throughput"):
@@ -791,6 +793,16 @@ def serving_section(args, peak, seconds: float) -> dict:
     reqs = serving.poisson_requests(specs, rate=args.rate, duration=seconds, seed=1)
     done = srv.run_plain(reqs, duration=seconds)
     out["plain"] = serving_summary(done, specs, seconds, peak)
+    # the same sessions below capacity (about 70% of the GPU one request at a time): latencies
+    # are then the servers' own, not queueing at the sessions
+    light = {"rate_per_s": args.light_rate, "seconds": args.light_seconds}
+    for name, fn in (("served_fifo", srv.run), ("plain", srv.run_plain)):
+        srv.policy = "fifo"
+        reqs = serving.poisson_requests(specs, rate=args.light_rate, duration=args.light_seconds, seed=2)
+        done = fn(reqs, duration=args.light_seconds + 5.0)
+        light[name] = serving_summary(done, specs, args.light_seconds, peak)
+        light[name]["offered"] = len(reqs)
+    out["below_capacity"] = light
     out["clocks"] = sampler.stop()
     srv.close()
     fifo, plain = out["served_fifo"], out["plain"]
@@ -844,6 +856,10 @@ def main():
                     help="4q workload: leave out the config3, solver_fp64, batched and serving sub-objects")
     ap.add_argument("--extra-serve-seconds", type=float, default=10.0,
                     help="4q workload: seconds of each serving run inside the default line")
+    ap.add_argument("--light-rate", type=float, default=8.0,
+                    help="serving: offered requests/s of the below-capacity stream")
+    ap.add_argument("--light-seconds", type=float, default=12.0,
+                    help="serving: seconds of arrivals of the below-capacity stream")
     ap.add_argument("--lookahead", type=int, default=16,
                     help="serving: requests the arrival-order policy may run ahead of the oldest one")
     ap.add_argument("--layout", choices=list(LAYOUTS), default="auto",
