@@ -297,6 +297,26 @@ msqoc_status msqoc_measure_fp64_peak(double* tflops);
  * way.  Synchronizes the device. */
 msqoc_status msqoc_selftest_bounded_wait(int64_t spins, int32_t arrive, double* seconds_out);
 
+/* Self-tests of the compensated FP32 arithmetic the mixed solver's adjoint uses for the
+ * gradient products of Eq. grad-int (not operations of the paper), on the host (on_device = 0)
+ * or on the current device (on_device != 0: device copies, a kernel, copies back; synchronizes).
+ * All arrays are host arrays of n entries; -2000 <= scales <= 2000.
+ *
+ * msqoc_selftest_split: x_i 2^-sh as hi_i + lo_i, two floats: hi the value rounded to 24 bits
+ * (ties away from zero), lo the remainder rounded to nearest; |x_i 2^-sh - hi_i - lo_i| <=
+ * 2^-48 |x_i 2^-sh| for 2^-74 <= |x_i 2^-sh| < 2^127, lo_i = 0 below 2^-74, both zero below
+ * 2^-126 (and for FP64 zeros and subnormals).
+ *
+ * msqoc_selftest_dot: *out = sum_i x_i y_i formed from the splits of x_i 2^-shx and y_i 2^-shy
+ * with exact FP32 product and two-sum error terms, returned as one double scaled by
+ * 2^(shx + shy); its error is about 2^-47 sum_i |x_i y_i| (plus the partial sums' magnitudes).
+ *
+ * Errors: MSQOC_ERR_INVALID_ARG for negative n, NULL arrays (n > 0) or scales out of range;
+ * MSQOC_ERR_CUDA for a failed device step. */
+msqoc_status msqoc_selftest_split(const double* x, int64_t n, int32_t sh, int32_t on_device, float* hi, float* lo);
+msqoc_status msqoc_selftest_dot(const double* x, const double* y, int64_t n, int32_t shx, int32_t shy,
+                                int32_t on_device, double* out);
+
 /* ---------------------------------------------------------------------------------------
  * Batched evaluation (many problems per launch).
  *

@@ -529,9 +529,12 @@ struct Mark {
 size_t reg_doubles(const ProbDev& pd) { return 2 * size_t(pd.d) + size_t(pd.q) * pd.d1 + 2; }
 
 // device bytes of the history, checkpoints and segment state of one problem
+// 16-byte blocks after the history that hold its column scale exponents ([M][nseg][E] ints)
+size_t hist_scale_blocks(const ProbDev& pd) { return (size_t(pd.M) * pd.nseg * pd.E * sizeof(int) + 15) / 16; }
+
 size_t gradient_bytes(const ProbDev& pd) {
     const size_t ne = size_t(pd.N) * pd.E;
-    size_t b = size_t(pd.M) * pd.kseg * ne * sizeof(double2);
+    size_t b = (size_t(pd.M) * pd.kseg * ne + hist_scale_blocks(pd)) * sizeof(double2);
     if (pd.nseg > 1) b += (size_t(pd.M) * pd.nseg * ne + size_t(pd.M) * ne) * sizeof(double2);
     return b;
 }
@@ -785,7 +788,7 @@ msqoc_status ensure_gradient_buffers(msqoc_problem* p, cudaStream_t s) {
     if (p->hist) return MSQOC_OK;
     ProbDev& pd = p->pd;
     const size_t M = pd.M;
-    cudaError_t e = dalloc(&p->hist, M * pd.kseg * p->ne);
+    cudaError_t e = dalloc(&p->hist, M * pd.kseg * p->ne + hist_scale_blocks(pd));
     if (e == cudaSuccess && pd.nseg > 1) e = dalloc(&p->ckpt, M * pd.nseg * p->ne);
     if (e == cudaSuccess && pd.nseg > 1) e = dalloc(&p->Lstate, M * p->ne);
     if (e != cudaSuccess) {
@@ -797,6 +800,7 @@ msqoc_status ensure_gradient_buffers(msqoc_problem* p, cudaStream_t s) {
                     p->ckpt_interval, cudaGetErrorString(e));
     }
     pd.hist = p->hist;
+    pd.hsh = reinterpret_cast<int*>(p->hist + M * pd.kseg * p->ne);
     pd.ckpt = p->ckpt;
     pd.Lstate = p->Lstate;
     p->bytes += p->grad_bytes;

@@ -96,6 +96,10 @@ struct ProbDev {
     Spline4* spl;                // [nsteps] (first spline index, solver counts, w0, w1, w2)
     double2* phase;              // [nsteps][nfsum] exp(i Omega t_{n+1/2})
     double2* hist;               // [M][kseg][E][N] midpoint states Ubar of one segment of every window
+                                 // (the mixed solver's one-thread families store each entry as the
+                                 // two-float split of Ubar 2^-hsh, hsh the column's scale exponent)
+    int* hsh;                    // [M][nseg][E] column scale exponent of each window segment's
+                                 // history (mixed solver, one thread per fiber), after hist
     double2* ckpt;               // [M][nseg][E][N] states at the segment starts (kseg < longest window)
     double2* Uend;               // [M][E][N] U^m(t_m)
     double2* Lterm;              // [M][E][N] Lambda^m(t_m)

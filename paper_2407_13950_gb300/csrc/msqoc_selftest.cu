@@ -1,11 +1,19 @@
-// Self-test of the sweeps' failure path: the bounded mbarrier wait (the one the adjoint sweep
-// uses for its midpoint-history fetches) on a barrier that nothing completes gives up after its
-// spin limit, and the launch reports it through the status word as MSQOC_ERR_TIMEOUT instead of
-// hanging the GPU.  The context stays usable afterwards.
+// Self-tests of pieces of the sweeps:
+//  * the failure path: the bounded mbarrier wait (the one the adjoint sweep uses for its
+//    midpoint-history fetches) on a barrier that nothing completes gives up after its spin
+//    limit, and the launch reports it through the status word as MSQOC_ERR_TIMEOUT instead of
+//    hanging the GPU.  The context stays usable afterwards.
+//  * the compensated FP32 arithmetic of the mixed solver's gradient products (msqoc_split.cuh),
+//    on the host or in a one-thread kernel: the split of doubles into two floats and a real
+//    dot product formed the way the adjoint forms its products.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "../../include/msqoc.h"
 #include "msqoc_host.h"
+#include "msqoc_split.cuh"
 #include "msqoc_sweep_common.cuh"
 
 namespace msqoc {
@@ -22,10 +30,104 @@ __global__ void k_wait_probe(int64_t spins, int arrive, int* status) {
     }
 }
 
+__global__ void k_split_probe(const double* x, int64_t n, int sh, float* hi, float* lo) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const float2 v = split_scaled(x[i], sh);
+        hi[i] = v.x;
+        lo[i] = v.y;
+    }
+}
+
+// sum_i x_i y_i with the split operands (x 2^-shx, y 2^-shy) and the compensated accumulation,
+// scaled back by 2^(shx + shy)
+__host__ __device__ double dot_split(const double* x, const double* y, int64_t n, int shx, int shy) {
+    DF acc{0.f, 0.f};
+    for (int64_t i = 0; i < n; ++i) {
+        const float2 a = split_scaled(x[i], shx), b = split_scaled(y[i], shy);
+        df_mac(acc, a.x, a.y, b.x, b.y);
+    }
+    return df_to_f64_scaled(acc, shx + shy);
+}
+
+__global__ void k_dot_probe(const double* x, const double* y, int64_t n, int shx, int shy, double* out) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *out = dot_split(x, y, n, shx, shy);
+}
+
+// device copies of n doubles; frees what it allocated on failure
+struct DevBufs {
+    std::vector<void*> p;
+    ~DevBufs() {
+        for (void* b : p) cudaFree(b);
+    }
+    template <typename T>
+    cudaError_t alloc(T** out, size_t n) {
+        void* b = nullptr;
+        const cudaError_t e = cudaMalloc(&b, n ? n * sizeof(T) : sizeof(T));
+        if (e == cudaSuccess) p.push_back(b);
+        *out = static_cast<T*>(b);
+        return e;
+    }
+};
+
 }  // namespace
 }  // namespace msqoc
 
 using namespace msqoc;
+
+extern "C" msqoc_status msqoc_selftest_split(const double* x, int64_t n, int32_t sh, int32_t on_device, float* hi,
+                                             float* lo) {
+    if (n < 0 || (n > 0 && (!x || !hi || !lo))) return fail(MSQOC_ERR_INVALID_ARG, "split self-test: bad arrays");
+    if (sh < -2000 || sh > 2000) return fail(MSQOC_ERR_INVALID_ARG, "split self-test: scale %d out of range", sh);
+    if (!on_device) {
+        for (int64_t i = 0; i < n; ++i) {
+            const float2 v = split_scaled(x[i], sh);
+            hi[i] = v.x;
+            lo[i] = v.y;
+        }
+        return MSQOC_OK;
+    }
+    if (n == 0) return MSQOC_OK;
+    DevBufs d;
+    double* xd = nullptr;
+    float *hd = nullptr, *ld = nullptr;
+    cudaError_t e = d.alloc(&xd, n);
+    if (e == cudaSuccess) e = d.alloc(&hd, n);
+    if (e == cudaSuccess) e = d.alloc(&ld, n);
+    if (e == cudaSuccess) e = cudaMemcpy(xd, x, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_split_probe<<<static_cast<int>(std::min<int64_t>((n + 255) / 256, 1024)), 256>>>(xd, n, sh, hd, ld);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(hi, hd, n * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(lo, ld, n * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(MSQOC_ERR_CUDA, "split self-test: %s", cudaGetErrorString(e));
+    return MSQOC_OK;
+}
+
+extern "C" msqoc_status msqoc_selftest_dot(const double* x, const double* y, int64_t n, int32_t shx, int32_t shy,
+                                           int32_t on_device, double* out) {
+    if (n < 0 || !out || (n > 0 && (!x || !y))) return fail(MSQOC_ERR_INVALID_ARG, "dot self-test: bad arrays");
+    if (shx < -2000 || shx > 2000 || shy < -2000 || shy > 2000)
+        return fail(MSQOC_ERR_INVALID_ARG, "dot self-test: scales %d, %d out of range", shx, shy);
+    if (!on_device) {
+        *out = dot_split(x, y, n, shx, shy);
+        return MSQOC_OK;
+    }
+    DevBufs d;
+    double *xd = nullptr, *yd = nullptr, *od = nullptr;
+    cudaError_t e = d.alloc(&xd, n);
+    if (e == cudaSuccess) e = d.alloc(&yd, n);
+    if (e == cudaSuccess) e = d.alloc(&od, 1);
+    if (e == cudaSuccess && n) e = cudaMemcpy(xd, x, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n) e = cudaMemcpy(yd, y, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_dot_probe<<<1, 32>>>(xd, yd, n, shx, shy, od);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, od, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(MSQOC_ERR_CUDA, "dot self-test: %s", cudaGetErrorString(e));
+    return MSQOC_OK;
+}
 
 extern "C" msqoc_status msqoc_selftest_bounded_wait(int64_t spins, int32_t arrive, double* seconds_out) {
     if (spins < 1 || spins > MBAR_WAIT_SPINS) return fail(MSQOC_ERR_INVALID_ARG, "spins %lld not in [1, %lld]",

@@ -1,0 +1,162 @@
+// Double values as unevaluated sums of two floats, and compensated FP32 arithmetic on them: the
+// mixed solver's adjoint forms the gradient products of Eq. grad-int with these instead of FP64
+// multiply-adds.  On this GPU a warp's FP64 instruction occupies the issuing warp for ~60 cycles
+// and the SM retires ~2 FP64 lanes a cycle, against 128 FP32 lanes; the products are a third of
+// the adjoint's FP64 work.  Every function here runs on the host too (the CPU tests pin them);
+// the host side must be compiled without floating-point contraction (-ffp-contract=off), the
+// device side uses the _rn intrinsics, which the compiler never fuses.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+
+#include <cuda_runtime.h>
+
+namespace msqoc {
+
+// ------------------------------------------------------------------ bit casts (host and device)
+__host__ __device__ __forceinline__ uint64_t bits_of(double x) {
+    uint64_t u;
+    memcpy(&u, &x, sizeof u);
+    return u;
+}
+__host__ __device__ __forceinline__ double double_of(uint64_t u) {
+    double x;
+    memcpy(&x, &u, sizeof x);
+    return x;
+}
+__host__ __device__ __forceinline__ uint32_t bits_of(float x) {
+    uint32_t u;
+    memcpy(&u, &x, sizeof u);
+    return u;
+}
+__host__ __device__ __forceinline__ float float_of(uint32_t u) {
+    float x;
+    memcpy(&x, &u, sizeof x);
+    return x;
+}
+
+// ------------------------------------------------------------------ FP32 operations, never fused
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ float fmul_n(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd_n(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub_n(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float ffma_n(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+#else
+inline float fmul_n(float a, float b) { return a * b; }
+inline float fadd_n(float a, float b) { return a + b; }
+inline float fsub_n(float a, float b) { return a - b; }
+inline float ffma_n(float a, float b, float c) { return __builtin_fmaf(a, b, c); }
+#endif
+
+// ------------------------------------------------------------------ the split
+// x 2^-sh = hi + lo + err with hi = x 2^-sh rounded to 24 bits (ties away from zero, as the
+// mixed solver's f64 -> f32 conversion), lo = the remainder rounded to nearest, |err| <= 2^-48
+// |x 2^-sh|.  Range (of the scaled value x'): |x'| < 2^-126 and FP64 zeros and subnormals give
+// hi = lo = signed zero; for 2^-126 <= |x'| < 2^-74 lo is zero (|err| <= 2^-24 |x'|); |x'| must
+// stay below 2^127 (the mixed solver's column scale keeps it below 1).  Integer and FP32
+// operations only: hi is the top 24 bits of the scaled double, lo is the dropped 29-bit
+// remainder k (a signed count of units 2^(e - 1075) of the scaled exponent field e) converted
+// in two exact halves and scaled by a power of two.
+__host__ __device__ __forceinline__ float2 split_scaled(double x, int sh) {
+    const uint64_t u = bits_of(x);
+    const uint32_t sgn = static_cast<uint32_t>(u >> 32) & 0x80000000u;
+    const uint64_t a = u & 0x7fffffffffffffffull;
+    const int ex = static_cast<int>(a >> 52);
+    const int e = ex - sh;   // exponent field of x 2^-sh
+    if (ex == 0 || e < 897) return make_float2(float_of(sgn), float_of(sgn));
+    const uint64_t r = (a - (static_cast<uint64_t>(static_cast<int64_t>(sh)) << 52)) + (uint64_t(1) << 28);
+    const float hi = float_of((static_cast<uint32_t>(r >> 29) - (896u << 23)) | sgn);
+    const int k = static_cast<int>(static_cast<uint32_t>(r) & 0x1fffffffu) - (1 << 28);
+    // float(k), rounded once: k = kh 2^14 + kl with both halves exact through the 1.5 2^23 trick
+    const float fkh = fsub_n(float_of(0x4b400000u + static_cast<uint32_t>(k >> 14)), 12582912.f);
+    const float fkl = fsub_n(float_of(0x4b400000u + static_cast<uint32_t>(k & 0x3fff)), 12582912.f);
+    const float kf = ffma_n(fkh, 16384.f, fkl);
+    const float unit = float_of((static_cast<uint32_t>(e - 948) << 23) | sgn);   // +-2^(e - 1075)
+    const float lo = e < 949 ? float_of(sgn) : fmul_n(kf, unit);
+    return make_float2(hi, lo);
+}
+// a complex entry: (hi.x, hi.y, lo.x, lo.y)
+__host__ __device__ __forceinline__ float4 split_scaled(double2 v, int sh) {
+    const float2 x = split_scaled(v.x, sh), y = split_scaled(v.y, sh);
+    return make_float4(x.x, y.x, x.y, y.y);
+}
+
+// ------------------------------------------------------------------ compensated accumulation
+// A sum kept as s + c (floats): s the running FP32 sum, c the accumulated rounding errors and
+// low-order terms.
+struct DF {
+    float s, c;
+};
+// a += x y for x = xh + xl, y = yh + yl: xh yh = p + e exactly (FMA), p added to s with an exact
+// two-sum, e, the two-sum's error and the cross terms xh yl + xl yh added to c; xl yl
+// (<= 2^-48 |x y|) is dropped.  Error of the finished sum: about 2^-47 times the sum of the
+// magnitudes of its terms and partial sums.
+__host__ __device__ __forceinline__ void df_mac(DF& a, float xh, float xl, float yh, float yl) {
+    const float p = fmul_n(xh, yh);
+    const float e = ffma_n(xh, yh, -p);
+    const float s = fadd_n(a.s, p);
+    const float bp = fsub_n(s, a.s);
+    const float t = fadd_n(fsub_n(a.s, fsub_n(s, bp)), fsub_n(p, bp));
+    a.s = s;
+    a.c = fadd_n(a.c, fadd_n(t, ffma_n(xh, yl, ffma_n(xl, yh, e))));
+}
+// a + b (exact two-sum of the leading parts)
+__host__ __device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = fadd_n(a.s, b.s);
+    const float bp = fsub_n(s, a.s);
+    const float t = fadd_n(fsub_n(a.s, fsub_n(s, bp)), fsub_n(b.s, bp));
+    return DF{s, fadd_n(fadd_n(a.c, b.c), t)};
+}
+// a w for w = wh + wl (a constant split the same way)
+__host__ __device__ __forceinline__ DF df_scale(DF a, float wh, float wl) {
+    const float p = fmul_n(a.s, wh);
+    const float e = ffma_n(a.s, wh, -p);
+    return DF{p, ffma_n(a.c, wh, ffma_n(a.s, wl, e))};
+}
+__host__ __device__ __forceinline__ DF df_neg(DF a) { return DF{-a.s, -a.c}; }
+
+// sqrt(j) for a ladder weight (j >= 1) as hi + lo floats (compile-time constants)
+__host__ __device__ constexpr float sqrt_hi(int j) {
+    return static_cast<float>(j == 1 ? 1.0 : j == 2 ? 1.4142135623730951 : j == 3 ? 1.7320508075688772 : 2.0);
+}
+__host__ __device__ constexpr float sqrt_lo(int j) {
+    return static_cast<float>((j == 1 ? 1.0 : j == 2 ? 1.4142135623730951 : j == 3 ? 1.7320508075688772 : 2.0) -
+                              static_cast<double>(sqrt_hi(j)));
+}
+// a sqrt(j), the identity for j = 1
+__host__ __device__ __forceinline__ DF df_scale_sqrt(DF a, int j) {
+    if (j == 1) return a;
+    return df_scale(a, j == 2 ? sqrt_hi(2) : j == 3 ? sqrt_hi(3) : sqrt_hi(4),
+                    j == 2 ? sqrt_lo(2) : j == 3 ? sqrt_lo(3) : sqrt_lo(4));
+}
+
+// f 2^sh as a double: exact where the result is a normal double, rounded to nearest (ties up)
+// among the double subnormals below that range, infinity above it; zero and FP32 subnormals
+// give signed zero.  Integer operations only.
+__host__ __device__ __forceinline__ double f64_of_float_scaled(float f, int sh) {
+    const uint32_t b = bits_of(f);
+    const uint64_t sgn = static_cast<uint64_t>(b & 0x80000000u) << 32;
+    const uint32_t a = b & 0x7fffffffu;
+    const int e = static_cast<int>(a >> 23) + 896 + sh;   // biased double exponent
+    uint64_t mag = 0;
+    if (a >= 0x00800000u) {
+        if (e >= 2047) {
+            mag = uint64_t(0x7ff) << 52;
+        } else if (e > 0) {
+            mag = static_cast<uint64_t>(e) << 52 | static_cast<uint64_t>(a & 0x7fffffu) << 29;
+        } else {
+            // subnormal: the 24-bit significand in units of 2^-1074 is m 2^(e + 28)
+            const uint64_t m = (a & 0x7fffffu) | 0x800000u;
+            const int s = e + 28;
+            mag = s >= 0 ? m << s : (s > -25 ? (m + (uint64_t(1) << (-s - 1))) >> -s : 0);
+        }
+    }
+    return double_of(sgn | mag);
+}
+// the finished sum s + c times 2^sh, as one double (one FP64 add)
+__host__ __device__ __forceinline__ double df_to_f64_scaled(DF a, int sh) {
+    return f64_of_float_scaled(a.s, sh) + f64_of_float_scaled(a.c, sh);
+}
+
+}  // namespace msqoc

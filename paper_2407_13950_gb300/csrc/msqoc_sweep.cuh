@@ -268,6 +268,83 @@ __device__ __forceinline__ double warp_reduce_scatter(double (&acc)[V], int lane
     return acc[0];
 }
 
+// ------------------------------------------------------------------ gradient products, split form
+// (R, I) += (Re, Im) of conj(x) u for split entries x, u = (hi.x, hi.y, lo.x, lo.y); sr = -1
+// subtracts the real part instead
+template <int SR>
+__device__ __forceinline__ void cjmac_split(DF& R, DF& I, const float4& x, const float4& u) {
+    if constexpr (SR > 0) {
+        df_mac(R, x.x, x.z, u.x, u.z);
+        df_mac(R, x.y, x.w, u.y, u.w);
+    } else {
+        df_mac(R, -x.x, -x.z, u.x, u.z);
+        df_mac(R, -x.y, -x.w, u.y, u.w);
+    }
+    df_mac(I, x.x, x.z, u.y, u.w);
+    df_mac(I, -x.y, -x.w, u.x, u.z);
+}
+
+// The mixed solver's gradient products of one fiber (the FP64 form is in the adjoint below):
+// acc[2k] = A_k and acc[2k + 1] = B_k, the fiber's rows of A_k = Im z_k + Im y_k and
+// B_k = Re z_k - Re y_k with z_k = <Lbar, a_k Ubar>, y_k = <Lbar, a_k^+ Ubar>.  Lbar comes in
+// FP64 (z, split here with the column's scale exponent shL), the midpoint states Ubar split by
+// the forward sweep (ub, scale exponent shU).  Each value is a compensated FP32 sum (about 2^-47
+// times its terms' magnitudes), one FP64 add to finish, scaled back by 2^(shL + shU).
+//   last subsystem, weight class j = 1 .. L-1 (weight sqrt j): the pairs (Lbar_{j-1}, Ubar_j)
+//     (a_k, real part +) and (Lbar_j, Ubar_{j-1}) (a_k^+, real part -);
+//   other subsystems: entry 1 of the neighbour list (weight sqrt(l_k + 1) for a_k, real part +;
+//     sqrt(l_k) for a_k^+ at the top level, real part -) and, at interior levels, entry 2
+//     (a_k^+, weight sqrt(l_k), real part -).
+template <int L, int Q>
+__device__ __forceinline__ void products_split(const double2 (&z)[L], const float4* __restrict__ ub,
+                                               const Fiber<L, Q>& fb, int shL, int shU, double* acc) {
+    float4 zs[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) zs[l] = split_scaled(z[l], shL);
+    const int S = shL + shU;
+    {
+        constexpr int kl = Q - 1;
+        DF A{0.f, 0.f}, B{0.f, 0.f};
+#pragma unroll
+        for (int j = 1; j < L; ++j) {
+            DF R{0.f, 0.f}, I{0.f, 0.f};
+            cjmac_split<+1>(R, I, zs[j - 1], ub[fb.xo + j]);
+            cjmac_split<-1>(R, I, zs[j], ub[fb.xo + j - 1]);
+            if (j == 1) {
+                A = I;
+                B = R;
+            } else {
+                A = df_add(A, df_scale_sqrt(I, j));
+                B = df_add(B, df_scale_sqrt(R, j));
+            }
+        }
+        acc[2 * kl + 0] = df_to_f64_scaled(A, S);
+        acc[2 * kl + 1] = df_to_f64_scaled(B, S);
+    }
+#pragma unroll
+    for (int k = 0; k < Fiber<L, Q>::NFIX; ++k) {
+        const int lk = (fb.f / ipow_c(L, Q - 2 - k)) % L;   // the fiber's level in subsystem k
+        DF R{0.f, 0.f}, I{0.f, 0.f};
+        const float4* u1 = ub + fb.nb1[k];
+#pragma unroll
+        for (int l = 0; l < L; ++l) cjmac_split<+1>(R, I, zs[l], u1[l]);
+        // entry 1: a_k (weight sqrt(l_k + 1)) or, at the top level, a_k^+ (sqrt(l_k), real part -)
+        DF A = df_scale_sqrt(I, fb.plus1[k] ? lk + 1 : lk);
+        DF B = df_scale_sqrt(R, fb.plus1[k] ? lk + 1 : lk);
+        if (!fb.plus1[k]) B = df_neg(B);
+        if (fb.two[k]) {   // an interior level (warp-uniform: lanes are sorted by class)
+            DF R2{0.f, 0.f}, I2{0.f, 0.f};
+            const float4* u2 = ub + fb.nb2[k];
+#pragma unroll
+            for (int l = 0; l < L; ++l) cjmac_split<-1>(R2, I2, zs[l], u2[l]);
+            A = df_add(A, df_scale_sqrt(I2, lk));
+            B = df_add(B, df_scale_sqrt(R2, lk));
+        }
+        acc[2 * k + 0] = df_to_f64_scaled(A, S);
+        acc[2 * k + 1] = df_to_f64_scaled(B, S);
+    }
+}
+
 // ------------------------------------------------------------------ the sweep kernel
 // One CTA per tile.  A tile covers one or two windows ("slots"); each slot has its own step
 // range, per-step coefficients, iteration counts and gradient fold, computed by warp `slot`
@@ -425,6 +502,17 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
         sh = column_shift(colexp_s[c < MAX_TILE_COLS ? c : 0]);
     }
     const ColScale cs = col_scale(sh);
+    // the history's column scale exponent: written by the forward launch that stores the
+    // segment's midpoint states, read by the adjoint launch of the segment
+    const int hseg = a.mode == SWEEP_HISTORY ? 0 : a.seg;
+    int* const hsh_col = pd.hsh + (size_t(m - 1) * pd.nseg + hseg) * E + col;
+    int shU = 0;
+    if constexpr (SOLVER == SOLVER_MIXED) {
+        if (!BWD && ((a.mode == SWEEP_HISTORY && pd.nseg == 1) || a.mode == SWEEP_RECOMPUTE) && act && f == 0 &&
+            my_cnt > 0)
+            *hsh_col = sh;
+        if (BWD && my_cnt > 0) shU = *hsh_col;
+    }
 
     // ---- history blocks: slot s of a tile covers a contiguous column range of its window
     const bool want_hist = !BWD && ((a.mode == SWEEP_HISTORY && pd.nseg == 1) || a.mode == SWEEP_RECOMPUTE);
@@ -745,8 +833,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                     }
                 }
                 if (act && live) {
+                    if constexpr (SOLVER == SOLVER_MIXED) {
+                        // the adjoint's gradient products read the split form (products_split)
+                        float4* Hs = reinterpret_cast<float4*>(H) + size_t(hpos) * hstride + fb.xo;
 #pragma unroll
-                    for (int l = 0; l < L; ++l) H[size_t(hpos) * hstride + fb.xo + l] = z[l];
+                        for (int l = 0; l < L; ++l) Hs[l] = split_scaled(z[l], sh);
+                    } else {
+#pragma unroll
+                        for (int l = 0; l < L; ++l) H[size_t(hpos) * hstride + fb.xo + l] = z[l];
+                    }
                 }
                 fence_proxy_async_smem();
             }
@@ -774,6 +869,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             double acc[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = 0.0;
+            if constexpr (SOLVER == SOLVER_MIXED) {
+                products_split<L, Q>(z, reinterpret_cast<const float4*>(UB), fb, sh, shU, acc);
+            } else {
             {
                 // last subsystem (stride 1) from the fiber itself, grouped by entry l of Lbar:
                 // A += Im(conj(Lbar_l) v+), B += Re(conj(Lbar_l) v-) with
@@ -848,6 +946,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 acc[2 * k + 0] = A;
                 acc[2 * k + 1] = B;
             }
+            }   // FP64 products
             if (!act || !live) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc[v] = 0.0;

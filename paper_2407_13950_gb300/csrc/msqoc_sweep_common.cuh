@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "msqoc_internal.h"
+#include "msqoc_split.cuh"
 
 namespace msqoc {
 

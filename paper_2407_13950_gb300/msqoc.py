@@ -28,7 +28,8 @@ EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_query_layout", "msqoc_
             "msqoc_batch_eval_objective", "msqoc_batch_eval_gradient", "msqoc_batch_destroy", "msqoc_set_inputs",
             "msqoc_get_objective", "msqoc_get_gradient", "msqoc_batch_eval_subset", "msqoc_autotune",
             "msqoc_rollout", "msqoc_rollout_estimate", "msqoc_eval_regularization", "msqoc_lbfgs_direction",
-            "msqoc_lbfgs_trial", "msqoc_lbfgs_update", "msqoc_selftest_bounded_wait"]
+            "msqoc_lbfgs_trial", "msqoc_lbfgs_update", "msqoc_selftest_bounded_wait",
+            "msqoc_selftest_split", "msqoc_selftest_dot"]
 BATCH_GRADIENT, BATCH_GRAPH = 1, 2
 KERNEL_NAMES = ["controls", "forward", "terminal", "adjoint", "finalize"]
 
@@ -86,6 +87,8 @@ def load(build_if_missing: bool = True):
             "msqoc_kernel_times": (i32, [vp, vp]),
             "msqoc_measure_fp64_peak": (i32, [vp]),
             "msqoc_selftest_bounded_wait": (i32, [ctypes.c_int64, i32, vp]),
+            "msqoc_selftest_split": (i32, [vp, i64, i32, i32, vp, vp]),
+            "msqoc_selftest_dot": (i32, [vp, vp, i64, i32, i32, i32, vp]),
             "msqoc_eval_objective_noalloc": (i32, [vp, vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, i32,
                                                    vp, vp, vp, vp, vp, vp]),
             "msqoc_batch_create": (i32, [vp, i32, i32, vp]),
@@ -327,6 +330,30 @@ def selftest_bounded_wait(spins: int, arrive: bool = False) -> float:
     t = ctypes.c_double()
     _check(load().msqoc_selftest_bounded_wait(int(spins), 1 if arrive else 0, ctypes.byref(t)))
     return t.value
+
+
+def selftest_split(x, sh: int = 0, device: bool = False):
+    """(hi, lo) float32 arrays with x 2^-sh = hi + lo to 2^-48 (the mixed solver's split of the
+    midpoint states for the gradient products), computed on the host or on the device."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    hi = np.empty(x.shape, np.float32)
+    lo = np.empty(x.shape, np.float32)
+    _check(load().msqoc_selftest_split(x.ctypes.data, x.size, int(sh), 1 if device else 0, hi.ctypes.data,
+                                       lo.ctypes.data))
+    return hi, lo
+
+
+def selftest_dot(x, y, shx: int = 0, shy: int = 0, device: bool = False) -> float:
+    """sum x_i y_i formed the way the mixed solver's adjoint forms its gradient products
+    (split operands, compensated FP32 accumulation, one double)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    if x.shape != y.shape:
+        raise ValueError("x and y differ in shape")
+    out = ctypes.c_double()
+    _check(load().msqoc_selftest_dot(x.ctypes.data, y.ctypes.data, x.size, int(shx), int(shy), 1 if device else 0,
+                                     ctypes.byref(out)))
+    return out.value
 
 
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024   # MSQOC_NOALLOC_SCRATCH_BYTES
