@@ -54,7 +54,10 @@ __device__ inline int step_counts(int solver, float rho) {
         }
         if (rho >= 0.5f) bad = 1;
     }
-    return a | (b << 8) | (r << 16) | (bad << 24);
+    // the compensated FP32 apply of the residual (error about 2^-47 |P iX_C z| <= 2^-47 rho |z|)
+    // stays below the FP64 rounding of z (2^-53 |z|) for rho <= 2^-7; above, the FP64 apply
+    const int f64_apply = rho > 0.0078125f ? 1 : 0;
+    return a | (b << 8) | (r << 16) | (bad << 24) | (f64_apply << 25);
 }
 
 // The quadratic cardinal B-splines active at time t: on [j dtau, (j+1) dtau) the three

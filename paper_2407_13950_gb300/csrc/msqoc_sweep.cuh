@@ -219,11 +219,13 @@ __device__ __forceinline__ void apply_off(const T2* __restrict__ buf, const T2* 
 
 // ------------------------------------------------------------------ per-step coefficients
 // Warp 0: slot (k, l, dir) -> i (h/2) sqrt(l+1) d_k (dir 0, a_k) or i (h/2) sqrt(l) conj(d_k)
-// (dir 1, a_k^+); lane k' < NSLOT holds d_k of its slot's subsystem.  The iteration counts of
-// the step (packed by step_counts in the controls kernel) are unpacked into prm.
+// (dir 1, a_k^+); lane k' < NSLOT holds d_k of its slot's subsystem.  The coefficients go out
+// in FP64, FP32 and (mixed solver, cfs != nullptr) split into two floats.  The iteration counts
+// of the step (packed by step_counts in the controls kernel) are unpacked into prm; prm[3] holds
+// the solver-range flag (bit 0) and the FP64-apply flag (bit 1).
 template <int L, int Q>
 __device__ __forceinline__ void step_coefficients(const ProbDev& pd, int lane, double2 dk, int cnt, double2* cfd,
-                                                  float2* cff, int* prm) {
+                                                  float2* cff, float4* cfs, int* prm) {
     constexpr int NSLOT = Q * L * 2;
     if (lane < NSLOT) {
         const int dir = lane & 1;
@@ -234,12 +236,13 @@ __device__ __forceinline__ void step_coefficients(const ProbDev& pd, int lane, d
         if (valid) v = dir == 0 ? make_double2(-s * dk.y, s * dk.x) : make_double2(s * dk.y, s * dk.x);
         cfd[lane] = v;
         cff[lane] = f32_of(v);
+        if (cfs) cfs[lane] = split_scaled(v, 0);
     }
     if (lane == 0) {
         prm[0] = cnt & 0xff;
         prm[1] = (cnt >> 8) & 0xff;
         prm[2] = (cnt >> 16) & 0xff;
-        prm[3] = (cnt >> 24) & 0xff;
+        prm[3] = (cnt >> 24) & 3;
     }
 }
 
@@ -266,6 +269,56 @@ __device__ __forceinline__ double warp_reduce_scatter(double (&acc)[V], int lane
         }
     }
     return acc[0];
+}
+
+// ------------------------------------------------------------------ compensated apply
+// w += c x for split complex operands (hi.x, hi.y, lo.x, lo.y); w[0] real, w[1] imaginary part
+__device__ __forceinline__ void cmac_df(DF (&w)[2], const float4& c, const float4& x) {
+    df_mac(w[0], c.x, c.z, x.x, x.z);
+    df_mac(w[0], -c.y, -c.w, x.y, x.w);
+    df_mac(w[1], c.x, c.z, x.y, x.w);
+    df_mac(w[1], c.y, c.w, x.x, x.z);
+}
+// w = iX_C x on the fiber (apply_off without exchange terms) from split entries: the fiber's own
+// in xr, the neighbours' in buf, the coefficients in cf; compensated FP32 sums (about 2^-47 of
+// the terms' magnitudes).  The mixed solver's residual needs P w to within 2^-53 |x| only, and
+// |P w| <= rho |x| with rho <= 2^-7 wherever this form is used.
+template <int L, int Q>
+__device__ __forceinline__ void apply_off_df(const float4* __restrict__ buf, const float4* __restrict__ cf,
+                                             const Fiber<L, Q>& fb, const float4 (&xr)[L], DF (&w)[L][2]) {
+#pragma unroll
+    for (int l = 0; l < L; ++l) w[l][0] = w[l][1] = DF{0.f, 0.f};
+    constexpr int kl = Q - 1;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        if (l < L - 1) cmac_df(w[l], cf[(kl * L + l) * 2 + 0], xr[l + 1]);
+        if (l > 0) cmac_df(w[l], cf[(kl * L + l) * 2 + 1], xr[l - 1]);
+    }
+#pragma unroll
+    for (int k = 0; k < Fiber<L, Q>::NFIX; ++k) {
+        const float4 c1 = cf[fb.sl1[k]];
+        const float4* p1 = buf + fb.nb1[k];
+#pragma unroll
+        for (int l = 0; l < L; ++l) cmac_df(w[l], c1, p1[l]);
+        if (fb.two[k]) {
+            const float4 c2 = cf[fb.sl2[k]];
+            const float4* p2 = buf + fb.nb2[k];
+#pragma unroll
+            for (int l = 0; l < L; ++l) cmac_df(w[l], c2, p2[l]);
+        }
+    }
+}
+// the residual -d + s P w of the refinement in scaled units, rounded to FP32: d = dh + dl and
+// P = (hi, lo) split, w from apply_off_df
+template <int S>
+__device__ __forceinline__ float2 resid_df(float2 dh, float2 dl, const float4& P, const DF (&w)[2]) {
+    DF re{-dh.x, -dl.x}, im{-dh.y, -dl.y};
+    constexpr float s = S > 0 ? 1.f : -1.f;
+    df_mac(re, s * P.x, s * P.z, w[0].s, w[0].c);
+    df_mac(re, -s * P.y, -s * P.w, w[1].s, w[1].c);
+    df_mac(im, s * P.x, s * P.z, w[1].s, w[1].c);
+    df_mac(im, s * P.y, s * P.w, w[0].s, w[0].c);
+    return make_float2(fadd_n(re.s, re.c), fadd_n(im.s, im.c));
 }
 
 // ------------------------------------------------------------------ gradient products, split form
@@ -370,6 +423,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
     const SweepSmem lay = sweep_layout(Q, L, N, a.cpt, blockDim.x, a.gmax, SOLVER, BWD, 0, a.hdepth);
     double2* coef_d = reinterpret_cast<double2*>(smem + lay.coef_d);
     float2* coef_f = reinterpret_cast<float2*>(smem + lay.coef_f);
+    float4* coef_s = SOLVER == SOLVER_MIXED ? reinterpret_cast<float4*>(smem + lay.coef_s) : nullptr;
     int* params = reinterpret_cast<int*>(smem + lay.params);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + lay.mbar);
     double* red = reinterpret_cast<double*>(smem + lay.red);
@@ -457,12 +511,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
     // preconditioner on the fiber: P (forward) or conj(P) (adjoint)
     double2 Pd[L];
     float2 Pf[L];
+    float4 Ps[L];   // split (mixed solver's compensated residual)
 #pragma unroll
     for (int l = 0; l < L; ++l) {
         double2 p = pd.P[f * L + l];
         if (BWD) p.y = -p.y;
         Pd[l] = p;
         Pf[l] = f32_of(p);
+        Ps[l] = split_scaled(p, 0);
     }
 
     // ---- initial state
@@ -640,7 +696,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             const int cnt = cnt_next;
             if (jj + 1 < nit) load_ctrl(jj + 1);
             step_coefficients<L, Q>(pd, lane, dk, cnt, coef_d + (par * 2 + cslot) * NSLOT,
-                                    coef_f + (par * 2 + cslot) * NSLOT, params + (par * 2 + cslot) * 4);
+                                    coef_f + (par * 2 + cslot) * NSLOT,
+                                    coef_s ? coef_s + (par * 2 + cslot) * NSLOT : nullptr,
+                                    params + (par * 2 + cslot) * 4);
         }
         // adjoint: the folding warps fetch what the fold of iteration jj - 1 needs now, so the
         // loads are in flight during the solve
@@ -659,6 +717,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
         }
         const double2* cfd = coef_d + (par * 2 + slot) * NSLOT;
         const float2* cff = coef_f + (par * 2 + slot) * NSLOT;
+        const float4* cfs = coef_s + (par * 2 + slot) * NSLOT;
         const int* prm = params + (par * 2 + slot) * 4;          // this thread's slot
         const int* prm0 = params + (par * 2) * 4;
         const int* prm1 = params + (par * 2 + 1) * 4;
@@ -768,8 +827,21 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 dacc[l] = f64_of_scaled(df[l], cs);
                 z[l] = make_double2(b[l].x + dacc[l].x, b[l].y + dacc[l].y);
             }
+            // the residual's apply in compensated FP32 (split entries in D0) where the step's
+            // contraction factor allows it (step_counts) and the problem has no exchange terms;
+            // uniform over a slot, so a column's entries in D0 have one form
+            const bool dfa = pd.nex == 0 && !(prm[3] & 2);
+            float4* D0s = reinterpret_cast<float4*>(D0);
             for (int pass = 0;; ++pass) {
-                if (act) {
+                float4 zs[L];
+                if (dfa) {
+#pragma unroll
+                    for (int l = 0; l < L; ++l) zs[l] = split_scaled(z[l], sh);
+                    if (act) {
+#pragma unroll
+                        for (int l = 0; l < L; ++l) D0s[fb.xo + l] = zs[l];
+                    }
+                } else if (act) {
 #pragma unroll
                     for (int l = 0; l < L; ++l) D0[fb.xo + l] = z[l];
                 }
@@ -778,14 +850,31 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 // waiting here, ahead of a barrier every step has, makes the staging barrier-free
                 if (!BWD && want_hist && pass == 0 && tid == 0 && hpos == 0) bulk_wait_read_all();
                 tile_sync();
-                double2 w[L];
-                apply_off<L, Q, double2>(D0, cfd, fb, z, w, pd);
                 float2 rf[L], e[L];
+                if (dfa) {
+                    DF w[L][2];
+                    apply_off_df<L, Q>(D0s, cfs, fb, zs, w);
 #pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    const double2 r = resid_from<S>(dacc[l], Pd[l], w[l]);
-                    rf[l] = f32_of_scaled(r, cs);
-                    e[l] = rf[l];
+                    for (int l = 0; l < L; ++l) {
+                        // d in scaled units: the FP32 stage's value in the first pass, then split
+                        float2 dh = df[l], dl = make_float2(0.f, 0.f);
+                        if (pass > 0) {
+                            const float4 ds = split_scaled(dacc[l], sh);
+                            dh = make_float2(ds.x, ds.y);
+                            dl = make_float2(ds.z, ds.w);
+                        }
+                        rf[l] = resid_df<S>(dh, dl, Ps[l], w[l]);
+                        e[l] = rf[l];
+                    }
+                } else {
+                    double2 w[L];
+                    apply_off<L, Q, double2>(D0, cfd, fb, z, w, pd);
+#pragma unroll
+                    for (int l = 0; l < L; ++l) {
+                        const double2 r = resid_from<S>(dacc[l], Pd[l], w[l]);
+                        rf[l] = f32_of_scaled(r, cs);
+                        e[l] = rf[l];
+                    }
                 }
                 for (int it = 0; it < j2max; ++it) {
                     float2* Fb = fsel ? FB : FA;
@@ -820,7 +909,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             }
         }
 
-        if (tid == 0 && (prm0[3] || (nslot > 1 && prm1[3]))) atomicOr(pd.status, ST_SOLVER_RANGE);
+        if (tid == 0 && ((prm0[3] & 1) || (nslot > 1 && (prm1[3] & 1)))) atomicOr(pd.status, ST_SOLVER_RANGE);
 
         if constexpr (!BWD) {
             // ---- midpoint states for the adjoint sweep (async bulk store at the next step)

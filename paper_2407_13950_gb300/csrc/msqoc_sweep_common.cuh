@@ -268,7 +268,7 @@ struct Fiber {
 // keep each coefficient in the form of either part, so their coefficient arrays are twice as
 // large.
 struct SweepSmem {
-    size_t coef_d, coef_f, params, mbar, red, zy, galpha, D0, D1, FA, FB, H, UB0, UB1, total;
+    size_t coef_d, coef_f, coef_s, params, mbar, red, zy, galpha, D0, D1, FA, FB, H, UB0, UB1, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -287,6 +287,9 @@ __host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cpt, 
     size_t o = 0;
     s.coef_d = o; o = align16(o + size_t(2) * 2 * ncoef * nslot * 16);  // [parity][slot][part][NSLOT]
     s.coef_f = o; o = align16(o + size_t(2) * 2 * ncoef * nslot * 8);
+    // the coefficients split into two floats (hi, lo) for the compensated apply of the mixed
+    // solver's one-thread families
+    s.coef_s = o; o = align16(o + (!pair && solver == SOLVER_MIXED ? size_t(2) * 2 * nslot * 16 : 0));
     s.params = o; o = align16(o + 2 * 2 * 4 * 4);                      // [parity][slot][4]
     s.mbar = o;   o = align16(o + 2 * 8);
     s.red = o;    o = align16(o + (bwd ? size_t(2) * 2 * nwarps * V * 8 : 0));   // [parity][slot][warp][V]

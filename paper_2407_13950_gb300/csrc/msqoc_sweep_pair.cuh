@@ -197,7 +197,7 @@ __device__ __forceinline__ void step_coefficients_pair(const ProbDev& pd, int la
         prm[0] = cnt & 0xff;
         prm[1] = (cnt >> 8) & 0xff;
         prm[2] = (cnt >> 16) & 0xff;
-        prm[3] = (cnt >> 24) & 0xff;
+        prm[3] = (cnt >> 24) & 1;
     }
 }
 
