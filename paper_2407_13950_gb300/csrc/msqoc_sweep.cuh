@@ -339,22 +339,18 @@ __device__ __forceinline__ void cjmac_split(DF& R, DF& I, const float4& x, const
 
 // The mixed solver's gradient products of one fiber (the FP64 form is in the adjoint below):
 // acc[2k] = A_k and acc[2k + 1] = B_k, the fiber's rows of A_k = Im z_k + Im y_k and
-// B_k = Re z_k - Re y_k with z_k = <Lbar, a_k Ubar>, y_k = <Lbar, a_k^+ Ubar>.  Lbar comes in
-// FP64 (z, split here with the column's scale exponent shL), the midpoint states Ubar split by
-// the forward sweep (ub, scale exponent shU).  Each value is a compensated FP32 sum (about 2^-47
-// times its terms' magnitudes), one FP64 add to finish, scaled back by 2^(shL + shU).
+// B_k = Re z_k - Re y_k with z_k = <Lbar, a_k Ubar>, y_k = <Lbar, a_k^+ Ubar>.  Lbar comes split
+// into two floats (zs, in units of its column's scale 2^shL), the midpoint states Ubar split by
+// the forward sweep (ub, scale 2^shU).  Each value is a compensated FP32 sum (about 2^-47 times
+// its terms' magnitudes), one FP64 add to finish, scaled back by 2^S, S = shL + shU.
 //   last subsystem, weight class j = 1 .. L-1 (weight sqrt j): the pairs (Lbar_{j-1}, Ubar_j)
 //     (a_k, real part +) and (Lbar_j, Ubar_{j-1}) (a_k^+, real part -);
 //   other subsystems: entry 1 of the neighbour list (weight sqrt(l_k + 1) for a_k, real part +;
 //     sqrt(l_k) for a_k^+ at the top level, real part -) and, at interior levels, entry 2
 //     (a_k^+, weight sqrt(l_k), real part -).
 template <int L, int Q>
-__device__ __forceinline__ void products_split(const double2 (&z)[L], const float4* __restrict__ ub,
-                                               const Fiber<L, Q>& fb, int shL, int shU, double* acc) {
-    float4 zs[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) zs[l] = split_scaled(z[l], shL);
-    const int S = shL + shU;
+__device__ __forceinline__ void products_split(const float4 (&zs)[L], const float4* __restrict__ ub,
+                                               const Fiber<L, Q>& fb, int S, double* acc) {
     {
         constexpr int kl = Q - 1;
         DF A{0.f, 0.f}, B{0.f, 0.f};
@@ -398,10 +394,46 @@ __device__ __forceinline__ void products_split(const double2 (&z)[L], const floa
     }
 }
 
+// ------------------------------------------------------------------ gradient fold (adjoint)
+// One step's fold of a window slot, run by that slot's folding warp: the warps' partial sums
+// red[w][v] (fixed order) of A_k = Im z_k + Im y_k and B_k = Re z_k - Re y_k into zy, then, per
+// (carrier kf, active spline jw) entry, dP/dalpha1_kfs += -2h B_s (p.x A + p.y B) and
+// dP/dalpha2_kfs += -2h B_s (p.x B - p.y A) with p = e^{i W t} at the midpoint (Eq. grad-int).
+// Kept out of line: it runs once per step on one warp, and inlined it enlarged the adjoint's
+// step loop, whose instruction fetches already stall its warps.
+template <int Q, int V>
+static __device__ __noinline__ void fold_step(const ProbDev& pd, const double* red, double* zy, double* ga,
+                                              int nwarps, int64_t np, Spline4 sp, double2 ph_lane, bool prefetched,
+                                              int s0, int lane) {
+    if (lane < 2 * Q) {
+        const double* r = red + lane;
+        double s_even = 0.0, s_odd = 0.0;
+        for (int w2 = 0; w2 < nwarps; w2 += 2) {
+            s_even += r[w2 * V];
+            if (w2 + 1 < nwarps) s_odd += r[(w2 + 1) * V];
+        }
+        zy[lane] = s_even + s_odd;
+    }
+    __syncwarp();
+    const int nscat = pd.nfsum * 3;
+    const double m2h = -2.0 * pd.h;
+    for (int i = lane; i < nscat; i += 32) {
+        const int kf = i / 3, jw = i % 3;
+        int k = 0;
+        while (k + 1 < Q && pd.cof[k + 1] <= kf) ++k;
+        const double2 ph = (prefetched && i == lane) ? ph_lane : pd.phase[size_t(np) * pd.nfsum + kf];
+        const double wgt = m2h * (jw == 0 ? sp.w0 : (jw == 1 ? sp.w1 : sp.w2));
+        const double A = zy[2 * k], B = zy[2 * k + 1];
+        const int idx = (kf * pd.gspan + s0 + jw) * 2;
+        ga[idx + 0] = fma(wgt, fma(ph.x, A, ph.y * B), ga[idx + 0]);
+        ga[idx + 1] = fma(wgt, fma(ph.x, B, -ph.y * A), ga[idx + 1]);
+    }
+}
+
 // ------------------------------------------------------------------ the sweep kernel
 // One CTA per tile.  A tile covers one or two windows ("slots"); each slot has its own step
-// range, per-step coefficients, iteration counts and gradient fold, computed by warp `slot`
-// (the host only builds two-slot tiles with at least two warps).  Loops run to the longer of
+// range, per-step coefficients and iteration counts, computed by warp `slot`, and gradient fold,
+// run by warp nwarps - 1 - slot (the host only builds two-slot tiles with at least two warps).  Loops run to the longer of
 // the slots' ranges; a thread whose slot has no step at an iteration keeps its state.
 // MAXT: the largest tile the instantiation serves; it sets the register budget (255 registers a
 // thread for MAX_TILE_THREADS, 168 for MAX_LEAN_TILE_THREADS: 12 warps on an SM).
@@ -620,9 +652,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
         if (tid == 0 && nit > 0) fetch_group(UB0, 0, &mbar[0]);
     }
 
-    // warp s < nslot computes slot s's coefficients and folds its gradient; it keeps d_k and
-    // the iteration counts of the slot's next step in registers (lane -> subsystem of its slot)
+    // warp s < nslot computes slot s's coefficients and keeps d_k and the iteration counts of
+    // the slot's next step in registers (lane -> subsystem of its slot); warp nwarps - 1 - s folds
+    // the slot's gradient (the two extra jobs of a step on different warps where there are two)
     const bool coef_warp = warp < nslot;
+    const bool fold_warp = nwarps - 1 - warp < nslot;
+    const int fslot = fold_warp ? nwarps - 1 - warp : 0;
     const int cslot = coef_warp ? warp : 0;
     const int my_k = (lane < NSLOT) ? (lane / (2 * L)) : 0;
     double2 dk_next = make_double2(0.0, 0.0);
@@ -634,12 +669,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             cnt_next = pd.spl[n].cnt;
         }
     };
-    // gradient entries of a step: (carrier, spline of the 3 active) pairs, one per lane; the
-    // carrier, spline offset and subsystem of this lane's first entry are fixed for the launch
+    // gradient entries of a step: (carrier, spline of the 3 active) pairs, one per lane of the
+    // folding warp (whose phases are prefetched for the lane's first entry)
     const int nscat = pd.nfsum * 3;
-    const int f_kf = lane / 3, f_jw = lane % 3;
-    int f_k = 0;
-    while (f_k + 1 < Q && pd.cof[f_k + 1] <= f_kf) ++f_k;
     // warps whose lanes belong to both slots reduce each slot separately
     const unsigned mask1 = __ballot_sync(0xffffffffu, act && slot == 1);
     const unsigned mask0 = __ballot_sync(0xffffffffu, act && slot == 0);
@@ -650,31 +682,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
     // i.e. with (A, B) = (Im z + Im y, Re z - Re y) and the phase p: -2h B_s (p.x A + p.y B) and
     // -2h B_s (p.x B - p.y A)
     auto fold = [&](int s, int pp, int64_t np, const Spline4& sp, double2 ph_lane, bool prefetched) {
-        if (lane < 2 * Q) {
-            double sum = 0.0;
-            for (int w2 = 0; w2 < nwarps; ++w2) sum += red[((pp * 2 + s) * nwarps + w2) * V + lane];
-            zy[(pp * 2 + s) * 4 * Q + lane] = sum;
+        if (!grad_fits) {
+            // the sums are not needed; keep the warp's lanes together as fold_step would
+            __syncwarp();
+            return;
         }
-        __syncwarp();
-        if (!grad_fits) return;
-        const int s0 = sp.s - (s ? slo_1 : slo_0);   // first active spline, window-local
-        double* ga = galpha + size_t(s) * a.gmax;
-        for (int i = lane; i < nscat; i += 32) {
-            int kf = f_kf, jw = f_jw, k = f_k;   // this lane's first entry, precomputed
-            if (i != lane) {
-                kf = i / 3;
-                jw = i % 3;
-                k = 0;
-                while (k + 1 < Q && pd.cof[k + 1] <= kf) ++k;
-            }
-            const double* zyk = zy + (pp * 2 + s) * 4 * Q + 2 * k;
-            const double2 ph = (prefetched && i == lane) ? ph_lane : pd.phase[size_t(np) * pd.nfsum + kf];
-            const double wgt = -2.0 * pd.h * (jw == 0 ? sp.w0 : (jw == 1 ? sp.w1 : sp.w2));
-            const double A = zyk[0], B = zyk[1];
-            const int idx = (kf * pd.gspan + s0 + jw) * 2;
-            ga[idx + 0] += wgt * fma(ph.x, A, ph.y * B);
-            ga[idx + 1] += wgt * fma(ph.x, B, -ph.y * A);
-        }
+        fold_step<Q, V>(pd, red + ((pp * 2 + s) * nwarps) * V, zy + (pp * 2 + s) * 4 * Q,
+                        galpha + size_t(s) * a.gmax, nwarps, np, sp, ph_lane, prefetched,
+                        sp.s - (s ? slo_1 : slo_0), lane);
     };
 
     __shared__ int tflag_s;   // a bounded history wait gave up (adjoint)
@@ -704,8 +719,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
         // loads are in flight during the solve
         Spline4 sp_prev{};
         double2 ph_prev = make_double2(0.0, 0.0);
-        if (BWD && jj > 0 && coef_warp && jj - 1 < (cslot ? cnt_1 : cnt_0)) {
-            const int64_t np = step_of(cslot, jj - 1);
+        if (BWD && jj > 0 && fold_warp && jj - 1 < (fslot ? cnt_1 : cnt_0)) {
+            const int64_t np = step_of(fslot, jj - 1);
             sp_prev = pd.spl[np];
             if (lane < nscat) ph_prev = pd.phase[size_t(np) * pd.nfsum + lane / 3];
         }
@@ -728,9 +743,22 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
         for (int l = 0; l < L; ++l) b[l] = cmul(Pd[l], u[l]);
 
         double2 z[L];   // the midpoint state being solved for (Ubar or Lbar)
+        // the final z split into two floats in the column's scaled units (zf_ok): the split of
+        // the refinement's last pass plus its FP32 correction, exact to 2^-48 |z|; used by the
+        // forward's history and the adjoint's gradient products instead of a split of z
+        float4 zf[L];
+        bool zf_ok = false;
 
         // first barrier of the step: the coefficients are published; thread 0 stores the
         // previous iteration's midpoints (forward) or fetches the next iteration's (adjoint)
+        // the folding warps add iteration jj - 1's reduced products into the alpha-gradient right
+        // after this iteration's first barrier (which published red[par ^ 1]): the other warps
+        // then run FP32 sweeps, so the fold's FP64 chain does not queue behind the FP64 work
+        // every warp issues at the ends of a step
+        auto fold_previous = [&]() {
+            if (BWD && jj > 0 && fold_warp && jj - 1 < (fslot ? cnt_1 : cnt_0))
+                fold(fslot, par ^ 1, step_of(fslot, jj - 1), sp_prev, ph_prev, true);
+        };
         auto first_sync_work = [&]() {
             if (BWD && *tflag) timed_out = true;   // uniform: read after a barrier
             if (!BWD && want_hist && tid == 0 && jj > 0 && hpos == 0) {
@@ -755,6 +783,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             tile_sync();
             first_sync_work();
             if (timed_out) break;
+            fold_previous();
             const int Kown = prm[0];
             const int Kmax = nslot > 1 ? max(prm0[0], prm1[0]) : prm0[0];
             for (int it = 0; it < Kmax; ++it) {
@@ -793,6 +822,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 tile_sync();
                 first_sync_work();
                 if (timed_out) break;
+                fold_previous();
                 float2 w[L];
                 apply_off<L, Q, float2>(Fb, cff, fb, y, w, pd);
 #pragma unroll
@@ -837,6 +867,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 if (dfa) {
 #pragma unroll
                     for (int l = 0; l < L; ++l) zs[l] = split_scaled(z[l], sh);
+#pragma unroll
+                    for (int l = 0; l < L; ++l) zf[l] = zs[l];
+                    zf_ok = true;
                     if (act) {
 #pragma unroll
                         for (int l = 0; l < L; ++l) D0s[fb.xo + l] = zs[l];
@@ -897,6 +930,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 if (pass < R) {
 #pragma unroll
                     for (int l = 0; l < L; ++l) z[l] = make_double2(z[l].x + ed[l].x, z[l].y + ed[l].y);
+                    if (dfa) {
+#pragma unroll
+                        for (int l = 0; l < L; ++l) {
+                            zf[l].z = fadd_n(zf[l].z, e[l].x);
+                            zf[l].w = fadd_n(zf[l].w, e[l].y);
+                        }
+                    }
                 }
                 if (pass + 1 >= Rmax) break;
                 // another pass: dacc accumulates the correction; it rewrites D0, so every thread
@@ -926,7 +966,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                         // the adjoint's gradient products read the split form (products_split)
                         float4* Hs = reinterpret_cast<float4*>(H) + size_t(hpos) * hstride + fb.xo;
 #pragma unroll
-                        for (int l = 0; l < L; ++l) Hs[l] = split_scaled(z[l], sh);
+                        for (int l = 0; l < L; ++l) Hs[l] = zf_ok ? zf[l] : split_scaled(z[l], sh);
                     } else {
 #pragma unroll
                         for (int l = 0; l < L; ++l) H[size_t(hpos) * hstride + fb.xo + l] = z[l];
@@ -959,7 +999,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = 0.0;
             if constexpr (SOLVER == SOLVER_MIXED) {
-                products_split<L, Q>(z, reinterpret_cast<const float4*>(UB), fb, sh, shU, acc);
+                if (!zf_ok) {
+#pragma unroll
+                    for (int l = 0; l < L; ++l) zf[l] = split_scaled(z[l], sh);
+                }
+                products_split<L, Q>(zf, reinterpret_cast<const float4*>(UB), fb, sh + shU, acc);
             } else {
             {
                 // last subsystem (stride 1) from the fiber itself, grouped by entry l of Lbar:
@@ -1074,10 +1118,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             }
         }
 
-        // the folding warps add iteration jj - 1's reduced products into the alpha-gradient
-        // (the barrier that published red[par ^ 1] was this iteration's first one)
-        if (BWD && jj > 0 && coef_warp && jj - 1 < (cslot ? cnt_1 : cnt_0))
-            fold(cslot, par ^ 1, step_of(cslot, jj - 1), sp_prev, ph_prev, true);
         if (++hpos == hd) {
             hpos = 0;
             ++hgrp;
@@ -1101,9 +1141,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             }
         } else {
             // the last fold of every slot whose range ends at the last iteration
-            if (coef_warp && nit > 0 && (cslot ? cnt_1 : cnt_0) == nit) {
-                const int64_t np = step_of(cslot, nit - 1);
-                fold(cslot, (nit - 1) & 1, np, pd.spl[np], make_double2(0.0, 0.0), false);
+            if (fold_warp && nit > 0 && (fslot ? cnt_1 : cnt_0) == nit) {
+                const int64_t np = step_of(fslot, nit - 1);
+                fold(fslot, (nit - 1) & 1, np, pd.spl[np], make_double2(0.0, 0.0), false);
             }
             tile_sync();
             // the tile's alpha-gradient partial, accumulated over the segment launches (the first
