@@ -31,6 +31,8 @@
 //   dP/dalpha2_kfs += -2h B_s Re(e^{i W t} z_k - e^{-i W t} y_k).
 #pragma once
 
+#include <type_traits>
+
 #include "msqoc_sweep_common.cuh"
 
 namespace msqoc {
@@ -246,9 +248,20 @@ __device__ __forceinline__ void step_coefficients(const ProbDev& pd, int lane, d
     }
 }
 
+// sums of the gradient products: FP64 (FP64 solver) or two-float (mixed solver; exact two-sums
+// of the leading parts, no FP64 instruction)
+__device__ __forceinline__ double gsum_add(double a, double b) { return a + b; }
+__device__ __forceinline__ DF gsum_add(DF a, DF b) { return df_add(a, b); }
+__device__ __forceinline__ double gsum_shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ DF gsum_shfl_xor(DF v, int o) {
+    return DF{__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.c, o)};
+}
+__device__ __forceinline__ void gsum_zero(double& v) { v = 0.0; }
+__device__ __forceinline__ void gsum_zero(DF& v) { v = DF{0.f, 0.f}; }
+
 // warp reduce-scatter of V values: lane ends with value (lane >> (5 - NH)) summed over the warp
-template <int V, int NH>
-__device__ __forceinline__ double warp_reduce_scatter(double (&acc)[V], int lane) {
+template <int V, int NH, typename T>
+__device__ __forceinline__ T warp_reduce_scatter(T (&acc)[V], int lane) {
     int cnt = V;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -258,14 +271,14 @@ __device__ __forceinline__ double warp_reduce_scatter(double (&acc)[V], int lane
 #pragma unroll
             for (int q2 = 0; q2 < V / 2; ++q2) {
                 if (q2 < half) {
-                    const double send = upper ? acc[q2] : acc[q2 + half];
-                    const double keep = upper ? acc[q2 + half] : acc[q2];
-                    acc[q2] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    const T send = upper ? acc[q2] : acc[q2 + half];
+                    const T keep = upper ? acc[q2 + half] : acc[q2];
+                    acc[q2] = gsum_add(keep, gsum_shfl_xor(send, o));
                 }
             }
             cnt = half;
         } else {
-            acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+            acc[0] = gsum_add(acc[0], gsum_shfl_xor(acc[0], o));
         }
     }
     return acc[0];
@@ -342,7 +355,8 @@ __device__ __forceinline__ void cjmac_split(DF& R, DF& I, const float4& x, const
 // B_k = Re z_k - Re y_k with z_k = <Lbar, a_k Ubar>, y_k = <Lbar, a_k^+ Ubar>.  Lbar comes split
 // into two floats (zs, in units of its column's scale 2^shL), the midpoint states Ubar split by
 // the forward sweep (ub, scale 2^shU).  Each value is a compensated FP32 sum (about 2^-47 times
-// its terms' magnitudes), one FP64 add to finish, scaled back by 2^S, S = shL + shU.
+// its terms' magnitudes) in units 2^(shL + shU), multiplied by pscale (a power of two) into the
+// tile's common units.
 //   last subsystem, weight class j = 1 .. L-1 (weight sqrt j): the pairs (Lbar_{j-1}, Ubar_j)
 //     (a_k, real part +) and (Lbar_j, Ubar_{j-1}) (a_k^+, real part -);
 //   other subsystems: entry 1 of the neighbour list (weight sqrt(l_k + 1) for a_k, real part +;
@@ -350,7 +364,7 @@ __device__ __forceinline__ void cjmac_split(DF& R, DF& I, const float4& x, const
 //     (a_k^+, weight sqrt(l_k), real part -).
 template <int L, int Q>
 __device__ __forceinline__ void products_split(const float4 (&zs)[L], const float4* __restrict__ ub,
-                                               const Fiber<L, Q>& fb, int S, double* acc) {
+                                               const Fiber<L, Q>& fb, float pscale, DF* acc) {
     {
         constexpr int kl = Q - 1;
         DF A{0.f, 0.f}, B{0.f, 0.f};
@@ -367,8 +381,8 @@ __device__ __forceinline__ void products_split(const float4 (&zs)[L], const floa
                 B = df_add(B, df_scale_sqrt(R, j));
             }
         }
-        acc[2 * kl + 0] = df_to_f64_scaled(A, S);
-        acc[2 * kl + 1] = df_to_f64_scaled(B, S);
+        acc[2 * kl + 0] = DF{fmul_n(A.s, pscale), fmul_n(A.c, pscale)};
+        acc[2 * kl + 1] = DF{fmul_n(B.s, pscale), fmul_n(B.c, pscale)};
     }
 #pragma unroll
     for (int k = 0; k < Fiber<L, Q>::NFIX; ++k) {
@@ -389,8 +403,8 @@ __device__ __forceinline__ void products_split(const float4 (&zs)[L], const floa
             A = df_add(A, df_scale_sqrt(I2, lk));
             B = df_add(B, df_scale_sqrt(R2, lk));
         }
-        acc[2 * k + 0] = df_to_f64_scaled(A, S);
-        acc[2 * k + 1] = df_to_f64_scaled(B, S);
+        acc[2 * k + 0] = DF{fmul_n(A.s, pscale), fmul_n(A.c, pscale)};
+        acc[2 * k + 1] = DF{fmul_n(B.s, pscale), fmul_n(B.c, pscale)};
     }
 }
 
@@ -430,6 +444,49 @@ static __device__ __noinline__ void fold_step(const ProbDev& pd, const double* r
     }
 }
 
+// The mixed solver's fold (the same sums as fold_step): the partial sums and zy are two-float
+// sums in units of 2^S (the tile's product scale, see the adjoint), the phase and spline weight
+// are split on the fly, and each step's contribution enters the slot's FP64 gradient ga with one
+// FP64 add and one FMA per component (a window's ~hundreds of steps accumulate in FP64).
+__device__ __forceinline__ void df_mac_full(DF& a, float xh, float xl, float yh, float yl) {
+    df_mac(a, xh, xl, yh, yl);
+    a.c = ffma_n(xl, yl, a.c);   // the low parts' product too: y may be a sum that cancelled
+}
+template <int Q, int V>
+static __device__ __noinline__ void fold_step_df(const ProbDev& pd, const DF* red, DF* zy, double* ga, int nwarps,
+                                                 int64_t np, Spline4 sp, double2 ph_lane, bool prefetched, int s0,
+                                                 int S, int lane) {
+    if (lane < 2 * Q) {
+        const DF* r = red + lane;
+        DF s_even{0.f, 0.f}, s_odd{0.f, 0.f};
+        for (int w2 = 0; w2 < nwarps; w2 += 2) {
+            s_even = df_add(s_even, r[w2 * V]);
+            if (w2 + 1 < nwarps) s_odd = df_add(s_odd, r[(w2 + 1) * V]);
+        }
+        zy[lane] = df_add(s_even, s_odd);
+    }
+    __syncwarp();
+    const int nscat = pd.nfsum * 3;
+    for (int i = lane; i < nscat; i += 32) {
+        const int kf = i / 3, jw = i % 3;
+        int k = 0;
+        while (k + 1 < Q && pd.cof[k + 1] <= kf) ++k;
+        const double2 ph = (prefetched && i == lane) ? ph_lane : pd.phase[size_t(np) * pd.nfsum + kf];
+        const float2 px = split_scaled(ph.x, 0), py = split_scaled(ph.y, 0);
+        const float2 wg = split_scaled(jw == 0 ? sp.w0 : (jw == 1 ? sp.w1 : sp.w2), 0);
+        const DF A = zy[2 * k], B = zy[2 * k + 1];
+        DF t1{0.f, 0.f}, t2{0.f, 0.f};
+        df_mac_full(t1, px.x, px.y, A.s, A.c);
+        df_mac_full(t1, py.x, py.y, B.s, B.c);
+        df_mac_full(t2, px.x, px.y, B.s, B.c);
+        df_mac_full(t2, -py.x, -py.y, A.s, A.c);
+        const double m2h = -2.0 * pd.h;
+        double* g = ga + (kf * pd.gspan + s0 + jw) * 2;
+        g[0] = fma(m2h, df_to_f64_scaled(df_scale(t1, wg.x, wg.y), S), g[0]);
+        g[1] = fma(m2h, df_to_f64_scaled(df_scale(t2, wg.x, wg.y), S), g[1]);
+    }
+}
+
 // ------------------------------------------------------------------ the sweep kernel
 // One CTA per tile.  A tile covers one or two windows ("slots"); each slot has its own step
 // range, per-step coefficients and iteration counts, computed by warp `slot`, and gradient fold,
@@ -458,8 +515,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
     float4* coef_s = SOLVER == SOLVER_MIXED ? reinterpret_cast<float4*>(smem + lay.coef_s) : nullptr;
     int* params = reinterpret_cast<int*>(smem + lay.params);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + lay.mbar);
-    double* red = reinterpret_cast<double*>(smem + lay.red);
-    double* zy = reinterpret_cast<double*>(smem + lay.zy);
+    // sums of the gradient products: two-float (mixed solver, in units 2^S_tile) or FP64; the
+    // tile's window gradients are FP64
+    using GT = std::conditional_t<SOLVER == SOLVER_MIXED, DF, double>;
+    GT* red = reinterpret_cast<GT*>(smem + lay.red);
+    GT* zy = reinterpret_cast<GT*>(smem + lay.zy);
     double* galpha = reinterpret_cast<double*>(smem + lay.galpha);
     double2* D0 = reinterpret_cast<double2*>(smem + lay.D0);
     double2* D1 = reinterpret_cast<double2*>(smem + lay.D1);
@@ -595,11 +655,22 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
     const int hseg = a.mode == SWEEP_HISTORY ? 0 : a.seg;
     int* const hsh_col = pd.hsh + (size_t(m - 1) * pd.nseg + hseg) * E + col;
     int shU = 0;
+    // adjoint, mixed solver: the gradient products of column c are in units 2^(sh + shU); the
+    // tile sums them in units 2^S_tile, the largest over its columns (pscale = 2^(sh + shU -
+    // S_tile) <= 1, set after the barrier below)
+    __shared__ int stile_s;
+    int S_tile = 0;
+    float pscale = 1.f;
     if constexpr (SOLVER == SOLVER_MIXED) {
         if (!BWD && ((a.mode == SWEEP_HISTORY && pd.nseg == 1) || a.mode == SWEEP_RECOMPUTE) && act && f == 0 &&
             my_cnt > 0)
             *hsh_col = sh;
-        if (BWD && my_cnt > 0) shU = *hsh_col;
+        if (BWD) {
+            if (tid == 0) stile_s = -(1 << 20);
+            tile_sync();
+            if (my_cnt > 0) shU = *hsh_col;
+            if (act && my_cnt > 0) atomicMax(&stile_s, sh + shU);
+        }
     }
 
     // ---- history blocks: slot s of a tile covers a contiguous column range of its window
@@ -650,6 +721,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
         }
         tile_sync();
         if (tid == 0 && nit > 0) fetch_group(UB0, 0, &mbar[0]);
+        if constexpr (SOLVER == SOLVER_MIXED) {
+            S_tile = stile_s > -(1 << 20) ? stile_s : 0;
+            const int k = sh + shU - S_tile;   // <= 0
+            pscale = k >= -126 ? float_of(static_cast<uint32_t>(127 + k) << 23)
+                               : (k >= -149 ? float_of(1u << (k + 149)) : 0.f);
+        }
     }
 
     // warp s < nslot computes slot s's coefficients and keeps d_k and the iteration counts of
@@ -687,9 +764,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             __syncwarp();
             return;
         }
-        fold_step<Q, V>(pd, red + ((pp * 2 + s) * nwarps) * V, zy + (pp * 2 + s) * 4 * Q,
-                        galpha + size_t(s) * a.gmax, nwarps, np, sp, ph_lane, prefetched,
-                        sp.s - (s ? slo_1 : slo_0), lane);
+        if constexpr (SOLVER == SOLVER_MIXED)
+            fold_step_df<Q, V>(pd, red + ((pp * 2 + s) * nwarps) * V, zy + (pp * 2 + s) * 4 * Q,
+                               galpha + size_t(s) * a.gmax, nwarps, np, sp, ph_lane, prefetched,
+                               sp.s - (s ? slo_1 : slo_0), S_tile, lane);
+        else
+            fold_step<Q, V>(pd, red + ((pp * 2 + s) * nwarps) * V, zy + (pp * 2 + s) * 4 * Q,
+                            galpha + size_t(s) * a.gmax, nwarps, np, sp, ph_lane, prefetched,
+                            sp.s - (s ? slo_1 : slo_0), lane);
     };
 
     __shared__ int tflag_s;   // a bounded history wait gave up (adjoint)
@@ -995,15 +1077,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             // a wait that gives up raises the tile's flag, read after the next barrier (the
             // products below then use whatever landed; the evaluation reports the timeout)
             if (hpos == 0 && !mbar_wait(&mbar[hgrp & 1], (hgrp >> 1) & 1)) *tflag = 1;
-            double acc[V];
+            GT acc[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = 0.0;
+            for (int v = 0; v < V; ++v) gsum_zero(acc[v]);
             if constexpr (SOLVER == SOLVER_MIXED) {
                 if (!zf_ok) {
 #pragma unroll
                     for (int l = 0; l < L; ++l) zf[l] = split_scaled(z[l], sh);
                 }
-                products_split<L, Q>(zf, reinterpret_cast<const float4*>(UB), fb, sh + shU, acc);
+                products_split<L, Q>(zf, reinterpret_cast<const float4*>(UB), fb, pscale, acc);
             } else {
             {
                 // last subsystem (stride 1) from the fiber itself, grouped by entry l of Lbar:
@@ -1082,32 +1164,34 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             }   // FP64 products
             if (!act || !live) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = 0.0;
+                for (int v = 0; v < V; ++v) gsum_zero(acc[v]);
             }
             // per-slot warp sums: lane (lane >> (5 - NH)) == v holds value v
             {
                 const int vi = lane >> (5 - NH);
                 const bool writer = (lane & ((1 << (5 - NH)) - 1)) == 0;
-                double* r0 = red + ((par * 2 + 0) * nwarps + warp) * V;
-                double* r1 = red + ((par * 2 + 1) * nwarps + warp) * V;
+                GT* r0 = red + ((par * 2 + 0) * nwarps + warp) * V;
+                GT* r1 = red + ((par * 2 + 1) * nwarps + warp) * V;
+                GT zero;
+                gsum_zero(zero);
                 if (mask0 && mask1) {
                     // lanes of both windows: reduce the window-1 lanes on a copy first
-                    double t[V];
+                    GT t[V];
 #pragma unroll
-                    for (int v = 0; v < V; ++v) t[v] = slot == 1 ? acc[v] : 0.0;
-                    const double s1 = warp_reduce_scatter<V, NH>(t, lane);
+                    for (int v = 0; v < V; ++v) t[v] = slot == 1 ? acc[v] : zero;
+                    const GT s1 = warp_reduce_scatter<V, NH>(t, lane);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) acc[v] = slot == 0 ? acc[v] : 0.0;
-                    const double s0 = warp_reduce_scatter<V, NH>(acc, lane);
+                    for (int v = 0; v < V; ++v) acc[v] = slot == 0 ? acc[v] : zero;
+                    const GT s0 = warp_reduce_scatter<V, NH>(acc, lane);
                     if (writer) {
                         r0[vi] = s0;
                         r1[vi] = s1;
                     }
                 } else {
-                    const double sv = warp_reduce_scatter<V, NH>(acc, lane);
+                    const GT sv = warp_reduce_scatter<V, NH>(acc, lane);
                     if (writer) {
-                        r0[vi] = mask1 ? 0.0 : sv;
-                        if (nslot > 1) r1[vi] = mask1 ? sv : 0.0;
+                        r0[vi] = mask1 ? zero : sv;
+                        if (nslot > 1) r1[vi] = mask1 ? sv : zero;
                     }
                 }
             }
