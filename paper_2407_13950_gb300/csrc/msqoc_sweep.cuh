@@ -105,6 +105,12 @@ __device__ __forceinline__ double2 resid_from(double2 d, double2 c, double2 w) {
 __device__ __forceinline__ double2 reflect(double2 z, double2 u) {
     return make_double2(fma(2.0, z.x, -u.x), fma(2.0, z.y, -u.y));
 }
+// the mixed solver's 2 z - u for z = P u + d: R u + 2 d with R = 2P - 1 (FP64; d a two-float
+// sum in units 2^-sh, doubled exactly through the scale): three FP64 instructions a component
+__device__ __forceinline__ double2 cayley_update(double2 R, double2 u, DF dre, DF dim, int sh) {
+    const double tx = df_to_f64_scaled(dre, sh + 1), ty = df_to_f64_scaled(dim, sh + 1);
+    return make_double2(fma(R.x, u.x, fma(-R.y, u.y, tx)), fma(R.x, u.y, fma(R.y, u.x, ty)));
+}
 
 // Dipole exchange on the fiber (fiber index f, entries at fb.xo of a [cols][N] buffer):
 // w += i (h/2) J_jk (a_k^+ a_j + a_k a_j^+) x for every coupled pair j < k.  a_k^+ a_j moves one
@@ -603,14 +609,16 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
     // preconditioner on the fiber: P (forward) or conj(P) (adjoint)
     double2 Pd[L];
     float2 Pf[L];
-    float4 Ps[L];   // split (mixed solver's compensated residual)
+    float4 Ps[L];   // split (mixed solver's right-hand side and compensated residual)
+    double2 Rd[L];  // R = 2P - 1, the Cayley factor of the diagonal part (mixed solver's state update)
 #pragma unroll
     for (int l = 0; l < L; ++l) {
         double2 p = pd.P[f * L + l];
         if (BWD) p.y = -p.y;
         Pd[l] = p;
-        Pf[l] = f32_of(p);
         Ps[l] = split_scaled(p, 0);
+        Pf[l] = make_float2(Ps[l].x, Ps[l].y);   // p rounded to FP32
+        Rd[l] = make_double2(fma(2.0, p.x, -1.0), 2.0 * p.y);
     }
 
     // ---- initial state
@@ -819,17 +827,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
         const int* prm0 = params + (par * 2) * 4;
         const int* prm1 = params + (par * 2 + 1) * 4;
 
-        // right-hand side of the preconditioned step equation: b = P u (conj(P) for the adjoint)
-        double2 b[L];
-#pragma unroll
-        for (int l = 0; l < L; ++l) b[l] = cmul(Pd[l], u[l]);
-
-        double2 z[L];   // the midpoint state being solved for (Ubar or Lbar)
-        // the final z split into two floats in the column's scaled units (zf_ok): the split of
-        // the refinement's last pass plus its FP32 correction, exact to 2^-48 |z|; used by the
-        // forward's history and the adjoint's gradient products instead of a split of z
+        // the midpoint state being solved for (Ubar or Lbar): FP64 (FP64 solver) or, for the
+        // mixed solver, the two-float sum zf = b + d_total in the column's scaled units (about
+        // 2^-47 |z|), which the forward's history and the adjoint's gradient products use; the
+        // mixed solver's state update needs only the correction d_total (dre, dim: two-float)
+        double2 z[L];
         float4 zf[L];
-        bool zf_ok = false;
+        DF dre[L], dim[L];
 
         // first barrier of the step: the coefficients are published; thread 0 stores the
         // previous iteration's midpoints (forward) or fetches the next iteration's (adjoint)
@@ -854,6 +858,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
         };
 
         if constexpr (SOLVER == SOLVER_FP64) {
+            // right-hand side of the preconditioned step equation: b = P u (conj(P) for the adjoint)
+            double2 b[L];
+#pragma unroll
+            for (int l = 0; l < L; ++l) b[l] = cmul(Pd[l], u[l]);
             // Dc/Dn alternate on every write (persisting across steps): a buffer is never
             // rewritten before the sync that follows its last read.
 #pragma unroll
@@ -887,11 +895,27 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 Dn = tmp;
             }
         } else {
+            // ---- b = P u (conj(P) for the adjoint) as a two-float sum in the column's scaled
+            // units: the FP32 stage's right-hand side and the point at which the refinement
+            // evaluates the off-diagonal apply.  The residual below is that of the exact P u
+            // (it is formed as s P w(z) - d_total), and the state update uses R u = (2P - 1) u in
+            // FP64, so b's 2^-47 error enters only the evaluation point of a term of size rho.
+            DF bre[L], bim[L];
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                const float4 us = split_scaled(u[l], sh);
+                bre[l] = DF{0.f, 0.f};
+                bim[l] = DF{0.f, 0.f};
+                df_mac(bre[l], Ps[l].x, Ps[l].z, us.x, us.z);
+                df_mac(bre[l], -Ps[l].y, -Ps[l].w, us.y, us.w);
+                df_mac(bim[l], Ps[l].x, Ps[l].z, us.y, us.w);
+                df_mac(bim[l], Ps[l].y, Ps[l].w, us.x, us.z);
+            }
             // ---- FP32 stage: d = Ubar - b from the preconditioned fixed point d = s P w(b + d)
             float2 bf[L], df[L], y[L];
 #pragma unroll
             for (int l = 0; l < L; ++l) {
-                bf[l] = f32_of_scaled(b[l], cs);
+                bf[l] = make_float2(fadd_n(bre[l].s, bre[l].c), fadd_n(bim[l].s, bim[l].c));
                 y[l] = bf[l];
             }
             {
@@ -931,34 +955,39 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                     for (int l = 0; l < L; ++l) df[l] = cadd_scaled<S>(make_float2(0.f, 0.f), Pf[l], w[l]);
                 }
             }
-            // ---- FP64 refinement: z = b + d, residual r = (b - z) + s P w(z), correction in FP32.
-            // dacc accumulates z - b (= d, then d + e, ...); b - z = -dacc up to the rounding of z.
-            double2 dacc[L];
+            // ---- refinement: z = b + d_total, residual r = s P w(z) - d_total (that of the exact
+            // P u), an FP32 correction e added to d_total (two-float, scaled units)
 #pragma unroll
             for (int l = 0; l < L; ++l) {
-                dacc[l] = f64_of_scaled(df[l], cs);
-                z[l] = make_double2(b[l].x + dacc[l].x, b[l].y + dacc[l].y);
+                dre[l] = DF{df[l].x, 0.f};
+                dim[l] = DF{df[l].y, 0.f};
             }
             // the residual's apply in compensated FP32 (split entries in D0) where the step's
-            // contraction factor allows it (step_counts) and the problem has no exchange terms;
-            // uniform over a slot, so a column's entries in D0 have one form
+            // contraction factor allows it (step_counts) and the problem has no exchange terms,
+            // else in FP64; uniform over a slot, so a column's entries in D0 have one form
             const bool dfa = pd.nex == 0 && !(prm[3] & 2);
             float4* D0s = reinterpret_cast<float4*>(D0);
             for (int pass = 0;; ++pass) {
                 float4 zs[L];
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    const DF zr = df_add(bre[l], dre[l]), zi = df_add(bim[l], dim[l]);
+                    zs[l] = make_float4(zr.s, zi.s, zr.c, zi.c);
+                }
                 if (dfa) {
-#pragma unroll
-                    for (int l = 0; l < L; ++l) zs[l] = split_scaled(z[l], sh);
-#pragma unroll
-                    for (int l = 0; l < L; ++l) zf[l] = zs[l];
-                    zf_ok = true;
                     if (act) {
 #pragma unroll
                         for (int l = 0; l < L; ++l) D0s[fb.xo + l] = zs[l];
                     }
-                } else if (act) {
+                } else {
 #pragma unroll
-                    for (int l = 0; l < L; ++l) D0[fb.xo + l] = z[l];
+                    for (int l = 0; l < L; ++l)
+                        z[l] = make_double2(df_to_f64_scaled(DF{zs[l].x, zs[l].z}, sh),
+                                            df_to_f64_scaled(DF{zs[l].y, zs[l].w}, sh));
+                    if (act) {
+#pragma unroll
+                        for (int l = 0; l < L; ++l) D0[fb.xo + l] = z[l];
+                    }
                 }
                 // forward: the staged midpoints of the previous step must have been read by their
                 // bulk store (issued at this step's first barrier) before this step's are staged;
@@ -971,14 +1000,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                     apply_off_df<L, Q>(D0s, cfs, fb, zs, w);
 #pragma unroll
                     for (int l = 0; l < L; ++l) {
-                        // d in scaled units: the FP32 stage's value in the first pass, then split
-                        float2 dh = df[l], dl = make_float2(0.f, 0.f);
-                        if (pass > 0) {
-                            const float4 ds = split_scaled(dacc[l], sh);
-                            dh = make_float2(ds.x, ds.y);
-                            dl = make_float2(ds.z, ds.w);
-                        }
-                        rf[l] = resid_df<S>(dh, dl, Ps[l], w[l]);
+                        rf[l] = resid_df<S>(make_float2(dre[l].s, dim[l].s), make_float2(dre[l].c, dim[l].c), Ps[l],
+                                            w[l]);
                         e[l] = rf[l];
                     }
                 } else {
@@ -986,7 +1009,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                     apply_off<L, Q, double2>(D0, cfd, fb, z, w, pd);
 #pragma unroll
                     for (int l = 0; l < L; ++l) {
-                        const double2 r = resid_from<S>(dacc[l], Pd[l], w[l]);
+                        double2 p = pd.P[f * L + l];
+                        if (BWD) p.y = -p.y;
+                        const double2 dacc = make_double2(df_to_f64_scaled(dre[l], sh), df_to_f64_scaled(dim[l], sh));
+                        const double2 r = resid_from<S>(dacc, p, w[l]);
                         rf[l] = f32_of_scaled(r, cs);
                         e[l] = rf[l];
                     }
@@ -1006,31 +1032,23 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                         for (int l = 0; l < L; ++l) e[l] = cadd_scaled<S>(rf[l], Pf[l], wf[l]);
                     }
                 }
-                double2 ed[L];
-#pragma unroll
-                for (int l = 0; l < L; ++l) ed[l] = f64_of_scaled(e[l], cs);
                 if (pass < R) {
 #pragma unroll
-                    for (int l = 0; l < L; ++l) z[l] = make_double2(z[l].x + ed[l].x, z[l].y + ed[l].y);
-                    if (dfa) {
-#pragma unroll
-                        for (int l = 0; l < L; ++l) {
-                            zf[l].z = fadd_n(zf[l].z, e[l].x);
-                            zf[l].w = fadd_n(zf[l].w, e[l].y);
-                        }
+                    for (int l = 0; l < L; ++l) {
+                        dre[l] = df_add(dre[l], DF{e[l].x, 0.f});
+                        dim[l] = df_add(dim[l], DF{e[l].y, 0.f});
                     }
                 }
                 if (pass + 1 >= Rmax) break;
-                // another pass: dacc accumulates the correction; it rewrites D0, so every thread
-                // must be done reading it
-                if (pass + 1 < R) {
-#pragma unroll
-                    for (int l = 0; l < L; ++l) dacc[l] = make_double2(dacc[l].x + ed[l].x, dacc[l].y + ed[l].y);
-                }
+                // another pass rewrites D0: every thread must be done reading it
                 tile_sync();
             }
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                const DF zr = df_add(bre[l], dre[l]), zi = df_add(bim[l], dim[l]);
+                zf[l] = make_float4(zr.s, zi.s, zr.c, zi.c);
+            }
         }
-
         if (tid == 0 && ((prm0[3] & 1) || (nslot > 1 && (prm1[3] & 1)))) atomicOr(pd.status, ST_SOLVER_RANGE);
 
         if constexpr (!BWD) {
@@ -1048,7 +1066,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                         // the adjoint's gradient products read the split form (products_split)
                         float4* Hs = reinterpret_cast<float4*>(H) + size_t(hpos) * hstride + fb.xo;
 #pragma unroll
-                        for (int l = 0; l < L; ++l) Hs[l] = zf_ok ? zf[l] : split_scaled(z[l], sh);
+                        for (int l = 0; l < L; ++l) Hs[l] = zf[l];
                     } else {
 #pragma unroll
                         for (int l = 0; l < L; ++l) H[size_t(hpos) * hstride + fb.xo + l] = z[l];
@@ -1058,7 +1076,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             }
             if (live) {
 #pragma unroll
-                for (int l = 0; l < L; ++l) u[l] = reflect(z[l], u[l]);
+                for (int l = 0; l < L; ++l) u[l] = SOLVER == SOLVER_MIXED ? cayley_update(Rd[l], u[l], dre[l], dim[l], sh) : reflect(z[l], u[l]);
             }
             // roll-out: U(t_m) when the step ends on a window boundary t_m, i.e. when n + 1 =
             // floor(m N_T / M) for some 1 <= m < M; the only candidate is m = ceil((n+1) M / N_T)
@@ -1081,10 +1099,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
 #pragma unroll
             for (int v = 0; v < V; ++v) gsum_zero(acc[v]);
             if constexpr (SOLVER == SOLVER_MIXED) {
-                if (!zf_ok) {
-#pragma unroll
-                    for (int l = 0; l < L; ++l) zf[l] = split_scaled(z[l], sh);
-                }
                 products_split<L, Q>(zf, reinterpret_cast<const float4*>(UB), fb, pscale, acc);
             } else {
             {
@@ -1198,7 +1212,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             // Lambda_n = 2 Lbar - Lambda_{n+1}
             if (live) {
 #pragma unroll
-                for (int l = 0; l < L; ++l) u[l] = reflect(z[l], u[l]);
+                for (int l = 0; l < L; ++l) u[l] = SOLVER == SOLVER_MIXED ? cayley_update(Rd[l], u[l], dre[l], dim[l], sh) : reflect(z[l], u[l]);
             }
         }
 
