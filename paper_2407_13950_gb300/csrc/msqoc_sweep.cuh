@@ -452,16 +452,17 @@ static __device__ __noinline__ void fold_step(const ProbDev& pd, const double* r
 
 // The mixed solver's fold (the same sums as fold_step): the partial sums and zy are two-float
 // sums in units of 2^S (the tile's product scale, see the adjoint), the phase and spline weight
-// are split on the fly, and each step's contribution enters the slot's FP64 gradient ga with one
-// FP64 add and one FMA per component (a window's ~hundreds of steps accumulate in FP64).
+// are split on the fly, and each step's contribution goes into a two-float copy gdf of the
+// slot's gradient, which is added into the FP64 gradient ga every FOLD_FLUSH steps (flush: one
+// FP64 add and FMA per element), so a window's hundreds of steps still accumulate in FP64.
 __device__ __forceinline__ void df_mac_full(DF& a, float xh, float xl, float yh, float yl) {
     df_mac(a, xh, xl, yh, yl);
     a.c = ffma_n(xl, yl, a.c);   // the low parts' product too: y may be a sum that cancelled
 }
 template <int Q, int V>
-static __device__ __noinline__ void fold_step_df(const ProbDev& pd, const DF* red, DF* zy, double* ga, int nwarps,
-                                                 int64_t np, Spline4 sp, double2 ph_lane, bool prefetched, int s0,
-                                                 int S, int lane) {
+static __device__ __noinline__ void fold_step_df(const ProbDev& pd, const DF* red, DF* zy, double* ga, DF* gdf,
+                                                 int gmax, int nwarps, int64_t np, Spline4 sp, double2 ph_lane,
+                                                 bool prefetched, int s0, int S, bool flush, int lane) {
     if (lane < 2 * Q) {
         const DF* r = red + lane;
         DF s_even{0.f, 0.f}, s_odd{0.f, 0.f};
@@ -486,10 +487,20 @@ static __device__ __noinline__ void fold_step_df(const ProbDev& pd, const DF* re
         df_mac_full(t1, py.x, py.y, B.s, B.c);
         df_mac_full(t2, px.x, px.y, B.s, B.c);
         df_mac_full(t2, -py.x, -py.y, A.s, A.c);
+        DF* g = gdf + (kf * pd.gspan + s0 + jw) * 2;
+        g[0] = df_add(g[0], df_scale(t1, wg.x, wg.y));
+        g[1] = df_add(g[1], df_scale(t2, wg.x, wg.y));
+    }
+    if (flush) {
+        __syncwarp();
         const double m2h = -2.0 * pd.h;
-        double* g = ga + (kf * pd.gspan + s0 + jw) * 2;
-        g[0] = fma(m2h, df_to_f64_scaled(df_scale(t1, wg.x, wg.y), S), g[0]);
-        g[1] = fma(m2h, df_to_f64_scaled(df_scale(t2, wg.x, wg.y), S), g[1]);
+        for (int e = lane; e < gmax; e += 32) {
+            const DF v = gdf[e];
+            if (v.s != 0.f || v.c != 0.f) {
+                ga[e] = fma(m2h, df_to_f64_scaled(v, S), ga[e]);
+                gdf[e] = DF{0.f, 0.f};
+            }
+        }
     }
 }
 
@@ -527,6 +538,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
     GT* red = reinterpret_cast<GT*>(smem + lay.red);
     GT* zy = reinterpret_cast<GT*>(smem + lay.zy);
     double* galpha = reinterpret_cast<double*>(smem + lay.galpha);
+    DF* gdf = reinterpret_cast<DF*>(smem + lay.gdf);   // two-float gradient terms (mixed solver)
     double2* D0 = reinterpret_cast<double2*>(smem + lay.D0);
     double2* D1 = reinterpret_cast<double2*>(smem + lay.D1);
     float2* FA = reinterpret_cast<float2*>(smem + lay.FA);
@@ -722,6 +734,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
 
     if (BWD) {
         for (int j = tid; j < 2 * a.gmax; j += blockDim.x) galpha[j] = 0.0;
+        if constexpr (SOLVER == SOLVER_MIXED)
+            for (int j = tid; j < 2 * a.gmax; j += blockDim.x) gdf[j] = DF{0.f, 0.f};
         if (tid == 0) {
             mbar_init(&mbar[0], 1);
             mbar_init(&mbar[1], 1);
@@ -766,7 +780,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
     // dP/dalpha2_kfs += -2h B_s Re(e^{iWt} z_k - e^{-iWt} y_k)  (Eq. grad-int at the midpoint),
     // i.e. with (A, B) = (Im z + Im y, Re z - Re y) and the phase p: -2h B_s (p.x A + p.y B) and
     // -2h B_s (p.x B - p.y A)
-    auto fold = [&](int s, int pp, int64_t np, const Spline4& sp, double2 ph_lane, bool prefetched) {
+    auto fold = [&](int s, int pp, int64_t np, const Spline4& sp, double2 ph_lane, bool prefetched, bool flush) {
         if (!grad_fits) {
             // the sums are not needed; keep the warp's lanes together as fold_step would
             __syncwarp();
@@ -774,8 +788,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
         }
         if constexpr (SOLVER == SOLVER_MIXED)
             fold_step_df<Q, V>(pd, red + ((pp * 2 + s) * nwarps) * V, zy + (pp * 2 + s) * 4 * Q,
-                               galpha + size_t(s) * a.gmax, nwarps, np, sp, ph_lane, prefetched,
-                               sp.s - (s ? slo_1 : slo_0), S_tile, lane);
+                               galpha + size_t(s) * a.gmax, gdf + size_t(s) * a.gmax, a.gmax, nwarps, np, sp,
+                               ph_lane, prefetched, sp.s - (s ? slo_1 : slo_0), S_tile, flush, lane);
         else
             fold_step<Q, V>(pd, red + ((pp * 2 + s) * nwarps) * V, zy + (pp * 2 + s) * 4 * Q,
                             galpha + size_t(s) * a.gmax, nwarps, np, sp, ph_lane, prefetched,
@@ -843,7 +857,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
         // every warp issues at the ends of a step
         auto fold_previous = [&]() {
             if (BWD && jj > 0 && fold_warp && jj - 1 < (fslot ? cnt_1 : cnt_0))
-                fold(fslot, par ^ 1, step_of(fslot, jj - 1), sp_prev, ph_prev, true);
+                fold(fslot, par ^ 1, step_of(fslot, jj - 1), sp_prev, ph_prev, true,
+                     ((jj - 1) & (FOLD_FLUSH - 1)) == FOLD_FLUSH - 1 || jj == (fslot ? cnt_1 : cnt_0));
         };
         auto first_sync_work = [&]() {
             if (BWD && *tflag) timed_out = true;   // uniform: read after a barrier
@@ -1241,7 +1256,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             // the last fold of every slot whose range ends at the last iteration
             if (fold_warp && nit > 0 && (fslot ? cnt_1 : cnt_0) == nit) {
                 const int64_t np = step_of(fslot, nit - 1);
-                fold(fslot, (nit - 1) & 1, np, pd.spl[np], make_double2(0.0, 0.0), false);
+                fold(fslot, (nit - 1) & 1, np, pd.spl[np], make_double2(0.0, 0.0), false, true);
             }
             tile_sync();
             // the tile's alpha-gradient partial, accumulated over the segment launches (the first

@@ -268,8 +268,10 @@ struct Fiber {
 // keep each coefficient in the form of either part, so their coefficient arrays are twice as
 // large.
 struct SweepSmem {
-    size_t coef_d, coef_f, coef_s, params, mbar, red, zy, galpha, D0, D1, FA, FB, H, UB0, UB1, total;
+    size_t coef_d, coef_f, coef_s, params, mbar, red, zy, galpha, gdf, D0, D1, FA, FB, H, UB0, UB1, total;
 };
+// steps between flushes of the mixed solver's two-float gradient accumulator into the FP64 one
+constexpr int FOLD_FLUSH = 8;
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -295,6 +297,8 @@ __host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cpt, 
     s.red = o;    o = align16(o + (bwd ? size_t(2) * 2 * nwarps * V * 8 : 0));   // [parity][slot][warp][V]
     s.zy = o;     o = align16(o + (bwd ? size_t(2) * 2 * 4 * q * 8 : 0));        // [parity][slot][4q]
     s.galpha = o; o = align16(o + (bwd ? size_t(2) * gmax * 8 : 0));             // [slot][nfsum][gspan][2]
+    // the mixed solver's one-thread families: the same, two-float, holding the last steps' terms
+    s.gdf = o;    o = align16(o + (bwd && !pair && solver == SOLVER_MIXED ? size_t(2) * gmax * 8 : 0));
     s.D0 = o;     o = align16(o + buf_d);
     s.D1 = o;     o = align16(o + (solver == SOLVER_FP64 ? buf_d : 0));
     s.FA = o;     o = align16(o + (solver == SOLVER_MIXED ? buf_f : 0));
