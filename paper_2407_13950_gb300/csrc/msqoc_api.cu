@@ -239,15 +239,14 @@ bool quad_admitted(const ProbDev& pd) { return pd.L == 2 && pd.nex <= MAXEXF; }
 // fixed_cpt > 0 restricts the width, layout (MSQOC_LAYOUT_*) the family; quad_ok: the problem
 // admits lane quads.  cpt = -1: none fits.
 constexpr double QUAD_C = 0.38, QUAD_C0 = 0.52;
-// the one-thread family with 168 registers a thread: an SM holds 12 warps.  Two or more of its
-// tiles on an SM fall out of step (each has its own barriers), so one tile's FP32 sweeps and
-// barrier waits overlap another's FP64 work: measured on the 4-transmon tiles, 7-column tiles
-// two to an SM 7% faster at 256 windows and 13% at 128 than the 255-register build's best
-// tiles, while one 14-column tile of 12 warps per SM gains only what its warp count predicts;
-// a warp of two or more co-resident lean tiles of four or more warps counts 0.9 (narrower tiles
-// pay their per-tile coefficient and gradient work once per warp or two, as one-warp tiles of
-// the 255-register build measured)
-constexpr double LEAN_C = 0.9;
+// the one-thread family with 168 registers a thread: an SM holds 12 warps.  While the sweeps
+// were bound by the FP64 pipe, two or more of its tiles on an SM did better than their warp
+// count (each has its own barriers, so one tile's FP32 sweeps overlapped another's FP64 work)
+// and a warp of such tiles counted 0.9.  With the mixed solver's compensated FP32 arithmetic
+// the sweeps are bound by issue and dependency latency instead, and on the 4-transmon tiles one
+// 14-column tile of 12 warps per SM steps 5% faster than two 7-column tiles (autotuner probes at
+// 256 windows: 2.78 against 2.93 ms), so the lean build's warps count like any others
+constexpr double LEAN_C = 1.0;
 TileChoice choose_tile_layout(int M, int E, int F, int q, int L, int N, int g, int solver, int sms, int fixed_cpt,
                               int layout, bool quad_ok) {
     TileChoice best{-1, 0, 0};

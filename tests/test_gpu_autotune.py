@@ -43,13 +43,14 @@ def test_autotune_tries_lane_quads_on_two_levels():
 
 
 def test_tile_model_picks_the_measured_fastest_tiles_of_the_benchmark_workload():
-    # 4 transmons at 256 and 128 windows: 7-column tiles of the 168-register build, two to an SM
-    # (12 warps), measured fastest (32.2 and 31.2 evaluations/s against 29.9 and 27.7 with the
-    # 255-register build's best tiles); at 64 windows (1024 columns, too few tiles for two an
-    # SM) 8-column tiles of the 255-register build (128 CTAs)
+    # 4 transmons at 256 and 128 windows: 14-column tiles of the 168-register build, one of 12
+    # warps to an SM, the autotuner's choice (probes at 256 windows: 2.78 ms against 2.93 for two
+    # 7-column tiles an SM and 3.17 for the 255-register build's best, 9 columns); at 64 windows
+    # (1024 columns, half the SMs for 14-column tiles) 8-column tiles of the 255-register build
+    # (128 CTAs)
     with msqoc.Problem(S.config_4q(M=256)) as p:
-        assert (p.layout, p.col_block, p.tiles) == (msqoc.LAYOUT_FIBER_LEAN, 7, 586)
+        assert (p.layout, p.col_block, p.tiles) == (msqoc.LAYOUT_FIBER_LEAN, 14, 293)
     with msqoc.Problem(S.config_4q(M=128)) as p:
-        assert (p.layout, p.col_block) == (msqoc.LAYOUT_FIBER_LEAN, 7)
+        assert (p.layout, p.col_block) == (msqoc.LAYOUT_FIBER_LEAN, 14)
     with msqoc.Problem(S.config_4q(M=64)) as p:
         assert (p.layout, p.col_block) == (msqoc.LAYOUT_FIBER, 8)
