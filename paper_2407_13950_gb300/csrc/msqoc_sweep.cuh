@@ -340,6 +340,49 @@ __device__ __forceinline__ float2 resid_df(float2 dh, float2 dl, const float4& P
     return make_float2(fadd_n(re.s, re.c), fadd_n(im.s, im.c));
 }
 
+// ------------------------------------------------------------------ FP64 residual, out of line
+// The mixed solver's refinement residual in FP64, for the steps whose contraction factor is
+// above the compensated form's bound (step_counts) and for exchange-coupled problems.  Out of
+// line: it is rare on the workloads that fill the GPU, and inlined into the step loop (with the
+// FP64 midpoint state and the FP64 apply it needs) it slowed the common path by 4-9%.  Values
+// travel by value; the fiber's neighbour list is rebuilt from (column, fiber).
+template <int L> struct SplitVals { float4 v[L]; };
+template <int L> struct ResidIn { float4 zs[L]; DF dre[L], dim[L]; };
+template <int L> struct ResidOut { float2 r[L]; };
+
+// the midpoint state z = zs 2^sh in FP64 into the shared apply buffer (the fiber's entries)
+template <int L>
+static __device__ __noinline__ void store_z64(double2* dst, SplitVals<L> zs, int sh) {
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+        dst[l] = make_double2(df_to_f64_scaled(DF{zs.v[l].x, zs.v[l].z}, sh),
+                              df_to_f64_scaled(DF{zs.v[l].y, zs.v[l].w}, sh));
+}
+// r = s P (iX_C) z - d_total in FP64, rounded to FP32 in the column's scaled units
+template <int L, int Q, int S, bool BWD>
+static __device__ __noinline__ ResidOut<L> resid_fp64(const double2* D0, const double2* cfd, const ProbDev& pd, int c,
+                                                      int f, int zero, ResidIn<L> in, int sh) {
+    Fiber<L, Q> fb;
+    fb.init(c, f, pd, zero);
+    double2 z[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+        z[l] = make_double2(df_to_f64_scaled(DF{in.zs[l].x, in.zs[l].z}, sh),
+                            df_to_f64_scaled(DF{in.zs[l].y, in.zs[l].w}, sh));
+    double2 w[L];
+    apply_off<L, Q, double2>(D0, cfd, fb, z, w, pd);
+    const ColScale cs = col_scale(sh);
+    ResidOut<L> o;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        double2 p = pd.P[f * L + l];
+        if (BWD) p.y = -p.y;
+        const double2 dacc = make_double2(df_to_f64_scaled(in.dre[l], sh), df_to_f64_scaled(in.dim[l], sh));
+        o.r[l] = f32_of_scaled(resid_from<S>(dacc, p, w[l]), cs);
+    }
+    return o;
+}
+
 // ------------------------------------------------------------------ gradient products, split form
 // (R, I) += (Re, Im) of conj(x) u for split entries x, u = (hi.x, hi.y, lo.x, lo.y); sr = -1
 // subtracts the real part instead
@@ -994,15 +1037,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
 #pragma unroll
                         for (int l = 0; l < L; ++l) D0s[fb.xo + l] = zs[l];
                     }
-                } else {
+                } else if (act) {
+                    SplitVals<L> zv;
 #pragma unroll
-                    for (int l = 0; l < L; ++l)
-                        z[l] = make_double2(df_to_f64_scaled(DF{zs[l].x, zs[l].z}, sh),
-                                            df_to_f64_scaled(DF{zs[l].y, zs[l].w}, sh));
-                    if (act) {
-#pragma unroll
-                        for (int l = 0; l < L; ++l) D0[fb.xo + l] = z[l];
-                    }
+                    for (int l = 0; l < L; ++l) zv.v[l] = zs[l];
+                    store_z64<L>(D0 + fb.xo, zv, sh);
                 }
                 // forward: the staged midpoints of the previous step must have been read by their
                 // bulk store (issued at this step's first barrier) before this step's are staged;
@@ -1020,15 +1059,17 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                         e[l] = rf[l];
                     }
                 } else {
-                    double2 w[L];
-                    apply_off<L, Q, double2>(D0, cfd, fb, z, w, pd);
+                    ResidIn<L> in;
 #pragma unroll
                     for (int l = 0; l < L; ++l) {
-                        double2 p = pd.P[f * L + l];
-                        if (BWD) p.y = -p.y;
-                        const double2 dacc = make_double2(df_to_f64_scaled(dre[l], sh), df_to_f64_scaled(dim[l], sh));
-                        const double2 r = resid_from<S>(dacc, p, w[l]);
-                        rf[l] = f32_of_scaled(r, cs);
+                        in.zs[l] = zs[l];
+                        in.dre[l] = dre[l];
+                        in.dim[l] = dim[l];
+                    }
+                    const ResidOut<L> o = resid_fp64<L, Q, S, BWD>(D0, cfd, pd, c, f, a.cpt * N, in, sh);
+#pragma unroll
+                    for (int l = 0; l < L; ++l) {
+                        rf[l] = o.r[l];
                         e[l] = rf[l];
                     }
                 }
