@@ -302,9 +302,12 @@ __device__ __forceinline__ void cmac_df(DF (&w)[2], const float4& c, const float
 // in xr, the neighbours' in buf, the coefficients in cf; compensated FP32 sums (about 2^-47 of
 // the terms' magnitudes).  The mixed solver's residual needs P w to within 2^-53 |x| only, and
 // |P w| <= rho |x| with rho <= 2^-7 wherever this form is used.
+// exc / nex: the exchange pairs' coefficients (h/2) J split into two floats and their count
+// (2-level problems with at most MAXEXF pairs; terms i (h/2) J x_src from the fiber's sources)
 template <int L, int Q>
 __device__ __forceinline__ void apply_off_df(const float4* __restrict__ buf, const float4* __restrict__ cf,
-                                             const Fiber<L, Q>& fb, const float4 (&xr)[L], DF (&w)[L][2]) {
+                                             const Fiber<L, Q>& fb, const float4 (&xr)[L], DF (&w)[L][2],
+                                             const float2 (&exc)[MAXEXF], int nex) {
 #pragma unroll
     for (int l = 0; l < L; ++l) w[l][0] = w[l][1] = DF{0.f, 0.f};
     constexpr int kl = Q - 1;
@@ -324,6 +327,18 @@ __device__ __forceinline__ void apply_off_df(const float4* __restrict__ buf, con
             const float4* p2 = buf + fb.nb2[k];
 #pragma unroll
             for (int l = 0; l < L; ++l) cmac_df(w[l], c2, p2[l]);
+        }
+    }
+    if constexpr (L == 2 && Q >= 2) {
+#pragma unroll
+        for (int e = 0; e < MAXEXF; ++e) {
+            if (e >= nex) break;   // uniform
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                const float4 x = buf[fb.exs[e][l]];   // the zero entry where the pair gives no term
+                df_mac(w[l][0], -exc[e].x, -exc[e].y, x.y, x.w);
+                df_mac(w[l][1], exc[e].x, exc[e].y, x.x, x.z);
+            }
         }
     }
 }
@@ -649,6 +664,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
 
     Fiber<L, Q> fb;
     fb.init(c, f, pd, a.cpt * N);
+    // the exchange coefficients split for the compensated apply (2-level problems)
+    float2 exc[MAXEXF];
+#pragma unroll
+    for (int e = 0; e < MAXEXF; ++e)
+        exc[e] = (L == 2 && Q >= 2 && e < pd.nex) ? split_scaled(pd.ex_c[e], 0) : make_float2(0.f, 0.f);
     // the apply buffers' zero entry (read by the exchange terms a fiber entry does not have; the
     // first barrier of the time loop orders these stores before any read)
     if (tid == 0) {
@@ -1021,9 +1041,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 dim[l] = DF{df[l].y, 0.f};
             }
             // the residual's apply in compensated FP32 (split entries in D0) where the step's
-            // contraction factor allows it (step_counts) and the problem has no exchange terms,
-            // else in FP64; uniform over a slot, so a column's entries in D0 have one form
-            const bool dfa = pd.nex == 0 && !(prm[3] & 2);
+            // contraction factor (exchange included) allows it (step_counts) and the exchange
+            // terms, if any, have precomputed sources, else in FP64; uniform over a slot, so a
+            // column's entries in D0 have one form
+            const bool dfa = (pd.nex == 0 || (L == 2 && pd.nex <= MAXEXF)) && !(prm[3] & 2);
             float4* D0s = reinterpret_cast<float4*>(D0);
             for (int pass = 0;; ++pass) {
                 float4 zs[L];
@@ -1051,7 +1072,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 float2 rf[L], e[L];
                 if (dfa) {
                     DF w[L][2];
-                    apply_off_df<L, Q>(D0s, cfs, fb, zs, w);
+                    apply_off_df<L, Q>(D0s, cfs, fb, zs, w, exc, pd.nex);
 #pragma unroll
                     for (int l = 0; l < L; ++l) {
                         rf[l] = resid_df<S>(make_float2(dre[l].s, dim[l].s), make_float2(dre[l].c, dim[l].c), Ps[l],
