@@ -297,8 +297,9 @@ msqoc_status msqoc_measure_fp64_peak(double* tflops);
  * way.  Synchronizes the device. */
 msqoc_status msqoc_selftest_bounded_wait(int64_t spins, int32_t arrive, double* seconds_out);
 
-/* Self-tests of the compensated FP32 arithmetic the mixed solver's adjoint uses for the
- * gradient products of Eq. grad-int (not operations of the paper), on the host (on_device = 0)
+/* Self-tests of the compensated FP32 arithmetic the mixed solver uses for the gradient products
+ * of Eq. grad-int and for the implicit-midpoint state update (not operations of the paper), on
+ * the host (on_device = 0)
  * or on the current device (on_device != 0: device copies, a kernel, copies back; synchronizes).
  * All arrays are host arrays of n entries; -2000 <= scales <= 2000.
  *
@@ -311,11 +312,22 @@ msqoc_status msqoc_selftest_bounded_wait(int64_t spins, int32_t arrive, double* 
  * with exact FP32 product and two-sum error terms, returned as one double scaled by
  * 2^(shx + shy); its error is about 2^-47 sum_i |x_i y_i| (plus the partial sums' magnitudes).
  *
- * Errors: MSQOC_ERR_INVALID_ARG for negative n, NULL arrays (n > 0) or scales out of range;
- * MSQOC_ERR_CUDA for a failed device step. */
+ * msqoc_selftest_carry: n steps of the state update of the implicit midpoint rule (Sec. 5) on
+ * one complex entry, U_{j+1} = R U_j + 2 d_j with R = 2P - 1, P = 1 / (1 + i kappa) the diagonal
+ * preconditioner entry (P: 2 doubles, re and im; kappa = -Im P / Re P) and d_j the corrections
+ * (d: n complex entries, 2n doubles, split into two floats in units 2^-sh as the solver's
+ * corrections are), formed as the mixed solver forms it where |2 kappa| <= 2^-4.5: the state
+ * an FP64 part u plus an FP32 carry, u' + carry' = u + carry + 2 kappa (Im b, -Re b) + 2 d_j with
+ * b = P (u + carry) (R - 1 = -2 i kappa P).  u0: 2 doubles; out: the final u + carry (2 doubles).
+ * -896 <= sh <= 896; Re P must lie in (1/2, 1] and (2 kappa)^2 <= 2^-9.
+ *
+ * Errors: MSQOC_ERR_INVALID_ARG for negative n, NULL arrays (n > 0), scales out of range or (carry
+ * test) P outside the bounds; MSQOC_ERR_CUDA for a failed device step. */
 msqoc_status msqoc_selftest_split(const double* x, int64_t n, int32_t sh, int32_t on_device, float* hi, float* lo);
 msqoc_status msqoc_selftest_dot(const double* x, const double* y, int64_t n, int32_t shx, int32_t shy,
                                 int32_t on_device, double* out);
+msqoc_status msqoc_selftest_carry(const double* u0, const double* P, const double* d, int64_t n, int32_t sh,
+                                  int32_t on_device, double* out);
 
 /* ---------------------------------------------------------------------------------------
  * Batched evaluation (many problems per launch).

@@ -3,9 +3,9 @@
 //    midpoint-history fetches) on a barrier that nothing completes gives up after its spin
 //    limit, and the launch reports it through the status word as MSQOC_ERR_TIMEOUT instead of
 //    hanging the GPU.  The context stays usable afterwards.
-//  * the compensated FP32 arithmetic of the mixed solver's gradient products (msqoc_split.cuh),
-//    on the host or in a one-thread kernel: the split of doubles into two floats and a real
-//    dot product formed the way the adjoint forms its products.
+//  * the compensated FP32 arithmetic of the mixed solver (msqoc_split.cuh), on the host or in a
+//    one-thread kernel: the split of doubles into two floats, a real dot product formed the way
+//    the adjoint forms its gradient products, and steps of the compensated state update.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,6 +51,33 @@ __host__ __device__ double dot_split(const double* x, const double* y, int64_t n
 
 __global__ void k_dot_probe(const double* x, const double* y, int64_t n, int shx, int shy, double* out) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *out = dot_split(x, y, n, shx, shy);
+}
+
+// n steps of the compensated state update on one complex entry from u0 with the preconditioner
+// entry P and the corrections d_j (absolute), in units 2^-sh; out = the final u + carry
+__host__ __device__ void carry_steps(const double* u0, const double* P, const double* d, int64_t n, int sh,
+                                     double* out) {
+    double2 u = make_double2(u0[0], u0[1]);
+    const double2 p = make_double2(P[0], P[1]);
+    const float4 Ps = split_scaled(p, 0);
+    const float2 P3 = make_float2(split_third(p.x, make_float2(Ps.x, Ps.z)), split_third(p.y, make_float2(Ps.y, Ps.w)));
+    const double k2d = -2.0 * p.y / p.x;
+    const float2 k2 = split_scaled(k2d, 0);
+    const float k3 = split_third(k2d, k2);
+    float2 car = make_float2(0.f, 0.f);
+    for (int64_t j = 0; j < n; ++j) {
+        DF bre, bim;
+        carry_rhs(split_scaled(u, sh), Ps, P3, car, bre, bim);
+        const float2 dr = split_scaled(d[2 * j], sh), di = split_scaled(d[2 * j + 1], sh);
+        u = carry_update(u, bre, bim, k2, k3, DF{dr.x, dr.y}, DF{di.x, di.y}, sh, car);
+    }
+    const double2 r = carry_finish(u, car, sh);
+    out[0] = r.x;
+    out[1] = r.y;
+}
+
+__global__ void k_carry_probe(const double* u0, const double* P, const double* d, int64_t n, int sh, double* out) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) carry_steps(u0, P, d, n, sh, out);
 }
 
 // device copies of n doubles; frees what it allocated on failure
@@ -126,6 +153,37 @@ extern "C" msqoc_status msqoc_selftest_dot(const double* x, const double* y, int
     }
     if (e == cudaSuccess) e = cudaMemcpy(out, od, sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail(MSQOC_ERR_CUDA, "dot self-test: %s", cudaGetErrorString(e));
+    return MSQOC_OK;
+}
+
+extern "C" msqoc_status msqoc_selftest_carry(const double* u0, const double* P, const double* d, int64_t n,
+                                             int32_t sh, int32_t on_device, double* out) {
+    if (n < 0 || !u0 || !P || !out || (n > 0 && !d)) return fail(MSQOC_ERR_INVALID_ARG, "carry self-test: bad arrays");
+    if (sh < -SCALE_SHIFT_MAX || sh > SCALE_SHIFT_MAX)
+        return fail(MSQOC_ERR_INVALID_ARG, "carry self-test: scale %d out of range", sh);
+    if (!(P[0] > 0.5 && P[0] <= 1.0)) return fail(MSQOC_ERR_INVALID_ARG, "carry self-test: Re P not in (1/2, 1]");
+    const double k2 = -2.0 * P[1] / P[0];
+    if (!(k2 * k2 <= CARRY_UPDATE_K2))
+        return fail(MSQOC_ERR_INVALID_ARG, "carry self-test: |2 kappa| above the compensated update's bound");
+    if (!on_device) {
+        carry_steps(u0, P, d, n, sh, out);
+        return MSQOC_OK;
+    }
+    DevBufs b;
+    double *ud = nullptr, *pdv = nullptr, *dd = nullptr, *od = nullptr;
+    cudaError_t e = b.alloc(&ud, 2);
+    if (e == cudaSuccess) e = b.alloc(&pdv, 2);
+    if (e == cudaSuccess) e = b.alloc(&dd, std::max<int64_t>(2 * n, 1));
+    if (e == cudaSuccess) e = b.alloc(&od, 2);
+    if (e == cudaSuccess) e = cudaMemcpy(ud, u0, 2 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pdv, P, 2 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n) e = cudaMemcpy(dd, d, 2 * n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_carry_probe<<<1, 32>>>(ud, pdv, dd, n, sh, od);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, od, 2 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(MSQOC_ERR_CUDA, "carry self-test: %s", cudaGetErrorString(e));
     return MSQOC_OK;
 }
 

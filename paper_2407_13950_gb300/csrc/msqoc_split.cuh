@@ -108,6 +108,31 @@ __host__ __device__ __forceinline__ DF df_add(DF a, DF b) {
     const float t = fadd_n(fsub_n(a.s, fsub_n(s, bp)), fsub_n(b.s, bp));
     return DF{s, fadd_n(fadd_n(a.c, b.c), t)};
 }
+// a + b as s + c with s = RN(a + b) and c its exact error (two-sum)
+__host__ __device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = fadd_n(a, b);
+    const float bp = fsub_n(s, a);
+    return DF{s, fadd_n(fsub_n(a, fsub_n(s, bp)), fsub_n(b, bp))};
+}
+// one real part of a complex product, x1 y1 + x2 y2 for split factors (h, l): the two leading
+// products exact (FMA) and added with an exact two-sum, their errors and the four cross terms
+// in the low part; the l l terms (<= 2^-48 of each product) are dropped
+__host__ __device__ __forceinline__ DF dot2_df(float x1h, float x1l, float y1h, float y1l, float x2h, float x2l,
+                                               float y2h, float y2l) {
+    const float p1 = fmul_n(x1h, y1h), e1 = ffma_n(x1h, y1h, -p1);
+    const float p2 = fmul_n(x2h, y2h), e2 = ffma_n(x2h, y2h, -p2);
+    const DF s = two_sum(p1, p2);
+    float c = ffma_n(x1h, y1l, e1);
+    c = ffma_n(x1l, y1h, c);
+    c = ffma_n(x2h, y2l, c);
+    c = ffma_n(x2l, y2h, c);
+    return DF{s.s, fadd_n(fadd_n(c, e2), s.c)};
+}
+// x y for split complex x = (hi.x, hi.y, lo.x, lo.y) and y split the same way
+__host__ __device__ __forceinline__ void cmul_df(const float4& x, const float4& y, DF& re, DF& im) {
+    re = dot2_df(x.x, x.z, y.x, y.z, -x.y, -x.w, y.y, y.w);
+    im = dot2_df(x.x, x.z, y.y, y.w, x.y, x.w, y.x, y.z);
+}
 // a w for w = wh + wl (a constant split the same way)
 __host__ __device__ __forceinline__ DF df_scale(DF a, float wh, float wl) {
     const float p = fmul_n(a.s, wh);
@@ -157,6 +182,53 @@ __host__ __device__ __forceinline__ double f64_of_float_scaled(float f, int sh) 
 // the finished sum s + c times 2^sh, as one double (one FP64 add)
 __host__ __device__ __forceinline__ double df_to_f64_scaled(DF a, int sh) {
     return f64_of_float_scaled(a.s, sh) + f64_of_float_scaled(a.c, sh);
+}
+
+// ------------------------------------------------------------------ the compensated state update
+// The mixed solver's implicit-midpoint state update U_{n+1} = 2 Ubar - U_n = R U_n + 2 d, with
+// R = 2P - 1, P = 1 / (1 + i kappa) the diagonal preconditioner entry (kappa = (h/2) D real) and d
+// the step's correction (Ubar = P U_n + d).  Since R - 1 = -2 i kappa P, where |2 kappa| <= 2^-4.5
+// the state is kept as an FP64 part u and an FP32 carry (units 2^-sh) and
+//   u' + carry' = u + carry + 2 kappa (Im b, -Re b) + 2 d,   b = P (u + carry),
+// the increment formed as a two-float sum s + c and renormalised: u' = u + s (one FP64 add; s is
+// exact as a double), carry' = c.  b is the step's right-hand side (carry_rhs); its compensated
+// error (about 2^-47 |b|) enters times |2 kappa|, of the order of the FP64 rounding of u.
+constexpr double CARRY_UPDATE_K2 = 0.001953125;   // (2 kappa)^2 <= 2^-9
+
+// The constants P and 2 kappa enter every step, so their splits are made exact with a third part
+// (x - hi - lo, at most 5 bits: exact as a float): otherwise the 2^-48 remainders of the splits
+// would act as a constant error of P and kappa and add up over the steps.
+__host__ __device__ __forceinline__ float split_third(double x, float2 s) {
+    return static_cast<float>((x - static_cast<double>(s.x)) - static_cast<double>(s.y));
+}
+// b = P (u + carry) from the split u (units 2^-sh), the split P and its third parts P3; the
+// carry (at most half an FP32 unit of the last increment) goes into the low parts
+__host__ __device__ __forceinline__ void carry_rhs(const float4& us, const float4& P, float2 P3, float2 car, DF& bre,
+                                                   DF& bim) {
+    cmul_df(us, P, bre, bim);
+    const float cr = ffma_n(P.x, car.x, ffma_n(-P.y, car.y, ffma_n(P3.x, us.x, fmul_n(-P3.y, us.y))));
+    const float ci = ffma_n(P.x, car.y, ffma_n(P.y, car.x, ffma_n(P3.x, us.y, fmul_n(P3.y, us.x))));
+    bre.c = fadd_n(bre.c, cr);
+    bim.c = fadd_n(bim.c, ci);
+}
+// u' (returned) and carry' from u, b = (bre, bim), the split 2 kappa (k2) and its third part k3,
+// and d = (dre, dim)
+__host__ __device__ __forceinline__ double2 carry_update(double2 u, DF bre, DF bim, float2 k2, float k3, DF dre, DF dim,
+                                                         int sh, float2& car) {
+    DF qr = df_scale(bim, k2.x, k2.y), qi = df_neg(df_scale(bre, k2.x, k2.y));
+    qr.c = fadd_n(qr.c, ffma_n(k3, bim.s, car.x));
+    qi.c = fadd_n(qi.c, ffma_n(-k3, bre.s, car.y));
+    const DF ar = df_add(qr, DF{fadd_n(dre.s, dre.s), fadd_n(dre.c, dre.c)});
+    const DF ai = df_add(qi, DF{fadd_n(dim.s, dim.s), fadd_n(dim.c, dim.c)});
+    // renormalised, so that u takes all but the last rounding of the increment and the carry
+    // stays within half an FP32 unit of it (else it would gather the low parts of every step)
+    const DF xr = two_sum(ar.s, ar.c), xi = two_sum(ai.s, ai.c);
+    car = make_float2(xr.c, xi.c);
+    return make_double2(u.x + f64_of_float_scaled(xr.s, sh), u.y + f64_of_float_scaled(xi.s, sh));
+}
+// the state u + carry as one double (one FP64 add a component)
+__host__ __device__ __forceinline__ double2 carry_finish(double2 u, float2 car, int sh) {
+    return make_double2(u.x + f64_of_float_scaled(car.x, sh), u.y + f64_of_float_scaled(car.y, sh));
 }
 
 }  // namespace msqoc

@@ -685,7 +685,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
     double2 Pd[L];
     float2 Pf[L];
     float4 Ps[L];   // split (mixed solver's right-hand side and compensated residual)
-    double2 Rd[L];  // R = 2P - 1, the Cayley factor of the diagonal part (mixed solver's state update)
+    // 2 kappa = -2 Im P / Re P split (P = 1 / (1 + i kappa)), for the mixed solver's state update
+    float2 k2s[L];
+    float4* cq = SOLVER == SOLVER_MIXED ? reinterpret_cast<float4*>(smem + lay.cq) : nullptr;
+    bool carry_ok = true;
 #pragma unroll
     for (int l = 0; l < L; ++l) {
         double2 p = pd.P[f * L + l];
@@ -693,8 +696,20 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
         Pd[l] = p;
         Ps[l] = split_scaled(p, 0);
         Pf[l] = make_float2(Ps[l].x, Ps[l].y);   // p rounded to FP32
-        Rd[l] = make_double2(fma(2.0, p.x, -1.0), 2.0 * p.y);
+        const double k2 = -2.0 * p.y / p.x;
+        k2s[l] = split_scaled(k2, 0);
+        carry_ok = carry_ok && k2 * k2 <= CARRY_UPDATE_K2;
+        // the splits' third parts, per entry of the fiber (the same for every column)
+        if (SOLVER == SOLVER_MIXED && act && c == 0)
+            cq[f * L + l] = make_float4(split_third(k2, k2s[l]), split_third(p.x, make_float2(Ps[l].x, Ps[l].z)),
+                                        split_third(p.y, make_float2(Ps[l].y, Ps[l].w)), 0.f);
     }
+    // the compensated state update for the whole tile (the same P table for every tile of the
+    // problem, so the same choice), else R u + 2 d in FP64
+    const bool carry_upd = SOLVER == SOLVER_MIXED && tile_sync_or(act && !carry_ok) == 0;
+    float2 car[L];   // the state's FP32 carry (compensated update), zero otherwise
+#pragma unroll
+    for (int l = 0; l < L; ++l) car[l] = make_float2(0.f, 0.f);
 
     // ---- initial state
     //   forward, whole window : U^m(t_{m-1}) = W^{m-1} (identity embedding for the first window
@@ -859,6 +874,31 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                             sp.s - (s ? slo_1 : slo_0), lane);
     };
 
+    // the step's state update: 2 z - u (FP64 solver); R u + 2 d in FP64 or the compensated form
+    // with the carry (mixed solver; the FP64 form reads R's P from the table: rare)
+    auto state_update = [&](double2 (&uu)[L], const double2 (&zz)[L], const DF (&br)[L], const DF (&bi)[L],
+                            const DF (&dr)[L], const DF (&di)[L]) {
+        if constexpr (SOLVER == SOLVER_MIXED) {
+            if (carry_upd) {
+#pragma unroll
+                for (int l = 0; l < L; ++l)
+                    uu[l] = carry_update(uu[l], br[l], bi[l], k2s[l], cq[f * L + l].x, dr[l], di[l], sh, car[l]);
+            } else {
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    double2 p = pd.P[f * L + l];
+                    if (BWD) p.y = -p.y;
+                    uu[l] = cayley_update(make_double2(fma(2.0, p.x, -1.0), 2.0 * p.y), uu[l], dr[l], di[l], sh);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int l = 0; l < L; ++l) uu[l] = reflect(zz[l], uu[l]);
+        }
+    };
+    // the state as stored (u + carry)
+    auto state_out = [&](int l) { return carry_upd ? carry_finish(u[l], car[l], sh) : u[l]; };
+
     __shared__ int tflag_s;   // a bounded history wait gave up (adjoint)
     int* tflag = &tflag_s;
     if (tid == 0) tflag_s = 0;
@@ -892,10 +932,21 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             if (lane < nscat) ph_prev = pd.phase[size_t(np) * pd.nfsum + lane / 3];
         }
         // checkpoint: the state at the start of every segment (forward over whole windows)
-        if (want_ckpt && live && act && jj % pd.kseg == 0) {
-            double2* ck = pd.ckpt + ((size_t(m - 1) * pd.nseg + jj / pd.kseg) * E + col) * N + f * L;
+        // (the carry is folded into u there, so that a segment recomputed from its checkpoint
+        // repeats these steps bit for bit)
+        if (want_ckpt && live && jj % pd.kseg == 0) {
+            if (carry_upd) {
 #pragma unroll
-            for (int l = 0; l < L; ++l) ck[l] = u[l];
+                for (int l = 0; l < L; ++l) {
+                    u[l] = carry_finish(u[l], car[l], sh);
+                    car[l] = make_float2(0.f, 0.f);
+                }
+            }
+            if (act) {
+                double2* ck = pd.ckpt + ((size_t(m - 1) * pd.nseg + jj / pd.kseg) * E + col) * N + f * L;
+#pragma unroll
+                for (int l = 0; l < L; ++l) ck[l] = u[l];
+            }
         }
         const double2* cfd = coef_d + (par * 2 + slot) * NSLOT;
         const float2* cff = coef_f + (par * 2 + slot) * NSLOT;
@@ -911,6 +962,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
         double2 z[L];
         float4 zf[L];
         DF dre[L], dim[L];
+        DF bre[L], bim[L];   // mixed solver: b = P u (conj(P) for the adjoint), two-float
 
         // first barrier of the step: the coefficients are published; thread 0 stores the
         // previous iteration's midpoints (forward) or fetches the next iteration's (adjoint)
@@ -976,18 +1028,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             // ---- b = P u (conj(P) for the adjoint) as a two-float sum in the column's scaled
             // units: the FP32 stage's right-hand side and the point at which the refinement
             // evaluates the off-diagonal apply.  The residual below is that of the exact P u
-            // (it is formed as s P w(z) - d_total), and the state update uses R u = (2P - 1) u in
-            // FP64, so b's 2^-47 error enters only the evaluation point of a term of size rho.
-            DF bre[L], bim[L];
+            // (it is formed as s P w(z) - d_total), so b's 2^-47 error enters the solve only
+            // through the evaluation point of a term of size rho.  The state update takes R u
+            // either in FP64 (R = 2P - 1) or, compensated, as u + 2 kappa (Im b, -Re b), where
+            // b's error enters times |2 kappa| <= 2^-4.5; there the state is u + carry, and
+            // P carry (|carry| <= half an FP32 unit of the last increment) joins the low parts.
 #pragma unroll
             for (int l = 0; l < L; ++l) {
-                const float4 us = split_scaled(u[l], sh);
-                bre[l] = DF{0.f, 0.f};
-                bim[l] = DF{0.f, 0.f};
-                df_mac(bre[l], Ps[l].x, Ps[l].z, us.x, us.z);
-                df_mac(bre[l], -Ps[l].y, -Ps[l].w, us.y, us.w);
-                df_mac(bim[l], Ps[l].x, Ps[l].z, us.y, us.w);
-                df_mac(bim[l], Ps[l].y, Ps[l].w, us.x, us.z);
+                const float4 t = cq[f * L + l];
+                carry_rhs(split_scaled(u[l], sh), Ps[l], make_float2(t.y, t.z), car[l], bre[l], bim[l]);
             }
             // ---- FP32 stage: d = Ubar - b from the preconditioned fixed point d = s P w(b + d)
             float2 bf[L], df[L], y[L];
@@ -1127,6 +1176,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             }
         }
         if (tid == 0 && ((prm0[3] & 1) || (nslot > 1 && (prm1[3] & 1)))) atomicOr(pd.status, ST_SOLVER_RANGE);
+        // the state update (U_{n+1} = 2 Ubar - U_n; Lambda_n = 2 Lbar - Lambda_{n+1}) as soon as
+        // the step is solved: what follows (history, gradient products) needs only the midpoint
+        if (live) state_update(u, z, bre, bim, dre, dim);
 
         if constexpr (!BWD) {
             // ---- midpoint states for the adjoint sweep (async bulk store at the next step)
@@ -1151,10 +1203,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 }
                 fence_proxy_async_smem();
             }
-            if (live) {
-#pragma unroll
-                for (int l = 0; l < L; ++l) u[l] = SOLVER == SOLVER_MIXED ? cayley_update(Rd[l], u[l], dre[l], dim[l], sh) : reflect(z[l], u[l]);
-            }
             // roll-out: U(t_m) when the step ends on a window boundary t_m, i.e. when n + 1 =
             // floor(m N_T / M) for some 1 <= m < M; the only candidate is m = ceil((n+1) M / N_T)
             if (rollout && live && act) {
@@ -1163,7 +1211,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 if (mb >= 1 && mb < pd.M && (mb * pd.nsteps) / pd.M == n1) {
                     double2* dst = a.out + (size_t(mb - 1) * E + col) * N + f * L;
 #pragma unroll
-                    for (int l = 0; l < L; ++l) dst[l] = u[l];
+                    for (int l = 0; l < L; ++l) dst[l] = state_out(l);
                 }
             }
         } else {
@@ -1286,11 +1334,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                     }
                 }
             }
-            // Lambda_n = 2 Lbar - Lambda_{n+1}
-            if (live) {
-#pragma unroll
-                for (int l = 0; l < L; ++l) u[l] = SOLVER == SOLVER_MIXED ? cayley_update(Rd[l], u[l], dre[l], dim[l], sh) : reflect(z[l], u[l]);
-            }
         }
 
         if (++hpos == hd) {
@@ -1312,7 +1355,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             }
             if (a.mode != SWEEP_RECOMPUTE && !rollout && act && my_cnt > 0) {
 #pragma unroll
-                for (int l = 0; l < L; ++l) pd.Uend[wcol + f * L + l] = u[l];
+                for (int l = 0; l < L; ++l) pd.Uend[wcol + f * L + l] = state_out(l);
             }
         } else {
             // the last fold of every slot whose range ends at the last iteration
@@ -1330,7 +1373,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
             if (act && my_cnt > 0) {
                 double2* dst = my_lo == 0 ? pd.Lam0 : pd.Lstate;
 #pragma unroll
-                for (int l = 0; l < L; ++l) dst[wcol + f * L + l] = u[l];
+                for (int l = 0; l < L; ++l) dst[wcol + f * L + l] = state_out(l);
             }
         }
     } else if (tid == 0) {

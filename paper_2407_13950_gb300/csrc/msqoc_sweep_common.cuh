@@ -268,7 +268,7 @@ struct Fiber {
 // keep each coefficient in the form of either part, so their coefficient arrays are twice as
 // large.
 struct SweepSmem {
-    size_t coef_d, coef_f, coef_s, params, mbar, red, zy, galpha, gdf, D0, D1, FA, FB, H, UB0, UB1, total;
+    size_t coef_d, coef_f, coef_s, params, mbar, red, zy, galpha, gdf, cq, D0, D1, FA, FB, H, UB0, UB1, total;
 };
 // steps between flushes of the mixed solver's two-float gradient accumulator into the FP64 one
 constexpr int FOLD_FLUSH = 8;
@@ -299,6 +299,9 @@ __host__ __device__ inline SweepSmem sweep_layout(int q, int L, int N, int cpt, 
     s.galpha = o; o = align16(o + (bwd ? size_t(2) * gmax * 8 : 0));             // [slot][nfsum][gspan][2]
     // the mixed solver's one-thread families: the same, two-float, holding the last steps' terms
     s.gdf = o;    o = align16(o + (bwd && !pair && solver == SOLVER_MIXED ? size_t(2) * gmax * 8 : 0));
+    // the mixed solver's one-thread families: per fiber entry the third parts of the splits of
+    // 2 kappa and P (the compensated state update)
+    s.cq = o;     o = align16(o + (!pair && solver == SOLVER_MIXED ? size_t(N) * 16 : 0));
     s.D0 = o;     o = align16(o + buf_d);
     s.D1 = o;     o = align16(o + (solver == SOLVER_FP64 ? buf_d : 0));
     s.FA = o;     o = align16(o + (solver == SOLVER_MIXED ? buf_f : 0));

@@ -29,7 +29,7 @@ EXPORTED = ["msqoc_create_problem", "msqoc_query", "msqoc_query_layout", "msqoc_
             "msqoc_get_objective", "msqoc_get_gradient", "msqoc_batch_eval_subset", "msqoc_autotune",
             "msqoc_rollout", "msqoc_rollout_estimate", "msqoc_eval_regularization", "msqoc_lbfgs_direction",
             "msqoc_lbfgs_trial", "msqoc_lbfgs_update", "msqoc_selftest_bounded_wait",
-            "msqoc_selftest_split", "msqoc_selftest_dot"]
+            "msqoc_selftest_split", "msqoc_selftest_dot", "msqoc_selftest_carry"]
 BATCH_GRADIENT, BATCH_GRAPH = 1, 2
 KERNEL_NAMES = ["controls", "forward", "terminal", "adjoint", "finalize"]
 
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
             "msqoc_selftest_bounded_wait": (i32, [ctypes.c_int64, i32, vp]),
             "msqoc_selftest_split": (i32, [vp, i64, i32, i32, vp, vp]),
             "msqoc_selftest_dot": (i32, [vp, vp, i64, i32, i32, i32, vp]),
+            "msqoc_selftest_carry": (i32, [vp, vp, vp, i64, i32, i32, vp]),
             "msqoc_eval_objective_noalloc": (i32, [vp, vp, vp, ctypes.c_double, i64, i32, ctypes.c_double, i32,
                                                    vp, vp, vp, vp, vp, vp]),
             "msqoc_batch_create": (i32, [vp, i32, i32, vp]),
@@ -354,6 +355,18 @@ def selftest_dot(x, y, shx: int = 0, shy: int = 0, device: bool = False) -> floa
     _check(load().msqoc_selftest_dot(x.ctypes.data, y.ctypes.data, x.size, int(shx), int(shy), 1 if device else 0,
                                      ctypes.byref(out)))
     return out.value
+
+
+def selftest_carry(u0, P, d, sh: int = 0, device: bool = False) -> complex:
+    """n steps of the mixed solver's compensated implicit-midpoint state update on one entry:
+    U_{j+1} = R U_j + 2 d_j with R = 2P - 1 (msqoc_selftest_carry); returns the final state."""
+    u = np.array([complex(u0).real, complex(u0).imag])
+    p = np.array([complex(P).real, complex(P).imag])
+    dd = np.ascontiguousarray(np.asarray(d, dtype=np.complex128).reshape(-1)).view(np.float64)
+    out = np.zeros(2)
+    _check(load().msqoc_selftest_carry(u.ctypes.data, p.ctypes.data, dd.ctypes.data, dd.size // 2, int(sh),
+                                       1 if device else 0, out.ctypes.data))
+    return complex(out[0], out[1])
 
 
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024   # MSQOC_NOALLOC_SCRATCH_BYTES

@@ -6,7 +6,11 @@ against another floating-point implementation:
 * the split x 2^-sh = hi + lo: hi is x 2^-sh rounded to 24 bits (float32 rounding, away from
   zero at ties), |x 2^-sh - hi - lo| <= 2^-48 |x 2^-sh|, and the documented range edges;
 * the dot product built from the splits: its error is at most a few 2^-47 of sum |x_i y_i|,
-  including sums that cancel to zero or almost.
+  including sums that cancel to zero or almost;
+* the compensated state update of the implicit midpoint rule (Sec. 5), U_{j+1} = R U_j + 2 d_j
+  with R = 2P - 1 = 1 - 2 i kappa P: against the same map in 320-bit arithmetic (mpmath) its
+  error is a random walk of about 2^-53 |U| a step, and with d = 0 it follows the exact Cayley
+  factor (1 - i kappa) / (1 + i kappa) of the diagonal step.
 """
 from fractions import Fraction as Fr
 
@@ -119,3 +123,84 @@ def test_selftests_reject_bad_arguments():
     assert lib.msqoc_selftest_split(None, 4, 0, 0, None, None) == -1
     assert lib.msqoc_selftest_split(None, 0, 5000, 0, None, None) == -1
     assert lib.msqoc_selftest_dot(None, None, -1, 0, 0, 0, None) == -1
+
+
+# ------------------------------------------------------------------ compensated state update
+def _carry_map(u0, P, d):
+    """u_{j+1} = u_j + k2 (Im(P u_j), -Re(P u_j)) + 2 d_j in 320-bit arithmetic, k2 = -2 Im P / Re P
+    rounded to a double as the library forms it (R - 1 = 2 (P - 1) = -2 i kappa P)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.prec = 320
+    M = mp.mpf
+    px, py = M(P.real), M(P.imag)
+    k2 = M(-2.0 * P.imag / P.real)
+    ur, ui = M(u0.real), M(u0.imag)
+    for dj in d:
+        br, bi = px * ur - py * ui, px * ui + py * ur
+        ur, ui = ur + k2 * bi + 2 * M(dj.real), ui - k2 * br + 2 * M(dj.imag)
+    return ur, ui
+
+
+def _carry_err(got, ref, mag):
+    return float(abs((got.real - ref[0]) + 1j * (got.imag - ref[1]))) / mag / 2.0 ** -53
+
+
+def test_carry_update_one_step():
+    rng = np.random.default_rng(2001)
+    worst = 0.0
+    for _ in range(200):
+        mag = rng.uniform(0.05, 1.0)
+        u0 = mag * np.exp(1j * rng.uniform(0, 2 * np.pi))
+        P = 1.0 / complex(1.0, rng.uniform(-0.022, 0.022))
+        d = (rng.standard_normal(1) + 1j * rng.standard_normal(1)) * 1e-3 * mag
+        got = msqoc.selftest_carry(u0, P, d, sh=int(rng.integers(-5, 6)))
+        worst = max(worst, _carry_err(got, _carry_map(u0, P, d), mag))
+    assert worst <= 6.0, worst          # a few units of 2^-53 |U| (measured: about 3)
+
+
+def test_carry_update_error_is_a_random_walk():
+    # 64 steps with corrections: the errors of the steps add like independent roundings
+    # (about 0.6 2^-53 |U| rms a step), not like a constant error of P or kappa (the splits of
+    # both are exact) nor like a carry that keeps the low parts of every step
+    rng = np.random.default_rng(2002)
+    n, errs = 64, []
+    for _ in range(30):
+        mag = rng.uniform(0.3, 1.0)
+        u0 = mag * np.exp(1j * rng.uniform(0, 2 * np.pi))
+        P = 1.0 / complex(1.0, rng.uniform(-0.022, 0.022))
+        d = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) * 1e-3 * mag
+        got = msqoc.selftest_carry(u0, P, d)
+        errs.append(_carry_err(got, _carry_map(u0, P, d), mag))
+    errs = np.array(errs)
+    assert np.sqrt(np.mean(errs ** 2)) <= 2.0 * np.sqrt(n), errs
+    assert errs.max() <= 6.0 * np.sqrt(n), errs
+
+
+def test_carry_update_follows_the_cayley_factor():
+    # d = 0: the diagonal part of the implicit midpoint step alone, U_n = R^n U_0 with the
+    # Cayley factor R = (1 - i kappa) / (1 + i kappa) of kappa = (h/2) D; P = 1 / (1 + i kappa)
+    # is rounded to doubles, which moves R by about |kappa| 2^-53 a step in this form (R = 2P - 1
+    # formed in FP64 from the rounded P would be off by up to 2^-52 a step: 300-800 units here)
+    mp = pytest.importorskip("mpmath")
+    mp.mp.prec = 320
+    rng = np.random.default_rng(2003)
+    n = 400
+    for kap in (0.0, 3e-4, -0.0083, 0.022):
+        u0 = 0.8 * np.exp(1j * rng.uniform(0, 2 * np.pi))
+        P = 1.0 / complex(1.0, kap)
+        got = msqoc.selftest_carry(u0, P, np.zeros(n, complex))
+        k = mp.mpf(kap)
+        R = (1 - 1j * k) / (1 + 1j * k)
+        want = mp.mpc(u0.real, u0.imag) * R ** n
+        err = float(abs(mp.mpc(got.real, got.imag) - want)) / 0.8 / 2.0 ** -53
+        assert err <= 3.0 * np.sqrt(n), (kap, err)        # measured: 2-12
+    assert msqoc.selftest_carry(0.3 - 0.4j, 1.0, np.zeros(5)) == 0.3 - 0.4j     # kappa = 0: exact
+
+
+def test_carry_selftest_rejects_bad_arguments():
+    with pytest.raises(msqoc.MsqocError):
+        msqoc.selftest_carry(1.0, 1.0 / complex(1.0, 0.03), np.zeros(3))     # |2 kappa| > 2^-4.5
+    with pytest.raises(msqoc.MsqocError):
+        msqoc.selftest_carry(1.0, complex(0.4, 0.0), np.zeros(3))            # Re P outside (1/2, 1]
+    with pytest.raises(msqoc.MsqocError):
+        msqoc.selftest_carry(1.0, 1.0, np.zeros(3), sh=897)
