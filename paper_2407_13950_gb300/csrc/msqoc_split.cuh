@@ -1,8 +1,9 @@
 // Double values as unevaluated sums of two floats, and compensated FP32 arithmetic on them: the
-// mixed solver's adjoint forms the gradient products of Eq. grad-int with these instead of FP64
+// mixed solver forms the right-hand side of its steps, the residual apply, the gradient products
+// of Eq. grad-int and the state update of the implicit midpoint rule with these instead of FP64
 // multiply-adds.  On this GPU a warp's FP64 instruction occupies the issuing warp for ~60 cycles
-// and the SM retires ~2 FP64 lanes a cycle, against 128 FP32 lanes; the products are a third of
-// the adjoint's FP64 work.  Every function here runs on the host too (the CPU tests pin them);
+// and the SM retires ~2 FP64 lanes a cycle, against 128 FP32 lanes.  Every function here runs on
+// the host too (the CPU tests pin them);
 // the host side must be compiled without floating-point contraction (-ffp-contract=off), the
 // device side uses the _rn intrinsics, which the compiler never fuses.
 #pragma once
