@@ -59,16 +59,26 @@ inline float ffma_n(float a, float b, float c) { return __builtin_fmaf(a, b, c);
 // operations only: hi is the top 24 bits of the scaled double, lo is the dropped 29-bit
 // remainder k (a signed count of units 2^(e - 1075) of the scaled exponent field e) converted
 // in two exact halves and scaled by a power of two.
+// The arithmetic is on the two 32-bit words of the double: with 64-bit integer arithmetic on the
+// double's bits the device executed one FP64 add per split (ncu), an FP64-pipe instruction
+// that the step's split of its state paid six times a fiber.
 __host__ __device__ __forceinline__ float2 split_scaled(double x, int sh) {
+#ifdef __CUDA_ARCH__
+    const uint32_t whi = static_cast<uint32_t>(__double2hiint(x)), wlo = static_cast<uint32_t>(__double2loint(x));
+#else
     const uint64_t u = bits_of(x);
-    const uint32_t sgn = static_cast<uint32_t>(u >> 32) & 0x80000000u;
-    const uint64_t a = u & 0x7fffffffffffffffull;
-    const int ex = static_cast<int>(a >> 52);
+    const uint32_t whi = static_cast<uint32_t>(u >> 32), wlo = static_cast<uint32_t>(u);
+#endif
+    const uint32_t sgn = whi & 0x80000000u;
+    const uint32_t ahi = whi & 0x7fffffffu;
+    const int ex = static_cast<int>(ahi >> 20);
     const int e = ex - sh;   // exponent field of x 2^-sh
     if (ex == 0 || e < 897) return make_float2(float_of(sgn), float_of(sgn));
-    const uint64_t r = (a - (static_cast<uint64_t>(static_cast<int64_t>(sh)) << 52)) + (uint64_t(1) << 28);
-    const float hi = float_of((static_cast<uint32_t>(r >> 29) - (896u << 23)) | sgn);
-    const int k = static_cast<int>(static_cast<uint32_t>(r) & 0x1fffffffu) - (1 << 28);
+    // r = |x| 2^-sh (exponent field lowered by sh) + 2^28, as words (rhi, rlo)
+    const uint32_t rlo = wlo + (1u << 28);
+    const uint32_t rhi = ahi - (static_cast<uint32_t>(sh) << 20) + (rlo < wlo ? 1u : 0u);
+    const float hi = float_of((((rhi << 3) | (rlo >> 29)) - (896u << 23)) | sgn);   // r >> 29
+    const int k = static_cast<int>(rlo & 0x1fffffffu) - (1 << 28);
     // float(k), rounded once: k = kh 2^14 + kl with both halves exact through the 1.5 2^23 trick
     const float fkh = fsub_n(float_of(0x4b400000u + static_cast<uint32_t>(k >> 14)), 12582912.f);
     const float fkl = fsub_n(float_of(0x4b400000u + static_cast<uint32_t>(k & 0x3fff)), 12582912.f);
