@@ -78,3 +78,18 @@ def test_mixed_solver_at_least_as_close_to_the_oracle_as_fp64_at_full_size():
         print(f"layout {layout}: relative gradient error against the oracle: mixed "
               f"{err(ra, 'grad_alpha'):.2e}, FP64 {eb['grad_alpha']:.2e}; P mixed "
               f"{abs(ra['P'] - want['P']) / abs(want['P']):.2e}, FP64 {abs(rb['P'] - want['P']) / abs(want['P']):.2e}")
+
+
+@pytest.mark.parametrize("nsteps", [560, 600])
+@pytest.mark.parametrize("layout", [msqoc.LAYOUT_FIBER, msqoc.LAYOUT_FIBER_LEAN])
+def test_state_update_forms_on_either_side_of_the_bound(nsteps, layout):
+    # 3 transmons over 6 ns, max |D| = 4.22: |2 kappa| = h max|D| is 0.0452 at 560 steps (above
+    # 2^-4.5 = 0.0442: the FP64 update R u + 2 d) and 0.0422 at 600 (the compensated update)
+    spec = S.transmon_spec(3, 6.0, nsteps, 4, 5)
+    alpha, W = S.random_alpha(spec, 43), S.random_W(spec, 43)
+    want = oracle.evaluate(spec, alpha, W)
+    with msqoc.Problem(spec, solver=msqoc.SOLVER_MIXED, layout=layout) as p:
+        got = p.eval_gradient(alpha, W)
+    assert_objective_close(got["P"], want["P"])
+    assert_grad_close(got["grad_alpha"], want["grad_alpha"], what="grad_alpha")
+    assert_grad_close(got["grad_W"], want["grad_W"], what="grad_W")
