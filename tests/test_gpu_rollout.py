@@ -29,6 +29,20 @@ def test_rollout_matches_oracle_and_zeroes_the_penalties(solver, layout):
     assert_objective_close(obj["J"], single["P"], rtol=1e-11)
 
 
+@pytest.mark.parametrize("layout", [msqoc.LAYOUT_FIBER, msqoc.LAYOUT_FIBER_LEAN])
+def test_rollout_with_the_compensated_state_update(layout):
+    # 4 transmons at the benchmark's step (|2 kappa| <= 0.034): the mixed solver keeps the state
+    # as an FP64 part plus an FP32 carry, which the roll-out adds up where it stores U(t_m)
+    spec = S.transmon_spec(4, 18.0, 3000, 3, 6)
+    alpha = S.random_alpha(spec, 74)
+    want = oracle.rollout(spec, alpha)
+    with msqoc.Problem(spec, solver=msqoc.SOLVER_MIXED, col_block=7, layout=layout) as p:
+        W = p.rollout(alpha)
+        np.testing.assert_allclose(W, want, rtol=0, atol=1e-12)
+        obj = p.eval_objective(alpha, W)
+    assert np.all(np.abs(obj["pen"]) < 1e-22)
+
+
 def test_rollout_estimate_is_the_formula_and_bounds_the_rollout_infidelity():
     spec = S.transmon_spec(2, 16.0, 320, 4, 6)
     alpha = S.random_alpha(spec, 72)
