@@ -308,13 +308,17 @@ template <int L, int Q>
 __device__ __forceinline__ void apply_off_df(const float4* __restrict__ buf, const float4* __restrict__ cf,
                                              const Fiber<L, Q>& fb, const float4 (&xr)[L], DF (&w)[L][2],
                                              const float2 (&exc)[MAXEXF], int nex) {
-#pragma unroll
-    for (int l = 0; l < L; ++l) w[l][0] = w[l][1] = DF{0.f, 0.f};
+    // the first term of each entry's sum initialises it (no two-sum with zero)
     constexpr int kl = Q - 1;
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-        if (l < L - 1) cmac_df(w[l], cf[(kl * L + l) * 2 + 0], xr[l + 1]);
-        if (l > 0) cmac_df(w[l], cf[(kl * L + l) * 2 + 1], xr[l - 1]);
+        if (l < L - 1) cmul_df(xr[l + 1], cf[(kl * L + l) * 2 + 0], w[l][0], w[l][1]);
+        if (l > 0) {
+            if (l < L - 1)
+                cmac_df(w[l], cf[(kl * L + l) * 2 + 1], xr[l - 1]);
+            else
+                cmul_df(xr[l - 1], cf[(kl * L + l) * 2 + 1], w[l][0], w[l][1]);
+        }
     }
 #pragma unroll
     for (int k = 0; k < Fiber<L, Q>::NFIX; ++k) {
@@ -413,6 +417,16 @@ __device__ __forceinline__ void cjmac_split(DF& R, DF& I, const float4& x, const
     df_mac(I, x.x, x.z, u.y, u.w);
     df_mac(I, -x.y, -x.w, u.x, u.z);
 }
+// the same as the first term of the sums (R = SR Re(conj(x) u), I = Im(conj(x) u)): no
+// two-sum with zero
+template <int SR>
+__device__ __forceinline__ void cjmul_split(DF& R, DF& I, const float4& x, const float4& u) {
+    if constexpr (SR > 0)
+        R = dot2_df(x.x, x.z, u.x, u.z, x.y, x.w, u.y, u.w);
+    else
+        R = dot2_df(-x.x, -x.z, u.x, u.z, -x.y, -x.w, u.y, u.w);
+    I = dot2_df(x.x, x.z, u.y, u.w, -x.y, -x.w, u.x, u.z);
+}
 
 // The mixed solver's gradient products of one fiber (the FP64 form is in the adjoint below):
 // acc[2k] = A_k and acc[2k + 1] = B_k, the fiber's rows of A_k = Im z_k + Im y_k and
@@ -434,8 +448,8 @@ __device__ __forceinline__ void products_split(const float4 (&zs)[L], const floa
         DF A{0.f, 0.f}, B{0.f, 0.f};
 #pragma unroll
         for (int j = 1; j < L; ++j) {
-            DF R{0.f, 0.f}, I{0.f, 0.f};
-            cjmac_split<+1>(R, I, zs[j - 1], ub[fb.xo + j]);
+            DF R, I;
+            cjmul_split<+1>(R, I, zs[j - 1], ub[fb.xo + j]);
             cjmac_split<-1>(R, I, zs[j], ub[fb.xo + j - 1]);
             if (j == 1) {
                 A = I;
@@ -451,19 +465,21 @@ __device__ __forceinline__ void products_split(const float4 (&zs)[L], const floa
 #pragma unroll
     for (int k = 0; k < Fiber<L, Q>::NFIX; ++k) {
         const int lk = (fb.f / ipow_c(L, Q - 2 - k)) % L;   // the fiber's level in subsystem k
-        DF R{0.f, 0.f}, I{0.f, 0.f};
+        DF R, I;
         const float4* u1 = ub + fb.nb1[k];
+        cjmul_split<+1>(R, I, zs[0], u1[0]);
 #pragma unroll
-        for (int l = 0; l < L; ++l) cjmac_split<+1>(R, I, zs[l], u1[l]);
+        for (int l = 1; l < L; ++l) cjmac_split<+1>(R, I, zs[l], u1[l]);
         // entry 1: a_k (weight sqrt(l_k + 1)) or, at the top level, a_k^+ (sqrt(l_k), real part -)
         DF A = df_scale_sqrt(I, fb.plus1[k] ? lk + 1 : lk);
         DF B = df_scale_sqrt(R, fb.plus1[k] ? lk + 1 : lk);
         if (!fb.plus1[k]) B = df_neg(B);
         if (fb.two[k]) {   // an interior level (warp-uniform: lanes are sorted by class)
-            DF R2{0.f, 0.f}, I2{0.f, 0.f};
+            DF R2, I2;
             const float4* u2 = ub + fb.nb2[k];
+            cjmul_split<-1>(R2, I2, zs[0], u2[0]);
 #pragma unroll
-            for (int l = 0; l < L; ++l) cjmac_split<-1>(R2, I2, zs[l], u2[l]);
+            for (int l = 1; l < L; ++l) cjmac_split<-1>(R2, I2, zs[l], u2[l]);
             A = df_add(A, df_scale_sqrt(I2, lk));
             B = df_add(B, df_scale_sqrt(R2, lk));
         }
