@@ -72,8 +72,11 @@ typedef int32_t msqoc_status;
 #define MSQOC_ERR_INTERNAL (-7)
 
 /* Linear solver inside each implicit-midpoint step.
- *  MIXED: FP64 residual of the step equation with FP32 inner corrections (iterative
- *         refinement); the step is solved to FP64 round-off.  Default.
+ *  MIXED: iterative refinement with FP32 inner corrections and a residual accurate to FP64
+ *         round-off (formed in compensated FP32 where the step's contraction factor allows,
+ *         else in FP64); the step is solved to FP64 round-off.  With one thread per fiber the
+ *         state is kept as FP64 plus an FP32 carry and updated in compensated FP32 where the
+ *         diagonal step |2 kappa| = h |D| <= 2^-4.5 (msqoc_selftest_carry).  Default.
  *  FP64 : diagonal-preconditioned fixed-point iteration carried out entirely in FP64. */
 #define MSQOC_SOLVER_DEFAULT 0
 #define MSQOC_SOLVER_FP64 1
