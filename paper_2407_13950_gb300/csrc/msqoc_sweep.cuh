@@ -1329,24 +1329,22 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep(const SweepArgs a) {
                 GT* r1 = red + ((par * 2 + 1) * nwarps + warp) * V;
                 GT zero;
                 gsum_zero(zero);
-                if (mask0 && mask1) {
-                    // lanes of both windows: reduce the window-1 lanes on a copy first
+                // a warp with lanes of both windows reduces each window's lanes in a pass of its
+                // own (one copy of the reduction in the code: the step loop's instruction fetches
+                // already stall the adjoint's warps)
+                const bool both = mask0 && mask1;
+                for (int pass = 0; pass < (both ? 2 : 1); ++pass) {
                     GT t[V];
 #pragma unroll
-                    for (int v = 0; v < V; ++v) t[v] = slot == 1 ? acc[v] : zero;
-                    const GT s1 = warp_reduce_scatter<V, NH>(t, lane);
-#pragma unroll
-                    for (int v = 0; v < V; ++v) acc[v] = slot == 0 ? acc[v] : zero;
-                    const GT s0 = warp_reduce_scatter<V, NH>(acc, lane);
+                    for (int v = 0; v < V; ++v) t[v] = (!both || slot == pass) ? acc[v] : zero;
+                    const GT sv = warp_reduce_scatter<V, NH>(t, lane);
                     if (writer) {
-                        r0[vi] = s0;
-                        r1[vi] = s1;
-                    }
-                } else {
-                    const GT sv = warp_reduce_scatter<V, NH>(acc, lane);
-                    if (writer) {
-                        r0[vi] = mask1 ? zero : sv;
-                        if (nslot > 1) r1[vi] = mask1 ? sv : zero;
+                        if (!both) {
+                            r0[vi] = mask1 ? zero : sv;
+                            if (nslot > 1) r1[vi] = mask1 ? sv : zero;
+                        } else {
+                            (pass == 0 ? r0 : r1)[vi] = sv;
+                        }
                     }
                 }
             }
