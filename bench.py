@@ -401,7 +401,10 @@ def run_ours(args, spec):
         "whole_eval": {"algorithmic_tflops": fl["total"] / (ms * 1e-3) / 1e12,
                        "frac_of_fp64_peak": fl["total"] / (ms * 1e-3) / 1e12 / peak_tflops},
         "e2e": {"value": world / (e2e_ms * 1e-3), "unit": UNIT, "buffers": "pinned host",
-                "h2d_bytes_per_step": 8 * (spec.d + spec.nW), "d2h_bytes_per_step": 8 * (1 + spec.d + spec.nW)},
+                "h2d_bytes_per_step": 8 * (spec.d + spec.nW), "d2h_bytes_per_step": 8 * (1 + spec.d + spec.nW),
+                # this rank's calls (host clock, ms): the value is from their mean
+                "call_ms": {"min": min(e2e_times) * 1e3, "median": float(np.median(e2e_times)) * 1e3,
+                            "max": max(e2e_times) * 1e3} if e2e_times else None},
         "gpu_launches": launches_per_eval * args.steps,
         "clocks": clocks,
     }
