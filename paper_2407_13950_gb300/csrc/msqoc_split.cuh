@@ -125,6 +125,11 @@ __host__ __device__ __forceinline__ DF two_sum(float a, float b) {
     const float bp = fsub_n(s, a);
     return DF{s, fadd_n(fsub_n(a, fsub_n(s, bp)), fsub_n(b, bp))};
 }
+// a + b as s + c for |a| >= |b| (or a = 0): s = RN(a + b), c its exact error
+__host__ __device__ __forceinline__ DF fast_two_sum(float a, float b) {
+    const float s = fadd_n(a, b);
+    return DF{s, fsub_n(b, fsub_n(s, a))};
+}
 // one real part of a complex product, x1 y1 + x2 y2 for split factors (h, l): the two leading
 // products exact (FMA) and added with an exact two-sum, their errors and the four cross terms
 // in the low part; the l l terms (<= 2^-48 of each product) are dropped
@@ -190,6 +195,21 @@ __host__ __device__ __forceinline__ double f64_of_float_scaled(float f, int sh) 
     }
     return double_of(sgn | mag);
 }
+// f 2^sh as a double for |sh| <= 896, where every normal float gives a normal double: the
+// exponent moved by 896 + sh, the significand widened; zero and FP32 subnormals give signed
+// zero (the mixed solver's column scale keeps its values' scaled magnitudes in that range).
+// Integer operations on the two 32-bit words only.
+__host__ __device__ __forceinline__ double f64_of_float_scaled_normal(float f, int sh) {
+    const uint32_t b = bits_of(f);
+    const uint32_t sgn = b & 0x80000000u, a = b & 0x7fffffffu;
+    const uint32_t hi = a < 0x00800000u ? sgn : (sgn | ((a >> 3) + (static_cast<uint32_t>(896 + sh) << 20)));
+    const uint32_t lo = a < 0x00800000u ? 0u : a << 29;
+#ifdef __CUDA_ARCH__
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+#else
+    return double_of(static_cast<uint64_t>(hi) << 32 | lo);
+#endif
+}
 // the finished sum s + c times 2^sh, as one double (one FP64 add)
 __host__ __device__ __forceinline__ double df_to_f64_scaled(DF a, int sh) {
     return f64_of_float_scaled(a.s, sh) + f64_of_float_scaled(a.c, sh);
@@ -233,13 +253,15 @@ __host__ __device__ __forceinline__ double2 carry_update(double2 u, DF bre, DF b
     const DF ai = df_add(qi, DF{fadd_n(dim.s, dim.s), fadd_n(dim.c, dim.c)});
     // renormalised, so that u takes all but the last rounding of the increment and the carry
     // stays within half an FP32 unit of it (else it would gather the low parts of every step)
-    const DF xr = two_sum(ar.s, ar.c), xi = two_sum(ai.s, ai.c);
+    // (a fast two-sum: |ar.c| is below |ar.s| but where ar.s cancels to nothing, and there the
+    // carry's error is of the order of the cancelled parts' rounding)
+    const DF xr = fast_two_sum(ar.s, ar.c), xi = fast_two_sum(ai.s, ai.c);
     car = make_float2(xr.c, xi.c);
-    return make_double2(u.x + f64_of_float_scaled(xr.s, sh), u.y + f64_of_float_scaled(xi.s, sh));
+    return make_double2(u.x + f64_of_float_scaled_normal(xr.s, sh), u.y + f64_of_float_scaled_normal(xi.s, sh));
 }
 // the state u + carry as one double (one FP64 add a component)
 __host__ __device__ __forceinline__ double2 carry_finish(double2 u, float2 car, int sh) {
-    return make_double2(u.x + f64_of_float_scaled(car.x, sh), u.y + f64_of_float_scaled(car.y, sh));
+    return make_double2(u.x + f64_of_float_scaled_normal(car.x, sh), u.y + f64_of_float_scaled_normal(car.y, sh));
 }
 
 }  // namespace msqoc
